@@ -1,0 +1,202 @@
+"""FP64 oracle of the DFEM S_n transport solve (Tano & Ragusa, arXiv:1906.04017).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py`` (its CPU-baseline and reference legs) may import this package.
+The product library never calls it and shares no code with it.
+
+The sweep, the per-cell assembly, the Gaussian elimination and the source
+iteration live in plain C (``sn_oracle.c``, FP64, built by ``oracle/build.py``);
+this module is the ctypes wrapper, plus the numpy FP64 oracle of the
+surrogate network (``oracle.mlp``) and of the discrete adjoint
+(``oracle.adjoint``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = ctypes.CDLL(_build.build())
+        _declare(_LIB)
+    return _LIB
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("ndir", ctypes.c_int), ("omega", _dp), ("w", _dp),
+        ("G", ctypes.c_int), ("sigt", _dp), ("sigs", _dp), ("q", _dp),
+        ("xfer", _dp), ("psi_inc", _dp),
+    ]
+
+
+def _declare(L):
+    L.or_ge.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+    L.or_lqn.argtypes = [ctypes.c_int, _dp, _dp]
+    L.or_element.argtypes = [ctypes.c_double] * 3 + [_dp] * 4
+    L.or_assemble.argtypes = [ctypes.c_double] * 3 + [_dp, ctypes.c_double, _dp, _dp, _dp, _dp]
+    L.or_assemble_inflow_form.argtypes = [ctypes.c_double] * 3 + [_dp, ctypes.c_double, _dp]
+    L.or_cell_solve.argtypes = [_dp, _dp]
+    L.or_cell_solve_batch.argtypes = [ctypes.c_long, _dp, _dp]
+    P = ctypes.POINTER(Problem)
+    L.or_sweep_dir.argtypes = [P, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.or_sweep.argtypes = [P, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    L.or_source.argtypes = [P, _dp, _dp]
+    L.or_source_iterate.argtypes = [P, ctypes.c_double, ctypes.c_int, _dp,
+                                    ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
+    L.or_num_threads.argtypes = []
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+def ge_solve(A, b):
+    """Gaussian elimination with partial pivoting (FP64) of one n x n system."""
+    A = _f64(A).copy()
+    b = _f64(b).copy()
+    n = b.shape[0]
+    x = np.zeros(n)
+    if lib().or_ge(n, _p(A), _p(b), _p(x)) != 0:
+        raise ZeroDivisionError("zero pivot")
+    return x
+
+
+def lqn(order):
+    """Level-symmetric LQ_N directions [ndir,3] and weights [ndir] (sum 4 pi)."""
+    n = order * (order + 2)
+    om = np.zeros((n, 3))
+    w = np.zeros(n)
+    nd = lib().or_lqn(order, _p(om), _p(w))
+    if nd < 0:
+        raise ValueError("unsupported LQ_N order %r" % order)
+    return om, w
+
+
+def element(dx, dy, dz):
+    """Element matrices (M, L[3], G[3], F[6]) of the Q1 box, by Gauss quadrature."""
+    M = np.zeros((8, 8)); L = np.zeros((3, 8, 8)); G = np.zeros((3, 8, 8)); F = np.zeros((6, 8, 8))
+    lib().or_element(dx, dy, dz, _p(M), _p(L), _p(G), _p(F))
+    return M, L, G, F
+
+
+def assemble(in27):
+    """(A, b) of one one-cell problem in the outflow form of Eq. (14)."""
+    x = _f64(in27)
+    A = np.zeros((8, 8)); b = np.zeros(8)
+    lib().or_assemble(x[3], x[4], x[5], _p(_f64(x[0:3])), x[6], _p(_f64(x[7:15])),
+                      _p(_f64(x[15:27])), _p(A), _p(b))
+    return A, b
+
+
+def assemble_inflow_form(in27):
+    x = _f64(in27)
+    A = np.zeros((8, 8))
+    lib().or_assemble_inflow_form(x[3], x[4], x[5], _p(_f64(x[0:3])), x[6], _p(A))
+    return A
+
+
+def cell_solve(in27):
+    """Solve a batch of one-cell problems in27[N,27] -> psi[N,8] (FP64 GE)."""
+    x = _f64(np.atleast_2d(in27))
+    out = np.zeros((x.shape[0], 8))
+    if lib().or_cell_solve_batch(x.shape[0], _p(x), _p(out)) != 0:
+        raise ZeroDivisionError("zero pivot")
+    return out
+
+
+class OracleProblem:
+    """Holds the FP64 arrays of one problem and the ctypes view of them.
+
+    Fields follow the workload dictionaries of ``paper_1906_04017_gb300.workloads``:
+    nx, ny, nz, lx, ly, lz, order (or omega/w), sigt[G,ncell], sigs[G,ncell],
+    q[G,ncell], xfer[G,G], psi_inc[G,6].
+    """
+
+    def __init__(self, wl, omega=None, w=None):
+        self.nx, self.ny, self.nz = int(wl["nx"]), int(wl["ny"]), int(wl["nz"])
+        self.ncell = self.nx * self.ny * self.nz
+        self.dx = wl["lx"] / self.nx
+        self.dy = wl["ly"] / self.ny
+        self.dz = wl["lz"] / self.nz
+        if omega is None:
+            omega, w = lqn(int(wl["order"]))
+        self.omega = _f64(omega)
+        self.w = _f64(w)
+        self.ndir = self.w.shape[0]
+        self.sigt = _f64(wl["sigt"]).reshape(-1, self.ncell)
+        self.G = self.sigt.shape[0]
+        self.sigs = _f64(wl["sigs"]).reshape(self.G, self.ncell)
+        self.q = _f64(wl["q"]).reshape(self.G, self.ncell)
+        self.xfer = _f64(wl["xfer"]).reshape(self.G, self.G)
+        self.psi_inc = _f64(wl["psi_inc"]).reshape(self.G, 6)
+        self.c = Problem(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.ndir,
+                         _p(self.omega), _p(self.w), self.G, _p(self.sigt), _p(self.sigs),
+                         _p(self.q), _p(self.xfer), _p(self.psi_inc))
+
+    def sweep_dir(self, d, g, S, bx=None, by=None, bz=None):
+        """psi[ncell,8] of direction d, group g, for the nodal source S[ncell,8].
+        Returns (psi, tallies[4] = leakage, collision, source, inflow)."""
+        S = _f64(S).reshape(self.ncell, 8)
+        psi = np.zeros((self.ncell, 8))
+        tal = np.zeros(4)
+        bx, by, bz = [None if b is None else _f64(b) for b in (bx, by, bz)]
+        if lib().or_sweep_dir(ctypes.byref(self.c), d, g, _p(S), _p(bx), _p(by), _p(bz),
+                              _p(psi), _p(tal)) != 0:
+            raise ZeroDivisionError("zero pivot")
+        return psi, tal
+
+    def sweep(self, S, groups=None, dirs=None):
+        """phi[G,ncell,8] = sum_d w_d psi_d for the isotropic source S[G,ncell,8].
+
+        ``groups`` / ``dirs`` are (begin, end) ranges; phi is zero outside them.
+        Returns (phi, tallies[4])."""
+        S = _f64(S).reshape(self.G, self.ncell, 8)
+        g0, g1 = groups if groups else (0, self.G)
+        d0, d1 = dirs if dirs else (0, self.ndir)
+        phi = np.zeros((self.G, self.ncell, 8))
+        tal = np.zeros(4)
+        if lib().or_sweep(ctypes.byref(self.c), _p(S), _p(phi), g0, g1, d0, d1, _p(tal)) != 0:
+            raise ZeroDivisionError("zero pivot")
+        return phi, tal
+
+    def source(self, phi):
+        S = np.zeros((self.G, self.ncell, 8))
+        lib().or_source(ctypes.byref(self.c), _p(_f64(phi).reshape(self.G, self.ncell, 8)), _p(S))
+        return S
+
+    def source_iterate(self, tol, maxit, phi0=None):
+        """Source iteration; returns dict(phi, iters, change_max, change_mean, tallies, converged)."""
+        phi = np.zeros((self.G, self.ncell, 8)) if phi0 is None else _f64(phi0).reshape(self.G, self.ncell, 8).copy()
+        it = ctypes.c_int(0)
+        cmax = ctypes.c_double(0.0)
+        cmean = ctypes.c_double(0.0)
+        tal = np.zeros(4)
+        rc = lib().or_source_iterate(ctypes.byref(self.c), tol, maxit, _p(phi), ctypes.byref(it),
+                                     ctypes.byref(cmax), ctypes.byref(cmean), _p(tal))
+        if rc < 0:
+            raise ZeroDivisionError("zero pivot")
+        return dict(phi=phi, iters=it.value, change_max=cmax.value, change_mean=cmean.value,
+                    tallies=tal, converged=(rc == 0))

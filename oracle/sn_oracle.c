@@ -1,0 +1,544 @@
+/*
+ * sn_oracle.c -- plain, slow, FP64 reference of the DFEM S_n transport solve
+ * of Tano & Ragusa, "Acceleration of Radiation Transport Solves Using
+ * Artificial Neural Networks" (arXiv:1906.04017).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, calls or
+ * reads this file; only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg use it.  It shares no code, header, table or constant
+ * generator with the CUDA path.
+ *
+ * Equation numbers are the paper's, counted in order of appearance:
+ *   (1) transport equation, (2) total source, (6)-(7) moment form,
+ *   (8)-(9) S_N discretisation, (10) inflow boundary condition,
+ *   (11) DFEM trial expansion, (12) discrete DFEM system, (13) phi = D psi,
+ *   (14) the per-cell system A psi = b, (21) source-iteration change.
+ *
+ * Readings of the paper taken here (each one is also listed in the design doc):
+ *   - Sec. 2 uses "+" for the inflow boundary (n.Omega < 0) when it defines
+ *     the faces, but the per-cell system (14) puts the outflow matrix in A
+ *     and the upwind matrix in b.  The oracle uses exactly that outflow form:
+ *        A = sum_a Omega_a L_a + sum_{f: Omega.n_f > 0} (Omega.n_f) F_f + sigma_t M
+ *        b = M S + sum_{f: Omega.n_f < 0} |Omega.n_f| F_f psi_up
+ *     with L_a[k][j] = -int u_j d_a w_k (the Green's-theorem volume term of
+ *     the streaming display in Sec. 2), F_f the face mass matrix and M the
+ *     sigma_t-free mass matrix.
+ *   - The scattering term of (12) multiplies the mass matrix without
+ *     sigma_t (the integral written beside it has no sigma_t).
+ *   - Trial space: tri-linear Q1 on axis-aligned boxes, 8 nodes, local node
+ *     n = a + 2b + 4c (x fastest); the paper's "P_1" label is read as the
+ *     8-node hexahedron it describes.
+ *   - Quadrature: level-symmetric LQ_N (the paper leaves the set open).
+ *   - Moments: sum of weights = 4 pi, phi = sum_d w_d psi_d, an isotropic
+ *     source density is divided by 4 pi.
+ *   - Groups: Jacobi source iteration (every group uses the previous phi).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian elimination with partial pivoting (Sec. 2, after Eq. (14): the   */
+/* per-cell system is "solved by direct Gauss Elimination").  Pivot = entry  */
+/* of largest magnitude in the column, ties go to the lowest row.  A (n x n, */
+/* row-major) and b are overwritten.  Returns 0, or -1 on a zero pivot.      */
+/* ------------------------------------------------------------------------ */
+int or_ge(int n, double *A, double *b, double *x)
+{
+    for (int col = 0; col < n; ++col) {
+        int p = col;
+        double best = fabs(A[col * n + col]);
+        for (int r = col + 1; r < n; ++r) {
+            double v = fabs(A[r * n + col]);
+            if (v > best) { best = v; p = r; }
+        }
+        if (best == 0.0) return -1;
+        if (p != col) {
+            for (int c = 0; c < n; ++c) {
+                double t = A[col * n + c]; A[col * n + c] = A[p * n + c]; A[p * n + c] = t;
+            }
+            double t = b[col]; b[col] = b[p]; b[p] = t;
+        }
+        for (int r = col + 1; r < n; ++r) {
+            double l = A[r * n + col] / A[col * n + col];
+            A[r * n + col] = 0.0;
+            for (int c = col + 1; c < n; ++c) A[r * n + c] -= l * A[col * n + c];
+            b[r] -= l * b[col];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int c = r + 1; c < n; ++c) s -= A[r * n + c] * x[c];
+        x[r] = s / A[r * n + r];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Level-symmetric LQ_N quadrature (Sec. 2, Eqs. (8)-(9): the pairs          */
+/* (Omega_d, w_d); the set itself is left open by the paper).                */
+/* Per octant the N(N+2)/8 points are (mu_i, mu_j, mu_k) with i+j+k = N/2+2, */
+/* mu_i^2 = mu_1^2 + (i-1) * 2 (1 - 3 mu_1^2) / (N - 2).  Points whose level */
+/* triples are permutations of each other share a weight; the class weights  */
+/* solve the even x-moment conditions sum w mu^(2m) = 1/(2m+1) for           */
+/* m = 0, 2, 3, ..., K (K classes; m = 1 follows from symmetry).  mu_1 is    */
+/* the standard LQ_N value.  Directions are ordered octant-major (octant bit */
+/* 0: mu < 0, bit 1: eta < 0, bit 2: xi < 0), then i ascending, j ascending. */
+/* Weights are scaled to sum to 4 pi.  Returns ndir, or -1 for an           */
+/* unsupported order.                                                        */
+/* ------------------------------------------------------------------------ */
+int or_lqn(int N, double *omega, double *w)
+{
+    double mu1;
+    switch (N) {
+    case 2:  mu1 = 0.57735026918962576; break;
+    case 4:  mu1 = 0.3500212; break;
+    case 6:  mu1 = 0.2666355; break;
+    case 8:  mu1 = 0.2182179; break;
+    case 10: mu1 = 0.1893213; break;
+    case 12: mu1 = 0.1672126; break;
+    default: return -1;
+    }
+    int n2 = N / 2;
+    double mu[8];
+    for (int i = 0; i < n2; ++i) {
+        double m2 = mu1 * mu1;
+        if (N > 2) m2 += i * 2.0 * (1.0 - 3.0 * mu1 * mu1) / (N - 2);
+        mu[i] = sqrt(m2);
+    }
+    /* points of one octant and their classes */
+    int lev[64][3], cls[64], ncls = 0, clsk[64][3], np = 0;
+    for (int i = 1; i <= n2; ++i)
+        for (int j = 1; j <= n2 + 1 - i; ++j) {
+            int k = n2 + 2 - i - j;
+            lev[np][0] = i; lev[np][1] = j; lev[np][2] = k;
+            int s[3] = {i, j, k};
+            for (int a = 0; a < 3; ++a)           /* sort the triple */
+                for (int b2 = a + 1; b2 < 3; ++b2)
+                    if (s[b2] < s[a]) { int t = s[a]; s[a] = s[b2]; s[b2] = t; }
+            int c = -1;
+            for (int q = 0; q < ncls; ++q)
+                if (clsk[q][0] == s[0] && clsk[q][1] == s[1] && clsk[q][2] == s[2]) c = q;
+            if (c < 0) { c = ncls++; clsk[c][0] = s[0]; clsk[c][1] = s[1]; clsk[c][2] = s[2]; }
+            cls[np++] = c;
+        }
+    /* moment conditions */
+    double A[64], b[8], x[8];
+    for (int r = 0; r < ncls; ++r) {
+        int m = (r == 0) ? 0 : r + 1;
+        for (int c = 0; c < ncls; ++c) A[r * ncls + c] = 0.0;
+        for (int p = 0; p < np; ++p) A[r * ncls + cls[p]] += pow(mu[lev[p][0] - 1], 2.0 * m);
+        b[r] = 1.0 / (2.0 * m + 1.0);
+    }
+    if (or_ge(ncls, A, b, x) != 0) return -1;
+    int d = 0;
+    for (int o = 0; o < 8; ++o)
+        for (int p = 0; p < np; ++p, ++d) {
+            omega[3 * d + 0] = ((o & 1) ? -1.0 : 1.0) * mu[lev[p][0] - 1];
+            omega[3 * d + 1] = ((o & 2) ? -1.0 : 1.0) * mu[lev[p][1] - 1];
+            omega[3 * d + 2] = ((o & 4) ? -1.0 : 1.0) * mu[lev[p][2] - 1];
+            w[d] = x[cls[p]] * (4.0 * PI / 8.0);
+        }
+    return d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Element matrices on the box [0,dx]x[0,dy]x[0,dz] (Sec. 2, the streaming,  */
+/* total-interaction and source displays before Eq. (12)), integrated with  */
+/* 2x2x2 Gauss-Legendre points (exact for products of tri-linear functions). */
+/*   M[k][j]    = int u_k u_j dV                                             */
+/*   L[a][k][j] = -int u_j d_a u_k dV       (Green's-theorem volume term)    */
+/*   G[a][k][j] = int u_k d_a u_j dV        (volume term before Green)       */
+/*   F[f][k][j] = int_f u_k u_j dA, f = x-, x+, y-, y+, z-, z+               */
+/* Basis u_n = beta_a(x) beta_b(y) beta_c(z), n = a + 2b + 4c,               */
+/* beta_0(t) = 1 - t/h, beta_1(t) = t/h.                                     */
+/* ------------------------------------------------------------------------ */
+static double beta(int a, double t, double h) { return a ? t / h : 1.0 - t / h; }
+static double dbeta(int a, double h) { return a ? 1.0 / h : -1.0 / h; }
+
+static void basis(const double h[3], const double r[3], double u[8], double du[3][8])
+{
+    for (int n = 0; n < 8; ++n) {
+        int ia[3] = {n & 1, (n >> 1) & 1, (n >> 2) & 1};
+        double v[3], dv[3];
+        for (int ax = 0; ax < 3; ++ax) { v[ax] = beta(ia[ax], r[ax], h[ax]); dv[ax] = dbeta(ia[ax], h[ax]); }
+        u[n] = v[0] * v[1] * v[2];
+        du[0][n] = dv[0] * v[1] * v[2];
+        du[1][n] = v[0] * dv[1] * v[2];
+        du[2][n] = v[0] * v[1] * dv[2];
+    }
+}
+
+void or_element(double dx, double dy, double dz, double *M, double *L, double *G, double *F)
+{
+    const double h[3] = {dx, dy, dz};
+    const double gp[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+    memset(M, 0, 64 * sizeof(double));
+    memset(L, 0, 3 * 64 * sizeof(double));
+    memset(G, 0, 3 * 64 * sizeof(double));
+    memset(F, 0, 6 * 64 * sizeof(double));
+    /* volume terms */
+    for (int p0 = 0; p0 < 2; ++p0)
+        for (int p1 = 0; p1 < 2; ++p1)
+            for (int p2 = 0; p2 < 2; ++p2) {
+                double r[3] = {gp[p0] * dx, gp[p1] * dy, gp[p2] * dz};
+                double wt = 0.125 * dx * dy * dz;
+                double u[8], du[3][8];
+                basis(h, r, u, du);
+                for (int k = 0; k < 8; ++k)
+                    for (int j = 0; j < 8; ++j) {
+                        M[k * 8 + j] += wt * u[k] * u[j];
+                        for (int ax = 0; ax < 3; ++ax) {
+                            L[ax * 64 + k * 8 + j] -= wt * u[j] * du[ax][k];
+                            G[ax * 64 + k * 8 + j] += wt * u[k] * du[ax][j];
+                        }
+                    }
+            }
+    /* face terms: face f = 2*axis + side, side 0 at coordinate 0, side 1 at h */
+    for (int f = 0; f < 6; ++f) {
+        int ax = f / 2, side = f % 2;
+        int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+        for (int p1 = 0; p1 < 2; ++p1)
+            for (int p2 = 0; p2 < 2; ++p2) {
+                double r[3];
+                r[ax] = side ? h[ax] : 0.0;
+                r[t1] = gp[p1] * h[t1];
+                r[t2] = gp[p2] * h[t2];
+                double wt = 0.25 * h[t1] * h[t2];
+                double u[8], du[3][8];
+                basis(h, r, u, du);
+                for (int k = 0; k < 8; ++k)
+                    for (int j = 0; j < 8; ++j) F[f * 64 + k * 8 + j] += wt * u[k] * u[j];
+            }
+    }
+}
+
+/* Outward normal component of face f along its axis. */
+static double face_sign(int f) { return (f % 2) ? 1.0 : -1.0; }
+
+/* Local node on face f of a cell with in-face index t (0..3).  For an x-face */
+/* t = b + 2c, for a y-face t = a + 2c, for a z-face t = a + 2b.             */
+static int face_node(int f, int t)
+{
+    int ax = f / 2, side = f % 2;
+    int lo = t & 1, hi = (t >> 1) & 1;
+    int a, b, c;
+    if (ax == 0) { a = side; b = lo; c = hi; }
+    else if (ax == 1) { a = lo; b = side; c = hi; }
+    else { a = lo; b = hi; c = side; }
+    return a + 2 * b + 4 * c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-cell system (14) in the outflow form (see the header).  up[12] holds  */
+/* the upwind face values on the inflow face of each axis: x-face (4), then  */
+/* y-face (4), then z-face (4), in-face order as in face_node().  Omega_a = 0 */
+/* means no flow through that axis' faces.                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct { double M[64], L[192], G[192], F[384]; } or_elem;
+
+static void assemble(const or_elem *e, const double om[3], double sigt,
+                     const double S[8], const double up[12], double A[64], double b[8])
+{
+    for (int i = 0; i < 64; ++i)
+        A[i] = om[0] * e->L[i] + om[1] * e->L[64 + i] + om[2] * e->L[128 + i] + sigt * e->M[i];
+    for (int k = 0; k < 8; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < 8; ++j) s += e->M[k * 8 + j] * S[j];
+        b[k] = s;
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        if (om[ax] == 0.0) continue;
+        int fout = 2 * ax + (om[ax] > 0.0 ? 1 : 0);
+        int fin = 2 * ax + (om[ax] > 0.0 ? 0 : 1);
+        double on_out = om[ax] * face_sign(fout);          /* > 0 */
+        double on_in = fabs(om[ax] * face_sign(fin));      /* |Omega.n| on inflow */
+        for (int i = 0; i < 64; ++i) A[i] += on_out * e->F[fout * 64 + i];
+        double ext[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int t = 0; t < 4; ++t) ext[face_node(fin, t)] = up[4 * ax + t];
+        for (int k = 0; k < 8; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < 8; ++j) s += e->F[fin * 64 + k * 8 + j] * ext[j];
+            b[k] += on_in * s;
+        }
+    }
+}
+
+/* Exported for the tests: the outflow form above and the inflow form that  */
+/* Green's theorem turns it into (A = sum Omega_a G_a + sum_inflow |Omega.n| */
+/* F_f + sigma_t M).  The two must agree to round-off.                       */
+void or_assemble(double dx, double dy, double dz, const double om[3], double sigt,
+                 const double S[8], const double up[12], double *A, double *b)
+{
+    or_elem e;
+    or_element(dx, dy, dz, e.M, e.L, e.G, e.F);
+    assemble(&e, om, sigt, S, up, A, b);
+}
+
+void or_assemble_inflow_form(double dx, double dy, double dz, const double om[3], double sigt, double *A)
+{
+    or_elem e;
+    or_element(dx, dy, dz, e.M, e.L, e.G, e.F);
+    for (int i = 0; i < 64; ++i)
+        A[i] = om[0] * e.G[i] + om[1] * e.G[64 + i] + om[2] * e.G[128 + i] + sigt * e.M[i];
+    for (int ax = 0; ax < 3; ++ax) {
+        if (om[ax] == 0.0) continue;
+        int fin = 2 * ax + (om[ax] > 0.0 ? 0 : 1);
+        for (int i = 0; i < 64; ++i) A[i] += fabs(om[ax]) * e.F[fin * 64 + i];
+    }
+}
+
+/* One-cell problem: in27 = Omega(3), (dx,dy,dz), sigma_t, S(8), up(12).     */
+/* Assemble (14) and solve it by Gaussian elimination.                       */
+int or_cell_solve(const double *in27, double *psi)
+{
+    or_elem e;
+    double A[64], b[8];
+    or_element(in27[3], in27[4], in27[5], e.M, e.L, e.G, e.F);
+    assemble(&e, in27, in27[6], in27 + 7, in27 + 15, A, b);
+    return or_ge(8, A, b, psi);
+}
+
+int or_cell_solve_batch(long n, const double *in27, double *psi)
+{
+    int bad = 0;
+    for (long i = 0; i < n; ++i)
+        if (or_cell_solve(in27 + 27 * i, psi + 8 * i) != 0) bad = 1;
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem description.                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    int ndir;
+    const double *omega;    /* [ndir][3]                                    */
+    const double *w;        /* [ndir], sum 4 pi                             */
+    int G;
+    const double *sigt;     /* [G][ncell] total cross section               */
+    const double *sigs;     /* [G][ncell] scattering out of group g         */
+    const double *q;        /* [G][ncell] isotropic emission density        */
+    const double *xfer;     /* [G][G] fraction of g' scattering into g      */
+    const double *psi_inc;  /* [G][6] isotropic inflow on x-,x+,y-,y+,z-,z+ */
+} or_problem;
+
+static long ncell_of(const or_problem *p) { return (long)p->nx * p->ny * p->nz; }
+
+/* ------------------------------------------------------------------------ */
+/* Sweep of one direction and group (Sec. 2, after Eq. (14): start at the    */
+/* cells whose inflow is known, move to downstream neighbours).  Cells are   */
+/* visited in upwind lexicographic order.  S is the nodal source density     */
+/* [ncell][8] for this direction.  Boundary inflow comes from bnd_{x,y,z}    */
+/* (per-face nodal values, layout [j + ny k][4], [i + nx k][4], [i + nx j][4]) */
+/* or, when a pointer is NULL, from the problem's constant psi_inc (Eq. (10)) */
+/* for group g.  tallies[0..3] += leakage, collision, source, inflow.        */
+/* ------------------------------------------------------------------------ */
+static int sweep_dir(const or_problem *p, const or_elem *e, int d, int g, const double *S,
+                     const double *bx, const double *by, const double *bz, double *psi, double tal[4])
+{
+    const double *om = p->omega + 3 * d;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const long nc = ncell_of(p);
+    int fin[3], fout[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        fin[ax] = 2 * ax + (om[ax] >= 0.0 ? 0 : 1);
+        fout[ax] = 2 * ax + (om[ax] >= 0.0 ? 1 : 0);
+    }
+    /* face integral weights: int_f u_j over face f = column sums of F_f */
+    double fint[6][8];
+    for (int f = 0; f < 6; ++f)
+        for (int j = 0; j < 8; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += e->F[f * 64 + k * 8 + j];
+            fint[f][j] = s;
+        }
+    double vint[8];
+    for (int j = 0; j < 8; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += e->M[k * 8 + j];
+        vint[j] = s;
+    }
+    for (int kk = 0; kk < nz; ++kk) {
+        int k = om[2] >= 0.0 ? kk : nz - 1 - kk;
+        for (int jj = 0; jj < ny; ++jj) {
+            int j = om[1] >= 0.0 ? jj : ny - 1 - jj;
+            for (int ii = 0; ii < nx; ++ii) {
+                int i = om[0] >= 0.0 ? ii : nx - 1 - ii;
+                long c = i + (long)nx * (j + (long)ny * k);
+                double up[12];
+                int onbnd[3];
+                for (int ax = 0; ax < 3; ++ax) {
+                    int idx[3] = {i, j, k}, n[3] = {nx, ny, nz};
+                    int ui = idx[ax] + (om[ax] >= 0.0 ? -1 : 1);
+                    onbnd[ax] = (ui < 0 || ui >= n[ax]);
+                    for (int t = 0; t < 4; ++t) {
+                        if (!onbnd[ax]) {
+                            int nb[3] = {i, j, k};
+                            nb[ax] = ui;
+                            long cu = nb[0] + (long)nx * (nb[1] + (long)ny * nb[2]);
+                            /* the upwind cell's node on its outflow face (the */
+                            /* face opposite to our inflow face, same in-face t) */
+                            up[4 * ax + t] = psi[8 * cu + face_node(fout[ax], t)];
+                        } else {
+                            const double *bv = ax == 0 ? bx : (ax == 1 ? by : bz);
+                            if (bv) {
+                                long fi = ax == 0 ? j + (long)ny * k : (ax == 1 ? i + (long)nx * k : i + (long)nx * j);
+                                up[4 * ax + t] = bv[4 * fi + t];
+                            } else {
+                                up[4 * ax + t] = p->psi_inc[6 * g + fin[ax]];
+                            }
+                        }
+                    }
+                }
+                double A[64], b[8], x[8];
+                assemble(e, om, p->sigt[(long)g * nc + c], S + 8 * c, up, A, b);
+                if (or_ge(8, A, b, x) != 0) return -1;
+                for (int n = 0; n < 8; ++n) psi[8 * c + n] = x[n];
+                if (tal) {
+                    for (int ax = 0; ax < 3; ++ax) {
+                        if (om[ax] == 0.0) continue;
+                        int idx[3] = {i, j, k}, n[3] = {nx, ny, nz};
+                        int di = idx[ax] + (om[ax] >= 0.0 ? 1 : -1);
+                        if (di < 0 || di >= n[ax]) {          /* boundary outflow */
+                            double s = 0.0;
+                            for (int jn = 0; jn < 8; ++jn) s += fint[fout[ax]][jn] * x[jn];
+                            tal[0] += fabs(om[ax]) * s;
+                        }
+                        if (onbnd[ax]) {                        /* boundary inflow */
+                            double s = 0.0;
+                            for (int t = 0; t < 4; ++t) s += fint[fin[ax]][face_node(fin[ax], t)] * up[4 * ax + t];
+                            tal[3] += fabs(om[ax]) * s;
+                        }
+                    }
+                    double sc = 0.0, ss = 0.0;
+                    for (int jn = 0; jn < 8; ++jn) { sc += vint[jn] * x[jn]; ss += vint[jn] * S[8 * c + jn]; }
+                    tal[1] += p->sigt[(long)g * nc + c] * sc;
+                    tal[2] += ss;
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+int or_sweep_dir(const or_problem *p, int d, int g, const double *S, const double *bx,
+                 const double *by, const double *bz, double *psi, double *tal)
+{
+    or_elem e;
+    or_element(p->dx, p->dy, p->dz, e.M, e.L, e.G, e.F);
+    return sweep_dir(p, &e, d, g, S, bx, by, bz, psi, tal);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Full sweep for groups [g0,g1) and directions [d0,d1) with the isotropic   */
+/* per-group source S[g][cell][8]; phi[g][cell][8] = sum_d w_d psi_d          */
+/* (Eq. (9) with Y_00 absorbed in the 4 pi normalisation, Eq. (13)).         */
+/* Groups run in parallel (each group's phi is summed over directions in a   */
+/* fixed order, so the result does not depend on the thread count).          */
+/* tal[4] receives the weighted balance tallies.  Returns 0 or -1.           */
+/* ------------------------------------------------------------------------ */
+int or_sweep(const or_problem *p, const double *S, double *phi, int g0, int g1, int d0, int d1, double *tal)
+{
+    or_elem e;
+    or_element(p->dx, p->dy, p->dz, e.M, e.L, e.G, e.F);
+    const long nc = ncell_of(p);
+    int bad = 0;
+    double gt[64][4];
+    memset(gt, 0, sizeof(gt));
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int g = g0; g < g1; ++g) {
+        double *psi = (double *)malloc(sizeof(double) * 8 * nc);
+        double *ph = phi + (long)g * nc * 8;
+        for (long i = 0; i < 8 * nc; ++i) ph[i] = 0.0;
+        for (int d = d0; d < d1; ++d) {
+            double t[4] = {0, 0, 0, 0};
+            if (sweep_dir(p, &e, d, g, S + (long)g * nc * 8, NULL, NULL, NULL, psi, t) != 0) bad = 1;
+            for (long i = 0; i < 8 * nc; ++i) ph[i] += p->w[d] * psi[i];
+            for (int m = 0; m < 4; ++m) gt[g][m] += p->w[d] * t[m];
+        }
+        free(psi);
+    }
+    if (tal)
+        for (int g = g0; g < g1; ++g)
+            for (int m = 0; m < 4; ++m) tal[m] += gt[g][m];
+    return bad ? -1 : 0;
+}
+
+/* Isotropic source build (Eqs. (2), (6) with the P_0 term only):           */
+/* S_g = (sum_g' xfer[g'][g] sigs_g' phi_g' + q_g) / (4 pi), nodal.           */
+void or_source(const or_problem *p, const double *phi, double *S)
+{
+    const long nc = ncell_of(p);
+    for (int g = 0; g < p->G; ++g)
+        for (long c = 0; c < nc; ++c)
+            for (int n = 0; n < 8; ++n) {
+                double s = p->q[(long)g * nc + c];
+                for (int gp = 0; gp < p->G; ++gp)
+                    s += p->xfer[gp * p->G + g] * p->sigs[(long)gp * nc + c] * phi[((long)gp * nc + c) * 8 + n];
+                S[((long)g * nc + c) * 8 + n] = s / (4.0 * PI);
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Source iteration (Sec. 2, after Eq. (7) and after Eq. (14)): build the   */
+/* source from phi, sweep, update phi, until the change is below tol.        */
+/* Change measures: max_{g,c,n} |phi_new - phi_old| / max |phi_new|, and the */
+/* mean form of Eq. (21) over cells (cell-averaged phi, all groups).         */
+/* The stop test uses the max form.  phi holds the guess and the result.     */
+/* Returns 0, 1 if maxit was reached, or -1 on a solve failure.             */
+/* ------------------------------------------------------------------------ */
+int or_source_iterate(const or_problem *p, double tol, int maxit, double *phi, int *iters,
+                      double *chg_max, double *chg_mean, double *tal)
+{
+    const long nc = ncell_of(p), n = (long)p->G * nc * 8;
+    double *S = (double *)malloc(sizeof(double) * n);
+    double *pn = (double *)malloc(sizeof(double) * n);
+    int rc = 1;
+    *iters = 0;
+    for (int it = 0; it < maxit; ++it) {
+        or_source(p, phi, S);
+        double t[4] = {0, 0, 0, 0};
+        if (or_sweep(p, S, pn, 0, p->G, 0, p->ndir, t) != 0) { rc = -1; break; }
+        double dmax = 0.0, pmax = 0.0, mean = 0.0;
+        for (long i = 0; i < n; ++i) {
+            double dd = fabs(pn[i] - phi[i]);
+            if (dd > dmax) dmax = dd;
+            if (fabs(pn[i]) > pmax) pmax = fabs(pn[i]);
+        }
+        long cnt = 0;
+        for (int g = 0; g < p->G; ++g)
+            for (long c = 0; c < nc; ++c) {
+                double a = 0.0, b = 0.0;
+                for (int k = 0; k < 8; ++k) {
+                    a += pn[((long)g * nc + c) * 8 + k];
+                    b += phi[((long)g * nc + c) * 8 + k];
+                }
+                if (a != 0.0) { mean += fabs(a - b) / fabs(a); ++cnt; }
+            }
+        memcpy(phi, pn, sizeof(double) * n);
+        *iters = it + 1;
+        *chg_max = pmax > 0.0 ? dmax / pmax : 0.0;
+        *chg_mean = cnt ? mean / cnt : 0.0;
+        if (tal) for (int m = 0; m < 4; ++m) tal[m] = t[m];
+        if (*chg_max <= tol) { rc = 0; break; }
+    }
+    free(S);
+    free(pn);
+    return rc;
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
