@@ -1,0 +1,271 @@
+"""Throughput of the DFEM S_n transport sweep on one GB300 (or N replicas).
+
+A step is one source iteration of the whole hot path on the blocked_64 workload
+(64^3 cells on a 10^3 box, LQ_8 = 80 directions, 8 groups, blocked lognormal
+opacity): source build -> hyperplane-wavefront sweep (8x8 DFEM system per cell,
+direction and group, FP32 Gaussian elimination with partial pivoting and one
+refinement step) -> octant reduction with FP64 change norms.  The metric is
+cell*direction*group solves per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the FP64 CPU oracle is timed on a bounded sample of the
+same workload on the host cores.  Under torchrun (N > 1) every rank runs an
+independent replica (the path has no data exchange between GPUs).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Sn sweep cell*dir*group solves/s (GE form, FP32 GE + 1 refinement step)"
+UNIT = "solves/s"
+# algorithmic FP32 flops of one solve (assembly + elimination + refinement + flux), see the design doc
+FLOPS_PER_SOLVE = 1306
+# algorithmic HBM bytes of one solve: 12 inflow + 12 outflow face floats
+BYTES_PER_SOLVE = 96
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def workload_config():
+    return {"workload": "blocked_64: 64^3 cells, 10^3 box, LQ_8 (80 dirs), 8 groups, sigma_t lognormal(0,1) "
+                        "on 8^3 blocks, scattering ratio U[0.3,0.9], downscatter-only, q=1 in a 16^3 box",
+            "mode": "ge32r", "step": "source build + full sweep + octant reduction + FP64 norms",
+            "l2": "working set > L2 (per-octant flux 537 MB, face planes 126 MB), no flush"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The FP64 oracle timed on a bounded sample of the same workload (all groups,
+    the first k directions of one sweep from a fixed source) on the host cores."""
+    import oracle
+    from paper_1906_04017_gb300 import workloads
+    wl = workloads.blocked_64()
+    P = oracle.OracleProblem(wl)
+    rng = np.random.default_rng(0)
+    S = rng.uniform(0.0, 1.0, (P.G, P.ncell, 8))
+    t0 = time.perf_counter()
+    P.sweep(S, dirs=(0, 1))
+    t1 = time.perf_counter() - t0
+    k = int(max(1, min(P.ndir, seconds_target / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    P.sweep(S, dirs=(0, k))
+    dt = time.perf_counter() - t0
+    solves = P.ncell * P.G * k
+    cores = min(P.G, oracle.num_threads())
+    return {"value": solves / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "blocked_64, one sweep of all 8 groups x %d of 80 directions (%d solves, %.1f s), "
+                      "FP64, groups in parallel" % (k, solves, dt)}
+
+
+def run_reference(args):
+    ws, rank = dist_env()
+    if rank != 0:
+        return 0
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(seconds_target=float(os.environ.get("SN_REF_SECONDS", "8")))
+        if i >= args.warmup:
+            times.append(r["value"])
+            cb = r
+    value = float(np.median(times))
+    cb = dict(cb, value=value)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank = dist_env()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1906_04017_gb300 import sn, workloads
+
+    wl = workloads.blocked_64()
+    P = sn.Problem(wl)
+    phi = P.flux_tensor()
+    solves = P.solves_per_sweep
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # warm-up: the first iterations also capture the CUDA graphs
+    P.source_iterate(phi=phi, tol=0.0, max_it=max(args.warmup, 3), use_graph=True, allow_noconv=True)
+    P.set_profiling(True)
+    P.profile(reset=True)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    r = P.source_iterate(phi=phi, tol=0.0, max_it=args.steps, use_graph=True, allow_noconv=True)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    sweep_ms, nsw = P.profile(reset=True)
+    P.set_profiling(False)
+    assert r["iters"] == args.steps
+
+    # end to end through the public API with host buffers: pinned S in, phi out
+    rng = np.random.default_rng(0)
+    S_host = torch.from_numpy(rng.uniform(0, 1, (P.G, P.ncell, 8)).astype(np.float32)).pin_memory()
+    phi_host = torch.empty_like(S_host).pin_memory()
+    S_dev = torch.empty_like(S_host, device="cuda")
+    phi_dev = torch.empty_like(S_dev)
+    for _ in range(2):
+        S_dev.copy_(S_host, non_blocking=True)
+        P.sweep(S_dev, phi_dev)
+        phi_host.copy_(phi_dev, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        S_dev.copy_(S_host, non_blocking=True)
+        P.sweep(S_dev, phi_dev)
+        phi_host.copy_(phi_dev, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    ms_t = torch.tensor([ms, e2e_ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms, e2e_ms = ms_t.tolist()
+    P.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    value = ws * solves * args.steps / (ms / 1e3)
+    e2e_value = ws * solves * args.steps / (e2e_ms / 1e3)
+    # roofline of the sweep kernel (dominant): FP32 ALU bound
+    sweep_s = sweep_ms / max(nsw, 1) / 1e3
+    achieved_tf = solves * FLOPS_PER_SOLVE / sweep_s / 1e12
+    peak_tf = N_SM * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(), parallelism="replicas" if ws > 1 else "single"),
+        "roofline": {"bound": "alu", "kernel": "sweep_plane_ge<refine>", "achieved": achieved_tf,
+                     "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
+                     "traffic": None,
+                     "flops_per_solve": FLOPS_PER_SOLVE,
+                     "hbm_achieved_gbs": solves * BYTES_PER_SOLVE / sweep_s / 1e9,
+                     "hbm_peak_gbs": hbm_peak,
+                     "peak_note": "FP32 peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
+                     "sweep_ms": sweep_s * 1e3},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(S_host.numel() * 4),
+                "d2h_bytes_per_step": int(phi_host.numel() * 4),
+                "what": "sn_sweep through the public API, pinned host source in, host flux out"},
+        "gpu_launches": int(args.steps * (P.nplanes + 2)),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * sn.h -- C ABI of the GB300 (sm_103a) DFEM S_n transport sweep library.
+ *
+ * Method: Tano & Ragusa, "Acceleration of Radiation Transport Solves Using
+ * Artificial Neural Networks" (arXiv:1906.04017).  Equation numbers are the
+ * paper's, counted in order of appearance: (1) transport equation, (2) total
+ * source, (8)-(9) discrete ordinates, (10) inflow condition, (11) DFEM trial
+ * expansion, (12)-(13) discrete system, (14) per-cell system A psi = b,
+ * (15)-(18) the network and its activations, (19) training loss, (20) error
+ * metric, (21) source-iteration change.
+ *
+ * Conventions shared by every call
+ *  - Mesh: nx x ny x nz uniform axis-aligned box cells on [0,lx]x[0,ly]x[0,lz];
+ *    cell c = i + nx (j + ny k).  Tri-linear (Q1) DFEM, 8 nodes per cell,
+ *    local node n = a + 2b + 4c (x fastest), node n of cell (i,j,k) sits at
+ *    ((i+a) dx, (j+b) dy, (k+c) dz).
+ *  - Scalar-flux and source arrays are [G][ncell][8] FP32, node-fastest.
+ *  - Directions are ordered octant-major (octant bit 0: mu < 0, bit 1: eta < 0,
+ *    bit 2: xi < 0); weights sum to 4 pi; phi = sum_d w_d psi_d (Eqs. (9), (13)).
+ *  - Device pointers are caller-owned device memory (e.g. torch tensors);
+ *    "host" pointers are caller-owned host memory.  The handle owns every
+ *    buffer it allocates and frees it in sn_destroy.
+ *  - Work is queued on the handle's CUDA stream (sn_setup / sn_set_stream; the
+ *    library never synchronises the whole device).  Calls that return host
+ *    scalars synchronise that stream before returning.
+ *  - Inputs are validated on the host; a rejected call returns SN_EINVAL and
+ *    queues nothing.  sn_last_error() gives the message.  There is no CPU
+ *    fallback: without a usable CUDA device calls return SN_ECUDA.
+ *  - The library is not thread-safe per handle.
+ */
+#ifndef SN_GB300_H
+#define SN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sn_handle_s *sn_handle;
+
+typedef enum {
+    SN_OK = 0,
+    SN_EINVAL = 1,    /* bad argument (size, pointer, range, non-finite value)  */
+    SN_ENOMEM = 2,    /* device allocation failed                               */
+    SN_ECUDA = 3,     /* CUDA runtime error or no device                        */
+    SN_ENOCONV = 4,   /* source iteration hit max_it before tol                 */
+    SN_ETIMEOUT = 5,  /* a bounded device wait gave up                          */
+    SN_ENAN = 6,      /* a non-finite value appeared in the flux                */
+    SN_ESTATE = 7     /* call not valid in the handle's state (e.g. no network) */
+} sn_status;
+
+/* How the per-cell system (14) is solved. */
+typedef enum {
+    SN_SOLVE_GE32R = 0,     /* FP32 Gaussian elimination with partial pivoting + one
+                               FP32 iterative-refinement step (Sec. 2, after (14))   */
+    SN_SOLVE_GE32 = 1,      /* FP32 elimination, no refinement                        */
+    SN_SOLVE_ANN = 2,       /* surrogate network only (Sec. 3, Eqs. (15)-(18))        */
+    SN_SOLVE_ANN_GATED = 3  /* surrogate, with cells whose residual fails the gate
+                               re-solved by SN_SOLVE_GE32R                          */
+} sn_solve_mode;
+
+typedef struct {
+    int32_t nx, ny, nz;     /* 1..1023 each                                     */
+    double lx, ly, lz;      /* > 0                                              */
+} sn_mesh;
+
+typedef struct {
+    int32_t order;          /* LQ_N order 2,4,6,8,10,12; or 0 for explicit      */
+    int32_t ndir;           /* explicit only: number of directions (8 * n)      */
+    const double *omega;    /* explicit only: host [ndir][3], unit vectors      */
+    const double *w;        /* explicit only: host [ndir], sum 4 pi             */
+} sn_quadrature;
+
+typedef struct {
+    int32_t ngroups;        /* G >= 1                                           */
+    const double *sigt;     /* host [G][ncell] total cross section, >= 0         */
+    const double *sigs;     /* host [G][ncell] scattering out of group g, >= 0   */
+    const double *q;        /* host [G][ncell] isotropic emission density       */
+    const double *xfer;     /* host [G][G]: fraction of g' scattering into g (row g') */
+    const double *psi_inc;  /* host [G][6] isotropic inflow on faces x-,x+,y-,y+,z-,z+
+                               (Eq. (10)); NULL = vacuum                        */
+} sn_xs;
+
+typedef struct {
+    int64_t ncell;
+    int32_t ndir, ngroups, nplanes;   /* nplanes = nx+ny+nz-2 hyperplanes/octant */
+    int32_t dirs_per_octant;
+    int64_t solves_per_sweep;         /* ncell * ndir * G                        */
+    int64_t device_bytes;             /* device memory held by the handle        */
+} sn_info;
+
+/* ---------------------------------------------------------------------------
+ * sn_setup: build a problem (Sec. 2: mesh, quadrature (8)-(9), cross sections
+ * of (1)-(2), inflow (10)).  Copies the host arrays to the device as FP32 and
+ * allocates the sweep's working buffers.  stream: a cudaStream_t (NULL =
+ * legacy default stream), borrowed, not owned.  On success *out is a new
+ * handle; on failure *out is NULL and the status says why.
+ * ------------------------------------------------------------------------- */
+sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *quad,
+                   const sn_xs *xs, void *stream);
+
+/* Replace the stream later calls are queued on. */
+sn_status sn_set_stream(sn_handle h, void *stream);
+
+sn_status sn_get_info(sn_handle h, sn_info *info);
+
+/* Copy the handle's directions (host [ndir][3]) and weights (host [ndir]). */
+sn_status sn_get_quadrature(sn_handle h, double *omega, double *w);
+
+/* ---------------------------------------------------------------------------
+ * sn_cell_solve_batch: n independent one-cell problems (the paper's one-cell
+ * problem, Sec. 3, and the per-cell system (14)).
+ *   in27: device [n][27] FP32 = Omega(3), (dx,dy,dz), sigma_t, S(8), up(12)
+ *         S: nodal angular source density (node order above);
+ *         up: upwind values on the inflow face of each axis (the face at
+ *         coordinate 0 if Omega_a >= 0, else at the cell size): x-face then
+ *         y-face then z-face, 4 each, in-face order x: b+2c, y: a+2c, z: a+2b.
+ *   psi:  device [n][8] FP32 nodal angular flux (output).
+ * mode SN_SOLVE_ANN / SN_SOLVE_ANN_GATED need a handle with a trained or
+ * loaded network; the GE modes accept h = NULL.  stream: cudaStream_t.
+ * Cell sizes must be > 0 and sigma_t >= 0 (not checked per problem on the
+ * device: the caller owns the data).
+ * ------------------------------------------------------------------------- */
+sn_status sn_cell_solve_batch(sn_handle h, const float *in27, float *psi, int64_t n,
+                              sn_solve_mode mode, void *stream);
+
+/* FP64 variant of the GE solve (same layout, double precision, device). */
+sn_status sn_cell_solve_batch_f64(const double *in27, double *psi, int64_t n, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * sn_sweep: one transport sweep of every direction and group (Sec. 2, after
+ * (14)) for the isotropic nodal source S (device [G][ncell][8], angular
+ * density, i.e. already divided by 4 pi); writes phi (device [G][ncell][8]).
+ * Hyperplane-wavefront order; all octants, directions and groups of one
+ * hyperplane run in one launch.  Balance tallies of this sweep are kept for
+ * sn_get_balance.  S and phi must not overlap.
+ * ------------------------------------------------------------------------- */
+sn_status sn_sweep(sn_handle h, const float *S, float *phi, sn_solve_mode mode);
+
+/* ---------------------------------------------------------------------------
+ * sn_source_iterate: scattering source iteration (Sec. 2, after (7)):
+ * S = (sum_g' xfer[g'][g] sigs_g' phi_g' + q_g) / (4 pi) -> sweep -> phi,
+ * Jacobi in groups, until change_max <= tol or max_it sweeps.
+ *   phi: device [G][ncell][8]; in: initial guess, out: last iterate.
+ *   iters: sweeps done; change_max: max |phi_n - phi_{n-1}| / max |phi_n|
+ *   (FP64 on the device); change_mean: the mean relative change of Eq. (21)
+ *   over cells and groups (cell-averaged flux).  Any output pointer may be NULL.
+ * Returns SN_OK on convergence, SN_ENOCONV if max_it was reached, SN_ENAN if
+ * the flux became non-finite.  use_graph != 0 replays one CUDA graph per
+ * iteration.
+ * ------------------------------------------------------------------------- */
+sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mode mode,
+                            float *phi, int32_t *iters, double *change_max,
+                            double *change_mean, int32_t use_graph);
+
+/* Balance tallies of the last sweep, FP64, particles per unit time:
+ * tallies[0] leakage through the boundary, [1] collisions sum sigma_t int phi,
+ * [2] emission 4 pi int S, [3] inflow through the boundary.  For any sweep
+ * [0] + [1] = [2] + [3] up to round-off (weight 1 in the weak form). */
+sn_status sn_get_balance(sn_handle h, double *tallies);
+
+/* CUDA-event timing of the sweep kernels.  With profiling on, every sweep records
+ * an event before its first hyperplane kernel and after its last one on the
+ * handle's stream; sn_get_profile returns the summed elapsed milliseconds and the
+ * number of sweeps timed (reset != 0 clears both).  Events add no
+ * synchronisation; the times are read at the synchronisations the library
+ * already makes. */
+sn_status sn_set_profiling(sn_handle h, int32_t enable);
+sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t reset);
+
+/* Status text, and the last error message recorded on a handle (h may be NULL
+ * for the last error of a call without a handle, per thread). */
+const char *sn_status_string(sn_status s);
+const char *sn_last_error(sn_handle h);
+
+void sn_destroy(sn_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SN_GB300_H */

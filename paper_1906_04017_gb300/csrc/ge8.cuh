@@ -1,0 +1,271 @@
+// ge8.cuh -- the per-cell DFEM system (14) of Tano & Ragusa (Sec. 2), assembled in
+// registers from its 1D factors and solved by Gaussian elimination with partial
+// pivoting (the paper's "direct Gauss Elimination"), one thread per system.
+//
+// Canonical orientation.  Every (cell, direction) problem is mirrored so that the
+// flow is along +x, +y, +z: local node k = a + 2b + 4c of the mirrored cell is
+// physical node k ^ mask, mask = (Omega_x<0) | (Omega_y<0)<<1 | (Omega_z<0)<<2.
+// In that frame, with tau_a = |Omega_a| / h_a and V the cell volume,
+//
+//   216/V * A = 3 tau_x (Ah x Mh x Mh) + 3 tau_y (Mh x Ah x Mh) + 3 tau_z (Mh x Mh x Ah)
+//               + sigma_t (Mh x Mh x Mh)
+//   216/V * b = (Mh x Mh x Mh) S + 6 tau_x (e0 x Mh x Mh) up_x + ... (y, z alike)
+//
+// with Mh = [[2,1],[1,2]] (6 x the 1D mass matrix on a unit interval) and
+// Ah = [[1,1],[-1,1]] (2 x the 1D streaming matrix plus the outflow-face mass:
+// the outflow form of (14) in one dimension), written per axis in the x-fastest
+// node order.  These are exactly the Gauss-integrated matrices of (12) divided by
+// V/216, so the solution psi is unchanged.
+#pragma once
+
+namespace sn {
+
+__host__ __device__ constexpr int mq(int a, int b) { return a == b ? 2 : 1; }
+__host__ __device__ constexpr int aq(int a, int b) { return (a == 1 && b == 0) ? -1 : 1; }
+
+// 216/V * A in canonical orientation (t3a = 3 tau_a).
+template <typename T>
+__device__ __forceinline__ void assemble_A(T t3x, T t3y, T t3z, T sig, T (&A)[8][8])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int a = k & 1, b = (k >> 1) & 1, c = k >> 2;
+            const int a2 = j & 1, b2 = (j >> 1) & 1, c2 = j >> 2;
+            const T cx = T(aq(a, a2) * mq(b, b2) * mq(c, c2));
+            const T cy = T(mq(a, a2) * aq(b, b2) * mq(c, c2));
+            const T cz = T(mq(a, a2) * mq(b, b2) * aq(c, c2));
+            const T cm = T(mq(a, a2) * mq(b, b2) * mq(c, c2));
+            A[k][j] = t3x * cx + t3y * cy + t3z * cz + sig * cm;
+        }
+    }
+}
+
+// Apply Mh along the node bit `bit` of an 8-vector (in place).
+template <int BIT, typename T>
+__device__ __forceinline__ void mh_axis(T (&v)[8])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k & (1 << BIT)) continue;
+        const T v0 = v[k], v1 = v[k | (1 << BIT)];
+        v[k] = T(2) * v0 + v1;
+        v[k | (1 << BIT)] = v0 + T(2) * v1;
+    }
+}
+
+// 4-vector on a face, in-face index t = p + 2q: apply Mh along p and q.
+template <typename T>
+__device__ __forceinline__ void mh_face(const T (&u)[4], T (&v)[4])
+{
+    const T a0 = T(2) * u[0] + u[1], a1 = u[0] + T(2) * u[1];
+    const T a2 = T(2) * u[2] + u[3], a3 = u[2] + T(2) * u[3];
+    v[0] = T(2) * a0 + a2;
+    v[2] = a0 + T(2) * a2;
+    v[1] = T(2) * a1 + a3;
+    v[3] = a1 + T(2) * a3;
+}
+
+// 216/V * b in canonical orientation (t6a = 6 tau_a).  ux: x-inflow face, in-face
+// t = b + 2c (node 2t); uy: t = a + 2c (node (t&1) + 4(t>>1)); uz: t = a + 2b (node t).
+template <typename T>
+__device__ __forceinline__ void build_b(T t6x, T t6y, T t6z, const T (&S)[8], const T (&ux)[4],
+                                        const T (&uy)[4], const T (&uz)[4], T (&b)[8])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = S[k];
+    mh_axis<0>(b);
+    mh_axis<1>(b);
+    mh_axis<2>(b);
+    T v[4];
+    mh_face(ux, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) b[2 * t] += t6x * v[t];
+    mh_face(uy, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) b[(t & 1) + 4 * (t >> 1)] += t6y * v[t];
+    mh_face(uz, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) b[t] += t6z * v[t];
+}
+
+// y = (216/V * A) x using the Kronecker factors (no 8x8 matrix needed).
+template <typename T>
+__device__ __forceinline__ void apply_A(T t3x, T t3y, T t3z, T sig, const T (&x)[8], T (&y)[8])
+{
+    T u[8], w[8];
+    // x-term and mass term share Mh along y and z
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u[k] = x[k];
+    mh_axis<1>(u);
+    mh_axis<2>(u);
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        const T u0 = u[k], u1 = u[k + 1];
+        y[k] = t3x * (u0 + u1) + sig * (T(2) * u0 + u1);
+        y[k + 1] = t3x * (u1 - u0) + sig * (u0 + T(2) * u1);
+    }
+    // y-term: Mh along x and z, Ah along y
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = x[k];
+    mh_axis<0>(w);
+    mh_axis<2>(w);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k & 2) continue;
+        const T w0 = w[k], w1 = w[k | 2];
+        y[k] += t3y * (w0 + w1);
+        y[k | 2] += t3y * (w1 - w0);
+    }
+    // z-term: Mh along x and y, Ah along z
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = x[k];
+    mh_axis<0>(w);
+    mh_axis<1>(w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T w0 = w[k], w1 = w[k | 4];
+        y[k] += t3z * (w0 + w1);
+        y[k | 4] += t3z * (w1 - w0);
+    }
+}
+
+// Gaussian elimination with partial pivoting on A (8x8, registers), right-hand side
+// b.  Pivot = entry of largest magnitude in the column (ties: the lowest row).
+// Row exchanges move the trailing columns and b only; each multiplier stays where
+// it was computed, so replay_solve() can repeat the same operations on another
+// right-hand side.  piv packs the pivot row of step k in bits 3k..3k+2; rinv holds
+// the reciprocal pivots.  On return b holds the transformed right-hand side and
+// x the solution.
+template <typename T>
+__device__ __forceinline__ void ge8_factor_solve(T (&A)[8][8], T (&b)[8], unsigned &piv,
+                                                 T (&rinv)[8], T (&x)[8])
+{
+    piv = 0u;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        int p = k;
+        T best = fabs(A[k][k]);
+#pragma unroll
+        for (int r = k + 1; r < 8; ++r) {
+            const T v = fabs(A[r][k]);
+            if (v > best) { best = v; p = r; }
+        }
+        piv |= unsigned(p) << (3 * k);
+        if (p != k) {
+#pragma unroll
+            for (int r = k + 1; r < 8; ++r) {
+                if (p == r) {
+#pragma unroll
+                    for (int c = k; c < 8; ++c) {
+                        const T t = A[k][c]; A[k][c] = A[r][c]; A[r][c] = t;
+                    }
+                    const T t = b[k]; b[k] = b[r]; b[r] = t;
+                }
+            }
+        }
+        rinv[k] = T(1) / A[k][k];
+#pragma unroll
+        for (int r = k + 1; r < 8; ++r) {
+            const T l = A[r][k] * rinv[k];
+            A[r][k] = l;
+#pragma unroll
+            for (int c = k + 1; c < 8; ++c) A[r][c] = fma(-l, A[k][c], A[r][c]);
+            b[r] = fma(-l, b[k], b[r]);
+        }
+    }
+    rinv[7] = T(1) / A[7][7];
+#pragma unroll
+    for (int r = 7; r >= 0; --r) {
+        T s = b[r];
+#pragma unroll
+        for (int c = r + 1; c < 8; ++c) s = fma(-A[r][c], x[c], s);
+        x[r] = s * rinv[r];
+    }
+}
+
+// Repeat the elimination recorded by ge8_factor_solve on a new right-hand side r
+// (overwritten) and back-substitute: dx = A^{-1} r.
+template <typename T>
+__device__ __forceinline__ void ge8_replay(const T (&A)[8][8], unsigned piv, const T (&rinv)[8],
+                                           T (&r)[8], T (&dx)[8])
+{
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int p = (piv >> (3 * k)) & 7u;
+        if (p != k) {
+#pragma unroll
+            for (int q = k + 1; q < 8; ++q)
+                if (p == q) { const T t = r[k]; r[k] = r[q]; r[q] = t; }
+        }
+#pragma unroll
+        for (int q = k + 1; q < 8; ++q) r[q] = fma(-A[q][k], r[k], r[q]);
+    }
+#pragma unroll
+    for (int q = 7; q >= 0; --q) {
+        T s = r[q];
+#pragma unroll
+        for (int c = q + 1; c < 8; ++c) s = fma(-A[q][c], dx[c], s);
+        dx[q] = s * rinv[q];
+    }
+}
+
+// Solve the canonical system; REFINE adds one iterative-refinement step in T.
+template <typename T, bool REFINE>
+__device__ __forceinline__ void cell_solve_canonical(T t3x, T t3y, T t3z, T sig, const T (&S)[8],
+                                                     const T (&ux)[4], const T (&uy)[4],
+                                                     const T (&uz)[4], T (&x)[8])
+{
+    T A[8][8], b[8], rinv[8];
+    unsigned piv;
+    assemble_A(t3x, t3y, t3z, sig, A);
+    build_b(T(2) * t3x, T(2) * t3y, T(2) * t3z, S, ux, uy, uz, b);
+    T b0[8];
+    if (REFINE) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b0[k] = b[k];
+    }
+    ge8_factor_solve(A, b, piv, rinv, x);
+    if (REFINE) {
+        T ax[8], dx[8];
+        apply_A(t3x, t3y, t3z, sig, x, ax);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b0[k] -= ax[k];
+        ge8_replay(A, piv, rinv, b0, dx);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] += dx[k];
+    }
+}
+
+// Swap the halves of an 8-vector along node bit BIT when flag is set (x[k] <-> x[k ^ 2^BIT]).
+template <int BIT, typename T>
+__device__ __forceinline__ void cswap_axis(T (&x)[8], bool flag)
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k & (1 << BIT)) continue;
+        const T a = x[k], b = x[k | (1 << BIT)];
+        x[k] = flag ? b : a;
+        x[k | (1 << BIT)] = flag ? a : b;
+    }
+}
+
+// x[k] <- x[k ^ mask] for a 3-bit mask (the map is its own inverse): physical <-> canonical.
+template <typename T>
+__device__ __forceinline__ void mirror8(T (&x)[8], int mask)
+{
+    cswap_axis<0>(x, mask & 1);
+    cswap_axis<1>(x, mask & 2);
+    cswap_axis<2>(x, mask & 4);
+}
+
+// u[t] <- u[t ^ mask] for a 2-bit mask on a face 4-vector.
+template <typename T>
+__device__ __forceinline__ void mirror4(T (&u)[4], int mask)
+{
+    if (mask & 1) { T t = u[0]; u[0] = u[1]; u[1] = t; t = u[2]; u[2] = u[3]; u[3] = t; }
+    if (mask & 2) { T t = u[0]; u[0] = u[2]; u[2] = t; t = u[1]; u[1] = u[3]; u[3] = t; }
+}
+
+}  // namespace sn

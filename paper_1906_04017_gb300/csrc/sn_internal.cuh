@@ -1,0 +1,118 @@
+// sn_internal.cuh -- the handle and the helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sn.h"
+
+namespace sn {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Per-direction data of one octant (every octant uses the same |Omega|):
+// x,y,z = 3 |Omega_a| / h_a, w = quadrature weight.
+struct DirData {
+    float t3x, t3y, t3z, w;
+};
+
+struct Graphs {
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};   // ping-pong parity
+    const float *phi_user = nullptr;                // buffer the graphs were captured for
+    int mode = -1;
+    bool prof = false;
+};
+
+}  // namespace sn
+
+struct sn_handle_s {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;   // owned stream used for graph capture
+
+    int nx = 0, ny = 0, nz = 0;
+    double lx = 0, ly = 0, lz = 0, dx = 0, dy = 0, dz = 0;
+    int64_t ncell = 0;
+    int G = 0, ndir = 0, Do = 0, nplanes = 0;
+    std::vector<double> omega, w;          // host copy of the quadrature
+    std::vector<int64_t> plane_off;        // [nplanes + 1] offsets into plane_cells
+    std::vector<double> sigt_h, q_h;       // host copies used for tallies
+
+    // device buffers (owned)
+    float *sigt = nullptr;       // [G][C]
+    float *sigs = nullptr;       // [G][C]
+    float *q = nullptr;          // [G][C]
+    float *xfer = nullptr;       // [G][G]
+    float *psi_inc = nullptr;    // [G][6]
+    sn::DirData *dir = nullptr;  // [Do]
+    uint32_t *plane_cells = nullptr;  // packed (i',j',k') of every cell, grouped by hyperplane
+    float4 *face = nullptr;      // face planes, see sn_sweep.cu
+    int64_t face_x = 0, face_y = 0, face_z = 0;  // float4 count of each plane set
+    float *phi_oct = nullptr;    // [8][C][G][8] per-octant partial scalar flux
+    float *S = nullptr;          // [G][C][8]
+    float *phi_b = nullptr;      // [G][C][8] iteration scratch
+    double *acc = nullptr;       // device accumulators (see sn_sweep.cu)
+    double *acc_host = nullptr;  // pinned mirror of acc
+    int64_t device_bytes = 0;
+
+    double inflow = 0.0;         // boundary inflow of one sweep (host, exact)
+    double tallies[4] = {0, 0, 0, 0};
+    bool tallies_valid = false;
+
+    sn::Graphs graphs;
+
+    // optional CUDA-event timing of the sweep kernels (sn_set_profiling)
+    bool prof = false;
+    cudaEvent_t ev_sweep[2] = {nullptr, nullptr};
+    double prof_ms = 0.0;          // accumulated sweep-kernel time
+    int64_t prof_sweeps = 0;       // sweeps timed
+    bool prof_pending = false;     // events recorded, elapsed time not yet read
+
+    // surrogate network (set by sn_surrogate_train / sn_surrogate_set_weights)
+    bool has_net = false;
+    void *net = nullptr;
+
+    std::string err;
+};
+
+namespace sn {
+
+// thread-local message for calls without a handle
+void set_global_error(const std::string &msg);
+sn_status fail(sn_handle h, sn_status s, const std::string &msg);
+sn_status cuda_fail(sn_handle h, cudaError_t e, const char *what);
+
+#define SN_CK(h, call)                                         \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return sn::cuda_fail((h), e_, #call); \
+    } while (0)
+
+// releases the surrogate network held by a handle (sn_ann.cu)
+void free_net(sn_handle h);
+
+// kernels launched by several translation units
+sn_status launch_sweep(sn_handle h, const float *S, float *phi_oct, sn_solve_mode mode,
+                       cudaStream_t st);
+sn_status launch_reduce(sn_handle h, const float *phi_old, float *phi_new, const float *S,
+                        bool norms, cudaStream_t st);
+sn_status launch_source(sn_handle h, const float *phi, float *S, cudaStream_t st);
+sn_status launch_cells_f32(const float *in27, float *psi, int64_t n, bool refine, cudaStream_t st);
+
+// accumulator slots in h->acc
+enum AccSlot {
+    ACC_LEAK = 0,      // boundary leakage of the sweep
+    ACC_COLL = 1,      // collisions sum sigma_t int phi
+    ACC_SRC = 2,       // emission 4 pi int S
+    ACC_DMAX = 3,      // max |phi_new - phi_old| (bit pattern, non-negative double)
+    ACC_PMAX = 4,      // max |phi_new|
+    ACC_MEAN = 5,      // sum over (g, c) of |dphi_bar| / |phi_bar|
+    ACC_MEANN = 6,     // number of terms in ACC_MEAN
+    ACC_FLAG = 7,      // non-zero: a non-finite flux value was seen
+    ACC_COUNT = 8
+};
+
+}  // namespace sn

@@ -1,0 +1,512 @@
+// sn_sweep.cu -- the hyperplane-wavefront transport sweep (Sec. 2, after Eq. (14)),
+// the scalar-flux reduction (Eqs. (9), (13)), the isotropic source build (Eqs. (2),
+// (6)) and the source iteration of the C ABI.
+//
+// Wavefront.  In octant o the mesh index is mirrored (i' = nx-1-i when Omega_x < 0,
+// likewise j', k'), so every direction of the octant flows from the corner
+// (0,0,0)' and a cell's upwind neighbours lie on hyperplane i'+j'+k' - 1.  One launch
+// handles hyperplane s of all 8 octants at once, every direction of each octant
+// and every group: the launch has 8 * cells(s) * G keys (octant, cell, group), and
+// each key has Do threads, one per direction of the octant.
+//
+// Face planes.  Octant o keeps three planes per (group, direction): the x-plane holds
+// the 4 canonical face values leaving each (j',k') column, and so on.  A cell reads
+// its inflow from the planes and overwrites the same slots with its outflow; within
+// one hyperplane no two cells share a slot, so the update is in place.  Slot
+// layout [o][column][g][d] of float4 makes the Do x G threads of one cell read and
+// write one contiguous run.  Cells on the inflow boundary take psi_inc instead.
+//
+// Scalar flux.  The Do threads of a key add w_d psi_d in shared memory in a fixed
+// order and write one per-octant partial phi_oct[o][c][g][8]; the reduction kernel
+// sums the 8 octants in a fixed order.  Nothing is atomic, so the flux is
+// bit-reproducible run to run.
+#include <cmath>
+
+#include "ge8.cuh"
+#include "sn_internal.cuh"
+
+namespace sn {
+
+struct SweepArgs {
+    int nx, ny, nz, G, Do, ncells_plane, keys_per_cta;
+    int64_t C;
+    const uint32_t *cells;   // packed (i',j',k') of the cells of this hyperplane
+    const float *sigt;       // [G][C]
+    const float *S;          // [G][C][8]
+    const float *psi_inc;    // [G][6]
+    const DirData *dir;      // [Do]
+    float4 *fx, *fy, *fz;    // face planes
+    float *phi_oct;          // [8][C][G][8]
+    double *leak;            // accumulator
+    float vol12;             // V / 12
+};
+
+__device__ __forceinline__ void load4(float (&u)[4], const float4 *p)
+{
+    const float4 v = *p;
+    u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
+}
+
+template <bool REFINE>
+__global__ void __launch_bounds__(256, 2) sweep_plane_ge(SweepArgs a)
+{
+    extern __shared__ float red[];   // [blockDim.x][9]
+    const int Do = a.Do;
+    const int lk = threadIdx.x / Do;
+    const int d = threadIdx.x - lk * Do;
+    const int64_t key = (int64_t)blockIdx.x * a.keys_per_cta + lk;
+    const int64_t nkeys = 8LL * a.ncells_plane * a.G;
+    // the block is rounded up to whole warps; threads past keys_per_cta * Do idle
+    const bool active = lk < a.keys_per_cta && key < nkeys;
+    int o = 0, g = 0;
+    int64_t c = 0;
+    float leak = 0.f;
+    if (active) {
+        g = (int)(key % a.G);
+        const int64_t t = key / a.G;
+        const int cidx = (int)(t % a.ncells_plane);
+        o = (int)(t / a.ncells_plane);
+        const uint32_t pk = a.cells[cidx];
+        const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
+        const int i = (o & 1) ? a.nx - 1 - ip : ip;
+        const int j = (o & 2) ? a.ny - 1 - jp : jp;
+        const int k = (o & 4) ? a.nz - 1 - kp : kp;
+        c = i + (int64_t)a.nx * (j + (int64_t)a.ny * k);
+        const DirData dd = a.dir[d];
+        const int64_t GD = (int64_t)a.G * Do, gd = (int64_t)g * Do + d;
+        const int64_t ix = ((int64_t)o * a.ny * a.nz + jp + (int64_t)a.ny * kp) * GD + gd;
+        const int64_t iy = ((int64_t)o * a.nx * a.nz + ip + (int64_t)a.nx * kp) * GD + gd;
+        const int64_t iz = ((int64_t)o * a.nx * a.ny + ip + (int64_t)a.nx * jp) * GD + gd;
+        float ux[4], uy[4], uz[4];
+        if (ip == 0) {
+            const float v = a.psi_inc[6 * g + (o & 1)];
+            ux[0] = ux[1] = ux[2] = ux[3] = v;
+        } else {
+            load4(ux, a.fx + ix);
+        }
+        if (jp == 0) {
+            const float v = a.psi_inc[6 * g + 2 + ((o >> 1) & 1)];
+            uy[0] = uy[1] = uy[2] = uy[3] = v;
+        } else {
+            load4(uy, a.fy + iy);
+        }
+        if (kp == 0) {
+            const float v = a.psi_inc[6 * g + 4 + ((o >> 2) & 1)];
+            uz[0] = uz[1] = uz[2] = uz[3] = v;
+        } else {
+            load4(uz, a.fz + iz);
+        }
+        const float sig = a.sigt[(int64_t)g * a.C + c];
+        const float4 *Sp = reinterpret_cast<const float4 *>(a.S + ((int64_t)g * a.C + c) * 8);
+        const float4 s0 = Sp[0], s1 = Sp[1];
+        float S[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        mirror8(S, o);
+        float x[8];
+        cell_solve_canonical<float, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
+        // outflow faces (canonical in-face order)
+        const float4 ox = make_float4(x[1], x[3], x[5], x[7]);
+        const float4 oy = make_float4(x[2], x[3], x[6], x[7]);
+        const float4 oz = make_float4(x[4], x[5], x[6], x[7]);
+        if (ip < a.nx - 1) a.fx[ix] = ox; else leak += dd.t3x * (ox.x + ox.y + ox.z + ox.w);
+        if (jp < a.ny - 1) a.fy[iy] = oy; else leak += dd.t3y * (oy.x + oy.y + oy.z + oy.w);
+        if (kp < a.nz - 1) a.fz[iz] = oz; else leak += dd.t3z * (oz.x + oz.y + oz.z + oz.w);
+        leak *= dd.w * a.vol12;
+        mirror8(x, o);
+        float *r = red + threadIdx.x * 9;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) r[n] = dd.w * x[n];
+    }
+    __syncthreads();
+    if (active) {
+        float *dst = a.phi_oct + (((int64_t)o * a.C + c) * a.G + g) * 8;
+        const float *base = red + (lk * Do) * 9;
+        for (int n = d; n < 8; n += Do) {
+            float s = 0.f;
+            for (int q = 0; q < Do; ++q) s += base[q * 9 + n];
+            dst[n] = s;
+        }
+    }
+    // leakage: warp sum, one double atomic per warp that saw any
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
+    if ((threadIdx.x & 31) == 0 && leak != 0.f) atomicAdd(a.leak, (double)leak);
+}
+
+sn_status launch_sweep(sn_handle h, const float *S, float *phi_oct, sn_solve_mode mode, cudaStream_t st)
+{
+    SweepArgs a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = h->ncell;
+    a.keys_per_cta = 256 / h->Do;
+    a.sigt = h->sigt; a.S = S; a.psi_inc = h->psi_inc; a.dir = h->dir;
+    a.fx = h->face; a.fy = h->face + h->face_x; a.fz = h->face + h->face_x + h->face_y;
+    a.phi_oct = phi_oct;
+    a.leak = h->acc + ACC_LEAK;
+    a.vol12 = (float)(h->dx * h->dy * h->dz / 12.0);
+    const int block = (a.keys_per_cta * h->Do + 31) / 32 * 32;   // whole warps (shuffles)
+    const size_t smem = sizeof(float) * 9 * block;
+    if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
+    for (int s = 0; s < h->nplanes; ++s) {
+        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+        a.cells = h->plane_cells + h->plane_off[s];
+        a.ncells_plane = (int)n;
+        const int64_t nkeys = 8 * n * h->G;
+        const int64_t grid = (nkeys + a.keys_per_cta - 1) / a.keys_per_cta;
+        if (mode == SN_SOLVE_GE32)
+            sweep_plane_ge<false><<<(unsigned)grid, block, smem, st>>>(a);
+        else
+            sweep_plane_ge<true><<<(unsigned)grid, block, smem, st>>>(a);
+    }
+    SN_CK(h, cudaGetLastError());
+    if (h->prof) {
+        SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));
+        h->prof_pending = true;
+    }
+    return SN_OK;
+}
+
+// After a stream synchronisation: add the time between the sweep's first and last
+// kernel to the profile.
+static void prof_collect(sn_handle h)
+{
+    if (!h->prof || !h->prof_pending) return;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_sweep[0], h->ev_sweep[1]) == cudaSuccess) {
+        h->prof_ms += ms;
+        h->prof_sweeps += 1;
+    }
+    h->prof_pending = false;
+}
+
+// ---------------------------------------------------------------------------------
+// Octant sum, balance tallies and (optionally) the change measures of the source
+// iteration, FP64 accumulation (Eq. (21) for the mean form).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_max_nonneg(double *p, double v)
+{
+    atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(256) reduce_kernel(const float *__restrict__ phi_oct,
+                                                     const float *__restrict__ phi_old,
+                                                     float *__restrict__ phi_new,
+                                                     const float *__restrict__ S,
+                                                     const float *__restrict__ sigt, int64_t C, int G,
+                                                     double vol8, double *acc, int norms)
+{
+    __shared__ double sh[8][6];
+    const int64_t total = (int64_t)G * C * 8;
+    double coll = 0, src = 0, dmax = 0, pmax = 0, mean = 0, cnt = 0;
+    int bad = 0;
+    // grid-stride over whole warps so that the 8 nodes of a (g, c) stay in one warp
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x % 32 < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const bool in = e < total;
+        float nv = 0.f, ov = 0.f;
+        if (in) {
+            const int n = (int)(e & 7);
+            const int64_t gc = e >> 3;
+            const int64_t c = gc % C;
+            const int g = (int)(gc / C);
+            double s = 0.0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) s += phi_oct[(((int64_t)o * C + c) * G + g) * 8 + n];
+            nv = (float)s;
+            phi_new[e] = nv;
+            if (!isfinite(nv)) bad = 1;
+            coll += (double)sigt[(int64_t)g * C + c] * vol8 * (double)nv;
+            src += 4.0 * kPi * vol8 * (double)S[e];
+            if (norms) {
+                ov = phi_old[e];
+                dmax = fmax(dmax, fabs((double)nv - (double)ov));
+                pmax = fmax(pmax, fabs((double)nv));
+            }
+        }
+        if (norms) {
+            float a = nv, b = ov;
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, off);
+                b += __shfl_xor_sync(0xffffffffu, b, off);
+            }
+            if (in && (e & 7) == 0 && a != 0.f) {
+                mean += fabs((double)a - (double)b) / fabs((double)a);
+                cnt += 1.0;
+            }
+        }
+    }
+    // block reduction
+    double v[6] = {coll, src, dmax, pmax, mean, cnt};
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const double t = __shfl_down_sync(0xffffffffu, v[m], off);
+            v[m] = (m == 2 || m == 3) ? fmax(v[m], t) : v[m] + t;
+        }
+    }
+    bad = __syncthreads_or(bad);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0)
+        for (int m = 0; m < 6; ++m) sh[warp][m] = v[m];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x / 32;
+        for (int w = 1; w < nw; ++w)
+            for (int m = 0; m < 6; ++m) v[m] = (m == 2 || m == 3) ? fmax(v[m], sh[w][m]) : v[m] + sh[w][m];
+        atomicAdd(acc + ACC_COLL, v[0]);
+        atomicAdd(acc + ACC_SRC, v[1]);
+        if (norms) {
+            atomic_max_nonneg(acc + ACC_DMAX, v[2]);
+            atomic_max_nonneg(acc + ACC_PMAX, v[3]);
+            atomicAdd(acc + ACC_MEAN, v[4]);
+            atomicAdd(acc + ACC_MEANN, v[5]);
+        }
+        if (bad) acc[ACC_FLAG] = 1.0;
+    }
+}
+
+static int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+sn_status launch_reduce(sn_handle h, const float *phi_old, float *phi_new, const float *S, bool norms,
+                        cudaStream_t st)
+{
+    const int64_t total = (int64_t)h->G * h->ncell * 8;
+    int64_t grid = (total + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    if (grid > cap) grid = cap;
+    reduce_kernel<<<(unsigned)grid, 256, 0, st>>>(h->phi_oct, phi_old, phi_new, S, h->sigt, h->ncell, h->G,
+                                                  h->dx * h->dy * h->dz / 8.0, h->acc, norms ? 1 : 0);
+    SN_CK(h, cudaGetLastError());
+    return SN_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Isotropic nodal source (Eqs. (2) and (6), P_0 term; scattering uses the mass
+// matrix without sigma_t, the reading of the scattering term of (12)):
+// S_g = (sum_g' xfer[g'][g] sigs_g' phi_g' + q_g) / (4 pi).
+// One thread per (cell, node) computes every group; GMAX bounds the register copy.
+// ---------------------------------------------------------------------------------
+template <int GMAX>
+__global__ void __launch_bounds__(256) source_kernel(const float *__restrict__ phi,
+                                                     const float *__restrict__ sigs,
+                                                     const float *__restrict__ q,
+                                                     const float *__restrict__ xfer,
+                                                     float *__restrict__ S, int64_t C, int G)
+{
+    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < C * 8;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e >> 3;
+        float sv[GMAX];
+#pragma unroll
+        for (int gp = 0; gp < GMAX; ++gp)
+            sv[gp] = gp < G ? sigs[(int64_t)gp * C + c] * phi[(int64_t)gp * C * 8 + e] : 0.f;
+#pragma unroll
+        for (int g = 0; g < GMAX; ++g) {
+            if (g >= G) break;
+            float acc = q[(int64_t)g * C + c];
+#pragma unroll
+            for (int gp = 0; gp < GMAX; ++gp)
+                if (gp < G) acc = fmaf(__ldg(xfer + gp * G + g), sv[gp], acc);
+            S[(int64_t)g * C * 8 + e] = acc * inv4pi;
+        }
+    }
+}
+
+__global__ void source_kernel_any(const float *__restrict__ phi, const float *__restrict__ sigs,
+                                  const float *__restrict__ q, const float *__restrict__ xfer,
+                                  float *__restrict__ S, int64_t C, int G)
+{
+    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)G * C * 8;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ce = e % (C * 8), c = ce >> 3;
+        const int g = (int)(e / (C * 8));
+        float acc = q[(int64_t)g * C + c];
+        for (int gp = 0; gp < G; ++gp)
+            acc = fmaf(xfer[gp * G + g], sigs[(int64_t)gp * C + c] * phi[(int64_t)gp * C * 8 + ce], acc);
+        S[e] = acc * inv4pi;
+    }
+}
+
+sn_status launch_source(sn_handle h, const float *phi, float *S, cudaStream_t st)
+{
+    const int64_t n = h->ncell * 8;
+    int64_t grid = (n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (grid > cap) grid = cap;
+    const unsigned gr = (unsigned)grid;
+    const int G = h->G;
+    if (G <= 1) source_kernel<1><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
+    else if (G <= 4) source_kernel<4><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
+    else if (G <= 8) source_kernel<8><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
+    else if (G <= 16) source_kernel<16><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
+    else if (G <= 32) source_kernel<32><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
+    else source_kernel_any<<<(unsigned)(cap * 4), 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
+    SN_CK(h, cudaGetLastError());
+    return SN_OK;
+}
+
+static sn_status check_mode(sn_handle h, sn_solve_mode mode)
+{
+    if (mode == SN_SOLVE_GE32R || mode == SN_SOLVE_GE32) return SN_OK;
+    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
+        if (!h->has_net) return fail(h, SN_ESTATE, "surrogate mode needs a trained or loaded network");
+        return SN_OK;
+    }
+    return fail(h, SN_EINVAL, "unknown solve mode");
+}
+
+// one sweep from S into phi (device), tallies into acc; queued on st
+static sn_status sweep_once(sn_handle h, const float *S, float *phi_out, const float *phi_old,
+                            sn_solve_mode mode, cudaStream_t st)
+{
+    SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
+    sn_status s = launch_sweep(h, S, h->phi_oct, mode, st);
+    if (s != SN_OK) return s;
+    return launch_reduce(h, phi_old, phi_out, S, phi_old != nullptr, st);
+}
+
+static void take_tallies(sn_handle h)
+{
+    h->tallies[0] = h->acc_host[ACC_LEAK];
+    h->tallies[1] = h->acc_host[ACC_COLL];
+    h->tallies[2] = h->acc_host[ACC_SRC];
+    h->tallies[3] = h->inflow;
+    h->tallies_valid = true;
+}
+
+}  // namespace sn
+
+using namespace sn;
+
+extern "C" {
+
+sn_status sn_sweep(sn_handle h, const float *S, float *phi, sn_solve_mode mode)
+{
+    if (!h || !S || !phi) return fail(h, SN_EINVAL, "sn_sweep: NULL argument");
+    sn_status s = check_mode(h, mode);
+    if (s != SN_OK) return s;
+    const cudaStream_t st = h->stream;
+    s = sweep_once(h, S, phi, nullptr, mode, st);
+    if (s != SN_OK) return s;
+    SN_CK(h, cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT, cudaMemcpyDeviceToHost, st));
+    SN_CK(h, cudaStreamSynchronize(st));
+    prof_collect(h);
+    take_tallies(h);
+    return SN_OK;
+}
+
+sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mode mode, float *phi,
+                            int32_t *iters, double *change_max, double *change_mean, int32_t use_graph)
+{
+    if (!h || !phi) return fail(h, SN_EINVAL, "sn_source_iterate: NULL argument");
+    if (max_it < 1 || !(tol >= 0.0)) return fail(h, SN_EINVAL, "sn_source_iterate: max_it >= 1, tol >= 0");
+    sn_status s = check_mode(h, mode);
+    if (s != SN_OK) return s;
+    const cudaStream_t st = h->stream;
+    float *buf[2] = {phi, h->phi_b};
+
+    if (use_graph) {
+        Graphs &gr = h->graphs;
+        if (gr.phi_user != phi || gr.mode != (int)mode || gr.prof != h->prof) {
+            for (int p = 0; p < 2; ++p)
+                if (gr.exec[p]) { cudaGraphExecDestroy(gr.exec[p]); gr.exec[p] = nullptr; }
+            for (int p = 0; p < 2; ++p) {
+                cudaGraph_t graph;
+                SN_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+                sn_status cs = launch_source(h, buf[p], h->S, h->cap_stream);
+                if (cs == SN_OK) cs = sweep_once(h, h->S, buf[1 - p], buf[p], mode, h->cap_stream);
+                cudaError_t me = cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT,
+                                                 cudaMemcpyDeviceToHost, h->cap_stream);
+                cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+                if (cs != SN_OK) return cs;
+                SN_CK(h, me);
+                SN_CK(h, ee);
+                cudaError_t ie = cudaGraphInstantiate(&gr.exec[p], graph, 0);
+                cudaGraphDestroy(graph);
+                SN_CK(h, ie);
+            }
+            gr.phi_user = phi;
+            gr.mode = (int)mode;
+            gr.prof = h->prof;
+            h->prof_pending = false;
+        }
+    }
+
+    int it = 0, cur = 0;
+    double cmax = 0, cmean = 0;
+    sn_status rc = SN_ENOCONV;
+    for (it = 0; it < max_it; ++it) {
+        if (use_graph) {
+            SN_CK(h, cudaGraphLaunch(h->graphs.exec[cur], st));
+        } else {
+            s = launch_source(h, buf[cur], h->S, st);
+            if (s == SN_OK) s = sweep_once(h, h->S, buf[1 - cur], buf[cur], mode, st);
+            if (s != SN_OK) return s;
+            SN_CK(h, cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT, cudaMemcpyDeviceToHost, st));
+        }
+        SN_CK(h, cudaStreamSynchronize(st));
+        if (use_graph) h->prof_pending = h->prof;
+        prof_collect(h);
+        cur = 1 - cur;
+        const double *a = h->acc_host;
+        cmax = a[ACC_PMAX] > 0 ? a[ACC_DMAX] / a[ACC_PMAX] : 0.0;
+        cmean = a[ACC_MEANN] > 0 ? a[ACC_MEAN] / a[ACC_MEANN] : 0.0;
+        take_tallies(h);
+        if (a[ACC_FLAG] != 0.0) {
+            rc = fail(h, SN_ENAN, "sn_source_iterate: non-finite scalar flux");
+            ++it;
+            break;
+        }
+        if (cmax <= tol) {
+            rc = SN_OK;
+            ++it;
+            break;
+        }
+    }
+    if (cur == 1) SN_CK(h, cudaMemcpyAsync(phi, h->phi_b, sizeof(float) * h->G * h->ncell * 8,
+                                           cudaMemcpyDeviceToDevice, st));
+    SN_CK(h, cudaStreamSynchronize(st));
+    if (iters) *iters = it;
+    if (change_max) *change_max = cmax;
+    if (change_mean) *change_mean = cmean;
+    if (rc == SN_ENOCONV) fail(h, SN_ENOCONV, "sn_source_iterate: max_it reached before tol");
+    return rc;
+}
+
+sn_status sn_set_profiling(sn_handle h, int32_t enable)
+{
+    if (!h) return fail(nullptr, SN_EINVAL, "sn_set_profiling: NULL handle");
+    if (enable && !h->ev_sweep[0]) {
+        SN_CK(h, cudaEventCreate(&h->ev_sweep[0]));
+        SN_CK(h, cudaEventCreate(&h->ev_sweep[1]));
+    }
+    h->prof = enable != 0;
+    h->prof_pending = false;
+    return SN_OK;
+}
+
+sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t reset)
+{
+    if (!h) return fail(nullptr, SN_EINVAL, "sn_get_profile: NULL handle");
+    if (sweep_ms) *sweep_ms = h->prof_ms;
+    if (sweeps) *sweeps = h->prof_sweeps;
+    if (reset) {
+        h->prof_ms = 0.0;
+        h->prof_sweeps = 0;
+    }
+    return SN_OK;
+}
+
+}  // extern "C"

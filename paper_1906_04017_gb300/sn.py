@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the C ABI in include/sn.h (argument marshalling only).
+
+Every step of the transport path runs in libsn_gb300.so; PyTorch only supplies
+device memory and the current CUDA stream.  If the library is missing this
+module raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsn_gb300.so")
+
+SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ENOCONV, SN_ETIMEOUT, SN_ENAN, SN_ESTATE = range(8)
+GE32R, GE32, ANN, ANN_GATED = 0, 1, 2, 3
+MODES = {"ge32r": GE32R, "ge32": GE32, "ann": ANN, "ann_gated": ANN_GATED}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.c_void_p
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class Quadrature(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("ndir", ctypes.c_int32), ("omega", _dp), ("w", _dp)]
+
+
+class XS(ctypes.Structure):
+    _fields_ = [("ngroups", ctypes.c_int32), ("sigt", _dp), ("sigs", _dp), ("q", _dp),
+                ("xfer", _dp), ("psi_inc", _dp)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("ncell", ctypes.c_int64), ("ndir", ctypes.c_int32), ("ngroups", ctypes.c_int32),
+                ("nplanes", ctypes.c_int32), ("dirs_per_octant", ctypes.c_int32),
+                ("solves_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class SnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+_LIB = None
+
+# (name, restype, argtypes) of every exported entry point
+_API = [
+    ("sn_setup", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Mesh),
+                                ctypes.POINTER(Quadrature), ctypes.POINTER(XS), ctypes.c_void_p]),
+    ("sn_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("sn_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
+    ("sn_get_quadrature", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    ("sn_cell_solve_batch", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_void_p]),
+    ("sn_cell_solve_batch_f64", ctypes.c_int, [_fp, _fp, ctypes.c_int64, ctypes.c_void_p]),
+    ("sn_sweep", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int]),
+    ("sn_source_iterate", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int,
+                                         _fp, ctypes.POINTER(ctypes.c_int32), _dp, _dp, ctypes.c_int32]),
+    ("sn_get_balance", ctypes.c_int, [ctypes.c_void_p, _dp]),
+    ("sn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("sn_get_profile", ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("sn_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("sn_destroy", None, [ctypes.c_void_p]),
+]
+
+
+def lib():
+    """Load libsn_gb300.so (raises if it was not built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsn_gb300.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _API:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def api_names():
+    return [n for n, _, _ in _API]
+
+
+def _check(st, h=None):
+    if st != SN_OK:
+        msg = lib().sn_last_error(h)
+        raise SnError(st, msg.decode() if msg else "error")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype, shape_tail=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("expected a contiguous %s tensor" % dtype)
+    if shape_tail is not None and tuple(t.shape[-len(shape_tail):]) != tuple(shape_tail):
+        raise ValueError("bad trailing shape %s, want %s" % (tuple(t.shape), shape_tail))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def cell_solve_batch(in27, mode=GE32R, handle=None, out=None):
+    """psi[N, 8] of N one-cell problems in27[N, 27] (FP32, CUDA)."""
+    n = in27.shape[0]
+    if out is None:
+        out = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+    h = handle.h if handle is not None else None
+    st = lib().sn_cell_solve_batch(h, _dev(in27, torch.float32, (27,)), _dev(out, torch.float32, (8,)),
+                                   n, int(mode), _stream())
+    _check(st, h)
+    return out
+
+
+def cell_solve_batch_f64(in27, out=None):
+    n = in27.shape[0]
+    if out is None:
+        out = torch.empty((n, 8), dtype=torch.float64, device=in27.device)
+    st = lib().sn_cell_solve_batch_f64(_dev(in27, torch.float64, (27,)), _dev(out, torch.float64, (8,)),
+                                       n, _stream())
+    _check(st)
+    return out
+
+
+class Problem:
+    """A set-up transport problem (sn_setup) on the current CUDA device.
+
+    ``wl`` is a workload dict (see paper_1906_04017_gb300.workloads); explicit
+    quadrature may be given as (omega[ndir,3], w[ndir])."""
+
+    def __init__(self, wl, quadrature=None):
+        self._keep = []
+        nx, ny, nz = int(wl["nx"]), int(wl["ny"]), int(wl["nz"])
+        mesh = Mesh(nx, ny, nz, float(wl["lx"]), float(wl["ly"]), float(wl["lz"]))
+        if quadrature is None:
+            quad = Quadrature(int(wl["order"]), 0, None, None)
+        else:
+            om = np.ascontiguousarray(quadrature[0], dtype=np.float64)
+            w = np.ascontiguousarray(quadrature[1], dtype=np.float64)
+            self._keep += [om, w]
+            quad = Quadrature(0, w.shape[0], _dptr(om), _dptr(w))
+        arrs = [np.ascontiguousarray(wl[k], dtype=np.float64) for k in ("sigt", "sigs", "q", "xfer", "psi_inc")]
+        self._keep += arrs
+        G = arrs[0].reshape(-1, nx * ny * nz).shape[0]
+        xs = XS(G, *[_dptr(a) for a in arrs])
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        st = lib().sn_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), ctypes.byref(xs), _stream())
+        _check(st)
+        self.h = h
+        self._keep = []
+        info = Info()
+        _check(lib().sn_get_info(self.h, ctypes.byref(info)), self.h)
+        self.ncell, self.ndir, self.G = info.ncell, info.ndir, info.ngroups
+        self.nplanes, self.dirs_per_octant = info.nplanes, info.dirs_per_octant
+        self.solves_per_sweep = info.solves_per_sweep
+        self.device_bytes = info.device_bytes
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        _check(lib().sn_set_stream(self.h, _stream()), self.h)
+
+    def quadrature(self):
+        om = np.zeros((self.ndir, 3))
+        w = np.zeros(self.ndir)
+        _check(lib().sn_get_quadrature(self.h, _dptr(om), _dptr(w)), self.h)
+        return om, w
+
+    def flux_tensor(self, device="cuda"):
+        return torch.zeros((self.G, self.ncell, 8), dtype=torch.float32, device=device)
+
+    def sweep(self, S, phi=None, mode=GE32R):
+        """One sweep: phi[G, ncell, 8] from the isotropic nodal source S[G, ncell, 8]."""
+        self._sync_stream()
+        if phi is None:
+            phi = torch.empty_like(S)
+        _check(lib().sn_sweep(self.h, _dev(S, torch.float32, (self.ncell, 8)),
+                              _dev(phi, torch.float32, (self.ncell, 8)), int(mode)), self.h)
+        return phi
+
+    def source_iterate(self, phi=None, tol=1e-6, max_it=500, mode=GE32R, use_graph=True, allow_noconv=False):
+        """Source iteration in place on phi[G, ncell, 8]; returns a dict of results."""
+        self._sync_stream()
+        if phi is None:
+            phi = self.flux_tensor()
+        it = ctypes.c_int32(0)
+        cmax = ctypes.c_double(0)
+        cmean = ctypes.c_double(0)
+        st = lib().sn_source_iterate(self.h, float(tol), int(max_it), int(mode),
+                                     _dev(phi, torch.float32, (self.ncell, 8)), ctypes.byref(it),
+                                     ctypes.byref(cmax), ctypes.byref(cmean), 1 if use_graph else 0)
+        if not (st == SN_ENOCONV and allow_noconv):
+            _check(st, self.h)
+        return dict(phi=phi, iters=it.value, change_max=cmax.value, change_mean=cmean.value,
+                    converged=(st == SN_OK))
+
+    def set_profiling(self, on=True):
+        _check(lib().sn_set_profiling(self.h, 1 if on else 0), self.h)
+
+    def profile(self, reset=True):
+        """(summed sweep-kernel milliseconds, sweeps timed) since the last reset."""
+        ms = ctypes.c_double(0)
+        n = ctypes.c_int64(0)
+        _check(lib().sn_get_profile(self.h, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0), self.h)
+        return ms.value, n.value
+
+    def balance(self):
+        t = np.zeros(4)
+        _check(lib().sn_get_balance(self.h, _dptr(t)), self.h)
+        return t
