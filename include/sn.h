@@ -56,8 +56,9 @@ typedef enum {
                                FP32 iterative-refinement step (Sec. 2, after (14))   */
     SN_SOLVE_GE32 = 1,      /* FP32 elimination, no refinement                        */
     SN_SOLVE_ANN = 2,       /* surrogate network only (Sec. 3, Eqs. (15)-(18))        */
-    SN_SOLVE_ANN_GATED = 3  /* surrogate, with cells whose residual fails the gate
+    SN_SOLVE_ANN_GATED = 3, /* surrogate, with cells whose residual fails the gate
                                re-solved by SN_SOLVE_GE32R                          */
+    SN_SOLVE_GE64 = 4       /* FP64 elimination with partial pivoting (FP64 handles only) */
 } sn_solve_mode;
 
 typedef struct {
@@ -83,6 +84,11 @@ typedef struct {
 } sn_xs;
 
 typedef struct {
+    int32_t fp64;           /* 0: FP32 flux buffers (modes GE32R, GE32, ANN, ANN_GATED)
+                               1: FP64 flux buffers (mode GE64 only)                     */
+} sn_options;
+
+typedef struct {
     int64_t ncell;
     int32_t ndir, ngroups, nplanes;   /* nplanes = nx+ny+nz-2 hyperplanes/octant */
     int32_t dirs_per_octant;
@@ -92,13 +98,16 @@ typedef struct {
 
 /* ---------------------------------------------------------------------------
  * sn_setup: build a problem (Sec. 2: mesh, quadrature (8)-(9), cross sections
- * of (1)-(2), inflow (10)).  Copies the host arrays to the device as FP32 and
- * allocates the sweep's working buffers.  stream: a cudaStream_t (NULL =
+ * of (1)-(2), inflow (10)).  Copies the host arrays to the device in the
+ * handle's precision (opts->fp64; opts may be NULL = FP32) and allocates the
+ * sweep's working buffers.  Every flux and source array later passed to this
+ * handle has that element type (float, or double for an FP64 handle).
+ * stream: a cudaStream_t (NULL =
  * legacy default stream), borrowed, not owned.  On success *out is a new
  * handle; on failure *out is NULL and the status says why.
  * ------------------------------------------------------------------------- */
 sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *quad,
-                   const sn_xs *xs, void *stream);
+                   const sn_xs *xs, const sn_options *opts, void *stream);
 
 /* Replace the stream later calls are queued on. */
 sn_status sn_set_stream(sn_handle h, void *stream);
@@ -130,13 +139,14 @@ sn_status sn_cell_solve_batch_f64(const double *in27, double *psi, int64_t n, vo
 
 /* ---------------------------------------------------------------------------
  * sn_sweep: one transport sweep of every direction and group (Sec. 2, after
- * (14)) for the isotropic nodal source S (device [G][ncell][8], angular
+ * (14)) for the isotropic nodal source S (device [G][ncell][8] of the
+ * handle's element type, angular
  * density, i.e. already divided by 4 pi); writes phi (device [G][ncell][8]).
  * Hyperplane-wavefront order; all octants, directions and groups of one
  * hyperplane run in one launch.  Balance tallies of this sweep are kept for
  * sn_get_balance.  S and phi must not overlap.
  * ------------------------------------------------------------------------- */
-sn_status sn_sweep(sn_handle h, const float *S, float *phi, sn_solve_mode mode);
+sn_status sn_sweep(sn_handle h, const void *S, void *phi, sn_solve_mode mode);
 
 /* ---------------------------------------------------------------------------
  * sn_source_iterate: scattering source iteration (Sec. 2, after (7)):
@@ -151,7 +161,7 @@ sn_status sn_sweep(sn_handle h, const float *S, float *phi, sn_solve_mode mode);
  * iteration.
  * ------------------------------------------------------------------------- */
 sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mode mode,
-                            float *phi, int32_t *iters, double *change_max,
+                            void *phi, int32_t *iters, double *change_max,
                             double *change_mean, int32_t use_graph);
 
 /* Balance tallies of the last sweep, FP64, particles per unit time:

@@ -14,14 +14,15 @@ namespace sn {
 constexpr double kPi = 3.14159265358979323846;
 
 // Per-direction data of one octant (every octant uses the same |Omega|):
-// x,y,z = 3 |Omega_a| / h_a, w = quadrature weight.
+// t3a = 3 |Omega_a| / h_a, w = quadrature weight.
+template <typename T>
 struct DirData {
-    float t3x, t3y, t3z, w;
+    T t3x, t3y, t3z, w;
 };
 
 struct Graphs {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // ping-pong parity
-    const float *phi_user = nullptr;                // buffer the graphs were captured for
+    const void *phi_user = nullptr;                 // buffer the graphs were captured for
     int mode = -1;
     bool prof = false;
 };
@@ -33,27 +34,29 @@ struct sn_handle_s {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // owned stream used for graph capture
 
+    bool fp64 = false;                   // element type of every flux buffer
+    size_t esz = 4;                      // sizeof(element)
+
     int nx = 0, ny = 0, nz = 0;
     double lx = 0, ly = 0, lz = 0, dx = 0, dy = 0, dz = 0;
     int64_t ncell = 0;
     int G = 0, ndir = 0, Do = 0, nplanes = 0;
     std::vector<double> omega, w;          // host copy of the quadrature
     std::vector<int64_t> plane_off;        // [nplanes + 1] offsets into plane_cells
-    std::vector<double> sigt_h, q_h;       // host copies used for tallies
 
-    // device buffers (owned)
-    float *sigt = nullptr;       // [G][C]
-    float *sigs = nullptr;       // [G][C]
-    float *q = nullptr;          // [G][C]
-    float *xfer = nullptr;       // [G][G]
-    float *psi_inc = nullptr;    // [G][6]
-    sn::DirData *dir = nullptr;  // [Do]
+    // device buffers (owned); element type T = float or double (fp64)
+    void *sigt = nullptr;        // T[G][C]
+    void *sigs = nullptr;        // T[G][C]
+    void *q = nullptr;           // T[G][C]
+    void *xfer = nullptr;        // T[G][G]
+    void *psi_inc = nullptr;     // T[G][6]
+    void *dir = nullptr;         // DirData<T>[Do]
     uint32_t *plane_cells = nullptr;  // packed (i',j',k') of every cell, grouped by hyperplane
-    float4 *face = nullptr;      // face planes, see sn_sweep.cu
-    int64_t face_x = 0, face_y = 0, face_z = 0;  // float4 count of each plane set
-    float *phi_oct = nullptr;    // [8][C][G][8] per-octant partial scalar flux
-    float *S = nullptr;          // [G][C][8]
-    float *phi_b = nullptr;      // [G][C][8] iteration scratch
+    void *face = nullptr;        // face planes: 4-vectors of T, see sn_sweep.cu
+    int64_t face_x = 0, face_y = 0, face_z = 0;  // 4-vector count of each plane set
+    void *phi_oct = nullptr;     // T[8][C][G][8] per-octant partial scalar flux
+    void *S = nullptr;           // T[G][C][8]
+    void *phi_b = nullptr;       // T[G][C][8] iteration scratch
     double *acc = nullptr;       // device accumulators (see sn_sweep.cu)
     double *acc_host = nullptr;  // pinned mirror of acc
     int64_t device_bytes = 0;
@@ -94,13 +97,13 @@ sn_status cuda_fail(sn_handle h, cudaError_t e, const char *what);
 // releases the surrogate network held by a handle (sn_ann.cu)
 void free_net(sn_handle h);
 
-// kernels launched by several translation units
-sn_status launch_sweep(sn_handle h, const float *S, float *phi_oct, sn_solve_mode mode,
-                       cudaStream_t st);
-sn_status launch_reduce(sn_handle h, const float *phi_old, float *phi_new, const float *S,
-                        bool norms, cudaStream_t st);
-sn_status launch_source(sn_handle h, const float *phi, float *S, cudaStream_t st);
+// kernels launched by several translation units (element type from h->fp64)
+sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st);
+sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, bool norms,
+                        cudaStream_t st);
+sn_status launch_source(sn_handle h, const void *phi, void *S, cudaStream_t st);
 sn_status launch_cells_f32(const float *in27, float *psi, int64_t n, bool refine, cudaStream_t st);
+int num_sms();
 
 // accumulator slots in h->acc
 enum AccSlot {

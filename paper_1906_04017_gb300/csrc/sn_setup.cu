@@ -121,21 +121,43 @@ static bool finite_all(const double *a, size_t n)
     return true;
 }
 
-template <typename T>
-static sn_status dalloc(sn_handle h, T **p, size_t count)
+static sn_status dalloc_bytes(sn_handle h, void **p, size_t bytes)
 {
-    size_t bytes = sizeof(T) * (count ? count : 1);
-    cudaError_t e = cudaMalloc((void **)p, bytes);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
     h->device_bytes += (int64_t)bytes;
     return SN_OK;
 }
 
-static sn_status upload_f32(sn_handle h, float *dst, const double *src, size_t n)
+// n elements of the handle's element type
+static sn_status dalloc(sn_handle h, void **p, size_t n) { return dalloc_bytes(h, p, n * h->esz); }
+
+// host FP64 -> device element type
+static sn_status upload(sn_handle h, void *dst, const double *src, size_t n)
 {
+    if (h->fp64) {
+        SN_CK(h, cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyHostToDevice));
+        return SN_OK;
+    }
     std::vector<float> tmp(n);
     for (size_t i = 0; i < n; ++i) tmp[i] = (float)src[i];
     SN_CK(h, cudaMemcpy(dst, tmp.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    return SN_OK;
+}
+
+template <typename T>
+static sn_status upload_dirs(sn_handle h)
+{
+    std::vector<DirData<T>> dd(h->Do);
+    for (int d = 0; d < h->Do; ++d) {
+        dd[d].t3x = (T)(3.0 * std::fabs(h->omega[3 * d + 0]) / h->dx);
+        dd[d].t3y = (T)(3.0 * std::fabs(h->omega[3 * d + 1]) / h->dy);
+        dd[d].t3z = (T)(3.0 * std::fabs(h->omega[3 * d + 2]) / h->dz);
+        dd[d].w = (T)h->w[d];
+    }
+    sn_status s = dalloc_bytes(h, &h->dir, sizeof(DirData<T>) * h->Do);
+    if (s != SN_OK) return s;
+    SN_CK(h, cudaMemcpy(h->dir, dd.data(), sizeof(DirData<T>) * h->Do, cudaMemcpyHostToDevice));
     return SN_OK;
 }
 
@@ -183,7 +205,7 @@ const char *sn_last_error(sn_handle h)
 }
 
 sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *quad, const sn_xs *xs,
-                   void *stream)
+                   const sn_options *opts, void *stream)
 {
     if (!out) return fail(nullptr, SN_EINVAL, "sn_setup: out is NULL");
     *out = nullptr;
@@ -202,6 +224,8 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
     sn_handle h = new (std::nothrow) sn_handle_s();
     if (!h) return fail(nullptr, SN_ENOMEM, "sn_setup: host allocation failed");
     h->stream = (cudaStream_t)stream;
+    h->fp64 = opts && opts->fp64;
+    h->esz = h->fp64 ? sizeof(double) : sizeof(float);
     h->nx = mesh->nx; h->ny = mesh->ny; h->nz = mesh->nz;
     h->lx = mesh->lx; h->ly = mesh->ly; h->lz = mesh->lz;
     h->dx = h->lx / h->nx; h->dy = h->ly / h->ny; h->dz = h->lz / h->nz;
@@ -262,8 +286,6 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
         delete h;
         return fail(nullptr, SN_EINVAL, "sn_setup: at most 256 directions per octant");
     }
-    h->sigt_h.assign(xs->sigt, xs->sigt + GC);
-    h->q_h.assign(xs->q, xs->q + GC);
 
     // every host-side check passed: now the device
     {
@@ -294,27 +316,16 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
     SN_TRY(dalloc(h, &h->q, GC));
     SN_TRY(dalloc(h, &h->xfer, (size_t)G * G));
     SN_TRY(dalloc(h, &h->psi_inc, 6 * (size_t)G));
-    SN_TRY(dalloc(h, &h->dir, (size_t)h->Do));
-    SN_TRY(upload_f32(h, h->sigt, xs->sigt, GC));
-    SN_TRY(upload_f32(h, h->sigs, xs->sigs, GC));
-    SN_TRY(upload_f32(h, h->q, xs->q, GC));
-    SN_TRY(upload_f32(h, h->xfer, xs->xfer, (size_t)G * G));
+    SN_TRY(upload(h, h->sigt, xs->sigt, GC));
+    SN_TRY(upload(h, h->sigs, xs->sigs, GC));
+    SN_TRY(upload(h, h->q, xs->q, GC));
+    SN_TRY(upload(h, h->xfer, xs->xfer, (size_t)G * G));
     std::vector<double> inc(6 * G, 0.0);
     if (xs->psi_inc) inc.assign(xs->psi_inc, xs->psi_inc + 6 * G);
-    SN_TRY(upload_f32(h, h->psi_inc, inc.data(), 6 * (size_t)G));
+    SN_TRY(upload(h, h->psi_inc, inc.data(), 6 * (size_t)G));
 
     // direction table (first octant; the others are its mirror images)
-    std::vector<DirData> dd(h->Do);
-    for (int d = 0; d < h->Do; ++d) {
-        dd[d].t3x = (float)(3.0 * std::fabs(h->omega[3 * d + 0]) / h->dx);
-        dd[d].t3y = (float)(3.0 * std::fabs(h->omega[3 * d + 1]) / h->dy);
-        dd[d].t3z = (float)(3.0 * std::fabs(h->omega[3 * d + 2]) / h->dz);
-        dd[d].w = (float)h->w[d];
-    }
-    {
-        cudaError_t e = cudaMemcpy(h->dir, dd.data(), sizeof(DirData) * h->Do, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(dir)"));
-    }
+    SN_TRY(h->fp64 ? upload_dirs<double>(h) : upload_dirs<float>(h));
 
     // boundary inflow of one sweep: sum over faces, groups and inflowing directions
     // of w_d |Omega.n| psi_inc * area
@@ -348,21 +359,22 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
             for (int j = 0; j < h->ny; ++j)
                 for (int i = 0; i < h->nx; ++i)
                     cells[fill[i + j + k]++] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
-        SN_TRY(dalloc(h, &h->plane_cells, (size_t)C));
+        SN_TRY(dalloc_bytes(h, (void **)&h->plane_cells, sizeof(uint32_t) * (size_t)C));
         cudaError_t e = cudaMemcpy(h->plane_cells, cells.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(plane_cells)"));
     }
 
-    // face planes: per octant, per (j',k') / (i',k') / (i',j'), per (group, direction): float4
+    // face planes: per octant, per (j',k') / (i',k') / (i',j'), per (group, direction):
+    // one 4-vector of the element type
     const int64_t GD = G * h->Do;
     h->face_x = 8LL * h->ny * h->nz * GD;
     h->face_y = 8LL * h->nx * h->nz * GD;
     h->face_z = 8LL * h->nx * h->ny * GD;
-    SN_TRY(dalloc(h, &h->face, (size_t)(h->face_x + h->face_y + h->face_z)));
+    SN_TRY(dalloc(h, &h->face, 4 * (size_t)(h->face_x + h->face_y + h->face_z)));
     SN_TRY(dalloc(h, &h->phi_oct, (size_t)8 * GC * 8));
     SN_TRY(dalloc(h, &h->S, GC * 8));
     SN_TRY(dalloc(h, &h->phi_b, GC * 8));
-    SN_TRY(dalloc(h, &h->acc, (size_t)ACC_COUNT));
+    SN_TRY(dalloc_bytes(h, (void **)&h->acc, sizeof(double) * ACC_COUNT));
     {
         cudaError_t e = cudaMallocHost((void **)&h->acc_host, sizeof(double) * ACC_COUNT);
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMallocHost"));

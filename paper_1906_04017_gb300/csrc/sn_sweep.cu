@@ -13,13 +13,15 @@
 // the 4 canonical face values leaving each (j',k') column, and so on.  A cell reads
 // its inflow from the planes and overwrites the same slots with its outflow; within
 // one hyperplane no two cells share a slot, so the update is in place.  Slot
-// layout [o][column][g][d] of float4 makes the Do x G threads of one cell read and
-// write one contiguous run.  Cells on the inflow boundary take psi_inc instead.
+// layout [o][column][g][d] of 4-vectors makes the Do x G threads of one cell read
+// and write one contiguous run.  Cells on the inflow boundary take psi_inc instead.
 //
 // Scalar flux.  The Do threads of a key add w_d psi_d in shared memory in a fixed
 // order and write one per-octant partial phi_oct[o][c][g][8]; the reduction kernel
 // sums the 8 octants in a fixed order.  Nothing is atomic, so the flux is
 // bit-reproducible run to run.
+//
+// Element type T: float (GE32R / GE32) or double (GE64, FP64 handles).
 #include <cmath>
 
 #include "ge8.cuh"
@@ -27,30 +29,55 @@
 
 namespace sn {
 
+template <typename T>
+struct Vec4 {
+    T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ void load4(T (&u)[4], const Vec4<T> *p)
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 f = *reinterpret_cast<const float4 *>(p);
+        u[0] = f.x; u[1] = f.y; u[2] = f.z; u[3] = f.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(Vec4<T> *p, T a, T b, T c, T d)
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+    }
+}
+
+template <typename T>
 struct SweepArgs {
     int nx, ny, nz, G, Do, ncells_plane, keys_per_cta;
     int64_t C;
     const uint32_t *cells;   // packed (i',j',k') of the cells of this hyperplane
-    const float *sigt;       // [G][C]
-    const float *S;          // [G][C][8]
-    const float *psi_inc;    // [G][6]
-    const DirData *dir;      // [Do]
-    float4 *fx, *fy, *fz;    // face planes
-    float *phi_oct;          // [8][C][G][8]
+    const T *sigt;           // [G][C]
+    const T *S;              // [G][C][8]
+    const T *psi_inc;        // [G][6]
+    const DirData<T> *dir;   // [Do]
+    Vec4<T> *fx, *fy, *fz;   // face planes
+    T *phi_oct;              // [8][C][G][8]
     double *leak;            // accumulator
-    float vol12;             // V / 12
+    T vol12;                 // V / 12
 };
 
-__device__ __forceinline__ void load4(float (&u)[4], const float4 *p)
+template <typename T, bool REFINE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(SweepArgs<T> a)
 {
-    const float4 v = *p;
-    u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
-}
-
-template <bool REFINE>
-__global__ void __launch_bounds__(256, 2) sweep_plane_ge(SweepArgs a)
-{
-    extern __shared__ float red[];   // [blockDim.x][9]
+    extern __shared__ __align__(16) unsigned char red_raw[];
+    T *red = reinterpret_cast<T *>(red_raw);   // [blockDim.x][9]
     const int Do = a.Do;
     const int lk = threadIdx.x / Do;
     const int d = threadIdx.x - lk * Do;
@@ -60,7 +87,7 @@ __global__ void __launch_bounds__(256, 2) sweep_plane_ge(SweepArgs a)
     const bool active = lk < a.keys_per_cta && key < nkeys;
     int o = 0, g = 0;
     int64_t c = 0;
-    float leak = 0.f;
+    T leak = T(0);
     if (active) {
         g = (int)(key % a.G);
         const int64_t t = key / a.G;
@@ -72,56 +99,59 @@ __global__ void __launch_bounds__(256, 2) sweep_plane_ge(SweepArgs a)
         const int j = (o & 2) ? a.ny - 1 - jp : jp;
         const int k = (o & 4) ? a.nz - 1 - kp : kp;
         c = i + (int64_t)a.nx * (j + (int64_t)a.ny * k);
-        const DirData dd = a.dir[d];
+        const DirData<T> dd = a.dir[d];
         const int64_t GD = (int64_t)a.G * Do, gd = (int64_t)g * Do + d;
         const int64_t ix = ((int64_t)o * a.ny * a.nz + jp + (int64_t)a.ny * kp) * GD + gd;
         const int64_t iy = ((int64_t)o * a.nx * a.nz + ip + (int64_t)a.nx * kp) * GD + gd;
         const int64_t iz = ((int64_t)o * a.nx * a.ny + ip + (int64_t)a.nx * jp) * GD + gd;
-        float ux[4], uy[4], uz[4];
+        T ux[4], uy[4], uz[4];
         if (ip == 0) {
-            const float v = a.psi_inc[6 * g + (o & 1)];
+            const T v = a.psi_inc[6 * g + (o & 1)];
             ux[0] = ux[1] = ux[2] = ux[3] = v;
         } else {
             load4(ux, a.fx + ix);
         }
         if (jp == 0) {
-            const float v = a.psi_inc[6 * g + 2 + ((o >> 1) & 1)];
+            const T v = a.psi_inc[6 * g + 2 + ((o >> 1) & 1)];
             uy[0] = uy[1] = uy[2] = uy[3] = v;
         } else {
             load4(uy, a.fy + iy);
         }
         if (kp == 0) {
-            const float v = a.psi_inc[6 * g + 4 + ((o >> 2) & 1)];
+            const T v = a.psi_inc[6 * g + 4 + ((o >> 2) & 1)];
             uz[0] = uz[1] = uz[2] = uz[3] = v;
         } else {
             load4(uz, a.fz + iz);
         }
-        const float sig = a.sigt[(int64_t)g * a.C + c];
-        const float4 *Sp = reinterpret_cast<const float4 *>(a.S + ((int64_t)g * a.C + c) * 8);
-        const float4 s0 = Sp[0], s1 = Sp[1];
-        float S[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        const T sig = a.sigt[(int64_t)g * a.C + c];
+        const Vec4<T> *Sp = reinterpret_cast<const Vec4<T> *>(a.S + ((int64_t)g * a.C + c) * 8);
+        T S[8], s0[4], s1[4];
+        load4(s0, Sp);
+        load4(s1, Sp + 1);
+#pragma unroll
+        for (int n = 0; n < 4; ++n) { S[n] = s0[n]; S[4 + n] = s1[n]; }
         mirror8(S, o);
-        float x[8];
-        cell_solve_canonical<float, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
-        // outflow faces (canonical in-face order)
-        const float4 ox = make_float4(x[1], x[3], x[5], x[7]);
-        const float4 oy = make_float4(x[2], x[3], x[6], x[7]);
-        const float4 oz = make_float4(x[4], x[5], x[6], x[7]);
-        if (ip < a.nx - 1) a.fx[ix] = ox; else leak += dd.t3x * (ox.x + ox.y + ox.z + ox.w);
-        if (jp < a.ny - 1) a.fy[iy] = oy; else leak += dd.t3y * (oy.x + oy.y + oy.z + oy.w);
-        if (kp < a.nz - 1) a.fz[iz] = oz; else leak += dd.t3z * (oz.x + oz.y + oz.z + oz.w);
+        T x[8];
+        cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
+        // outflow faces (canonical in-face order): x-face a=1, y-face b=1, z-face c=1
+        if (ip < a.nx - 1) store4(a.fx + ix, x[1], x[3], x[5], x[7]);
+        else leak += dd.t3x * (x[1] + x[3] + x[5] + x[7]);
+        if (jp < a.ny - 1) store4(a.fy + iy, x[2], x[3], x[6], x[7]);
+        else leak += dd.t3y * (x[2] + x[3] + x[6] + x[7]);
+        if (kp < a.nz - 1) store4(a.fz + iz, x[4], x[5], x[6], x[7]);
+        else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
         leak *= dd.w * a.vol12;
         mirror8(x, o);
-        float *r = red + threadIdx.x * 9;
+        T *r = red + threadIdx.x * 9;
 #pragma unroll
         for (int n = 0; n < 8; ++n) r[n] = dd.w * x[n];
     }
     __syncthreads();
     if (active) {
-        float *dst = a.phi_oct + (((int64_t)o * a.C + c) * a.G + g) * 8;
-        const float *base = red + (lk * Do) * 9;
+        T *dst = a.phi_oct + (((int64_t)o * a.C + c) * a.G + g) * 8;
+        const T *base = red + (lk * Do) * 9;
         for (int n = d; n < 8; n += Do) {
-            float s = 0.f;
+            T s = T(0);
             for (int q = 0; q < Do; ++q) s += base[q * 9 + n];
             dst[n] = s;
         }
@@ -129,21 +159,25 @@ __global__ void __launch_bounds__(256, 2) sweep_plane_ge(SweepArgs a)
     // leakage: warp sum, one double atomic per warp that saw any
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
-    if ((threadIdx.x & 31) == 0 && leak != 0.f) atomicAdd(a.leak, (double)leak);
+    if ((threadIdx.x & 31) == 0 && leak != T(0)) atomicAdd(a.leak, (double)leak);
 }
 
-sn_status launch_sweep(sn_handle h, const float *S, float *phi_oct, sn_solve_mode mode, cudaStream_t st)
+template <typename T>
+static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine, cudaStream_t st)
 {
-    SweepArgs a;
+    SweepArgs<T> a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = h->ncell;
     a.keys_per_cta = 256 / h->Do;
-    a.sigt = h->sigt; a.S = S; a.psi_inc = h->psi_inc; a.dir = h->dir;
-    a.fx = h->face; a.fy = h->face + h->face_x; a.fz = h->face + h->face_x + h->face_y;
+    a.sigt = (const T *)h->sigt; a.S = S; a.psi_inc = (const T *)h->psi_inc;
+    a.dir = (const DirData<T> *)h->dir;
+    a.fx = (Vec4<T> *)h->face;
+    a.fy = a.fx + h->face_x;
+    a.fz = a.fy + h->face_y;
     a.phi_oct = phi_oct;
     a.leak = h->acc + ACC_LEAK;
-    a.vol12 = (float)(h->dx * h->dy * h->dz / 12.0);
+    a.vol12 = (T)(h->dx * h->dy * h->dz / 12.0);
     const int block = (a.keys_per_cta * h->Do + 31) / 32 * 32;   // whole warps (shuffles)
-    const size_t smem = sizeof(float) * 9 * block;
+    const size_t smem = sizeof(T) * 9 * block;
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
     for (int s = 0; s < h->nplanes; ++s) {
         const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
@@ -151,10 +185,10 @@ sn_status launch_sweep(sn_handle h, const float *S, float *phi_oct, sn_solve_mod
         a.ncells_plane = (int)n;
         const int64_t nkeys = 8 * n * h->G;
         const int64_t grid = (nkeys + a.keys_per_cta - 1) / a.keys_per_cta;
-        if (mode == SN_SOLVE_GE32)
-            sweep_plane_ge<false><<<(unsigned)grid, block, smem, st>>>(a);
+        if (refine)
+            sweep_plane_ge<T, true><<<(unsigned)grid, block, smem, st>>>(a);
         else
-            sweep_plane_ge<true><<<(unsigned)grid, block, smem, st>>>(a);
+            sweep_plane_ge<T, false><<<(unsigned)grid, block, smem, st>>>(a);
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {
@@ -162,6 +196,12 @@ sn_status launch_sweep(sn_handle h, const float *S, float *phi_oct, sn_solve_mod
         h->prof_pending = true;
     }
     return SN_OK;
+}
+
+sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st)
+{
+    if (h->fp64) return launch_sweep_t<double>(h, (const double *)S, (double *)phi_oct, false, st);
+    return launch_sweep_t<float>(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R, st);
 }
 
 // After a stream synchronisation: add the time between the sweep's first and last
@@ -186,12 +226,11 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v)
     atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void __launch_bounds__(256) reduce_kernel(const float *__restrict__ phi_oct,
-                                                     const float *__restrict__ phi_old,
-                                                     float *__restrict__ phi_new,
-                                                     const float *__restrict__ S,
-                                                     const float *__restrict__ sigt, int64_t C, int G,
-                                                     double vol8, double *acc, int norms)
+template <typename T>
+__global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_oct, const T *__restrict__ phi_old,
+                                                     T *__restrict__ phi_new, const T *__restrict__ S,
+                                                     const T *__restrict__ sigt, int64_t C, int G, double vol8,
+                                                     double *acc, int norms)
 {
     __shared__ double sh[8][6];
     const int64_t total = (int64_t)G * C * 8;
@@ -201,7 +240,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const float *__restrict__ p
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x % 32 < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const bool in = e < total;
-        float nv = 0.f, ov = 0.f;
+        T nv = T(0), ov = T(0);
         if (in) {
             const int n = (int)(e & 7);
             const int64_t gc = e >> 3;
@@ -209,10 +248,10 @@ __global__ void __launch_bounds__(256) reduce_kernel(const float *__restrict__ p
             const int g = (int)(gc / C);
             double s = 0.0;
 #pragma unroll
-            for (int o = 0; o < 8; ++o) s += phi_oct[(((int64_t)o * C + c) * G + g) * 8 + n];
-            nv = (float)s;
+            for (int o = 0; o < 8; ++o) s += (double)phi_oct[(((int64_t)o * C + c) * G + g) * 8 + n];
+            nv = (T)s;
             phi_new[e] = nv;
-            if (!isfinite(nv)) bad = 1;
+            if (!isfinite((double)nv)) bad = 1;
             coll += (double)sigt[(int64_t)g * C + c] * vol8 * (double)nv;
             src += 4.0 * kPi * vol8 * (double)S[e];
             if (norms) {
@@ -222,14 +261,14 @@ __global__ void __launch_bounds__(256) reduce_kernel(const float *__restrict__ p
             }
         }
         if (norms) {
-            float a = nv, b = ov;
+            double a = (double)nv, b = (double)ov;
 #pragma unroll
             for (int off = 1; off < 8; off <<= 1) {
                 a += __shfl_xor_sync(0xffffffffu, a, off);
                 b += __shfl_xor_sync(0xffffffffu, b, off);
             }
-            if (in && (e & 7) == 0 && a != 0.f) {
-                mean += fabs((double)a - (double)b) / fabs((double)a);
+            if (in && (e & 7) == 0 && a != 0.0) {
+                mean += fabs(a - b) / fabs(a);
                 cnt += 1.0;
             }
         }
@@ -265,27 +304,33 @@ __global__ void __launch_bounds__(256) reduce_kernel(const float *__restrict__ p
     }
 }
 
-static int num_sms()
+int num_sms()
 {
     static int n = 0;
     if (!n) {
-        int dev = 0;
+        int dev = 0, m = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+        n = m > 0 ? m : 1;
     }
     return n;
 }
 
-sn_status launch_reduce(sn_handle h, const float *phi_old, float *phi_new, const float *S, bool norms,
-                        cudaStream_t st)
+sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, bool norms, cudaStream_t st)
 {
     const int64_t total = (int64_t)h->G * h->ncell * 8;
     int64_t grid = (total + 255) / 256;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (grid > cap) grid = cap;
-    reduce_kernel<<<(unsigned)grid, 256, 0, st>>>(h->phi_oct, phi_old, phi_new, S, h->sigt, h->ncell, h->G,
-                                                  h->dx * h->dy * h->dz / 8.0, h->acc, norms ? 1 : 0);
+    const double vol8 = h->dx * h->dy * h->dz / 8.0;
+    if (h->fp64)
+        reduce_kernel<double><<<(unsigned)grid, 256, 0, st>>>(
+            (const double *)h->phi_oct, (const double *)phi_old, (double *)phi_new, (const double *)S,
+            (const double *)h->sigt, h->ncell, h->G, vol8, h->acc, norms ? 1 : 0);
+    else
+        reduce_kernel<float><<<(unsigned)grid, 256, 0, st>>>(
+            (const float *)h->phi_oct, (const float *)phi_old, (float *)phi_new, (const float *)S,
+            (const float *)h->sigt, h->ncell, h->G, vol8, h->acc, norms ? 1 : 0);
     SN_CK(h, cudaGetLastError());
     return SN_OK;
 }
@@ -296,50 +341,49 @@ sn_status launch_reduce(sn_handle h, const float *phi_old, float *phi_new, const
 // S_g = (sum_g' xfer[g'][g] sigs_g' phi_g' + q_g) / (4 pi).
 // One thread per (cell, node) computes every group; GMAX bounds the register copy.
 // ---------------------------------------------------------------------------------
-template <int GMAX>
-__global__ void __launch_bounds__(256) source_kernel(const float *__restrict__ phi,
-                                                     const float *__restrict__ sigs,
-                                                     const float *__restrict__ q,
-                                                     const float *__restrict__ xfer,
-                                                     float *__restrict__ S, int64_t C, int G)
+template <typename T, int GMAX>
+__global__ void __launch_bounds__(256) source_kernel(const T *__restrict__ phi, const T *__restrict__ sigs,
+                                                     const T *__restrict__ q, const T *__restrict__ xfer,
+                                                     T *__restrict__ S, int64_t C, int G)
 {
-    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    const T inv4pi = (T)(1.0 / (4.0 * kPi));
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < C * 8;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e >> 3;
-        float sv[GMAX];
+        T sv[GMAX];
 #pragma unroll
         for (int gp = 0; gp < GMAX; ++gp)
-            sv[gp] = gp < G ? sigs[(int64_t)gp * C + c] * phi[(int64_t)gp * C * 8 + e] : 0.f;
+            sv[gp] = gp < G ? sigs[(int64_t)gp * C + c] * phi[(int64_t)gp * C * 8 + e] : T(0);
 #pragma unroll
         for (int g = 0; g < GMAX; ++g) {
             if (g >= G) break;
-            float acc = q[(int64_t)g * C + c];
+            T acc = q[(int64_t)g * C + c];
 #pragma unroll
             for (int gp = 0; gp < GMAX; ++gp)
-                if (gp < G) acc = fmaf(__ldg(xfer + gp * G + g), sv[gp], acc);
+                if (gp < G) acc = fma(__ldg(xfer + gp * G + g), sv[gp], acc);
             S[(int64_t)g * C * 8 + e] = acc * inv4pi;
         }
     }
 }
 
-__global__ void source_kernel_any(const float *__restrict__ phi, const float *__restrict__ sigs,
-                                  const float *__restrict__ q, const float *__restrict__ xfer,
-                                  float *__restrict__ S, int64_t C, int G)
+template <typename T>
+__global__ void source_kernel_any(const T *__restrict__ phi, const T *__restrict__ sigs, const T *__restrict__ q,
+                                  const T *__restrict__ xfer, T *__restrict__ S, int64_t C, int G)
 {
-    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    const T inv4pi = (T)(1.0 / (4.0 * kPi));
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)G * C * 8;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ce = e % (C * 8), c = ce >> 3;
         const int g = (int)(e / (C * 8));
-        float acc = q[(int64_t)g * C + c];
+        T acc = q[(int64_t)g * C + c];
         for (int gp = 0; gp < G; ++gp)
-            acc = fmaf(xfer[gp * G + g], sigs[(int64_t)gp * C + c] * phi[(int64_t)gp * C * 8 + ce], acc);
+            acc = fma(xfer[gp * G + g], sigs[(int64_t)gp * C + c] * phi[(int64_t)gp * C * 8 + ce], acc);
         S[e] = acc * inv4pi;
     }
 }
 
-sn_status launch_source(sn_handle h, const float *phi, float *S, cudaStream_t st)
+template <typename T>
+static sn_status launch_source_t(sn_handle h, const T *phi, T *S, cudaStream_t st)
 {
     const int64_t n = h->ncell * 8;
     int64_t grid = (n + 255) / 256;
@@ -347,29 +391,40 @@ sn_status launch_source(sn_handle h, const float *phi, float *S, cudaStream_t st
     if (grid > cap) grid = cap;
     const unsigned gr = (unsigned)grid;
     const int G = h->G;
-    if (G <= 1) source_kernel<1><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
-    else if (G <= 4) source_kernel<4><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
-    else if (G <= 8) source_kernel<8><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
-    else if (G <= 16) source_kernel<16><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
-    else if (G <= 32) source_kernel<32><<<gr, 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
-    else source_kernel_any<<<(unsigned)(cap * 4), 256, 0, st>>>(phi, h->sigs, h->q, h->xfer, S, h->ncell, G);
+    const T *sg = (const T *)h->sigs, *q = (const T *)h->q, *xf = (const T *)h->xfer;
+    if (G <= 1) source_kernel<T, 1><<<gr, 256, 0, st>>>(phi, sg, q, xf, S, h->ncell, G);
+    else if (G <= 4) source_kernel<T, 4><<<gr, 256, 0, st>>>(phi, sg, q, xf, S, h->ncell, G);
+    else if (G <= 8) source_kernel<T, 8><<<gr, 256, 0, st>>>(phi, sg, q, xf, S, h->ncell, G);
+    else if (G <= 16) source_kernel<T, 16><<<gr, 256, 0, st>>>(phi, sg, q, xf, S, h->ncell, G);
+    else source_kernel_any<T><<<(unsigned)(cap * 4), 256, 0, st>>>(phi, sg, q, xf, S, h->ncell, G);
     SN_CK(h, cudaGetLastError());
     return SN_OK;
 }
 
+sn_status launch_source(sn_handle h, const void *phi, void *S, cudaStream_t st)
+{
+    if (h->fp64) return launch_source_t<double>(h, (const double *)phi, (double *)S, st);
+    return launch_source_t<float>(h, (const float *)phi, (float *)S, st);
+}
+
 static sn_status check_mode(sn_handle h, sn_solve_mode mode)
 {
+    if (h->fp64) {
+        if (mode == SN_SOLVE_GE64) return SN_OK;
+        return fail(h, SN_EINVAL, "an FP64 handle only runs SN_SOLVE_GE64");
+    }
     if (mode == SN_SOLVE_GE32R || mode == SN_SOLVE_GE32) return SN_OK;
     if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
         if (!h->has_net) return fail(h, SN_ESTATE, "surrogate mode needs a trained or loaded network");
         return SN_OK;
     }
+    if (mode == SN_SOLVE_GE64) return fail(h, SN_EINVAL, "SN_SOLVE_GE64 needs an FP64 handle");
     return fail(h, SN_EINVAL, "unknown solve mode");
 }
 
 // one sweep from S into phi (device), tallies into acc; queued on st
-static sn_status sweep_once(sn_handle h, const float *S, float *phi_out, const float *phi_old,
-                            sn_solve_mode mode, cudaStream_t st)
+static sn_status sweep_once(sn_handle h, const void *S, void *phi_out, const void *phi_old, sn_solve_mode mode,
+                            cudaStream_t st)
 {
     SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
     sn_status s = launch_sweep(h, S, h->phi_oct, mode, st);
@@ -392,7 +447,7 @@ using namespace sn;
 
 extern "C" {
 
-sn_status sn_sweep(sn_handle h, const float *S, float *phi, sn_solve_mode mode)
+sn_status sn_sweep(sn_handle h, const void *S, void *phi, sn_solve_mode mode)
 {
     if (!h || !S || !phi) return fail(h, SN_EINVAL, "sn_sweep: NULL argument");
     sn_status s = check_mode(h, mode);
@@ -407,7 +462,7 @@ sn_status sn_sweep(sn_handle h, const float *S, float *phi, sn_solve_mode mode)
     return SN_OK;
 }
 
-sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mode mode, float *phi,
+sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mode mode, void *phi,
                             int32_t *iters, double *change_max, double *change_mean, int32_t use_graph)
 {
     if (!h || !phi) return fail(h, SN_EINVAL, "sn_source_iterate: NULL argument");
@@ -415,13 +470,14 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
     sn_status s = check_mode(h, mode);
     if (s != SN_OK) return s;
     const cudaStream_t st = h->stream;
-    float *buf[2] = {phi, h->phi_b};
+    void *buf[2] = {phi, h->phi_b};
 
     if (use_graph) {
         Graphs &gr = h->graphs;
         if (gr.phi_user != phi || gr.mode != (int)mode || gr.prof != h->prof) {
             for (int p = 0; p < 2; ++p)
                 if (gr.exec[p]) { cudaGraphExecDestroy(gr.exec[p]); gr.exec[p] = nullptr; }
+            gr.phi_user = nullptr;
             for (int p = 0; p < 2; ++p) {
                 cudaGraph_t graph;
                 SN_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -475,8 +531,8 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
             break;
         }
     }
-    if (cur == 1) SN_CK(h, cudaMemcpyAsync(phi, h->phi_b, sizeof(float) * h->G * h->ncell * 8,
-                                           cudaMemcpyDeviceToDevice, st));
+    if (cur == 1)
+        SN_CK(h, cudaMemcpyAsync(phi, h->phi_b, h->esz * h->G * h->ncell * 8, cudaMemcpyDeviceToDevice, st));
     SN_CK(h, cudaStreamSynchronize(st));
     if (iters) *iters = it;
     if (change_max) *change_max = cmax;

@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsn_gb300.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ENOCONV, SN_ETIMEOUT, SN_ENAN, SN_ESTATE = range(8)
-GE32R, GE32, ANN, ANN_GATED = 0, 1, 2, 3
-MODES = {"ge32r": GE32R, "ge32": GE32, "ann": ANN, "ann_gated": ANN_GATED}
+GE32R, GE32, ANN, ANN_GATED, GE64 = 0, 1, 2, 3, 4
+MODES = {"ge32r": GE32R, "ge32": GE32, "ann": ANN, "ann_gated": ANN_GATED, "ge64": GE64}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.c_void_p
@@ -35,6 +35,10 @@ class XS(ctypes.Structure):
                 ("xfer", _dp), ("psi_inc", _dp)]
 
 
+class Options(ctypes.Structure):
+    _fields_ = [("fp64", ctypes.c_int32)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("ncell", ctypes.c_int64), ("ndir", ctypes.c_int32), ("ngroups", ctypes.c_int32),
                 ("nplanes", ctypes.c_int32), ("dirs_per_octant", ctypes.c_int32),
@@ -52,7 +56,8 @@ _LIB = None
 # (name, restype, argtypes) of every exported entry point
 _API = [
     ("sn_setup", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Mesh),
-                                ctypes.POINTER(Quadrature), ctypes.POINTER(XS), ctypes.c_void_p]),
+                                ctypes.POINTER(Quadrature), ctypes.POINTER(XS), ctypes.POINTER(Options),
+                                ctypes.c_void_p]),
     ("sn_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("sn_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
     ("sn_get_quadrature", ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
@@ -141,9 +146,13 @@ class Problem:
     """A set-up transport problem (sn_setup) on the current CUDA device.
 
     ``wl`` is a workload dict (see paper_1906_04017_gb300.workloads); explicit
-    quadrature may be given as (omega[ndir,3], w[ndir])."""
+    quadrature may be given as (omega[ndir,3], w[ndir]).  fp64=True makes every
+    flux buffer of the handle double precision (mode GE64)."""
 
-    def __init__(self, wl, quadrature=None):
+    def __init__(self, wl, quadrature=None, fp64=False):
+        self.fp64 = bool(fp64)
+        self.dtype = torch.float64 if fp64 else torch.float32
+        self.default_mode = GE64 if fp64 else GE32R
         self._keep = []
         nx, ny, nz = int(wl["nx"]), int(wl["ny"]), int(wl["nz"])
         mesh = Mesh(nx, ny, nz, float(wl["lx"]), float(wl["ly"]), float(wl["lz"]))
@@ -160,7 +169,9 @@ class Problem:
         xs = XS(G, *[_dptr(a) for a in arrs])
         h = ctypes.c_void_p()
         torch.cuda.init()
-        st = lib().sn_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), ctypes.byref(xs), _stream())
+        opts = Options(1 if fp64 else 0)
+        st = lib().sn_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), ctypes.byref(xs),
+                            ctypes.byref(opts), _stream())
         _check(st)
         self.h = h
         self._keep = []
@@ -192,27 +203,29 @@ class Problem:
         return om, w
 
     def flux_tensor(self, device="cuda"):
-        return torch.zeros((self.G, self.ncell, 8), dtype=torch.float32, device=device)
+        return torch.zeros((self.G, self.ncell, 8), dtype=self.dtype, device=device)
 
-    def sweep(self, S, phi=None, mode=GE32R):
+    def sweep(self, S, phi=None, mode=None):
         """One sweep: phi[G, ncell, 8] from the isotropic nodal source S[G, ncell, 8]."""
         self._sync_stream()
         if phi is None:
             phi = torch.empty_like(S)
-        _check(lib().sn_sweep(self.h, _dev(S, torch.float32, (self.ncell, 8)),
-                              _dev(phi, torch.float32, (self.ncell, 8)), int(mode)), self.h)
+        mode = self.default_mode if mode is None else mode
+        _check(lib().sn_sweep(self.h, _dev(S, self.dtype, (self.ncell, 8)),
+                              _dev(phi, self.dtype, (self.ncell, 8)), int(mode)), self.h)
         return phi
 
-    def source_iterate(self, phi=None, tol=1e-6, max_it=500, mode=GE32R, use_graph=True, allow_noconv=False):
+    def source_iterate(self, phi=None, tol=1e-6, max_it=500, mode=None, use_graph=True, allow_noconv=False):
         """Source iteration in place on phi[G, ncell, 8]; returns a dict of results."""
         self._sync_stream()
+        mode = self.default_mode if mode is None else mode
         if phi is None:
             phi = self.flux_tensor()
         it = ctypes.c_int32(0)
         cmax = ctypes.c_double(0)
         cmean = ctypes.c_double(0)
         st = lib().sn_source_iterate(self.h, float(tol), int(max_it), int(mode),
-                                     _dev(phi, torch.float32, (self.ncell, 8)), ctypes.byref(it),
+                                     _dev(phi, self.dtype, (self.ncell, 8)), ctypes.byref(it),
                                      ctypes.byref(cmax), ctypes.byref(cmean), 1 if use_graph else 0)
         if not (st == SN_ENOCONV and allow_noconv):
             _check(st, self.h)

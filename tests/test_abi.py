@@ -46,7 +46,7 @@ def _setup_raw(mesh=(2, 2, 2, 1.0, 1.0, 1.0), order=4, G=1, sigt=1.0):
     xs = sn.XS(G, *[a.ctypes.data_as(sn._dp) for a in arrs])
     h = ctypes.c_void_p()
     st = sn.lib().sn_setup(ctypes.byref(h), ctypes.byref(sn.Mesh(*mesh)),
-                           ctypes.byref(sn.Quadrature(order, 0, None, None)), ctypes.byref(xs), None)
+                           ctypes.byref(sn.Quadrature(order, 0, None, None)), ctypes.byref(xs), None, None)
     msg = sn.lib().sn_last_error(None)
     if st == 0:
         sn.lib().sn_destroy(h)
@@ -75,14 +75,14 @@ def _setup_g0(mesh):
     xs = sn.XS(0, None, None, None, None, None)
     h = ctypes.c_void_p()
     st = sn.lib().sn_setup(ctypes.byref(h), ctypes.byref(sn.Mesh(*mesh)),
-                           ctypes.byref(sn.Quadrature(4, 0, None, None)), ctypes.byref(xs), None)
+                           ctypes.byref(sn.Quadrature(4, 0, None, None)), ctypes.byref(xs), None, None)
     return st, sn.lib().sn_last_error(None)
 
 
 def test_null_arguments():
     from paper_1906_04017_gb300 import sn
     L = sn.lib()
-    assert L.sn_setup(None, None, None, None, None) == sn.SN_EINVAL
+    assert L.sn_setup(None, None, None, None, None, None) == sn.SN_EINVAL
     assert L.sn_sweep(None, None, None, 0) == sn.SN_EINVAL
     assert L.sn_cell_solve_batch(None, None, None, -1, 0, None) == sn.SN_EINVAL
     assert L.sn_cell_solve_batch(None, None, None, 0, 0, None) == sn.SN_OK

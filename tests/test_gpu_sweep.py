@@ -52,15 +52,46 @@ def test_quadrature_matches_oracle(sn):
         assert np.allclose(om, ro, atol=1e-15) and np.allclose(w, rw, rtol=1e-14)
 
 
-def test_source_iteration_onecube_converged(sn):
-    """The small plain-method case (8^3, LQ_4, 1 group) to 1e-8."""
+def test_source_iteration_onecube_fp64(sn):
+    """The small plain-method case (8^3, LQ_4, 1 group) with FP64 elimination, to a
+    1e-8 relative change as specified for it; the FP64 GPU flux matches the FP64
+    oracle to 1e-12 at equal iteration counts and to the iteration error at the
+    converged point."""
     wl = W.onecube_8()
-    P = sn.Problem(wl)
+    P = sn.Problem(wl, fp64=True)
     r = P.source_iterate(tol=1e-8, max_it=200)
     P.close()
-    ref = oracle.OracleProblem(wl).source_iterate(1e-13, 500)
+    assert r["converged"]
+    ref_same = oracle.OracleProblem(wl).source_iterate(1e-8, 200)
+    assert ref_same["iters"] == r["iters"]
+    assert rel_err(r["phi"].cpu().numpy(), ref_same["phi"]) < 1e-12
+    ref = oracle.OracleProblem(wl).source_iterate(1e-14, 500)
+    assert rel_err(r["phi"].cpu().numpy(), ref["phi"]) < 1e-7
+
+
+def test_source_iteration_onecube_fp32(sn):
+    """The same case in FP32 elimination with refinement: converged as far as FP32
+    allows (1e-6 relative change), within 1e-5 of the converged FP64 oracle."""
+    wl = W.onecube_8()
+    P = sn.Problem(wl)
+    r = P.source_iterate(tol=1e-6, max_it=200)
+    P.close()
+    ref = oracle.OracleProblem(wl).source_iterate(1e-14, 500)
     assert r["converged"]
     assert rel_err(r["phi"].cpu().numpy(), ref["phi"]) < TOL
+
+
+def test_fp64_sweep_matches_oracle(sn):
+    wl = W.random_small(7, 5, 6, order=8, G=2, seed=3, psi_inc=True)
+    P = sn.Problem(wl, fp64=True)
+    rng = np.random.default_rng(0)
+    S = rng.uniform(0.0, 1.0, (P.G, P.ncell, 8))
+    phi = P.sweep(torch.from_numpy(S).cuda()).cpu().numpy()
+    bal = P.balance()
+    P.close()
+    ref, tal = oracle.OracleProblem(wl).sweep(S)
+    assert rel_err(phi, ref) < 1e-12
+    assert np.allclose(bal, tal, rtol=1e-12)
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
