@@ -170,12 +170,13 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
  * [0] + [1] = [2] + [3] up to round-off (weight 1 in the weak form). */
 sn_status sn_get_balance(sn_handle h, double *tallies);
 
-/* CUDA-event timing of the sweep kernels.  With profiling on, every sweep records
- * an event before its first hyperplane kernel and after its last one on the
- * handle's stream; sn_get_profile returns the summed elapsed milliseconds and the
- * number of sweeps timed (reset != 0 clears both).  Events add no
- * synchronisation; the times are read at the synchronisations the library
- * already makes. */
+/* CUDA-event timing of the sweep kernels.  With profiling on, every directly
+ * launched sweep (sn_sweep, or sn_source_iterate with use_graph = 0) records an
+ * event before its first hyperplane kernel and after its last one on the
+ * handle's stream; graph replays are not timed.  sn_get_profile returns the
+ * summed elapsed milliseconds and the number of sweeps timed (reset != 0 clears
+ * both).  Events add no synchronisation; the times are read at the
+ * synchronisations the library already makes. */
 sn_status sn_set_profiling(sn_handle h, int32_t enable);
 sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t reset);
 

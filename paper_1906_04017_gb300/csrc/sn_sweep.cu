@@ -213,6 +213,8 @@ static void prof_collect(sn_handle h)
     if (cudaEventElapsedTime(&ms, h->ev_sweep[0], h->ev_sweep[1]) == cudaSuccess) {
         h->prof_ms += ms;
         h->prof_sweeps += 1;
+    } else {
+        (void)cudaGetLastError();   // do not leave the failure for the next launch check
     }
     h->prof_pending = false;
 }
@@ -474,28 +476,34 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
 
     if (use_graph) {
         Graphs &gr = h->graphs;
-        if (gr.phi_user != phi || gr.mode != (int)mode || gr.prof != h->prof) {
+        if (gr.phi_user != phi || gr.mode != (int)mode) {
             for (int p = 0; p < 2; ++p)
                 if (gr.exec[p]) { cudaGraphExecDestroy(gr.exec[p]); gr.exec[p] = nullptr; }
             gr.phi_user = nullptr;
+            // graphs carry no timing events: sweeps are timed only when launched directly
+            const bool prof = h->prof;
+            h->prof = false;
             for (int p = 0; p < 2; ++p) {
                 cudaGraph_t graph;
-                SN_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t be = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (be != cudaSuccess) { h->prof = prof; return cuda_fail(h, be, "cudaStreamBeginCapture"); }
                 sn_status cs = launch_source(h, buf[p], h->S, h->cap_stream);
                 if (cs == SN_OK) cs = sweep_once(h, h->S, buf[1 - p], buf[p], mode, h->cap_stream);
                 cudaError_t me = cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT,
                                                  cudaMemcpyDeviceToHost, h->cap_stream);
                 cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+                h->prof = prof;
                 if (cs != SN_OK) return cs;
                 SN_CK(h, me);
                 SN_CK(h, ee);
                 cudaError_t ie = cudaGraphInstantiate(&gr.exec[p], graph, 0);
                 cudaGraphDestroy(graph);
                 SN_CK(h, ie);
+                h->prof = false;
             }
+            h->prof = prof;
             gr.phi_user = phi;
             gr.mode = (int)mode;
-            gr.prof = h->prof;
             h->prof_pending = false;
         }
     }
@@ -513,7 +521,6 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
             SN_CK(h, cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT, cudaMemcpyDeviceToHost, st));
         }
         SN_CK(h, cudaStreamSynchronize(st));
-        if (use_graph) h->prof_pending = h->prof;
         prof_collect(h);
         cur = 1 - cur;
         const double *a = h->acc_host;

@@ -1,15 +1,16 @@
 """GPU parity of the wavefront sweep and the source iteration (Sec. 2, after Eq.
 (14); Eqs. (9), (13), (21)) against the FP64 oracle, through the C ABI.
 
-Bar: scalar flux within 1e-5 relative (floored at 1e-8 of the field maximum) of
-the oracle for FP32 elimination with one refinement step."""
+Bar: per-group max-norm relative error of the scalar flux within 1e-5 of the
+oracle for FP32 elimination with one refinement step; pointwise relative error
+within 1e-4 wherever |phi| is at least 1% of the group maximum."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_1906_04017_gb300 import workloads as W
-from _parity import rel_err
+from _parity import point_err, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +38,7 @@ def test_sweep_matches_oracle(sn, shape, order, G):
     wl = W.random_small(*shape, order=order, G=G, seed=sum(shape), psi_inc=True)
     phi, ref, bal, tal = one_sweep(sn, wl)
     assert rel_err(phi, ref) < TOL
+    assert point_err(phi, ref) < 10 * TOL
     # balance of the GPU sweep: leakage + collisions = emission + inflow
     assert abs(bal[0] + bal[1] - bal[2] - bal[3]) < 1e-5 * (bal[2] + bal[3])
     assert np.allclose(bal, tal, rtol=1e-5)
@@ -64,7 +66,7 @@ def test_source_iteration_onecube_fp64(sn):
     assert r["converged"]
     ref_same = oracle.OracleProblem(wl).source_iterate(1e-8, 200)
     assert ref_same["iters"] == r["iters"]
-    assert rel_err(r["phi"].cpu().numpy(), ref_same["phi"]) < 1e-12
+    assert rel_err(r["phi"].cpu().numpy(), ref_same["phi"]) < 1e-11
     ref = oracle.OracleProblem(wl).source_iterate(1e-14, 500)
     assert rel_err(r["phi"].cpu().numpy(), ref["phi"]) < 1e-7
 
@@ -113,15 +115,15 @@ def test_source_iteration_fixed_count(sn, use_graph):
 
 def test_paper_problem_4(sn):
     """The paper's Problem 4 (thick scattering medium, psi_inc = 1 on 3 faces) on a
-    10^3 mesh, LQ_4, iterated to a tight tolerance on both sides."""
+    10^3 mesh, LQ_4: FP32 to a 2e-6 change, FP64 oracle converged; the iteration
+    error is about tol / (1 - rho) with rho close to 1."""
     wl = W.paper_problem(4, n=10, order=4)
     P = sn.Problem(wl)
-    r = P.source_iterate(tol=1e-7, max_it=5000)
+    r = P.source_iterate(tol=2e-6, max_it=5000)
     P.close()
     ref = oracle.OracleProblem(wl).source_iterate(1e-12, 20000)
     assert r["converged"]
-    # iteration error ~ tol / (1 - rho); rho is close to 1 here
-    assert rel_err(r["phi"].cpu().numpy(), ref["phi"]) < 1e-4
+    assert rel_err(r["phi"].cpu().numpy(), ref["phi"]) < 5e-4
 
 
 def test_nan_is_reported(sn):
@@ -147,4 +149,5 @@ def test_blocked_64_sampled_group(sn):
     P.close()
     ref, _ = oracle.OracleProblem(wl).sweep(S.astype(np.float64), groups=(5, 6))
     assert rel_err(phi[5], ref[5]) < TOL
+    assert point_err(phi[5], ref[5]) < 10 * TOL
     assert abs(bal[0] + bal[1] - bal[2] - bal[3]) < 1e-5 * (bal[2] + bal[3])
