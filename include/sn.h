@@ -170,6 +170,62 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
  * [0] + [1] = [2] + [3] up to round-off (weight 1 in the weak form). */
 sn_status sn_get_balance(sn_handle h, double *tallies);
 
+/* ---------------------------------------------------------------------------
+ * Surrogate network (Sec. 3, Eq. (15): one hidden layer, here 27 inputs, 64 ReLU
+ * units, 8 linear outputs; loss of Eq. (19); Adam).  The network lives in the
+ * handle.  Parameters are 2312 FP32 values: W1[64][27] row-major, b1[64],
+ * W2[8][64], b2[8].  Inputs (27) are built from a one-cell problem after it is
+ * mirrored into the positive octant (one network serves every octant):
+ *   x[0:3] = 2|Omega_a| - 1, x[3:6] = (ln h_a + 1.15)/1.15,
+ *   x[6] = ln(max(sigma_t, 1e-6))/4.5, x[7:15] = S/s, x[15:27] = up/s,
+ *   s = max(max|S|, max|up|);
+ * the network predicts psi_canonical / s (s = 0 gives psi = 0).  Inference runs
+ * in BF16 on the tcgen05 tensor cores with FP32 accumulation; the gate accepts a
+ * prediction when ||b - A psi||_2 <= tau ||b||_2 for the cell's system (14),
+ * otherwise the cell is re-solved by SN_SOLVE_GE32R.
+ * ------------------------------------------------------------------------- */
+
+/* Features [n][27] and targets [n][8] (device FP32) of n one-cell problems in27
+ * (device [n][27], layout of sn_cell_solve_batch); targets are the canonical
+ * FP32 elimination solution divided by s. */
+sn_status sn_surrogate_prepare(const float *in27, int64_t n, float *feat, float *targ, void *stream);
+
+/* Uniform(-1/sqrt(fan_in), +1/sqrt(fan_in)) initialisation from a seed; resets Adam. */
+sn_status sn_surrogate_init(sn_handle h, uint64_t seed);
+
+/* Host [2312] FP32 parameters in / out; set resets Adam. */
+sn_status sn_surrogate_set_weights(sn_handle h, const float *params);
+sn_status sn_surrogate_get_weights(sn_handle h, float *params);
+
+/* Gate threshold tau >= 0 (default 0.01). */
+sn_status sn_surrogate_set_gate(sn_handle h, float tau);
+
+/* Loss (19) averaged over n rows and its gradient (host [2312]) at the current
+ * weights; FP32 on the device, per-block partial sums added in a fixed order. */
+sn_status sn_surrogate_grad(sn_handle h, const float *feat, const float *targ, int64_t n, float *grad,
+                            double *loss);
+
+/* steps Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) on batches of `batch` rows;
+ * batch k takes rows [(k*batch) mod nrows, ...) in order, wrapping.  last_loss:
+ * the loss of the last batch (may be NULL). */
+sn_status sn_surrogate_fit(sn_handle h, const float *feat, const float *targ, int64_t nrows, int32_t steps,
+                           int32_t batch, float lr, double *last_loss);
+
+/* Mean absolute error (over rows and the 8 outputs) of the FP32 network. */
+sn_status sn_surrogate_eval(sn_handle h, const float *feat, const float *targ, int64_t n, double *mae);
+
+/* Label n one-cell problems (device in27) with the library's elimination, keep the
+ * last n_test for testing, initialise from seed and fit; train / test MAE out. */
+sn_status sn_surrogate_train(sn_handle h, const float *in27, int64_t n, int64_t n_test, int32_t steps,
+                             int32_t batch, float lr, uint64_t seed, double *train_mae, double *test_mae);
+
+/* psi (device [n][8]) of n one-cell problems by the tensor-core network; gated != 0
+ * applies the residual gate with elimination fallback; *n_fallback (may be NULL)
+ * receives the number of fallbacks.  Synchronises the handle's stream.
+ * SN_ETIMEOUT if a tensor-core completion wait gave up. */
+sn_status sn_surrogate_apply(sn_handle h, const float *in27, float *psi, int64_t n, int32_t gated,
+                             int64_t *n_fallback);
+
 /* CUDA-event timing of the sweep kernels.  With profiling on, every directly
  * launched sweep (sn_sweep, or sn_source_iterate with use_graph = 0) records an
  * event before its first hyperplane kernel and after its last one on the

@@ -1,14 +1,782 @@
-// sn_ann.cu -- the shallow-network surrogate of the per-cell solve (Sec. 3) and the
-// FP32 one-cell entry point that dispatches between elimination and surrogate.
+// sn_ann.cu -- the shallow-network surrogate of the per-cell solve (Sec. 3 of Tano &
+// Ragusa): training on one-cell problems labelled by the library's own elimination
+// (Sec. 4: loss of Eq. (19), Adam), and BF16 inference on the tcgen05 tensor cores
+// with a residual gate that sends failing cells back to elimination.
+//
+// Network: Eq. (15) with 27 inputs, 64 ReLU hidden units and 8 linear outputs.
+// Parameters (2312, FP32 masters): W1[64][27], b1[64], W2[8][64], b2[8].
+//
+// Inference (ann_cells_kernel): a CTA of 128 threads owns a 128-problem tile.  Each
+// thread builds its problem's 27 inputs, rounds them to BF16 and writes one row of
+// the A operand in shared memory; one thread issues tcgen05.mma (M=128, N=64, K=16,
+// twice) with the accumulator in tensor memory; the four warps read their 32 TMEM
+// lanes back (tcgen05.ld), add b1, apply ReLU, write the BF16 hidden tile and the
+// second layer runs the same way (N=16, only 8 columns used).
+//
+// Shared-memory operands use the no-swizzle K-major core-matrix layout: a core
+// matrix is 8 rows x 16 bytes, stored row after row; core matrices follow each other
+// along K every 128 bytes (leading byte offset) and along M/N every K/8 * 128 bytes
+// (stride byte offset).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cell_problem.cuh"
 #include "sn_internal.cuh"
+
+#include <cuda_bf16.h>
 
 namespace sn {
 
+// --------------------------------------------------------------------------------
+// tcgen05 / mbarrier helpers (inline PTX)
+// --------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after the iteration limit.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < (1u << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate, cta_group::1
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one per thread), waited.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major, descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle operand with kdim columns.
+__host__ __device__ constexpr uint32_t umma_off(int row, int k, int kdim)
+{
+    return (uint32_t)((row >> 3) * (kdim / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+constexpr int kTile = 128;
+constexpr int kK1 = 32;                        // 27 inputs padded
+constexpr int kN2 = 16;                        // 8 outputs padded
+constexpr uint32_t kW1Bytes = kNhid * kK1 * 2; // 4096
+constexpr uint32_t kW2Bytes = kN2 * kNhid * 2; // 2048
+constexpr uint32_t kXBytes = kTile * kK1 * 2;  // 8192
+constexpr uint32_t kHBytes = kTile * kNhid * 2;// 16384
+constexpr uint32_t kTmemCols = 128;
+
+struct Net {
+    float *p = nullptr;        // [kNparam] FP32 master weights
+    float *m = nullptr, *v = nullptr;
+    int64_t t = 0;             // Adam steps taken
+    unsigned char *w1p = nullptr;  // BF16 W1 in the operand layout
+    unsigned char *w2p = nullptr;  // BF16 W2 (rows 8..15 zero)
+    float *b1 = nullptr, *b2 = nullptr;   // [64], [16]
+    bool dirty = true;         // packed copies stale
+    float tau = 1e-2f;         // gate threshold
+    float *gpart = nullptr;    // per-CTA gradient partials
+    double *lpart = nullptr;
+    int64_t gpart_blocks = 0;
+    unsigned long long *counter = nullptr;   // [0] fallbacks, [1] error flags
+    double *dacc = nullptr;    // scratch accumulator
+};
+
+static Net *net_of(sn_handle h) { return reinterpret_cast<Net *>(h->net); }
+
 void free_net(sn_handle h)
 {
-    if (!h) return;
+    if (!h || !h->net) return;
+    Net *n = net_of(h);
+    void *bufs[] = {n->p, n->m, n->v, n->w1p, n->w2p, n->b1, n->b2, n->gpart, n->lpart, n->counter, n->dacc};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete n;
     h->net = nullptr;
     h->has_net = false;
+}
+
+static sn_status ensure_net(sn_handle h)
+{
+    if (h->net) return SN_OK;
+    Net *n = new Net();
+    h->net = n;
+    SN_CK(h, cudaMalloc(&n->p, sizeof(float) * kNparam));
+    SN_CK(h, cudaMalloc(&n->m, sizeof(float) * kNparam));
+    SN_CK(h, cudaMalloc(&n->v, sizeof(float) * kNparam));
+    SN_CK(h, cudaMalloc(&n->w1p, kW1Bytes));
+    SN_CK(h, cudaMalloc(&n->w2p, kW2Bytes));
+    SN_CK(h, cudaMalloc(&n->b1, sizeof(float) * kNhid));
+    SN_CK(h, cudaMalloc(&n->b2, sizeof(float) * kN2));
+    SN_CK(h, cudaMalloc(&n->counter, sizeof(unsigned long long) * 2));
+    SN_CK(h, cudaMalloc(&n->dacc, sizeof(double) * 4));
+    SN_CK(h, cudaMemset(n->m, 0, sizeof(float) * kNparam));
+    SN_CK(h, cudaMemset(n->v, 0, sizeof(float) * kNparam));
+    SN_CK(h, cudaMemset(n->counter, 0, sizeof(unsigned long long) * 2));
+    return SN_OK;
+}
+
+// --------------------------------------------------------------------------------
+// Training data: canonical features and elimination labels psi_c / s.
+// --------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) prepare_kernel(const float *__restrict__ in27, int64_t n,
+                                                      float *__restrict__ feat, float *__restrict__ targ)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float *p = in27 + 27 * i;
+        CanonCell<float> c;
+        canonicalize(p, c);
+        const float s = input_scale(c.S, c.ux, c.uy, c.uz);
+        const float inv = s > 0.f ? 1.f / s : 0.f;
+        float x[kNin];
+        ann_features(fabsf(p[0]), fabsf(p[1]), fabsf(p[2]), p[3], p[4], p[5], c.sig, c.S, c.ux, c.uy, c.uz, inv, x);
+#pragma unroll
+        for (int k = 0; k < kNin; ++k) feat[kNin * i + k] = x[k];
+        float psi[8];
+        cell_solve_canonical<float, true>(c.t3x, c.t3y, c.t3z, c.sig, c.S, c.ux, c.uy, c.uz, psi);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) targ[8 * i + k] = psi[k] * inv;
+    }
+}
+
+// --------------------------------------------------------------------------------
+// Loss (19) and its back-propagated gradient over a batch, FP32, one CTA per 128
+// samples; partial gradients per CTA are summed in a fixed order by adam_kernel.
+// Batch row i is dataset row (row0 + i) mod nrows.
+// --------------------------------------------------------------------------------
+constexpr float kLambda = 0.2f, kGamma1 = 10.f, kGamma2 = 0.01f;
+constexpr int kXs = 28, kHs = 65, kOs = 9;    // shared-memory row strides
+
+__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+
+__global__ void __launch_bounds__(128) grad_kernel(const float *__restrict__ P, const float *__restrict__ feat,
+                                                   const float *__restrict__ targ, int64_t nrows, int64_t row0,
+                                                   int batch, float inv_batch, float *__restrict__ gpart,
+                                                   double *__restrict__ lpart)
+{
+    extern __shared__ __align__(16) float sm[];
+    float *sP = sm;                          // kNparam
+    float *sX = sP + kNparam;                // [128][28]
+    float *sH = sX + 128 * kXs;              // [128][65]
+    float *sGA = sH + 128 * kHs;             // [128][65]
+    float *sGO = sGA + 128 * kHs;            // [128][9]
+    __shared__ double sl[4];
+    for (int e = threadIdx.x; e < kNparam; e += blockDim.x) sP[e] = P[e];
+    __syncthreads();
+    const float *W1 = sP, *b1 = sP + kNhid * kNin, *W2 = b1 + kNhid, *b2 = W2 + kNout * kNhid;
+    const int t = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * 128 + t;
+    double lsum = 0.0;
+    float *xr = sX + t * kXs, *hr = sH + t * kHs, *gar = sGA + t * kHs, *gor = sGO + t * kOs;
+    if (i < batch) {
+        const int64_t r = (row0 + i) % nrows;
+        float x[kNin], tt[8], h[kNhid], o[8];
+#pragma unroll
+        for (int k = 0; k < kNin; ++k) { x[k] = feat[kNin * r + k]; xr[k] = x[k]; }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tt[k] = targ[8 * r + k];
+#pragma unroll 4
+        for (int j = 0; j < kNhid; ++j) {
+            float a = b1[j];
+#pragma unroll
+            for (int k = 0; k < kNin; ++k) a = fmaf(W1[j * kNin + k], x[k], a);
+            h[j] = fmaxf(a, 0.f);
+            hr[j] = h[j];
+        }
+        float d[8], sd = 0.f, st = 0.f, mae = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float a = b2[q];
+#pragma unroll
+            for (int j = 0; j < kNhid; ++j) a = fmaf(W2[q * kNhid + j], h[j], a);
+            o[q] = a;
+            d[q] = tt[q] - a;
+            sd += d[q];
+            st += tt[q];
+            mae += fabsf(d[q]);
+        }
+        const float den = kGamma1 * fabsf(st) + kGamma2;
+        lsum = (double)(mae / 8.f + kLambda * fabsf(sd) / den);
+        float go[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            go[q] = -(sgnf(d[q]) / 8.f + kLambda * sgnf(sd) / den) * inv_batch;
+            gor[q] = go[q];
+        }
+#pragma unroll 4
+        for (int j = 0; j < kNhid; ++j) {
+            float gh = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) gh = fmaf(go[q], W2[q * kNhid + j], gh);
+            gar[j] = h[j] > 0.f ? gh : 0.f;
+        }
+    } else {
+        for (int k = 0; k < kNin; ++k) xr[k] = 0.f;
+        for (int j = 0; j < kNhid; ++j) { hr[j] = 0.f; gar[j] = 0.f; }
+        for (int q = 0; q < 8; ++q) gor[q] = 0.f;
+    }
+    __syncthreads();
+    float *gp = gpart + (int64_t)blockIdx.x * kNparam;
+    for (int e = t; e < kNparam; e += 128) {
+        float acc = 0.f;
+        if (e < kNhid * kNin) {
+            const int j = e / kNin, k = e % kNin;
+            for (int s = 0; s < 128; ++s) acc = fmaf(sGA[s * kHs + j], sX[s * kXs + k], acc);
+        } else if (e < kNhid * kNin + kNhid) {
+            const int j = e - kNhid * kNin;
+            for (int s = 0; s < 128; ++s) acc += sGA[s * kHs + j];
+        } else if (e < kNhid * kNin + kNhid + kNout * kNhid) {
+            const int q = (e - kNhid * kNin - kNhid) / kNhid, j = (e - kNhid * kNin - kNhid) % kNhid;
+            for (int s = 0; s < 128; ++s) acc = fmaf(sGO[s * kOs + q], sH[s * kHs + j], acc);
+        } else {
+            const int q = e - (kNhid * kNin + kNhid + kNout * kNhid);
+            for (int s = 0; s < 128; ++s) acc += sGO[s * kOs + q];
+        }
+        gp[e] = acc;
+    }
+    // batch loss partial
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
+    if ((t & 31) == 0) sl[t >> 5] = lsum;
+    __syncthreads();
+    if (t == 0) lpart[blockIdx.x] = sl[0] + sl[1] + sl[2] + sl[3];
+}
+
+constexpr size_t kGradSmem = sizeof(float) * (kNparam + 128 * kXs + 2 * 128 * kHs + 128 * kOs);
+
+// Sum the partials (fixed order); optionally write the gradient, then Adam.
+__global__ void adam_kernel(float *__restrict__ P, float *__restrict__ M, float *__restrict__ V,
+                            const float *__restrict__ gpart, int nblk, float lr, float bc1, float bc2,
+                            float *__restrict__ gout, int do_step)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kNparam) return;
+    double g = 0.0;
+    for (int b = 0; b < nblk; ++b) g += (double)gpart[(int64_t)b * kNparam + e];
+    const float gf = (float)g;
+    if (gout) gout[e] = gf;
+    if (!do_step) return;
+    const float m = 0.9f * M[e] + 0.1f * gf;
+    const float v = 0.999f * V[e] + 0.001f * gf * gf;
+    M[e] = m;
+    V[e] = v;
+    P[e] -= lr * (m / bc1) / (sqrtf(v / bc2) + 1e-8f);
+}
+
+__global__ void sum_kernel(const double *__restrict__ part, int n, double *__restrict__ out)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        *out = s;
+    }
+}
+
+// mean |t - o| over a set (FP32 forward), partial sums per CTA into acc (atomic)
+__global__ void __launch_bounds__(128) mae_kernel(const float *__restrict__ P, const float *__restrict__ feat,
+                                                  const float *__restrict__ targ, int64_t n, double *acc)
+{
+    __shared__ float sP[kNparam];
+    __shared__ double sl[4];
+    for (int e = threadIdx.x; e < kNparam; e += blockDim.x) sP[e] = P[e];
+    __syncthreads();
+    const float *W1 = sP, *b1 = sP + kNhid * kNin, *W2 = b1 + kNhid, *b2 = W2 + kNout * kNhid;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float x[kNin], h[kNhid];
+#pragma unroll
+        for (int k = 0; k < kNin; ++k) x[k] = feat[kNin * i + k];
+#pragma unroll 4
+        for (int j = 0; j < kNhid; ++j) {
+            float a = b1[j];
+#pragma unroll
+            for (int k = 0; k < kNin; ++k) a = fmaf(W1[j * kNin + k], x[k], a);
+            h[j] = fmaxf(a, 0.f);
+        }
+        float e = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float a = b2[q];
+#pragma unroll
+            for (int j = 0; j < kNhid; ++j) a = fmaf(W2[q * kNhid + j], h[j], a);
+            e += fabsf(targ[8 * i + q] - a);
+        }
+        s += (double)e;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(acc, sl[0] + sl[1] + sl[2] + sl[3]);
+}
+
+// FP32 masters -> BF16 operands in the tcgen05 layout, biases copied.
+__global__ void pack_kernel(const float *__restrict__ P, unsigned char *__restrict__ w1p,
+                            unsigned char *__restrict__ w2p, float *__restrict__ b1, float *__restrict__ b2)
+{
+    const float *W1 = P, *B1 = P + kNhid * kNin, *W2 = B1 + kNhid, *B2 = W2 + kNout * kNhid;
+    for (int e = threadIdx.x; e < kNhid * kK1; e += blockDim.x) {
+        const int n = e / kK1, k = e % kK1;
+        const float v = k < kNin ? W1[n * kNin + k] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(w1p + umma_off(n, k, kK1)) = __float2bfloat16_rn(v);
+    }
+    for (int e = threadIdx.x; e < kN2 * kNhid; e += blockDim.x) {
+        const int n = e / kNhid, k = e % kNhid;
+        const float v = n < kNout ? W2[n * kNhid + k] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(w2p + umma_off(n, k, kNhid)) = __float2bfloat16_rn(v);
+    }
+    for (int e = threadIdx.x; e < kNhid; e += blockDim.x) b1[e] = B1[e];
+    for (int e = threadIdx.x; e < kN2; e += blockDim.x) b2[e] = e < kNout ? B2[e] : 0.f;
+}
+
+// --------------------------------------------------------------------------------
+// tcgen05 inference over independent one-cell problems (+ residual gate).
+// --------------------------------------------------------------------------------
+struct AnnArgs {
+    const unsigned char *w1p, *w2p;
+    const float *b1, *b2;
+    float tau;
+    unsigned long long *counter;   // [0] fallbacks, [1] timeouts
+};
+
+constexpr uint32_t kOffW1 = 0, kOffW2 = kOffW1 + kW1Bytes, kOffX = kOffW2 + kW2Bytes, kOffH = kOffX + kXBytes;
+constexpr uint32_t kOffB = kOffH + kHBytes;                   // b1[64], b2[16]
+constexpr uint32_t kOffStage = kOffB + 4 * (kNhid + kN2);      // [128][27] floats
+constexpr uint32_t kOffBar = kOffStage + 4 * kTile * 27;
+constexpr uint32_t kOffMisc = kOffBar + 8;                     // tmem slot, queue count, abort
+constexpr uint32_t kOffQueue = kOffMisc + 16;                  // [128] ints
+constexpr uint32_t kAnnSmem = kOffQueue + 4 * kTile;
+
+// Two FP32 values rounded to BF16 and packed, the first in the low half (lower address).
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&t);
+}
+
+// Write one row of a BF16 operand tile from FP32 values (kdim multiple of 8).
+template <int KDIM>
+__device__ __forceinline__ void write_row_bf16(unsigned char *base, int row, const float *v)
+{
+#pragma unroll
+    for (int kg = 0; kg < KDIM / 8; ++kg) {
+        uint4 u;
+        u.x = pack_bf16x2(v[kg * 8 + 0], v[kg * 8 + 1]);
+        u.y = pack_bf16x2(v[kg * 8 + 2], v[kg * 8 + 3]);
+        u.z = pack_bf16x2(v[kg * 8 + 4], v[kg * 8 + 5]);
+        u.w = pack_bf16x2(v[kg * 8 + 6], v[kg * 8 + 7]);
+        *reinterpret_cast<uint4 *>(base + umma_off(row, kg * 8, KDIM)) = u;
+    }
+}
+
+// Two-layer forward of the 128 rows staged in sX; each thread gets its row's 8 outputs.
+// Returns false if a wait timed out (then the CTA must stop).
+__device__ __forceinline__ bool mlp_tile(unsigned char *smem, uint32_t tbase, uint32_t &phase, float (&o)[8])
+{
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar = sbase + kOffBar;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kOffMisc + 8);
+    const float *sb1 = reinterpret_cast<const float *>(smem + kOffB), *sb2 = sb1 + kNhid;
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+        constexpr uint32_t id1 = idesc_bf16(128, kNhid);
+#pragma unroll
+        for (int kk = 0; kk < kK1 / 16; ++kk)
+            umma_bf16(tbase, sdesc(sbase + kOffX + kk * 256, 128, (kK1 / 8) * 128),
+                      sdesc(sbase + kOffW1 + kk * 256, 128, (kK1 / 8) * 128), id1, kk > 0);
+        umma_commit(bar);
+    }
+    if (!mbar_wait_bounded(bar, phase)) *abort_flag = 1;
+    phase ^= 1u;
+    __syncthreads();
+    if (*abort_flag) return false;
+    tc_fence_after();
+    __syncwarp();
+    const uint32_t lane_base = tbase + ((uint32_t)(threadIdx.x & ~31) << 16);
+    float hrow[kNhid];
+#pragma unroll
+    for (int c = 0; c < kNhid / 16; ++c) {
+        float v[16];
+        tmem_ld16(lane_base + 16 * c, v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) hrow[16 * c + u] = fmaxf(v[u] + sb1[16 * c + u], 0.f);
+    }
+    write_row_bf16<kNhid>(smem + kOffH, threadIdx.x, hrow);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+        constexpr uint32_t id2 = idesc_bf16(128, kN2);
+#pragma unroll
+        for (int kk = 0; kk < kNhid / 16; ++kk)
+            umma_bf16(tbase + kNhid, sdesc(sbase + kOffH + kk * 256, 128, (kNhid / 8) * 128),
+                      sdesc(sbase + kOffW2 + kk * 256, 128, (kNhid / 8) * 128), id2, kk > 0);
+        umma_commit(bar);
+    }
+    if (!mbar_wait_bounded(bar, phase)) *abort_flag = 1;
+    phase ^= 1u;
+    __syncthreads();
+    if (*abort_flag) return false;
+    tc_fence_after();
+    __syncwarp();
+    float v[16];
+    tmem_ld16(lane_base + kNhid, v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) o[q] = v[q] + sb2[q];
+    return true;
+}
+
+// Per-CTA set-up shared by the inference kernels: weights to shared memory, the
+// mbarrier, and 128 TMEM columns.
+__device__ __forceinline__ uint32_t ann_setup(unsigned char *smem, const AnnArgs &a)
+{
+    const uint4 *g1 = reinterpret_cast<const uint4 *>(a.w1p), *g2 = reinterpret_cast<const uint4 *>(a.w2p);
+    uint4 *s1 = reinterpret_cast<uint4 *>(smem + kOffW1), *s2 = reinterpret_cast<uint4 *>(smem + kOffW2);
+    for (int e = threadIdx.x; e < (int)(kW1Bytes / 16); e += blockDim.x) s1[e] = g1[e];
+    for (int e = threadIdx.x; e < (int)(kW2Bytes / 16); e += blockDim.x) s2[e] = g2[e];
+    float *sb = reinterpret_cast<float *>(smem + kOffB);
+    for (int e = threadIdx.x; e < kNhid; e += blockDim.x) sb[e] = a.b1[e];
+    for (int e = threadIdx.x; e < kN2; e += blockDim.x) sb[kNhid + e] = a.b2[e];
+    int *misc = reinterpret_cast<int *>(smem + kOffMisc);
+    if (threadIdx.x == 0) {
+        misc[1] = 0;   // queue count
+        misc[2] = 0;   // abort flag
+        mbar_init(smem_u32(smem + kOffBar), 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (threadIdx.x < 32) {
+        tmem_alloc(smem_u32(smem + kOffMisc), kTmemCols);
+        tmem_relinquish();
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *reinterpret_cast<volatile uint32_t *>(smem + kOffMisc);
+}
+
+__device__ __forceinline__ void ann_teardown(unsigned char *smem, uint32_t tbase, const AnnArgs &a)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0 && reinterpret_cast<volatile int *>(smem + kOffMisc)[2]) atomicAdd(a.counter + 1, 1ull);
+    __syncwarp();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, kTmemCols);
+}
+
+template <bool GATED>
+__global__ void __launch_bounds__(128, 4) ann_cells_kernel(const float *__restrict__ in27, float *__restrict__ out,
+                                                           int64_t n, AnnArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t tbase = ann_setup(smem, a);
+    float *stage = reinterpret_cast<float *>(smem + kOffStage);
+    int *misc = reinterpret_cast<int *>(smem + kOffMisc);
+    int *queue = reinterpret_cast<int *>(smem + kOffQueue);
+    uint32_t phase = 0;
+    unsigned long long nfb = 0;
+    for (int64_t base = (int64_t)blockIdx.x * kTile; base < n; base += (int64_t)gridDim.x * kTile) {
+        const int cnt = (int)(n - base < kTile ? n - base : kTile);
+        for (int e = threadIdx.x; e < cnt * 27; e += blockDim.x) stage[e] = in27[base * 27 + e];
+        __syncthreads();
+        const int t = threadIdx.x;
+        CanonCell<float> c;
+        float s = 0.f, x[kNin];
+        if (t < cnt) {
+            const float *p = stage + 27 * t;
+            canonicalize(p, c);
+            s = input_scale(c.S, c.ux, c.uy, c.uz);
+            ann_features(fabsf(p[0]), fabsf(p[1]), fabsf(p[2]), p[3], p[4], p[5], c.sig, c.S, c.ux, c.uy, c.uz,
+                         s > 0.f ? 1.f / s : 0.f, x);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kNin; ++k) x[k] = 0.f;
+        }
+        float xp[kK1];
+#pragma unroll
+        for (int k = 0; k < kK1; ++k) xp[k] = k < kNin ? x[k] : 0.f;
+        write_row_bf16<kK1>(smem + kOffX, t, xp);
+        float o[8];
+        if (!mlp_tile(smem, tbase, phase, o)) break;
+        float psi[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) psi[q] = s * o[q];
+        bool pass = true;
+        if (GATED && t < cnt && s > 0.f) pass = gate_pass(c, psi, a.tau);
+        if (t < cnt && pass) {
+            mirror8(psi, c.mask);
+            float *dst = out + (base + t) * 8;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[q] = psi[q];
+        }
+        if (GATED) {
+            if (t < cnt && !pass) queue[atomicAdd(&misc[1], 1)] = t;
+            __syncthreads();
+            const int nq = misc[1];
+            for (int q = t; q < nq; q += blockDim.x) {
+                const int row = queue[q];
+                float ge[8];
+                solve_in27<float, true>(stage + 27 * row, ge);
+                float *dst = out + (base + row) * 8;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) dst[k] = ge[k];
+            }
+            if (t == 0) nfb += (unsigned long long)nq;
+            __syncthreads();
+            if (t == 0) misc[1] = 0;
+        }
+        __syncthreads();
+    }
+    if (GATED && threadIdx.x == 0 && nfb) atomicAdd(a.counter, nfb);
+    ann_teardown(smem, tbase, a);
+}
+
+static sn_status pack_if_dirty(sn_handle h, cudaStream_t st)
+{
+    Net *n = net_of(h);
+    if (!n->dirty) return SN_OK;
+    pack_kernel<<<1, 256, 0, st>>>(n->p, n->w1p, n->w2p, n->b1, n->b2);
+    SN_CK(h, cudaGetLastError());
+    n->dirty = false;
+    return SN_OK;
+}
+
+static AnnArgs ann_args(sn_handle h)
+{
+    Net *n = net_of(h);
+    AnnArgs a;
+    a.w1p = n->w1p; a.w2p = n->w2p; a.b1 = n->b1; a.b2 = n->b2; a.tau = n->tau; a.counter = n->counter;
+    return a;
+}
+
+static sn_status need_net(sn_handle h, const char *who)
+{
+    if (!h) return fail(nullptr, SN_EINVAL, std::string(who) + ": NULL handle");
+    if (!h->has_net) return fail(h, SN_ESTATE, std::string(who) + ": no network (train, init or set weights first)");
+    return SN_OK;
+}
+
+static sn_status apply_cells(sn_handle h, const float *in27, float *psi, int64_t n, bool gated, int64_t *n_fallback,
+                             cudaStream_t st)
+{
+    Net *net = net_of(h);
+    sn_status s = pack_if_dirty(h, st);
+    if (s != SN_OK) return s;
+    SN_CK(h, cudaMemsetAsync(net->counter, 0, sizeof(unsigned long long) * 2, st));
+    if (n > 0) {
+        int64_t grid = (n + kTile - 1) / kTile;
+        const int64_t cap = (int64_t)num_sms() * 4;
+        if (grid > cap) grid = cap;
+        const AnnArgs a = ann_args(h);
+        if (gated) {
+            SN_CK(h, cudaFuncSetAttribute(ann_cells_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAnnSmem));
+            ann_cells_kernel<true><<<(unsigned)grid, kTile, kAnnSmem, st>>>(in27, psi, n, a);
+        } else {
+            SN_CK(h, cudaFuncSetAttribute(ann_cells_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAnnSmem));
+            ann_cells_kernel<false><<<(unsigned)grid, kTile, kAnnSmem, st>>>(in27, psi, n, a);
+        }
+        SN_CK(h, cudaGetLastError());
+    }
+    unsigned long long c[2] = {0, 0};
+    SN_CK(h, cudaMemcpyAsync(c, net->counter, sizeof(c), cudaMemcpyDeviceToHost, st));
+    SN_CK(h, cudaStreamSynchronize(st));
+    if (c[1]) return fail(h, SN_ETIMEOUT, "surrogate: a tensor-core completion wait timed out");
+    if (n_fallback) *n_fallback = (int64_t)c[0];
+    return SN_OK;
+}
+
+// Host-side uniform initialisation (SplitMix64 stream), +-1/sqrt(fan_in).
+static void init_params(std::vector<float> &p, uint64_t seed)
+{
+    uint64_t x = seed;
+    auto next = [&x]() {
+        uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    p.resize(kNparam);
+    const double a1 = 1.0 / std::sqrt((double)kNin), a2 = 1.0 / std::sqrt((double)kNhid);
+    int e = 0;
+    for (int i = 0; i < kNhid * kNin + kNhid; ++i) p[e++] = (float)((2.0 * next() - 1.0) * a1);
+    for (int i = 0; i < kNout * kNhid + kNout; ++i) p[e++] = (float)((2.0 * next() - 1.0) * a2);
+}
+
+static sn_status upload_params(sn_handle h, const float *host)
+{
+    sn_status s = ensure_net(h);
+    if (s != SN_OK) return s;
+    Net *n = net_of(h);
+    SN_CK(h, cudaMemcpy(n->p, host, sizeof(float) * kNparam, cudaMemcpyHostToDevice));
+    SN_CK(h, cudaMemset(n->m, 0, sizeof(float) * kNparam));
+    SN_CK(h, cudaMemset(n->v, 0, sizeof(float) * kNparam));
+    n->t = 0;
+    n->dirty = true;
+    h->has_net = true;
+    return SN_OK;
+}
+
+static sn_status ensure_gpart(sn_handle h, int64_t blocks)
+{
+    Net *n = net_of(h);
+    if (n->gpart_blocks >= blocks) return SN_OK;
+    if (n->gpart) cudaFree(n->gpart);
+    if (n->lpart) cudaFree(n->lpart);
+    n->gpart = nullptr;
+    n->lpart = nullptr;
+    n->gpart_blocks = 0;
+    SN_CK(h, cudaMalloc(&n->gpart, sizeof(float) * kNparam * blocks));
+    SN_CK(h, cudaMalloc(&n->lpart, sizeof(double) * blocks));
+    n->gpart_blocks = blocks;
+    return SN_OK;
+}
+
+// one gradient evaluation (and optionally one Adam step) on `batch` rows from row0
+static sn_status grad_step(sn_handle h, const float *feat, const float *targ, int64_t nrows, int64_t row0, int batch,
+                           float lr, bool step, float *gout, cudaStream_t st)
+{
+    Net *n = net_of(h);
+    const int nblk = (batch + 127) / 128;
+    sn_status s = ensure_gpart(h, nblk);
+    if (s != SN_OK) return s;
+    SN_CK(h, cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem));
+    grad_kernel<<<nblk, 128, kGradSmem, st>>>(n->p, feat, targ, nrows, row0, batch, 1.f / (float)batch, n->gpart,
+                                              n->lpart);
+    float bc1 = 1.f, bc2 = 1.f;
+    if (step) {
+        n->t += 1;
+        bc1 = (float)(1.0 - std::pow(0.9, (double)n->t));
+        bc2 = (float)(1.0 - std::pow(0.999, (double)n->t));
+        n->dirty = true;
+    }
+    adam_kernel<<<(kNparam + 255) / 256, 256, 0, st>>>(n->p, n->m, n->v, n->gpart, nblk, lr, bc1, bc2, gout,
+                                                       step ? 1 : 0);
+    sum_kernel<<<1, 32, 0, st>>>(n->lpart, nblk, n->dacc);
+    SN_CK(h, cudaGetLastError());
+    return SN_OK;
+}
+
+static sn_status mean_abs_err(sn_handle h, const float *feat, const float *targ, int64_t n, double *mae,
+                              cudaStream_t st)
+{
+    Net *net = net_of(h);
+    SN_CK(h, cudaMemsetAsync(net->dacc + 1, 0, sizeof(double), st));
+    if (n > 0) {
+        int64_t grid = (n + 127) / 128;
+        if (grid > (int64_t)num_sms() * 8) grid = (int64_t)num_sms() * 8;
+        mae_kernel<<<(unsigned)grid, 128, 0, st>>>(net->p, feat, targ, n, net->dacc + 1);
+        SN_CK(h, cudaGetLastError());
+    }
+    double v = 0.0;
+    SN_CK(h, cudaMemcpyAsync(&v, net->dacc + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SN_CK(h, cudaStreamSynchronize(st));
+    *mae = n > 0 ? v / (8.0 * (double)n) : 0.0;
+    return SN_OK;
+}
+
+static sn_status launch_prepare(sn_handle h, const float *in27, int64_t n, float *feat, float *targ, cudaStream_t st)
+{
+    if (n <= 0) return SN_OK;
+    int64_t grid = (n + 127) / 128;
+    if (grid > (int64_t)num_sms() * 16) grid = (int64_t)num_sms() * 16;
+    prepare_kernel<<<(unsigned)grid, 128, 0, st>>>(in27, n, feat, targ);
+    SN_CK(h, cudaGetLastError());
+    return SN_OK;
+}
+
+static sn_status fit_loop(sn_handle h, const float *feat, const float *targ, int64_t nrows, int steps, int batch,
+                          float lr, double *last_loss, cudaStream_t st)
+{
+    Net *n = net_of(h);
+    for (int k = 0; k < steps; ++k) {
+        const int64_t row0 = ((int64_t)k * batch) % nrows;
+        sn_status s = grad_step(h, feat, targ, nrows, row0, batch, lr, true, nullptr, st);
+        if (s != SN_OK) return s;
+    }
+    if (last_loss) {
+        SN_CK(h, cudaMemcpyAsync(last_loss, n->dacc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    SN_CK(h, cudaStreamSynchronize(st));
+    return SN_OK;
 }
 
 }  // namespace sn
@@ -17,8 +785,121 @@ using namespace sn;
 
 extern "C" {
 
-sn_status sn_cell_solve_batch(sn_handle h, const float *in27, float *psi, int64_t n, sn_solve_mode mode,
-                              void *stream)
+sn_status sn_surrogate_prepare(const float *in27, int64_t n, float *feat, float *targ, void *stream)
+{
+    if (n < 0) return fail(nullptr, SN_EINVAL, "sn_surrogate_prepare: n < 0");
+    if (n > 0 && (!in27 || !feat || !targ)) return fail(nullptr, SN_EINVAL, "sn_surrogate_prepare: NULL pointer");
+    return launch_prepare(nullptr, in27, n, feat, targ, (cudaStream_t)stream);
+}
+
+sn_status sn_surrogate_init(sn_handle h, uint64_t seed)
+{
+    if (!h) return fail(nullptr, SN_EINVAL, "sn_surrogate_init: NULL handle");
+    std::vector<float> p;
+    init_params(p, seed);
+    return upload_params(h, p.data());
+}
+
+sn_status sn_surrogate_set_weights(sn_handle h, const float *params)
+{
+    if (!h || !params) return fail(h, SN_EINVAL, "sn_surrogate_set_weights: NULL argument");
+    for (int i = 0; i < kNparam; ++i)
+        if (!std::isfinite(params[i])) return fail(h, SN_EINVAL, "sn_surrogate_set_weights: non-finite weight");
+    return upload_params(h, params);
+}
+
+sn_status sn_surrogate_get_weights(sn_handle h, float *params)
+{
+    sn_status s = need_net(h, "sn_surrogate_get_weights");
+    if (s != SN_OK) return s;
+    if (!params) return fail(h, SN_EINVAL, "sn_surrogate_get_weights: NULL argument");
+    SN_CK(h, cudaMemcpy(params, net_of(h)->p, sizeof(float) * kNparam, cudaMemcpyDeviceToHost));
+    return SN_OK;
+}
+
+sn_status sn_surrogate_set_gate(sn_handle h, float tau)
+{
+    if (!h) return fail(nullptr, SN_EINVAL, "sn_surrogate_set_gate: NULL handle");
+    if (!(tau >= 0.f) || !std::isfinite(tau)) return fail(h, SN_EINVAL, "sn_surrogate_set_gate: tau must be >= 0");
+    sn_status s = ensure_net(h);
+    if (s != SN_OK) return s;
+    net_of(h)->tau = tau;
+    return SN_OK;
+}
+
+sn_status sn_surrogate_grad(sn_handle h, const float *feat, const float *targ, int64_t n, float *grad,
+                            double *loss)
+{
+    sn_status s = need_net(h, "sn_surrogate_grad");
+    if (s != SN_OK) return s;
+    if (n < 1 || n > (1 << 24) || !feat || !targ || !grad) return fail(h, SN_EINVAL, "sn_surrogate_grad: bad argument");
+    Net *net = net_of(h);
+    float *dg = nullptr;
+    SN_CK(h, cudaMalloc(&dg, sizeof(float) * kNparam));
+    s = grad_step(h, feat, targ, n, 0, (int)n, 0.f, false, dg, h->stream);
+    if (s == SN_OK) {
+        cudaError_t e = cudaMemcpyAsync(grad, dg, sizeof(float) * kNparam, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, net->dacc, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) s = cuda_fail(h, e, "sn_surrogate_grad");
+    }
+    cudaFree(dg);
+    return s;
+}
+
+sn_status sn_surrogate_fit(sn_handle h, const float *feat, const float *targ, int64_t nrows, int32_t steps,
+                           int32_t batch, float lr, double *last_loss)
+{
+    sn_status s = need_net(h, "sn_surrogate_fit");
+    if (s != SN_OK) return s;
+    if (nrows < 1 || steps < 0 || batch < 1 || batch > (1 << 22) || !(lr >= 0.f) || !feat || !targ)
+        return fail(h, SN_EINVAL, "sn_surrogate_fit: bad argument");
+    return fit_loop(h, feat, targ, nrows, steps, batch, lr, last_loss, h->stream);
+}
+
+sn_status sn_surrogate_eval(sn_handle h, const float *feat, const float *targ, int64_t n, double *mae)
+{
+    sn_status s = need_net(h, "sn_surrogate_eval");
+    if (s != SN_OK) return s;
+    if (n < 0 || !mae || (n > 0 && (!feat || !targ))) return fail(h, SN_EINVAL, "sn_surrogate_eval: bad argument");
+    return mean_abs_err(h, feat, targ, n, mae, h->stream);
+}
+
+sn_status sn_surrogate_train(sn_handle h, const float *in27, int64_t n, int64_t n_test, int32_t steps, int32_t batch,
+                             float lr, uint64_t seed, double *train_mae, double *test_mae)
+{
+    if (!h) return fail(nullptr, SN_EINVAL, "sn_surrogate_train: NULL handle");
+    if (n < 2 || n_test < 1 || n_test >= n || !in27 || steps < 0 || batch < 1 || batch > (1 << 22) || !(lr > 0.f))
+        return fail(h, SN_EINVAL, "sn_surrogate_train: bad argument");
+    const cudaStream_t st = h->stream;
+    float *feat = nullptr, *targ = nullptr;
+    SN_CK(h, cudaMalloc(&feat, sizeof(float) * kNin * n));
+    cudaError_t e = cudaMalloc(&targ, sizeof(float) * 8 * n);
+    if (e != cudaSuccess) {
+        cudaFree(feat);
+        return cuda_fail(h, e, "cudaMalloc");
+    }
+    sn_status s = launch_prepare(h, in27, n, feat, targ, st);
+    if (s == SN_OK) s = sn_surrogate_init(h, seed);
+    const int64_t ntr = n - n_test;
+    if (s == SN_OK) s = fit_loop(h, feat, targ, ntr, steps, batch, lr, nullptr, st);
+    if (s == SN_OK && train_mae) s = mean_abs_err(h, feat, targ, ntr, train_mae, st);
+    if (s == SN_OK && test_mae) s = mean_abs_err(h, feat + kNin * ntr, targ + 8 * ntr, n_test, test_mae, st);
+    cudaStreamSynchronize(st);
+    cudaFree(feat);
+    cudaFree(targ);
+    return s;
+}
+
+sn_status sn_surrogate_apply(sn_handle h, const float *in27, float *psi, int64_t n, int32_t gated, int64_t *n_fallback)
+{
+    sn_status s = need_net(h, "sn_surrogate_apply");
+    if (s != SN_OK) return s;
+    if (n < 0 || (n > 0 && (!in27 || !psi))) return fail(h, SN_EINVAL, "sn_surrogate_apply: bad argument");
+    return apply_cells(h, in27, psi, n, gated != 0, n_fallback, h->stream);
+}
+
+sn_status sn_cell_solve_batch(sn_handle h, const float *in27, float *psi, int64_t n, sn_solve_mode mode, void *stream)
 {
     if (n < 0) return fail(h, SN_EINVAL, "sn_cell_solve_batch: n < 0");
     if (mode == SN_SOLVE_GE32R || mode == SN_SOLVE_GE32) {
@@ -29,8 +910,10 @@ sn_status sn_cell_solve_batch(sn_handle h, const float *in27, float *psi, int64_
         return s;
     }
     if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
-        if (!h || !h->has_net) return fail(h, SN_ESTATE, "sn_cell_solve_batch: no surrogate network");
-        return fail(h, SN_ESTATE, "sn_cell_solve_batch: surrogate not available");
+        sn_status s = need_net(h, "sn_cell_solve_batch");
+        if (s != SN_OK) return s;
+        if (n > 0 && (!in27 || !psi)) return fail(h, SN_EINVAL, "sn_cell_solve_batch: NULL pointer");
+        return apply_cells(h, in27, psi, n, mode == SN_SOLVE_ANN_GATED, nullptr, (cudaStream_t)stream);
     }
     return fail(h, SN_EINVAL, "sn_cell_solve_batch: unknown mode");
 }

@@ -2,37 +2,10 @@
 // Sec. 3; the per-cell system (14) of Sec. 2), one thread per problem.
 #include <cmath>
 
-#include "ge8.cuh"
+#include "cell_problem.cuh"
 #include "sn_internal.cuh"
 
 namespace sn {
-
-// Physical one-cell problem (27 values) -> canonical inputs, solve, physical output.
-template <typename T, bool REFINE>
-__device__ __forceinline__ void solve_in27(const T *p, T (&psi)[8])
-{
-    const int fx = p[0] < T(0), fy = p[1] < T(0), fz = p[2] < T(0);
-    const int mask = fx | (fy << 1) | (fz << 2);
-    const T t3x = T(3) * fabs(p[0]) / p[3];
-    const T t3y = T(3) * fabs(p[1]) / p[4];
-    const T t3z = T(3) * fabs(p[2]) / p[5];
-    const T sig = p[6];
-    T S[8], ux[4], uy[4], uz[4];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) S[k] = p[7 + k];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        ux[t] = p[15 + t];
-        uy[t] = p[19 + t];
-        uz[t] = p[23 + t];
-    }
-    mirror8(S, mask);
-    mirror4(ux, fy | (fz << 1));    // x-face in-face index b + 2c
-    mirror4(uy, fx | (fz << 1));    // y-face a + 2c
-    mirror4(uz, fx | (fy << 1));    // z-face a + 2b
-    cell_solve_canonical<T, REFINE>(t3x, t3y, t3z, sig, S, ux, uy, uz, psi);
-    mirror8(psi, mask);
-}
 
 // The 27 inputs of a block's problems are staged through shared memory so that the
 // global loads are coalesced.

@@ -70,6 +70,20 @@ _API = [
     ("sn_get_balance", ctypes.c_int, [ctypes.c_void_p, _dp]),
     ("sn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("sn_get_profile", ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("sn_surrogate_prepare", ctypes.c_int, [_fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
+    ("sn_surrogate_init", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("sn_surrogate_set_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("sn_surrogate_get_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("sn_surrogate_set_gate", ctypes.c_int, [ctypes.c_void_p, ctypes.c_float]),
+    ("sn_surrogate_grad", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_float), _dp]),
+    ("sn_surrogate_fit", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_float, _dp]),
+    ("sn_surrogate_eval", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, _dp]),
+    ("sn_surrogate_train", ctypes.c_int, [ctypes.c_void_p, _fp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _dp, _dp]),
+    ("sn_surrogate_apply", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int64)]),
     ("sn_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sn_destroy", None, [ctypes.c_void_p]),
@@ -140,6 +154,24 @@ def cell_solve_batch_f64(in27, out=None):
                                        n, _stream())
     _check(st)
     return out
+
+
+NPARAM = 2312
+
+
+def surrogate_prepare(in27):
+    """(features [N, 27], targets [N, 8]) of one-cell problems, targets labelled by
+    the library's FP32 elimination (canonical frame, divided by the input scale)."""
+    n = in27.shape[0]
+    feat = torch.empty((n, 27), dtype=torch.float32, device=in27.device)
+    targ = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+    _check(lib().sn_surrogate_prepare(_dev(in27, torch.float32, (27,)), n, _dev(feat, torch.float32, (27,)),
+                                      _dev(targ, torch.float32, (8,)), _stream()))
+    return feat, targ
+
+
+def _f32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
 class Problem:
@@ -246,3 +278,66 @@ class Problem:
         t = np.zeros(4)
         _check(lib().sn_get_balance(self.h, _dptr(t)), self.h)
         return t
+
+    # ---- surrogate network (Sec. 3) ----
+    def surrogate_init(self, seed=0):
+        self._sync_stream()
+        _check(lib().sn_surrogate_init(self.h, int(seed)), self.h)
+
+    def surrogate_set_weights(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == NPARAM
+        self._sync_stream()
+        _check(lib().sn_surrogate_set_weights(self.h, _f32p(p)), self.h)
+
+    def surrogate_weights(self):
+        p = np.zeros(NPARAM, dtype=np.float32)
+        _check(lib().sn_surrogate_get_weights(self.h, _f32p(p)), self.h)
+        return p
+
+    def surrogate_set_gate(self, tau):
+        _check(lib().sn_surrogate_set_gate(self.h, float(tau)), self.h)
+
+    def surrogate_grad(self, feat, targ):
+        """(loss, gradient [2312]) of Eq. (19) at the current weights over all rows."""
+        self._sync_stream()
+        g = np.zeros(NPARAM, dtype=np.float32)
+        loss = ctypes.c_double(0)
+        _check(lib().sn_surrogate_grad(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
+                                       feat.shape[0], _f32p(g), ctypes.byref(loss)), self.h)
+        return loss.value, g
+
+    def surrogate_fit(self, feat, targ, steps, batch, lr):
+        self._sync_stream()
+        loss = ctypes.c_double(0)
+        _check(lib().sn_surrogate_fit(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
+                                      feat.shape[0], int(steps), int(batch), float(lr), ctypes.byref(loss)), self.h)
+        return loss.value
+
+    def surrogate_eval(self, feat, targ):
+        self._sync_stream()
+        mae = ctypes.c_double(0)
+        _check(lib().sn_surrogate_eval(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
+                                       feat.shape[0], ctypes.byref(mae)), self.h)
+        return mae.value
+
+    def surrogate_train(self, in27, n_test, steps, batch, lr, seed=0):
+        """Label in27 with elimination, initialise, train with Adam; (train MAE, test MAE)."""
+        self._sync_stream()
+        a = ctypes.c_double(0)
+        b = ctypes.c_double(0)
+        _check(lib().sn_surrogate_train(self.h, _dev(in27, torch.float32, (27,)), in27.shape[0], int(n_test),
+                                        int(steps), int(batch), float(lr), int(seed), ctypes.byref(a),
+                                        ctypes.byref(b)), self.h)
+        return a.value, b.value
+
+    def surrogate_apply(self, in27, gated=True, out=None):
+        """psi [N, 8] from the tensor-core network; returns (psi, number of gate fallbacks)."""
+        self._sync_stream()
+        n = in27.shape[0]
+        if out is None:
+            out = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+        nfb = ctypes.c_int64(0)
+        _check(lib().sn_surrogate_apply(self.h, _dev(in27, torch.float32, (27,)), _dev(out, torch.float32, (8,)),
+                                        n, 1 if gated else 0, ctypes.byref(nfb)), self.h)
+        return out, nfb.value

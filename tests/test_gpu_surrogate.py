@@ -1,0 +1,154 @@
+"""GPU parity of the surrogate network (Sec. 3, Eq. (15); Sec. 4, Eq. (19), Adam)
+against the FP64 oracle (oracle.mlp), through the C ABI: input construction and
+elimination labels, the back-propagated gradient, Adam steps, and the tcgen05
+BF16 inference with and without the residual gate."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp
+from paper_1906_04017_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    """Round FP32 values to BF16 (nearest, ties to even) and back, as the tensor cores see them."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def predict_bf16(p, in27):
+    """The oracle's network evaluated with the rounding steps of the BF16 path:
+    inputs, weights and hidden activations rounded to BF16, FP64 sums, FP32 biases."""
+    W1, b1, W2, b2 = mlp.unpack(np.asarray(p, dtype=np.float32).astype(np.float64))
+    x, s, mask = mlp.features(in27)
+    x = bf16(x.astype(np.float32))
+    h = np.maximum(x @ bf16(W1).T + b1, 0.0)
+    h = bf16(h.astype(np.float32))
+    o = h @ bf16(W2).T + b2
+    k = np.arange(8)
+    return np.take_along_axis(o * s[:, None], k[None, :] ^ mask[:, None], 1)
+
+
+@pytest.fixture(scope="module")
+def handle(sn):
+    wl = W.random_small(2, 2, 2, order=2, G=1)
+    P = sn.Problem(wl)
+    yield P
+    P.close()
+
+
+def cuda(a, dt=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dt).cuda()
+
+
+def test_prepare_matches_oracle(sn):
+    x = W.onecell_problems(50001, seed=21).astype(np.float32).astype(np.float64)
+    feat, targ = sn.surrogate_prepare(cuda(x))
+    f_ref, s, _ = mlp.features(x)
+    t_ref = mlp.targets(oracle.cell_solve(x), x)
+    assert np.abs(feat.cpu().numpy() - f_ref).max() < 2e-6
+    t = targ.cpu().numpy()
+    scale = np.maximum(np.abs(t_ref).max(axis=1), 1e-30)
+    assert (np.abs(t - t_ref).max(axis=1) / scale).max() < 1e-5
+
+
+def test_no_network_is_a_state_error(sn):
+    wl = W.random_small(2, 2, 2, order=2, G=1)
+    P = sn.Problem(wl)
+    with pytest.raises(sn.SnError) as e:
+        P.surrogate_apply(cuda(W.onecell_problems(4)))
+    P.close()
+    assert e.value.status == sn.SN_ESTATE
+
+
+def clean_batch(n, seed, p):
+    """Rows whose residuals and pre-activations stay away from the kinks of |.| and
+    ReLU, so FP32 and FP64 agree on every sign in the sub-gradient."""
+    x = W.onecell_problems(4 * n, seed=seed)
+    f, _, _ = mlp.features(x)
+    t = mlp.targets(oracle.cell_solve(x), x)
+    f = f.astype(np.float32).astype(np.float64)
+    t = t.astype(np.float32).astype(np.float64)
+    o, a, _ = mlp.forward(p, f)
+    d = t - o
+    ok = (np.abs(a).min(1) > 1e-4) & (np.abs(d).min(1) > 1e-4) & (np.abs(d.sum(1)) > 1e-4)
+    return f[ok][:n], t[ok][:n]
+
+
+def test_gradient_matches_oracle(handle):
+    p = mlp.init_params(3).astype(np.float32).astype(np.float64)
+    f, t = clean_batch(3000, 5, p)
+    handle.surrogate_set_weights(p)
+    loss, g = handle.surrogate_grad(cuda(f), cuda(t))
+    L, gref = mlp.loss_grad(p, f, t)
+    assert abs(loss - L) < 1e-5 * L
+    assert np.abs(g - gref).max() < 2e-5 * np.abs(gref).max()
+
+
+def test_adam_steps_match_oracle(handle):
+    p = mlp.init_params(4).astype(np.float32).astype(np.float64)
+    f, t = clean_batch(2048, 9, p)
+    handle.surrogate_set_weights(p)
+    handle.surrogate_fit(cuda(f), cuda(t), steps=3, batch=512, lr=1e-3)
+    got = handle.surrogate_weights().astype(np.float64)
+    ref = mlp.train(p, f, t, steps=3, batch=512, lr=1e-3)
+    # Adam's early steps move each weight by about lr * sign(gradient): compare the
+    # weights whose gradient is not vanishingly small (a sign decided by round-off
+    # there is not a defect)
+    _, g0 = mlp.loss_grad(p, f[:512], t[:512])
+    sel = np.abs(g0) > 1e-3 * np.abs(g0).max()
+    assert sel.mean() > 0.8
+    assert np.abs(got - ref)[sel].max() < 2e-6
+
+
+def test_tensor_core_inference(handle):
+    x = W.onecell_problems(100003, seed=31)
+    x[:7, 7:27] = 0.0                          # zero input scale: psi = 0
+    x32 = x.astype(np.float32)
+    xd = x32.astype(np.float64)
+    p = mlp.init_params(6)
+    handle.surrogate_set_weights(p)
+    psi, nfb = handle.surrogate_apply(cuda(x32), gated=False)
+    psi = psi.cpu().numpy().astype(np.float64)
+    assert nfb == 0
+    assert np.all(psi[:7] == 0.0)
+    ref = predict_bf16(p, xd)
+    err = (np.abs(psi[7:] - ref[7:]) / np.abs(ref).max(axis=1)[7:, None]).max(axis=1)
+    # the FP32 inputs and hidden sums can land on the other side of a BF16 rounding
+    # boundary than the FP64 emulation (one BF16 ulp, 2^-8 relative, in one value):
+    # nearly every row agrees to accumulation round-off, none by more than such flips
+    assert np.percentile(err, 99.0) < 1e-4
+    assert err.max() < 3e-2
+    # and against the exact FP64 network: the BF16 rounding bound
+    exact = mlp.predict(np.asarray(p, dtype=np.float32).astype(np.float64), xd)
+    assert (np.abs(psi[7:] - exact[7:]) / np.abs(exact).max(axis=1)[7:, None]).max() < 5e-2
+
+
+@pytest.mark.parametrize("n", [1, 128, 1000])
+def test_gate_extremes(sn, handle, n):
+    """tau = 0 rejects every prediction, so the result is the elimination's; a huge
+    tau accepts every one, so the result is the network's."""
+    x = cuda(W.onecell_problems(n, seed=n).astype(np.float32))
+    handle.surrogate_set_weights(mlp.init_params(7))
+    handle.surrogate_set_gate(0.0)
+    psi, nfb = handle.surrogate_apply(x, gated=True)
+    ge = sn.cell_solve_batch(x, sn.GE32R)
+    assert nfb == n
+    assert torch.allclose(psi, ge, rtol=1e-6, atol=1e-7)
+    handle.surrogate_set_gate(1e30)
+    psi2, nfb2 = handle.surrogate_apply(x, gated=True)
+    psi3, _ = handle.surrogate_apply(x, gated=False)
+    assert nfb2 == 0 and torch.equal(psi2, psi3)
+    handle.surrogate_set_gate(1e-2)
+
+
+def test_training_reduces_error(handle):
+    x = cuda(W.onecell_problems(1 << 16, seed=41).astype(np.float32))
+    tr, te = handle.surrogate_train(x, n_test=4096, steps=0, batch=4096, lr=1e-3, seed=1)
+    tr2, te2 = handle.surrogate_train(x, n_test=4096, steps=600, batch=4096, lr=2e-3, seed=1)
+    assert tr2 < 0.5 * tr and te2 < 0.5 * te

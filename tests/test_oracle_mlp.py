@@ -1,0 +1,111 @@
+"""Pins of the surrogate-network oracle (Sec. 3, Eq. (15); Sec. 4, Eq. (19) and
+the Adam optimiser): finite differences for the back-propagated gradient,
+hand-computed loss values, Adam's closed-form first step, and the mirror
+symmetry that lets one network serve every octant, checked against the
+oracle's own physical-frame elimination."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1906_04017_gb300 import workloads as W
+
+
+def smooth_batch(seed, n=6):
+    """Random parameters and data with every residual and pre-activation away from
+    the kinks of |.| and ReLU, so that central differences are exact to O(h^2)."""
+    rng = np.random.default_rng(seed)
+    for _ in range(1000):
+        p = mlp.init_params(seed) * 2.0
+        x = rng.uniform(-1, 1, (n, mlp.NIN))
+        t = rng.uniform(-1, 1, (n, mlp.NOUT))
+        o, a, _ = mlp.forward(p, x)
+        d = t - o
+        if np.abs(a).min() > 1e-3 and np.abs(d).min() > 1e-3 and np.abs(d.sum(1)).min() > 1e-3:
+            return p, x, t
+        seed += 1000
+    raise RuntimeError("no smooth batch")
+
+
+def test_gradient_matches_central_differences():
+    p, x, t = smooth_batch(3)
+    L, g = mlp.loss_grad(p, x, t)
+    assert np.isclose(L, mlp.loss(p, x, t), rtol=1e-14)
+    h = 1e-7
+    fd = np.empty_like(p)
+    for i in range(p.size):
+        e = np.zeros_like(p)
+        e[i] = h
+        fd[i] = (mlp.loss(p + e, x, t) - mlp.loss(p - e, x, t)) / (2 * h)
+    assert np.allclose(g, fd, rtol=1e-5, atol=1e-9)
+
+
+def test_loss_hand_values():
+    """One sample, zero network (all outputs = b2 = 0): the loss is the mean |t| plus
+    lambda |sum t| / (gamma_1 |sum t| + gamma_2)."""
+    p = np.zeros(mlp.NPARAM)
+    x = np.zeros((1, mlp.NIN))
+    t = np.array([[1.0, -1.0, 0, 0, 0, 0, 0, 0]])
+    assert mlp.loss(p, x, t) == pytest.approx(0.25)
+    t = np.full((1, 8), 0.5)
+    assert mlp.loss(p, x, t) == pytest.approx(0.5 + 0.2 * 4.0 / (10 * 4.0 + 0.01))
+    # a perfect fit has zero loss
+    W1, b1, W2, b2 = mlp.unpack(p)
+    b2 = t[0].copy()
+    assert mlp.loss(mlp.pack(W1, b1, W2, b2), x, t) == 0.0
+
+
+def test_adam_first_step_closed_form():
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    opt = mlp.Adam(4, lr=0.01)
+    p1 = opt.step(np.zeros(4), g)
+    assert np.allclose(p1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+def test_canonical_frame_commutes_with_elimination():
+    """Mirroring a one-cell problem into the positive octant and solving it there
+    gives the mirrored solution of the original problem (the DFEM system is
+    symmetric under axis reflection)."""
+    x = W.onecell_problems(3000, seed=11)
+    psi = oracle.cell_solve(x)
+    aom, h, sig, S, U, mask = mlp.canonical(x)
+    xc = np.concatenate([aom, h, sig[:, None], S, U], 1)
+    psic = oracle.cell_solve(xc)
+    _, s, _ = mlp.features(x)
+    assert np.allclose(mlp.targets(psi, x) * s[:, None], psic, rtol=1e-10, atol=1e-12)
+
+
+def test_predict_is_octant_symmetric():
+    p = mlp.init_params(5)
+    x = W.onecell_problems(500, seed=2)
+    x[:, 0:3] = np.abs(x[:, 0:3])
+    out = mlp.predict(p, x)
+    # flip Omega_x: reverse the node order along x in S, swap in-face order of y, z faces
+    y = x.copy()
+    y[:, 0] *= -1
+    k = np.arange(8)
+    y[:, 7:15] = x[:, 7:15][:, k ^ 1]
+    t = np.arange(4)
+    y[:, 19:23] = x[:, 19:23][:, t ^ 1]
+    y[:, 23:27] = x[:, 23:27][:, t ^ 1]
+    out2 = mlp.predict(p, y)
+    assert np.allclose(out2, out[:, k ^ 1], rtol=1e-12, atol=1e-14)
+
+
+def test_features_ranges_and_zero_scale():
+    x = W.onecell_problems(2000, seed=4)
+    x[:5, 7:27] = 0.0
+    f, s, _ = mlp.features(x)
+    assert np.all(s[:5] == 0) and np.all(f[:5, 7:] == 0)
+    assert np.all(np.abs(f[:, 0:3]) <= 1.0)
+    assert np.all((f[5:, 7:] >= 0) & (f[5:, 7:] <= 1.0))
+    assert np.allclose(f[5:, 7:].max(axis=1), 1.0, rtol=1e-15)
+
+
+def test_training_reduces_loss():
+    x = W.onecell_problems(4096, seed=7)
+    f, s, _ = mlp.features(x)
+    t = mlp.targets(oracle.cell_solve(x), x)
+    p0 = mlp.init_params(0)
+    p1 = mlp.train(p0, f, t, steps=300, batch=256, lr=2e-3)
+    assert mlp.loss(p1, f, t) < 0.5 * mlp.loss(p0, f, t)
