@@ -131,6 +131,16 @@ __device__ __forceinline__ void apply_A(T t3x, T t3y, T t3z, T sig, const T (&x)
     }
 }
 
+// Reciprocal of a pivot: the PTX approximate reciprocal (max error 1 ulp) in FP32
+// -- the refinement step absorbs it -- and the IEEE quotient in FP64.
+__device__ __forceinline__ float pivot_recip(float v)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double pivot_recip(double v) { return 1.0 / v; }
+
 // Gaussian elimination with partial pivoting on A (8x8, registers), right-hand side
 // b.  Pivot = entry of largest magnitude in the column (ties: the lowest row).
 // Row exchanges move the trailing columns and b only; each multiplier stays where
@@ -165,7 +175,7 @@ __device__ __forceinline__ void ge8_factor_solve(T (&A)[8][8], T (&b)[8], unsign
                 }
             }
         }
-        rinv[k] = T(1) / A[k][k];
+        rinv[k] = pivot_recip(A[k][k]);
 #pragma unroll
         for (int r = k + 1; r < 8; ++r) {
             const T l = A[r][k] * rinv[k];
@@ -175,7 +185,7 @@ __device__ __forceinline__ void ge8_factor_solve(T (&A)[8][8], T (&b)[8], unsign
             b[r] = fma(-l, b[k], b[r]);
         }
     }
-    rinv[7] = T(1) / A[7][7];
+    rinv[7] = pivot_recip(A[7][7]);
 #pragma unroll
     for (int r = 7; r >= 0; --r) {
         T s = b[r];

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(128) grad_kernel(const float *__restrict__ P, 
             mae += fabsf(d[q]);
         }
         const float den = kGamma1 * fabsf(st) + kGamma2;
-        lsum = (double)(mae / 8.f + kLambda * fabsf(sd) / den);
+        lsum = (double)((mae / 8.f + kLambda * fabsf(sd) / den) * inv_batch);
         float go[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {

@@ -20,6 +20,27 @@ struct DirData {
     T t3x, t3y, t3z, w;
 };
 
+// Division of 32-bit unsigned n < 2^31 by a run-time constant d >= 1 with a multiply
+// and a shift (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994): q = (umulhi(n, m) + n) >> s, s = ceil(log2 d),
+// m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+    uint32_t d = 1, m = 1, s = 0;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t dv) : d(dv)
+    {
+        s = 0;
+        while ((1ull << s) < dv) ++s;
+        m = (uint32_t)(((1ull << 32) * ((1ull << s) - dv)) / dv + 1);
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ uint32_t div(uint32_t n) const
+    {
+        return (uint32_t)(((uint64_t)__umulhi(n, m) + n) >> s);
+    }
+#endif
+};
+
 struct Graphs {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // ping-pong parity
     const void *phi_user = nullptr;                 // buffer the graphs were captured for
