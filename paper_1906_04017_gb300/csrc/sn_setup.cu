@@ -282,6 +282,10 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
             delete h;
             return fail(nullptr, SN_EINVAL, "sn_setup: negative cross section");
         }
+    if ((int64_t)G * C * 8 >= (1LL << 31)) {
+        delete h;
+        return fail(nullptr, SN_EINVAL, "sn_setup: ngroups * cells * 8 must stay below 2^31");
+    }
     if (h->Do > 256) {
         delete h;
         return fail(nullptr, SN_EINVAL, "sn_setup: at most 256 directions per octant");

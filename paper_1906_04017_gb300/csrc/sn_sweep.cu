@@ -61,7 +61,8 @@ __device__ __forceinline__ void store4(Vec4<T> *p, T a, T b, T c, T d)
 template <typename T>
 struct SweepArgs {
     int nx, ny, nz, G, Do, ncells_plane, keys_per_cta;
-    int64_t C;
+    int C;                   // cells (G * C * 8 < 2^31 is checked at set-up)
+    FastDiv divG;            // key -> (cell index, group)
     const uint32_t *cells;   // packed (i',j',k') of the cells of this hyperplane
     const T *sigt;           // [G][C]
     const T *S;              // [G][C][8]
@@ -73,37 +74,36 @@ struct SweepArgs {
     T vol12;                 // V / 12
 };
 
+// grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
+// rounded up to whole warps.
 template <typename T, bool REFINE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(SweepArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char red_raw[];
     T *red = reinterpret_cast<T *>(red_raw);   // [blockDim.x][9]
     const int Do = a.Do;
-    const int lk = threadIdx.x / Do;
-    const int d = threadIdx.x - lk * Do;
-    const int64_t key = (int64_t)blockIdx.x * a.keys_per_cta + lk;
-    const int64_t nkeys = 8LL * a.ncells_plane * a.G;
-    // the block is rounded up to whole warps; threads past keys_per_cta * Do idle
-    const bool active = lk < a.keys_per_cta && key < nkeys;
-    int o = 0, g = 0;
-    int64_t c = 0;
+    const int o = blockIdx.y;                  // octant: sign bits of Omega
+    const int lk = (int)threadIdx.x / Do;
+    const int d = (int)threadIdx.x - lk * Do;
+    const uint32_t key = blockIdx.x * (uint32_t)a.keys_per_cta + (uint32_t)lk;
+    // threads past keys_per_cta * Do (warp rounding) or past the last key idle
+    const bool active = lk < a.keys_per_cta && key < (uint32_t)a.ncells_plane * (uint32_t)a.G;
+    int g = 0, c = 0;
     T leak = T(0);
     if (active) {
-        g = (int)(key % a.G);
-        const int64_t t = key / a.G;
-        const int cidx = (int)(t % a.ncells_plane);
-        o = (int)(t / a.ncells_plane);
+        const uint32_t cidx = a.divG.div(key);
+        g = (int)(key - cidx * (uint32_t)a.G);
         const uint32_t pk = a.cells[cidx];
         const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
         const int i = (o & 1) ? a.nx - 1 - ip : ip;
         const int j = (o & 2) ? a.ny - 1 - jp : jp;
         const int k = (o & 4) ? a.nz - 1 - kp : kp;
-        c = i + (int64_t)a.nx * (j + (int64_t)a.ny * k);
+        c = i + a.nx * (j + a.ny * k);
         const DirData<T> dd = a.dir[d];
-        const int64_t GD = (int64_t)a.G * Do, gd = (int64_t)g * Do + d;
-        const int64_t ix = ((int64_t)o * a.ny * a.nz + jp + (int64_t)a.ny * kp) * GD + gd;
-        const int64_t iy = ((int64_t)o * a.nx * a.nz + ip + (int64_t)a.nx * kp) * GD + gd;
-        const int64_t iz = ((int64_t)o * a.nx * a.ny + ip + (int64_t)a.nx * jp) * GD + gd;
+        const int GD = a.G * Do, gd = g * Do + d;
+        const int64_t ix = (int64_t)(o * a.ny * a.nz + jp + a.ny * kp) * GD + gd;
+        const int64_t iy = (int64_t)(o * a.nx * a.nz + ip + a.nx * kp) * GD + gd;
+        const int64_t iz = (int64_t)(o * a.nx * a.ny + ip + a.nx * jp) * GD + gd;
         T ux[4], uy[4], uz[4];
         if (ip == 0) {
             const T v = a.psi_inc[6 * g + (o & 1)];
@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(Sw
         } else {
             load4(uz, a.fz + iz);
         }
-        const T sig = a.sigt[(int64_t)g * a.C + c];
-        const Vec4<T> *Sp = reinterpret_cast<const Vec4<T> *>(a.S + ((int64_t)g * a.C + c) * 8);
+        const int gc = g * a.C + c;
+        const T sig = a.sigt[gc];
+        const Vec4<T> *Sp = reinterpret_cast<const Vec4<T> *>(a.S + (int64_t)gc * 8);
         T S[8], s0[4], s1[4];
         load4(s0, Sp);
         load4(s1, Sp + 1);
@@ -141,10 +142,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(Sw
         if (kp < a.nz - 1) store4(a.fz + iz, x[4], x[5], x[6], x[7]);
         else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
         leak *= dd.w * a.vol12;
-        mirror8(x, o);
+        // w_d psi in physical node order: canonical node n lands on physical n ^ o
         T *r = red + threadIdx.x * 9;
 #pragma unroll
-        for (int n = 0; n < 8; ++n) r[n] = dd.w * x[n];
+        for (int n = 0; n < 8; ++n) r[n ^ o] = dd.w * x[n];
     }
     __syncthreads();
     if (active) {
@@ -166,7 +167,8 @@ template <typename T>
 static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine, cudaStream_t st)
 {
     SweepArgs<T> a;
-    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = h->ncell;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
+    a.divG = FastDiv((uint32_t)h->G);
     a.keys_per_cta = 256 / h->Do;
     a.sigt = (const T *)h->sigt; a.S = S; a.psi_inc = (const T *)h->psi_inc;
     a.dir = (const DirData<T> *)h->dir;
@@ -183,12 +185,12 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
         const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
         a.cells = h->plane_cells + h->plane_off[s];
         a.ncells_plane = (int)n;
-        const int64_t nkeys = 8 * n * h->G;
-        const int64_t grid = (nkeys + a.keys_per_cta - 1) / a.keys_per_cta;
+        const int64_t nkeys = n * h->G;
+        const dim3 grid((unsigned)((nkeys + a.keys_per_cta - 1) / a.keys_per_cta), 8);
         if (refine)
-            sweep_plane_ge<T, true><<<(unsigned)grid, block, smem, st>>>(a);
+            sweep_plane_ge<T, true><<<grid, block, smem, st>>>(a);
         else
-            sweep_plane_ge<T, false><<<(unsigned)grid, block, smem, st>>>(a);
+            sweep_plane_ge<T, false><<<grid, block, smem, st>>>(a);
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {
@@ -228,55 +230,61 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v)
     atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
 }
 
+// One thread per (g, c, node): octant sum in the element type (fixed order), per-
+// element quantities in the element type, FP64 only for the running sums and the
+// block / grid accumulation (the FP64 rate of the part is low).
 template <typename T>
 __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_oct, const T *__restrict__ phi_old,
                                                      T *__restrict__ phi_new, const T *__restrict__ S,
-                                                     const T *__restrict__ sigt, int64_t C, int G, double vol8,
-                                                     double *acc, int norms)
+                                                     const T *__restrict__ sigt, int C, int G, FastDiv divC,
+                                                     double vol8, double *acc, int norms)
 {
     __shared__ double sh[8][6];
-    const int64_t total = (int64_t)G * C * 8;
-    double coll = 0, src = 0, dmax = 0, pmax = 0, mean = 0, cnt = 0;
+    const int total = G * C * 8;
+    const int stride_oct = C * G * 8;
+    double coll = 0, src = 0, mean = 0, cnt = 0;
+    T dmax = T(0), pmax = T(0);
     int bad = 0;
     // grid-stride over whole warps so that the 8 nodes of a (g, c) stay in one warp
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x % 32 < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e - (int)(threadIdx.x % 32) < total;
+         e += gridDim.x * blockDim.x) {
         const bool in = e < total;
         T nv = T(0), ov = T(0);
         if (in) {
-            const int n = (int)(e & 7);
-            const int64_t gc = e >> 3;
-            const int64_t c = gc % C;
-            const int g = (int)(gc / C);
-            double s = 0.0;
+            const int n = e & 7;
+            const uint32_t gc = (uint32_t)e >> 3;
+            const uint32_t g = divC.div(gc);
+            const int c = (int)(gc - g * (uint32_t)C);
+            const T *po = phi_oct + ((int64_t)c * G + g) * 8 + n;
+            T s = T(0);
 #pragma unroll
-            for (int o = 0; o < 8; ++o) s += (double)phi_oct[(((int64_t)o * C + c) * G + g) * 8 + n];
-            nv = (T)s;
+            for (int o = 0; o < 8; ++o) s += po[(int64_t)o * stride_oct];
+            nv = s;
             phi_new[e] = nv;
-            if (!isfinite((double)nv)) bad = 1;
-            coll += (double)sigt[(int64_t)g * C + c] * vol8 * (double)nv;
-            src += 4.0 * kPi * vol8 * (double)S[e];
+            if (!isfinite(nv)) bad = 1;
+            coll += (double)(sigt[gc] * nv);
+            src += (double)S[e];
             if (norms) {
                 ov = phi_old[e];
-                dmax = fmax(dmax, fabs((double)nv - (double)ov));
-                pmax = fmax(pmax, fabs((double)nv));
+                dmax = fmax(dmax, fabs(nv - ov));
+                pmax = fmax(pmax, fabs(nv));
             }
         }
         if (norms) {
-            double a = (double)nv, b = (double)ov;
+            T a = nv, b = ov;
 #pragma unroll
             for (int off = 1; off < 8; off <<= 1) {
                 a += __shfl_xor_sync(0xffffffffu, a, off);
                 b += __shfl_xor_sync(0xffffffffu, b, off);
             }
-            if (in && (e & 7) == 0 && a != 0.0) {
-                mean += fabs(a - b) / fabs(a);
+            if (in && (e & 7) == 0 && a != T(0)) {
+                mean += (double)(fabs(a - b) / fabs(a));
                 cnt += 1.0;
             }
         }
     }
     // block reduction
-    double v[6] = {coll, src, dmax, pmax, mean, cnt};
+    double v[6] = {coll * vol8, src * 4.0 * kPi * vol8, (double)dmax, (double)pmax, mean, cnt};
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
@@ -325,14 +333,15 @@ sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const v
     const int64_t cap = (int64_t)num_sms() * 8;
     if (grid > cap) grid = cap;
     const double vol8 = h->dx * h->dy * h->dz / 8.0;
+    const FastDiv divC((uint32_t)h->ncell);
     if (h->fp64)
         reduce_kernel<double><<<(unsigned)grid, 256, 0, st>>>(
             (const double *)h->phi_oct, (const double *)phi_old, (double *)phi_new, (const double *)S,
-            (const double *)h->sigt, h->ncell, h->G, vol8, h->acc, norms ? 1 : 0);
+            (const double *)h->sigt, (int)h->ncell, h->G, divC, vol8, h->acc, norms ? 1 : 0);
     else
         reduce_kernel<float><<<(unsigned)grid, 256, 0, st>>>(
             (const float *)h->phi_oct, (const float *)phi_old, (float *)phi_new, (const float *)S,
-            (const float *)h->sigt, h->ncell, h->G, vol8, h->acc, norms ? 1 : 0);
+            (const float *)h->sigt, (int)h->ncell, h->G, divC, vol8, h->acc, norms ? 1 : 0);
     SN_CK(h, cudaGetLastError());
     return SN_OK;
 }
