@@ -226,6 +226,12 @@ sn_status sn_surrogate_train(sn_handle h, const float *in27, int64_t n, int64_t 
 sn_status sn_surrogate_apply(sn_handle h, const float *in27, float *psi, int64_t n, int32_t gated,
                              int64_t *n_fallback);
 
+/* Surrogate counters of the last sweep (sn_sweep) or of the last iteration of
+ * sn_source_iterate in an ANN mode, or of the last sn_surrogate_apply: cells sent
+ * back to elimination by the gate, and CTAs that gave up a bounded tensor-core
+ * wait (non-zero means the results of that call are invalid). */
+sn_status sn_surrogate_stats(sn_handle h, int64_t *fallbacks, int64_t *timeouts);
+
 /* CUDA-event timing of the sweep kernels.  With profiling on, every directly
  * launched sweep (sn_sweep, or sn_source_iterate with use_graph = 0) records an
  * event before its first hyperplane kernel and after its last one on the

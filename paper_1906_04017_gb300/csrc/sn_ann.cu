@@ -23,6 +23,7 @@
 
 #include "cell_problem.cuh"
 #include "sn_internal.cuh"
+#include "sweep_common.cuh"
 
 #include <cuda_bf16.h>
 
@@ -609,6 +610,175 @@ __global__ void __launch_bounds__(128, 4) ann_cells_kernel(const float *__restri
     ann_teardown(smem, tbase, a);
 }
 
+// --------------------------------------------------------------------------------
+// Surrogate sweep: one hyperplane of every octant, the per-cell elimination of the
+// wavefront replaced by the network (Sec. 4: "construction of the input vector and a
+// feed-forward evaluation"), with the residual gate and an in-CTA compacted
+// elimination pass for the cells that fail it.  Same keys, face planes and flux
+// reduction as sweep_plane_ge; a tile is one CTA of 128 threads = keys_per_tile keys x
+// Do directions (rows past that are idle MMA rows).
+// --------------------------------------------------------------------------------
+struct AnnSweepArgs {
+    int nx, ny, nz, G, Do, ncells_plane, keys_per_tile, ntiles;   // tiles per octant
+    int C;
+    FastDiv divG;
+    const uint32_t *cells;
+    const float *sigt, *S, *psi_inc;
+    const DirData<float> *dir;
+    const float4 *dir_abs;
+    Vec4<float> *fx, *fy, *fz;
+    float *phi_oct;
+    double *leak;
+    float vol12, hx, hy, hz;
+    AnnArgs ann;
+};
+
+constexpr uint32_t kOffRed = kAnnSmem;                      // [128][9] floats
+constexpr uint32_t kSweepSmem = kOffRed + 4 * kTile * 9;
+constexpr int kCanon = 24;                                  // floats of a stored canonical cell
+
+template <bool GATED>
+__global__ void __launch_bounds__(128, 4) sweep_plane_ann(AnnSweepArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t tbase = ann_setup(smem, a.ann);
+    float *canon = reinterpret_cast<float *>(smem + kOffStage);    // [128][24], failing rows
+    float *red = reinterpret_cast<float *>(smem + kOffRed);
+    int *misc = reinterpret_cast<int *>(smem + kOffMisc);
+    int *queue = reinterpret_cast<int *>(smem + kOffQueue);
+    const int o = blockIdx.y, t = threadIdx.x, Do = a.Do;
+    const int lk = t / Do, d = t - lk * Do;
+    const bool lane_used = lk < a.keys_per_tile;
+    DirData<float> dd = {0.f, 0.f, 0.f, 0.f};
+    float4 dab = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane_used) {
+        dd = a.dir[d];
+        dab = a.dir_abs[d];
+    }
+    const float lhx = (logf(a.hx) + kLogHShift) / kLogHScale;
+    const float lhy = (logf(a.hy) + kLogHShift) / kLogHScale;
+    const float lhz = (logf(a.hz) + kLogHShift) / kLogHScale;
+    const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
+    uint32_t phase = 0;
+    unsigned long long nfb = 0;
+    float leak = 0.f;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const uint32_t key = (uint32_t)tile * (uint32_t)a.keys_per_tile + (uint32_t)lk;
+        const bool active = lane_used && key < nkeys;
+        CanonCell<float> c;
+        float s = 0.f, xp[kK1];
+#pragma unroll
+        for (int k = 0; k < kK1; ++k) xp[k] = 0.f;
+        int g = 0, cell = 0, ip = 0, jp = 0, kp = 0;
+        int64_t ix = 0, iy = 0, iz = 0;
+        if (active) {
+            const uint32_t cidx = a.divG.div(key);
+            g = (int)(key - cidx * (uint32_t)a.G);
+            const uint32_t pk = a.cells[cidx];
+            ip = pk & 1023; jp = (pk >> 10) & 1023; kp = pk >> 20;
+            const int i = (o & 1) ? a.nx - 1 - ip : ip;
+            const int j = (o & 2) ? a.ny - 1 - jp : jp;
+            const int k = (o & 4) ? a.nz - 1 - kp : kp;
+            cell = i + a.nx * (j + a.ny * k);
+            const int GD = a.G * Do, gd = g * Do + d;
+            ix = (int64_t)(o * a.ny * a.nz + jp + a.ny * kp) * GD + gd;
+            iy = (int64_t)(o * a.nx * a.nz + ip + a.nx * kp) * GD + gd;
+            iz = (int64_t)(o * a.nx * a.ny + ip + a.nx * jp) * GD + gd;
+            if (ip == 0) { const float v = a.psi_inc[6 * g + (o & 1)]; c.ux[0] = c.ux[1] = c.ux[2] = c.ux[3] = v; }
+            else load4(c.ux, a.fx + ix);
+            if (jp == 0) { const float v = a.psi_inc[6 * g + 2 + ((o >> 1) & 1)]; c.uy[0] = c.uy[1] = c.uy[2] = c.uy[3] = v; }
+            else load4(c.uy, a.fy + iy);
+            if (kp == 0) { const float v = a.psi_inc[6 * g + 4 + ((o >> 2) & 1)]; c.uz[0] = c.uz[1] = c.uz[2] = c.uz[3] = v; }
+            else load4(c.uz, a.fz + iz);
+            const int gc = g * a.C + cell;
+            c.sig = a.sigt[gc];
+            const Vec4<float> *Sp = reinterpret_cast<const Vec4<float> *>(a.S + (int64_t)gc * 8);
+            float s0[4], s1[4];
+            load4(s0, Sp);
+            load4(s1, Sp + 1);
+#pragma unroll
+            for (int n = 0; n < 4; ++n) { c.S[n] = s0[n]; c.S[4 + n] = s1[n]; }
+            mirror8(c.S, o);
+            c.t3x = dd.t3x; c.t3y = dd.t3y; c.t3z = dd.t3z;
+            c.mask = o;
+            s = input_scale(c.S, c.ux, c.uy, c.uz);
+            float x[kNin];
+            ann_features(dab.x, dab.y, dab.z, a.hx, a.hy, a.hz, c.sig, c.S, c.ux, c.uy, c.uz,
+                         s > 0.f ? 1.f / s : 0.f, x);
+            x[3] = lhx; x[4] = lhy; x[5] = lhz;
+#pragma unroll
+            for (int k = 0; k < kNin; ++k) xp[k] = x[k];
+        }
+        write_row_bf16<kK1>(smem + kOffX, t, xp);
+        float out[8];
+        if (!mlp_tile(smem, tbase, phase, out)) break;
+        float psi[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) psi[q] = s * out[q];
+        if (GATED) {
+            const bool pass = !active || s == 0.f || gate_pass(c, psi, a.ann.tau);
+            float *cr = canon + t * kCanon;
+            if (!pass) {
+                queue[atomicAdd(&misc[1], 1)] = t;
+                cr[0] = c.t3x; cr[1] = c.t3y; cr[2] = c.t3z; cr[3] = c.sig;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) cr[4 + k] = c.S[k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { cr[12 + q] = c.ux[q]; cr[16 + q] = c.uy[q]; cr[20 + q] = c.uz[q]; }
+            }
+            __syncthreads();
+            const int nq = misc[1];
+            for (int qi = t; qi < nq; qi += blockDim.x) {
+                float *r = canon + queue[qi] * kCanon;
+                float S2[8], u1[4], u2[4], u3[4], xs[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) S2[k] = r[4 + k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { u1[q] = r[12 + q]; u2[q] = r[16 + q]; u3[q] = r[20 + q]; }
+                cell_solve_canonical<float, true>(r[0], r[1], r[2], r[3], S2, u1, u2, u3, xs);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) r[k] = xs[k];
+            }
+            __syncthreads();
+            if (!pass) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) psi[k] = cr[k];
+            }
+            if (t == 0) {
+                nfb += (unsigned long long)nq;
+                misc[1] = 0;
+            }
+        }
+        if (active) {
+            if (ip < a.nx - 1) store4(a.fx + ix, psi[1], psi[3], psi[5], psi[7]);
+            else leak += dd.w * a.vol12 * dd.t3x * (psi[1] + psi[3] + psi[5] + psi[7]);
+            if (jp < a.ny - 1) store4(a.fy + iy, psi[2], psi[3], psi[6], psi[7]);
+            else leak += dd.w * a.vol12 * dd.t3y * (psi[2] + psi[3] + psi[6] + psi[7]);
+            if (kp < a.nz - 1) store4(a.fz + iz, psi[4], psi[5], psi[6], psi[7]);
+            else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
+            float *rr = red + t * 9;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) rr[n ^ o] = dd.w * psi[n];
+        }
+        __syncthreads();
+        if (active) {
+            float *dst = a.phi_oct + (((int64_t)o * a.C + cell) * a.G + g) * 8;
+            const float *base = red + (lk * Do) * 9;
+            for (int n = d; n < 8; n += Do) {
+                float sum = 0.f;
+                for (int q = 0; q < Do; ++q) sum += base[q * 9 + n];
+                dst[n] = sum;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
+    if ((threadIdx.x & 31) == 0 && leak != 0.f) atomicAdd(a.leak, (double)leak);
+    if (GATED && threadIdx.x == 0 && nfb) atomicAdd(a.ann.counter, nfb);
+    ann_teardown(smem, tbase, a.ann);
+}
+
 static sn_status pack_if_dirty(sn_handle h, cudaStream_t st)
 {
     Net *n = net_of(h);
@@ -625,6 +795,67 @@ static AnnArgs ann_args(sn_handle h)
     AnnArgs a;
     a.w1p = n->w1p; a.w2p = n->w2p; a.b1 = n->b1; a.b2 = n->b2; a.tau = n->tau; a.counter = n->counter;
     return a;
+}
+
+// After a synchronised surrogate sweep: SN_ETIMEOUT if any CTA gave up a wait.
+sn_status check_ann_timeouts(sn_handle h)
+{
+    if (!h->net) return SN_OK;
+    unsigned long long c[2] = {0, 0};
+    SN_CK(h, cudaMemcpy(c, net_of(h)->counter, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c[1]) return fail(h, SN_ETIMEOUT, "surrogate sweep: a tensor-core completion wait timed out");
+    return SN_OK;
+}
+
+sn_status reset_ann_counters(sn_handle h, cudaStream_t st)
+{
+    if (!h->net) return SN_OK;
+    SN_CK(h, cudaMemsetAsync(net_of(h)->counter, 0, sizeof(unsigned long long) * 2, st));
+    return SN_OK;
+}
+
+sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gated, cudaStream_t st)
+{
+    sn_status s = pack_if_dirty(h, st);
+    if (s != SN_OK) return s;
+    AnnSweepArgs a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
+    a.divG = FastDiv((uint32_t)h->G);
+    a.keys_per_tile = kTile / h->Do;
+    a.sigt = (const float *)h->sigt; a.S = S; a.psi_inc = (const float *)h->psi_inc;
+    a.dir = (const DirData<float> *)h->dir;
+    a.dir_abs = h->dir_abs;
+    a.fx = (Vec4<float> *)h->face;
+    a.fy = a.fx + h->face_x;
+    a.fz = a.fy + h->face_y;
+    a.phi_oct = phi_oct;
+    a.leak = h->acc + ACC_LEAK;
+    a.vol12 = (float)(h->dx * h->dy * h->dz / 12.0);
+    a.hx = (float)h->dx; a.hy = (float)h->dy; a.hz = (float)h->dz;
+    a.ann = ann_args(h);
+    if (gated)
+        SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
+    else
+        SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
+    const int cap = num_sms() * 4 / 8;     // persistent CTAs per octant: 4 per SM in total
+    if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
+    for (int p = 0; p < h->nplanes; ++p) {
+        const int64_t n = h->plane_off[p + 1] - h->plane_off[p];
+        a.cells = h->plane_cells + h->plane_off[p];
+        a.ncells_plane = (int)n;
+        a.ntiles = (int)((n * h->G + a.keys_per_tile - 1) / a.keys_per_tile);
+        const dim3 grid((unsigned)(a.ntiles < cap ? a.ntiles : cap), 8);
+        if (gated)
+            sweep_plane_ann<true><<<grid, kTile, kSweepSmem, st>>>(a);
+        else
+            sweep_plane_ann<false><<<grid, kTile, kSweepSmem, st>>>(a);
+    }
+    SN_CK(h, cudaGetLastError());
+    if (h->prof) {
+        SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));
+        h->prof_pending = true;
+    }
+    return SN_OK;
 }
 
 static sn_status need_net(sn_handle h, const char *who)
@@ -897,6 +1128,18 @@ sn_status sn_surrogate_apply(sn_handle h, const float *in27, float *psi, int64_t
     if (s != SN_OK) return s;
     if (n < 0 || (n > 0 && (!in27 || !psi))) return fail(h, SN_EINVAL, "sn_surrogate_apply: bad argument");
     return apply_cells(h, in27, psi, n, gated != 0, n_fallback, h->stream);
+}
+
+sn_status sn_surrogate_stats(sn_handle h, int64_t *fallbacks, int64_t *timeouts)
+{
+    sn_status s = need_net(h, "sn_surrogate_stats");
+    if (s != SN_OK) return s;
+    unsigned long long c[2] = {0, 0};
+    SN_CK(h, cudaMemcpyAsync(c, net_of(h)->counter, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    SN_CK(h, cudaStreamSynchronize(h->stream));
+    if (fallbacks) *fallbacks = (int64_t)c[0];
+    if (timeouts) *timeouts = (int64_t)c[1];
+    return SN_OK;
 }
 
 sn_status sn_cell_solve_batch(sn_handle h, const float *in27, float *psi, int64_t n, sn_solve_mode mode, void *stream)

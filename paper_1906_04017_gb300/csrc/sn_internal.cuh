@@ -72,6 +72,7 @@ struct sn_handle_s {
     void *xfer = nullptr;        // T[G][G]
     void *psi_inc = nullptr;     // T[G][6]
     void *dir = nullptr;         // DirData<T>[Do]
+    float4 *dir_abs = nullptr;   // [Do] (|Omega_x|, |Omega_y|, |Omega_z|, 0) for the surrogate inputs
     uint32_t *plane_cells = nullptr;  // packed (i',j',k') of every cell, grouped by hyperplane
     void *face = nullptr;        // face planes: 4-vectors of T, see sn_sweep.cu
     int64_t face_x = 0, face_y = 0, face_z = 0;  // 4-vector count of each plane set
@@ -124,6 +125,11 @@ sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const v
                         cudaStream_t st);
 sn_status launch_source(sn_handle h, const void *phi, void *S, cudaStream_t st);
 sn_status launch_cells_f32(const float *in27, float *psi, int64_t n, bool refine, cudaStream_t st);
+// surrogate sweep (sn_ann.cu): every hyperplane of one sweep, FP32 handles only
+sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gated, cudaStream_t st);
+// zero the surrogate's fallback / timeout counters (stream-ordered)
+sn_status reset_ann_counters(sn_handle h, cudaStream_t st);
+sn_status check_ann_timeouts(sn_handle h);
 int num_sms();
 
 // accumulator slots in h->acc

@@ -166,7 +166,7 @@ static void release(sn_handle h)
     if (!h) return;
     for (int i = 0; i < 2; ++i)
         if (h->graphs.exec[i]) cudaGraphExecDestroy(h->graphs.exec[i]);
-    void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->plane_cells,
+    void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->dir_abs, h->plane_cells,
                     h->face, h->phi_oct, h->S, h->phi_b, h->acc};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -330,6 +330,15 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
 
     // direction table (first octant; the others are its mirror images)
     SN_TRY(h->fp64 ? upload_dirs<double>(h) : upload_dirs<float>(h));
+    {
+        std::vector<float4> da(h->Do);
+        for (int d = 0; d < h->Do; ++d)
+            da[d] = make_float4((float)std::fabs(h->omega[3 * d]), (float)std::fabs(h->omega[3 * d + 1]),
+                                (float)std::fabs(h->omega[3 * d + 2]), 0.f);
+        SN_TRY(dalloc_bytes(h, (void **)&h->dir_abs, sizeof(float4) * h->Do));
+        cudaError_t e = cudaMemcpy(h->dir_abs, da.data(), sizeof(float4) * h->Do, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(dir_abs)"));
+    }
 
     // boundary inflow of one sweep: sum over faces, groups and inflowing directions
     // of w_d |Omega.n| psi_inc * area

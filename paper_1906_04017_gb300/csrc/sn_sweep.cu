@@ -26,37 +26,9 @@
 
 #include "ge8.cuh"
 #include "sn_internal.cuh"
+#include "sweep_common.cuh"
 
 namespace sn {
-
-template <typename T>
-struct Vec4 {
-    T v[4];
-};
-
-template <typename T>
-__device__ __forceinline__ void load4(T (&u)[4], const Vec4<T> *p)
-{
-    if constexpr (sizeof(T) == 4) {
-        const float4 f = *reinterpret_cast<const float4 *>(p);
-        u[0] = f.x; u[1] = f.y; u[2] = f.z; u[3] = f.w;
-    } else {
-        const double2 a = reinterpret_cast<const double2 *>(p)[0];
-        const double2 b = reinterpret_cast<const double2 *>(p)[1];
-        u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void store4(Vec4<T> *p, T a, T b, T c, T d)
-{
-    if constexpr (sizeof(T) == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
-    } else {
-        reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
-        reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
-    }
-}
 
 template <typename T>
 struct SweepArgs {
@@ -203,6 +175,8 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
 sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st)
 {
     if (h->fp64) return launch_sweep_t<double>(h, (const double *)S, (double *)phi_oct, false, st);
+    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED)
+        return launch_sweep_ann(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_ANN_GATED, st);
     return launch_sweep_t<float>(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R, st);
 }
 
@@ -438,6 +412,10 @@ static sn_status sweep_once(sn_handle h, const void *S, void *phi_out, const voi
                             cudaStream_t st)
 {
     SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
+    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
+        sn_status r = reset_ann_counters(h, st);
+        if (r != SN_OK) return r;
+    }
     sn_status s = launch_sweep(h, S, h->phi_oct, mode, st);
     if (s != SN_OK) return s;
     return launch_reduce(h, phi_old, phi_out, S, phi_old != nullptr, st);
@@ -470,6 +448,7 @@ sn_status sn_sweep(sn_handle h, const void *S, void *phi, sn_solve_mode mode)
     SN_CK(h, cudaStreamSynchronize(st));
     prof_collect(h);
     take_tallies(h);
+    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) return check_ann_timeouts(h);
     return SN_OK;
 }
 
@@ -536,6 +515,10 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
         cmax = a[ACC_PMAX] > 0 ? a[ACC_DMAX] / a[ACC_PMAX] : 0.0;
         cmean = a[ACC_MEANN] > 0 ? a[ACC_MEAN] / a[ACC_MEANN] : 0.0;
         take_tallies(h);
+        if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
+            s = check_ann_timeouts(h);
+            if (s != SN_OK) return s;
+        }
         if (a[ACC_FLAG] != 0.0) {
             rc = fail(h, SN_ENAN, "sn_source_iterate: non-finite scalar flux");
             ++it;

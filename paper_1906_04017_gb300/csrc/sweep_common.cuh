@@ -1,0 +1,38 @@
+// sweep_common.cuh -- 4-vector face-plane access shared by the elimination and the
+// surrogate sweep kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sn {
+
+template <typename T>
+struct Vec4 {
+    T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ void load4(T (&u)[4], const Vec4<T> *p)
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 f = *reinterpret_cast<const float4 *>(p);
+        u[0] = f.x; u[1] = f.y; u[2] = f.z; u[3] = f.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(Vec4<T> *p, T a, T b, T c, T d)
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+    }
+}
+
+}  // namespace sn

@@ -84,6 +84,8 @@ _API = [
                                           ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _dp, _dp]),
     ("sn_surrogate_apply", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int64)]),
+    ("sn_surrogate_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]),
     ("sn_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sn_destroy", None, [ctypes.c_void_p]),
@@ -341,3 +343,10 @@ class Problem:
         _check(lib().sn_surrogate_apply(self.h, _dev(in27, torch.float32, (27,)), _dev(out, torch.float32, (8,)),
                                         n, 1 if gated else 0, ctypes.byref(nfb)), self.h)
         return out, nfb.value
+
+    def surrogate_stats(self):
+        """(fallbacks, timeouts) of the last surrogate sweep / iteration / apply."""
+        a = ctypes.c_int64(0)
+        b = ctypes.c_int64(0)
+        _check(lib().sn_surrogate_stats(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
+        return a.value, b.value
