@@ -56,6 +56,8 @@ def _declare(L):
     L.or_source_iterate.argtypes = [P, ctypes.c_double, ctypes.c_int, _dp,
                                     ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
     L.or_num_threads.argtypes = []
+    L.or_adjoint.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp,
+                             ctypes.POINTER(ctypes.c_int)]
 
 
 def _p(a):
@@ -200,3 +202,17 @@ class OracleProblem:
             raise ZeroDivisionError("zero pivot")
         return dict(phi=phi, iters=it.value, change_max=cmax.value, change_mean=cmean.value,
                     tallies=tal, converged=(rc == 0))
+
+    def adjoint(self, phi, resp, tol=1e-13, maxit=2000):
+        """Discrete adjoint of R = resp . phi at the converged forward flux phi:
+        dict(Lam [G,ncell,8] = sum_d lambda_d, grad_sigt, grad_sigs, grad_q [G,ncell], iters)."""
+        phi = _f64(phi).reshape(self.G, self.ncell, 8)
+        resp = _f64(resp).reshape(self.G, self.ncell, 8)
+        Lam = np.zeros((self.G, self.ncell, 8))
+        gt = np.zeros((self.G, self.ncell)); gs = np.zeros((self.G, self.ncell)); gq = np.zeros((self.G, self.ncell))
+        it = ctypes.c_int(0)
+        rc = lib().or_adjoint(ctypes.byref(self.c), _p(phi), _p(resp), tol, maxit, _p(Lam), _p(gt), _p(gs), _p(gq),
+                              ctypes.byref(it))
+        if rc < 0:
+            raise ZeroDivisionError("zero pivot")
+        return dict(Lam=Lam, grad_sigt=gt, grad_sigs=gs, grad_q=gq, iters=it.value, converged=(rc == 0))

@@ -542,3 +542,203 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ======================================================================== */
+/* Discrete adjoint (not in the paper; the gradient of a detector response  */
+/* with respect to sigma_t, sigma_s and q).  With L the upwind sweep        */
+/* operator of every (direction, group), Phi psi = phi (Eq. (9)), B phi the  */
+/* scattering source M (1/4pi) sum_g' xfer[g'][g] sigs_g' phi_g' and Q the   */
+/* external source, the converged fluxes satisfy (L - B Phi) psi = Q and the */
+/* response is R = r^T phi.  The adjoint lambda solves                       */
+/*   (L - B Phi)^T lambda = Phi^T r,                                          */
+/* by source iteration: lambda_dg = L_dg^{-T} (w_d x_g),                     */
+/* x = r + B^T lambda, and                                                    */
+/*   dR/dsigma_t[g,c] = -sum_d lambda_dgc^T M_c psi_dgc                       */
+/*   dR/dsigma_s[g',c] = (1/4pi) sum_g xfer[g'][g] Lam_gc^T M_c phi_g'c       */
+/*   dR/dq[g,c]        = (1/4pi) Lam_gc^T M_c 1,   Lam_g = sum_d lambda_dg.  */
+/* ======================================================================== */
+
+/* L_dg^T lam = rhs for one direction and group: the transposed block system is */
+/* upper triangular in the upwind order, so cells are visited downwind first,   */
+/* each solving A_c^T lam_c = rhs_c + (transposed face coupling from the        */
+/* downstream neighbours).                                                      */
+static int adjoint_sweep_dir(const or_problem *p, const or_elem *e, int d, int g, const double *rhs, double *lam)
+{
+    const double *om = p->omega + 3 * d;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const long nc = ncell_of(p);
+    int fin[3], fout[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        fin[ax] = 2 * ax + (om[ax] >= 0.0 ? 0 : 1);
+        fout[ax] = 2 * ax + (om[ax] >= 0.0 ? 1 : 0);
+    }
+    const double S0[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const double up0[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int kk = nz - 1; kk >= 0; --kk) {
+        int k = om[2] >= 0.0 ? kk : nz - 1 - kk;
+        for (int jj = ny - 1; jj >= 0; --jj) {
+            int j = om[1] >= 0.0 ? jj : ny - 1 - jj;
+            for (int ii = nx - 1; ii >= 0; --ii) {
+                int i = om[0] >= 0.0 ? ii : nx - 1 - ii;
+                long c = i + (long)nx * (j + (long)ny * k);
+                double b[8];
+                for (int n = 0; n < 8; ++n) b[n] = rhs[8 * c + n];
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (om[ax] == 0.0) continue;
+                    int idx[3] = {i, j, k}, n3[3] = {nx, ny, nz};
+                    int di = idx[ax] + (om[ax] >= 0.0 ? 1 : -1);
+                    if (di < 0 || di >= n3[ax]) continue;
+                    int nb[3] = {i, j, k};
+                    nb[ax] = di;
+                    long cd = nb[0] + (long)nx * (nb[1] + (long)ny * nb[2]);
+                    /* forward: row (cd, kr) gets |Om_a| F_fin[kr][face_node(fin,t)] * psi_c[face_node(fout,t)] */
+                    for (int t = 0; t < 4; ++t) {
+                        double s = 0.0;
+                        for (int kr = 0; kr < 8; ++kr)
+                            s += e->F[fin[ax] * 64 + kr * 8 + face_node(fin[ax], t)] * lam[8 * cd + kr];
+                        b[face_node(fout[ax], t)] += fabs(om[ax]) * s;
+                    }
+                }
+                double A[64], AT[64], bb[8], x[8];
+                assemble(e, om, p->sigt[(long)g * nc + c], S0, up0, A, bb);
+                for (int r = 0; r < 8; ++r)
+                    for (int q = 0; q < 8; ++q) AT[r * 8 + q] = A[q * 8 + r];
+                if (or_ge(8, AT, b, x) != 0) return -1;
+                for (int n = 0; n < 8; ++n) lam[8 * c + n] = x[n];
+            }
+        }
+    }
+    return 0;
+}
+
+/* (M v) for the cell mass matrix */
+static void mass_apply(const or_elem *e, const double *v, double *out)
+{
+    for (int k = 0; k < 8; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < 8; ++j) s += e->M[k * 8 + j] * v[j];
+        out[k] = s;
+    }
+}
+
+/* Adjoint source iteration and gradients.  phi: converged forward flux
+   [G][C][8]; resp: dR/dphi [G][C][8].  Outputs Lam [G][C][8] and the
+   gradients [G][C].  Groups of each sweep run in parallel (fixed order per
+   group).  Returns 0, 1 if maxit was reached, -1 on a solve failure. */
+int or_adjoint(const or_problem *p, const double *phi, const double *resp, double tol, int maxit, double *Lam,
+               double *gsigt, double *gsigs, double *gq, int *iters)
+{
+    or_elem e;
+    or_element(p->dx, p->dy, p->dz, e.M, e.L, e.G, e.F);
+    const long nc = ncell_of(p), n = (long)p->G * nc * 8;
+    const int G = p->G;
+    double *x = (double *)malloc(sizeof(double) * n);
+    double *Ln = (double *)malloc(sizeof(double) * n);
+    int rc = 1, bad = 0;
+    for (long i = 0; i < n; ++i) Lam[i] = 0.0;
+    *iters = 0;
+    for (int it = 0; it < maxit; ++it) {
+        /* x = r + B^T Lam: x_g'c = r_g'c + (sigs_g'c / 4pi) sum_g xfer[g'][g] M Lam_gc */
+        for (int gp = 0; gp < G; ++gp)
+            for (long c = 0; c < nc; ++c) {
+                double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ml[8];
+                for (int g = 0; g < G; ++g) {
+                    double f = p->xfer[gp * G + g];
+                    if (f == 0.0) continue;
+                    mass_apply(&e, Lam + ((long)g * nc + c) * 8, ml);
+                    for (int k = 0; k < 8; ++k) acc[k] += f * ml[k];
+                }
+                double sc = p->sigs[(long)gp * nc + c] / (4.0 * PI);
+                for (int k = 0; k < 8; ++k)
+                    x[((long)gp * nc + c) * 8 + k] = resp[((long)gp * nc + c) * 8 + k] + sc * acc[k];
+            }
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+        for (int g = 0; g < G; ++g) {
+            double *lam = (double *)malloc(sizeof(double) * 8 * nc);
+            double *rhs = (double *)malloc(sizeof(double) * 8 * nc);
+            double *out = Ln + (long)g * nc * 8;
+            for (long i = 0; i < 8 * nc; ++i) out[i] = 0.0;
+            for (int d = 0; d < p->ndir; ++d) {
+                for (long i = 0; i < 8 * nc; ++i) rhs[i] = p->w[d] * x[(long)g * nc * 8 + i];
+                if (adjoint_sweep_dir(p, &e, d, g, rhs, lam) != 0) bad = 1;
+                for (long i = 0; i < 8 * nc; ++i) out[i] += lam[i];
+            }
+            free(lam);
+            free(rhs);
+        }
+        if (bad) { rc = -1; break; }
+        double dmax = 0.0, pmax = 0.0;
+        for (long i = 0; i < n; ++i) {
+            double dd = fabs(Ln[i] - Lam[i]);
+            if (dd > dmax) dmax = dd;
+            if (fabs(Ln[i]) > pmax) pmax = fabs(Ln[i]);
+        }
+        memcpy(Lam, Ln, sizeof(double) * n);
+        *iters = it + 1;
+        if (pmax == 0.0 || dmax <= tol * pmax) { rc = 0; break; }
+    }
+    if (rc < 0) { free(x); free(Ln); return rc; }
+    /* the adjoint source at the converged Lam */
+    for (int gp = 0; gp < G; ++gp)
+        for (long c = 0; c < nc; ++c) {
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ml[8];
+            for (int g = 0; g < G; ++g) {
+                double f = p->xfer[gp * G + g];
+                if (f == 0.0) continue;
+                mass_apply(&e, Lam + ((long)g * nc + c) * 8, ml);
+                for (int k = 0; k < 8; ++k) acc[k] += f * ml[k];
+            }
+            double sc = p->sigs[(long)gp * nc + c] / (4.0 * PI);
+            for (int k = 0; k < 8; ++k)
+                x[((long)gp * nc + c) * 8 + k] = resp[((long)gp * nc + c) * 8 + k] + sc * acc[k];
+        }
+    /* dR/dq and dR/dsigma_s from Lam */
+    for (int g = 0; g < G; ++g)
+        for (long c = 0; c < nc; ++c) {
+            double ml[8];
+            mass_apply(&e, Lam + ((long)g * nc + c) * 8, ml);
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += ml[k];
+            gq[(long)g * nc + c] = s / (4.0 * PI);
+        }
+    for (int gp = 0; gp < G; ++gp)
+        for (long c = 0; c < nc; ++c) {
+            double mp[8], s = 0.0;
+            mass_apply(&e, phi + ((long)gp * nc + c) * 8, mp);
+            for (int g = 0; g < G; ++g) {
+                double f = p->xfer[gp * G + g];
+                if (f == 0.0) continue;
+                const double *lg = Lam + ((long)g * nc + c) * 8;
+                for (int k = 0; k < 8; ++k) s += f * lg[k] * mp[k];
+            }
+            gsigs[(long)gp * nc + c] = s / (4.0 * PI);
+        }
+    /* dR/dsigma_t: pair each direction's adjoint and forward angular flux */
+    double *S = (double *)malloc(sizeof(double) * n);
+    or_source(p, phi, S);
+    for (long i = 0; i < (long)G * nc; ++i) gsigt[i] = 0.0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int g = 0; g < G; ++g) {
+        double *lam = (double *)malloc(sizeof(double) * 8 * nc);
+        double *psi = (double *)malloc(sizeof(double) * 8 * nc);
+        double *rhs = (double *)malloc(sizeof(double) * 8 * nc);
+        for (int d = 0; d < p->ndir; ++d) {
+            for (long i = 0; i < 8 * nc; ++i) rhs[i] = p->w[d] * x[(long)g * nc * 8 + i];
+            if (adjoint_sweep_dir(p, &e, d, g, rhs, lam) != 0) bad = 1;
+            if (sweep_dir(p, &e, d, g, S + (long)g * nc * 8, NULL, NULL, NULL, psi, NULL) != 0) bad = 1;
+            for (long c = 0; c < nc; ++c) {
+                double mp[8], s = 0.0;
+                mass_apply(&e, psi + 8 * c, mp);
+                for (int k = 0; k < 8; ++k) s += lam[8 * c + k] * mp[k];
+                gsigt[(long)g * nc + c] -= s;
+            }
+        }
+        free(lam);
+        free(psi);
+        free(rhs);
+    }
+    free(S);
+    free(x);
+    free(Ln);
+    return bad ? -1 : rc;
+}
