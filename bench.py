@@ -162,33 +162,46 @@ def ann_form(P, steps):
     ref = P.source_iterate(tol=1e-6, max_it=500, mode=sn.GE32R, use_graph=True, allow_noconv=True)["phi"].clone()
     stream = torch.cuda.current_stream()
 
+    S_ref = P.source(ref)
+
+    def sweep_rate(mode, reps=5):
+        """Kernel-level solves/s of one sweep from the converged source (CUDA events
+        around the hyperplane launches)."""
+        out_phi = P.flux_tensor()
+        P.sweep(S_ref, out_phi, mode=mode)
+        P.set_profiling(True)
+        P.profile(reset=True)
+        for _ in range(reps):
+            P.sweep(S_ref, out_phi, mode=mode)
+        ms, n = P.profile(reset=True)
+        P.set_profiling(False)
+        fb, _ = P.surrogate_stats() if mode in (sn.ANN, sn.ANN_GATED) else (0, 0)
+        one = eps_p(out_phi, P.sweep(S_ref, mode=sn.GE32R))
+        return P.solves_per_sweep / (ms / n / 1e3), fb / P.solves_per_sweep, one
+
     def run(mode, tau):
         if tau is not None:
             P.surrogate_set_gate(tau)
+        rate, fb, one_sweep_err = sweep_rate(mode)
+        res = {"tau": tau, "sweep_solves_per_s": rate, "fallback_frac": fb, "one_sweep_eps_P_vs_ge": one_sweep_err}
         phi = P.flux_tensor()
-        r = P.source_iterate(phi=phi, tol=1e-5, max_it=300, mode=mode, use_graph=True, allow_noconv=True)
-        fb, _ = P.surrogate_stats()
-        err = eps_p(phi, ref)
-        nodal = float(((phi - ref).abs() / (ref.abs() + 1e-8 * ref.abs().max())).mean())
-        work = P.flux_tensor()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        P.source_iterate(phi=work, tol=0.0, max_it=steps, mode=mode, use_graph=True, allow_noconv=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        return {"tau": tau, "solves_per_s": P.solves_per_sweep / (ms / 1e3), "ms_per_step": ms,
-                "eps_P_vs_ge": err, "mean_nodal_rel_vs_ge": nodal, "iters": r["iters"],
-                "converged": r["converged"], "fallback_frac_last_sweep": fb / P.solves_per_sweep}
+        try:
+            r = P.source_iterate(phi=phi, tol=1e-5, max_it=300, mode=mode, use_graph=True, allow_noconv=True)
+            res.update({"eps_P_vs_ge": eps_p(phi, ref), "iters": r["iters"], "converged": r["converged"],
+                        "mean_nodal_rel_vs_ge":
+                            float(((phi - ref).abs() / (ref.abs() + 1e-8 * ref.abs().max())).mean())})
+        except sn.SnError as e:
+            res.update({"eps_P_vs_ge": None, "converged": False, "diverged": str(e)})
+        return res
 
     out = {"train_mae": tr, "test_mae": te, "train_s": train_s, "train_samples": 1 << 20,
-           "ungated": run(sn.ANN, None)}
+           "ge_sweep_solves_per_s": sweep_rate(sn.GE32R)[0], "ungated": run(sn.ANN, None)}
     sweep = [run(sn.ANN_GATED, t) for t in (0.1, 0.05, 0.03, 0.02, 0.01)]
-    ok = [r for r in sweep if r["eps_P_vs_ge"] <= 0.03]
-    best = max(ok, key=lambda r: r["solves_per_s"]) if ok else None
-    out.update({"gated_sweep": sweep, "value": best["solves_per_s"] if best else None,
+    ok = [r for r in sweep if r.get("eps_P_vs_ge") is not None and r["eps_P_vs_ge"] <= 0.03]
+    best = max(ok, key=lambda r: r["sweep_solves_per_s"]) if ok else None
+    out.update({"gated_sweep": sweep, "value": best["sweep_solves_per_s"] if best else None,
                 "unit": UNIT, "at_tau": best["tau"] if best else None,
+                "speedup_vs_ge_sweep": (best["sweep_solves_per_s"] / out["ge_sweep_solves_per_s"]) if best else None,
                 "error_ref": "converged FP32 GE flux (itself within 1e-5 of FP64)"})
     return out
 

@@ -164,6 +164,11 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
                             void *phi, int32_t *iters, double *change_max,
                             double *change_mean, int32_t use_graph);
 
+/* The isotropic nodal source of the source iteration for a given flux (Eqs. (2),
+ * (6), P_0 term): S_g = (sum_g' xfer[g'][g] sigs_g' phi_g' + q_g) / (4 pi);
+ * phi, S: device [G][ncell][8] of the handle's element type.  Asynchronous. */
+sn_status sn_source(sn_handle h, const void *phi, void *S);
+
 /* Balance tallies of the last sweep, FP64, particles per unit time:
  * tallies[0] leakage through the boundary, [1] collisions sum sigma_t int phi,
  * [2] emission 4 pi int S, [3] inflow through the boundary.  For any sweep

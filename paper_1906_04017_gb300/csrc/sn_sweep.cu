@@ -540,6 +540,12 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
     return rc;
 }
 
+sn_status sn_source(sn_handle h, const void *phi, void *S)
+{
+    if (!h || !phi || !S) return fail(h, SN_EINVAL, "sn_source: NULL argument");
+    return launch_source(h, phi, S, h->stream);
+}
+
 sn_status sn_set_profiling(sn_handle h, int32_t enable)
 {
     if (!h) return fail(nullptr, SN_EINVAL, "sn_set_profiling: NULL handle");

@@ -68,6 +68,7 @@ _API = [
     ("sn_source_iterate", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int,
                                          _fp, ctypes.POINTER(ctypes.c_int32), _dp, _dp, ctypes.c_int32]),
     ("sn_get_balance", ctypes.c_int, [ctypes.c_void_p, _dp]),
+    ("sn_source", ctypes.c_int, [ctypes.c_void_p, _fp, _fp]),
     ("sn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("sn_get_profile", ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("sn_surrogate_prepare", ctypes.c_int, [_fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
@@ -265,6 +266,15 @@ class Problem:
             _check(st, self.h)
         return dict(phi=phi, iters=it.value, change_max=cmax.value, change_mean=cmean.value,
                     converged=(st == SN_OK))
+
+    def source(self, phi, S=None):
+        """The isotropic nodal source S[G, ncell, 8] built from phi by the library."""
+        self._sync_stream()
+        if S is None:
+            S = torch.empty_like(phi)
+        _check(lib().sn_source(self.h, _dev(phi, self.dtype, (self.ncell, 8)), _dev(S, self.dtype, (self.ncell, 8))),
+               self.h)
+        return S
 
     def set_profiling(self, on=True):
         _check(lib().sn_set_profiling(self.h, 1 if on else 0), self.h)
