@@ -169,6 +169,25 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
  * phi, S: device [G][ncell][8] of the handle's element type.  Asynchronous. */
 sn_status sn_source(sn_handle h, const void *phi, void *S);
 
+/* ---------------------------------------------------------------------------
+ * sn_adjoint_sweep: gradients of a detector response R = sum resp * phi with
+ * respect to the per-cell, per-group sigma_t, sigma_s (scattering out of the group)
+ * and q (not in the paper: the discrete adjoint of the system of Sec. 2, (12)-(14),
+ * and of the source iteration).  FP32 handles only.
+ *   phi:  device [G][ncell][8] converged forward flux (sn_source_iterate);
+ *   resp: device [G][ncell][8] dR/dphi (e.g. V/8 at every node of the detector cells);
+ *   Lam:  device [G][ncell][8] out, adjoint scalar flux sum_d lambda_d;
+ *   dR_dsigt, dR_dsigs, dR_dq: device FP64 [G][ncell] out.
+ * Adjoint source iteration to tol (max-norm relative change) in at most max_it
+ * sweeps (*iters, may be NULL), then a final pass that pairs every forward and
+ * adjoint angular flux for dR/dsigma_t, recomputing the forward sweep from face
+ * planes checkpointed every ceil(sqrt(nplanes)) hyperplanes (no full angular flux
+ * is stored).  Synchronises the stream.  SN_ENOCONV if max_it was reached (the
+ * gradients are still written).
+ * ------------------------------------------------------------------------- */
+sn_status sn_adjoint_sweep(sn_handle h, const float *phi, const float *resp, double tol, int32_t max_it,
+                           float *Lam, double *dR_dsigt, double *dR_dsigs, double *dR_dq, int32_t *iters);
+
 /* Balance tallies of the last sweep, FP64, particles per unit time:
  * tallies[0] leakage through the boundary, [1] collisions sum sigma_t int phi,
  * [2] emission 4 pi int S, [3] inflow through the boundary.  For any sweep

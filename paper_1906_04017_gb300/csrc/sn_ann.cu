@@ -923,6 +923,7 @@ static sn_status upload_params(sn_handle h, const float *host)
     n->t = 0;
     n->dirty = true;
     h->has_net = true;
+    h->net_gen++;
     return SN_OK;
 }
 
@@ -958,6 +959,7 @@ static sn_status grad_step(sn_handle h, const float *feat, const float *targ, in
         bc1 = (float)(1.0 - std::pow(0.9, (double)n->t));
         bc2 = (float)(1.0 - std::pow(0.999, (double)n->t));
         n->dirty = true;
+        h->net_gen++;
     }
     adam_kernel<<<(kNparam + 255) / 256, 256, 0, st>>>(n->p, n->m, n->v, n->gpart, nblk, lr, bc1, bc2, gout,
                                                        step ? 1 : 0);
@@ -1055,6 +1057,7 @@ sn_status sn_surrogate_set_gate(sn_handle h, float tau)
     sn_status s = ensure_net(h);
     if (s != SN_OK) return s;
     net_of(h)->tau = tau;
+    h->net_gen++;
     return SN_OK;
 }
 

@@ -41,11 +41,25 @@ struct FastDiv {
 #endif
 };
 
+// One pass of the adjoint machinery over a range of hyperplanes (sn_adjoint.cu).
+struct AdjPass {
+    int mode = 0;               // 0 plain, 1 store the angular flux, 2 pair with it
+    const float *S = nullptr;   // nodal source [G][C][8]
+    const float *psi_inc = nullptr;
+    void *face = nullptr;       // face planes to use
+    float *phi_oct = nullptr;
+    double *leak = nullptr;
+    float *psi_blk = nullptr;   // stored angular fluxes of a block of hyperplanes
+    int64_t blk_cell0 = 0;      // plane_off of the block's first hyperplane
+    double *grad = nullptr;     // dR/dsigma_t [G][C]
+};
+
 struct Graphs {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // ping-pong parity
     const void *phi_user = nullptr;                 // buffer the graphs were captured for
     int mode = -1;
     bool prof = false;
+    uint64_t net_gen = 0;                           // surrogate state the graphs were captured with
 };
 
 }  // namespace sn
@@ -74,6 +88,7 @@ struct sn_handle_s {
     void *dir = nullptr;         // DirData<T>[Do]
     float4 *dir_abs = nullptr;   // [Do] (|Omega_x|, |Omega_y|, |Omega_z|, 0) for the surrogate inputs
     uint32_t *plane_cells = nullptr;  // packed (i',j',k') of every cell, grouped by hyperplane
+    uint32_t *plane_pos = nullptr;    // [C] position of primed cell i'+nx(j'+ny k') within its hyperplane
     void *face = nullptr;        // face planes: 4-vectors of T, see sn_sweep.cu
     int64_t face_x = 0, face_y = 0, face_z = 0;  // 4-vector count of each plane set
     void *phi_oct = nullptr;     // T[8][C][G][8] per-octant partial scalar flux
@@ -96,7 +111,11 @@ struct sn_handle_s {
     int64_t prof_sweeps = 0;       // sweeps timed
     bool prof_pending = false;     // events recorded, elapsed time not yet read
 
+    // adjoint working buffers (allocated on first sn_adjoint_sweep)
+    void *adj = nullptr;
+
     // surrogate network (set by sn_surrogate_train / sn_surrogate_set_weights)
+    uint64_t net_gen = 1;        // bumped whenever weights or gate change (graphs bake both in)
     bool has_net = false;
     void *net = nullptr;
 
@@ -130,6 +149,8 @@ sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gat
 // zero the surrogate's fallback / timeout counters (stream-ordered)
 sn_status reset_ann_counters(sn_handle h, cudaStream_t st);
 sn_status check_ann_timeouts(sn_handle h);
+sn_status launch_planes_adjoint(sn_handle h, const AdjPass &p, int s0, int s1, cudaStream_t st);
+void free_adjoint(sn_handle h);
 int num_sms();
 
 // accumulator slots in h->acc

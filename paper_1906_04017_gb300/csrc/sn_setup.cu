@@ -166,7 +166,8 @@ static void release(sn_handle h)
     if (!h) return;
     for (int i = 0; i < 2; ++i)
         if (h->graphs.exec[i]) cudaGraphExecDestroy(h->graphs.exec[i]);
-    void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->dir_abs, h->plane_cells,
+    free_adjoint(h);
+    void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->dir_abs, h->plane_cells, h->plane_pos,
                     h->face, h->phi_oct, h->S, h->phi_b, h->acc};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -375,6 +376,16 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
         SN_TRY(dalloc_bytes(h, (void **)&h->plane_cells, sizeof(uint32_t) * (size_t)C));
         cudaError_t e = cudaMemcpy(h->plane_cells, cells.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(plane_cells)"));
+        std::vector<uint32_t> pos(C);
+        for (int s2 = 0; s2 < h->nplanes; ++s2)
+            for (int64_t q = count[s2]; q < count[s2 + 1]; ++q) {
+                const uint32_t pk = cells[q];
+                const int64_t lin = (pk & 1023) + (int64_t)h->nx * (((pk >> 10) & 1023) + (int64_t)h->ny * (pk >> 20));
+                pos[lin] = (uint32_t)(q - count[s2]);
+            }
+        SN_TRY(dalloc_bytes(h, (void **)&h->plane_pos, sizeof(uint32_t) * (size_t)C));
+        e = cudaMemcpy(h->plane_pos, pos.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(plane_pos)"));
     }
 
     // face planes: per octant, per (j',k') / (i',k') / (i',j'), per (group, direction):

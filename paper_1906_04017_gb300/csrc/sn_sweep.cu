@@ -44,11 +44,20 @@ struct SweepArgs {
     T *phi_oct;              // [8][C][G][8]
     double *leak;            // accumulator
     T vol12;                 // V / 12
+    // adjoint passes (XMODE 1: store the angular flux, 2: pair it with the adjoint)
+    Vec4<T> *psi_blk;        // [block cells][8 octants][G][Do] x 8 nodes (two 4-vectors)
+    uint32_t blk_base;       // STORE: offset of this hyperplane's cells in psi_blk
+    uint32_t pair_base;      // PAIR: offset of the forward hyperplane's cells in psi_blk
+    const uint32_t *plane_pos;   // position of each primed cell within its hyperplane
+    double *grad;            // PAIR: dR/dsigma_t [G][C]
+    T vol216;                // V / 216
 };
 
 // grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
-// rounded up to whole warps.
-template <typename T, bool REFINE>
+// rounded up to whole warps.  XMODE 0: plain sweep; 1: also store each angular flux
+// (physical node order) for the adjoint; 2: adjoint pass that pairs its angular flux
+// with the stored forward one of the opposite direction (see sn_adjoint.cu).
+template <typename T, bool REFINE, int XMODE = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(SweepArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char red_raw[];
@@ -61,7 +70,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(Sw
     // threads past keys_per_cta * Do (warp rounding) or past the last key idle
     const bool active = lk < a.keys_per_cta && key < (uint32_t)a.ncells_plane * (uint32_t)a.G;
     int g = 0, c = 0;
-    T leak = T(0);
+    T leak = T(0), pair = T(0);
     if (active) {
         const uint32_t cidx = a.divG.div(key);
         g = (int)(key - cidx * (uint32_t)a.G);
@@ -114,10 +123,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(Sw
         if (kp < a.nz - 1) store4(a.fz + iz, x[4], x[5], x[6], x[7]);
         else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
         leak *= dd.w * a.vol12;
+        if (XMODE == 1) {
+            // forward angular flux, physical node order
+            T xp[8];
+#pragma unroll
+            for (int n = 0; n < 8; ++n) xp[n] = x[n];
+            mirror8(xp, o);
+            Vec4<T> *slot = a.psi_blk + 2 * (((int64_t)(a.blk_base + cidx) * 8 + o) * GD + gd);
+            store4(slot, xp[0], xp[1], xp[2], xp[3]);
+            store4(slot + 1, xp[4], xp[5], xp[6], xp[7]);
+        }
+        if (XMODE == 2) {
+            // the forward flux of the opposite direction (octant o ^ 7, same index d) at
+            // this cell: it sits on forward hyperplane nplanes - 1 - s at the position of
+            // the mirrored primed index
+            const uint32_t cf = a.plane_pos[(a.nx - 1 - ip) + a.nx * ((a.ny - 1 - jp) + a.ny * (a.nz - 1 - kp))];
+            const Vec4<T> *slot = a.psi_blk + 2 * (((int64_t)(a.pair_base + cf) * 8 + (o ^ 7)) * GD + gd);
+            T pf[8], p0[4], p1[4];
+            load4(p0, slot);
+            load4(p1, slot + 1);
+#pragma unroll
+            for (int n = 0; n < 4; ++n) { pf[n] = p0[n]; pf[4 + n] = p1[n]; }
+            mirror8(pf, o);          // into this direction's canonical frame
+            mh_axis<0>(pf);
+            mh_axis<1>(pf);
+            mh_axis<2>(pf);
+            T dot = T(0);
+#pragma unroll
+            for (int n = 0; n < 8; ++n) dot += x[n] * pf[n];
+            pair = -dd.w * a.vol216 * dot;
+        }
         // w_d psi in physical node order: canonical node n lands on physical n ^ o
         T *r = red + threadIdx.x * 9;
 #pragma unroll
         for (int n = 0; n < 8; ++n) r[n ^ o] = dd.w * x[n];
+        if (XMODE == 2) r[8] = pair;
     }
     __syncthreads();
     if (active) {
@@ -127,6 +167,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(Sw
             T s = T(0);
             for (int q = 0; q < Do; ++q) s += base[q * 9 + n];
             dst[n] = s;
+        }
+        if (XMODE == 2 && d == 0) {
+            double s = 0.0;
+            for (int q = 0; q < Do; ++q) s += (double)base[q * 9 + 8];
+            atomicAdd(a.grad + (int64_t)g * a.C + c, s);
         }
     }
     // leakage: warp sum, one double atomic per warp that saw any
@@ -169,6 +214,49 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
         SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));
         h->prof_pending = true;
     }
+    return SN_OK;
+}
+
+// Hyperplanes [s0, s1) of an FP32 GE32R sweep in an adjoint pass mode (see sn_adjoint.cu).
+sn_status launch_planes_adjoint(sn_handle h, const AdjPass &p, int s0, int s1, cudaStream_t st)
+{
+    SweepArgs<float> a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
+    a.divG = FastDiv((uint32_t)h->G);
+    a.keys_per_cta = 256 / h->Do;
+    a.sigt = (const float *)h->sigt; a.S = p.S; a.psi_inc = p.psi_inc;
+    a.dir = (const DirData<float> *)h->dir;
+    a.fx = reinterpret_cast<Vec4<float> *>(p.face);
+    a.fy = a.fx + h->face_x;
+    a.fz = a.fy + h->face_y;
+    a.phi_oct = p.phi_oct;
+    a.leak = p.leak;
+    a.vol12 = (float)(h->dx * h->dy * h->dz / 12.0);
+    a.vol216 = (float)(h->dx * h->dy * h->dz / 216.0);
+    a.psi_blk = reinterpret_cast<Vec4<float> *>(p.psi_blk);
+    a.plane_pos = h->plane_pos;
+    a.grad = p.grad;
+    const int block = (a.keys_per_cta * h->Do + 31) / 32 * 32;
+    const size_t smem = sizeof(float) * 9 * block;
+    for (int s = s0; s < s1; ++s) {
+        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+        a.cells = h->plane_cells + h->plane_off[s];
+        a.ncells_plane = (int)n;
+        a.blk_base = p.mode == 1 ? (uint32_t)(h->plane_off[s] - p.blk_cell0) : 0u;
+        if (p.mode == 2) {
+            const int sf = h->nplanes - 1 - s;
+            a.pair_base = (uint32_t)(h->plane_off[sf] - p.blk_cell0);
+        }
+        const int64_t nkeys = n * h->G;
+        const dim3 grid((unsigned)((nkeys + a.keys_per_cta - 1) / a.keys_per_cta), 8);
+        if (p.mode == 1)
+            sweep_plane_ge<float, true, 1><<<grid, block, smem, st>>>(a);
+        else if (p.mode == 2)
+            sweep_plane_ge<float, true, 2><<<grid, block, smem, st>>>(a);
+        else
+            sweep_plane_ge<float, true, 0><<<grid, block, smem, st>>>(a);
+    }
+    SN_CK(h, cudaGetLastError());
     return SN_OK;
 }
 
@@ -464,7 +552,7 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
 
     if (use_graph) {
         Graphs &gr = h->graphs;
-        if (gr.phi_user != phi || gr.mode != (int)mode) {
+        if (gr.phi_user != phi || gr.mode != (int)mode || gr.net_gen != h->net_gen) {
             for (int p = 0; p < 2; ++p)
                 if (gr.exec[p]) { cudaGraphExecDestroy(gr.exec[p]); gr.exec[p] = nullptr; }
             gr.phi_user = nullptr;
@@ -492,6 +580,7 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
             h->prof = prof;
             gr.phi_user = phi;
             gr.mode = (int)mode;
+            gr.net_gen = h->net_gen;
             h->prof_pending = false;
         }
     }

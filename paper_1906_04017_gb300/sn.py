@@ -87,6 +87,8 @@ _API = [
                                           ctypes.POINTER(ctypes.c_int64)]),
     ("sn_surrogate_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]),
+    ("sn_adjoint_sweep", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_double, ctypes.c_int32, _fp, _fp, _fp,
+                                        _fp, ctypes.POINTER(ctypes.c_int32)]),
     ("sn_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sn_destroy", None, [ctypes.c_void_p]),
@@ -360,3 +362,22 @@ class Problem:
         b = ctypes.c_int64(0)
         _check(lib().sn_surrogate_stats(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
         return a.value, b.value
+
+    # ---- discrete adjoint ----
+    def adjoint(self, phi, resp, tol=1e-6, max_it=500, allow_noconv=False):
+        """Gradients of R = resp . phi at the converged forward flux phi (device
+        [G, ncell, 8]): dict(Lam [G, ncell, 8], grad_sigt, grad_sigs, grad_q [G, ncell]
+        FP64, iters)."""
+        self._sync_stream()
+        G, C = self.G, self.ncell
+        Lam = torch.empty((G, C, 8), dtype=torch.float32, device=phi.device)
+        gt = torch.empty((G, C), dtype=torch.float64, device=phi.device)
+        gs = torch.empty_like(gt)
+        gq = torch.empty_like(gt)
+        it = ctypes.c_int32(0)
+        st = lib().sn_adjoint_sweep(self.h, _dev(phi, torch.float32, (C, 8)), _dev(resp, torch.float32, (C, 8)),
+                                    float(tol), int(max_it), _dev(Lam, torch.float32, (C, 8)), _dev(gt, torch.float64),
+                                    _dev(gs, torch.float64), _dev(gq, torch.float64), ctypes.byref(it))
+        if not (st == SN_ENOCONV and allow_noconv):
+            _check(st, self.h)
+        return dict(Lam=Lam, grad_sigt=gt, grad_sigs=gs, grad_q=gq, iters=it.value, converged=(st == SN_OK))

@@ -230,3 +230,19 @@ def test_ann_sweep_gate_zero_is_elimination(sn):
     P.close()
     assert to == 0 and fb == P.solves_per_sweep
     assert torch.allclose(ann, ge, rtol=1e-6, atol=1e-7 * ge.abs().max().item())
+
+
+def test_graph_replays_follow_gate_changes(sn):
+    """Source-iteration graphs bake the gate threshold and the packed weights into
+    their kernel arguments; changing either must re-capture them: with tau = 0 after
+    a run at tau = 1e30 the gated iteration is the elimination iteration again."""
+    wl = W.random_small(5, 6, 4, order=4, G=2, seed=6, psi_inc=True)
+    P = sn.Problem(wl)
+    P.surrogate_set_weights(mlp.init_params(14))
+    P.surrogate_set_gate(1e30)
+    P.source_iterate(tol=0.0, max_it=3, mode=sn.ANN_GATED, use_graph=True, allow_noconv=True)
+    P.surrogate_set_gate(0.0)
+    a = P.source_iterate(tol=0.0, max_it=3, mode=sn.ANN_GATED, use_graph=True, allow_noconv=True)["phi"]
+    b = P.source_iterate(tol=0.0, max_it=3, mode=sn.GE32R, use_graph=True, allow_noconv=True)["phi"]
+    P.close()
+    assert torch.allclose(a, b, rtol=1e-6, atol=1e-7 * b.abs().max().item())
