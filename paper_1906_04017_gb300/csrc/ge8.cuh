@@ -163,7 +163,9 @@ __device__ __forceinline__ void ge8_factor_solve(T (&A)[8][8], T (&b)[8], unsign
             if (v > best) { best = v; p = r; }
         }
         piv |= unsigned(p) << (3 * k);
-        if (p != k) {
+        // a warp-uniform test keeps the exchange code off the instruction stream when
+        // no lane of the warp needs it (the usual case for these matrices)
+        if (__any_sync(__activemask(), p != k)) {
 #pragma unroll
             for (int r = k + 1; r < 8; ++r) {
                 if (p == r) {
@@ -204,7 +206,7 @@ __device__ __forceinline__ void ge8_replay(const T (&A)[8][8], unsigned piv, con
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         const int p = (piv >> (3 * k)) & 7u;
-        if (p != k) {
+        if (__any_sync(__activemask(), p != k)) {
 #pragma unroll
             for (int q = k + 1; q < 8; ++q)
                 if (p == q) { const T t = r[k]; r[k] = r[q]; r[q] = t; }

@@ -287,9 +287,9 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
         delete h;
         return fail(nullptr, SN_EINVAL, "sn_setup: ngroups * cells * 8 must stay below 2^31");
     }
-    if (h->Do > 256) {
+    if (h->Do > 128) {
         delete h;
-        return fail(nullptr, SN_EINVAL, "sn_setup: at most 256 directions per octant");
+        return fail(nullptr, SN_EINVAL, "sn_setup: at most 128 directions per octant");
     }
 
     // every host-side check passed: now the device

@@ -57,8 +57,14 @@ struct SweepArgs {
 // rounded up to whole warps.  XMODE 0: plain sweep; 1: also store each angular flux
 // (physical node order) for the adjoint; 2: adjoint pass that pairs its angular flux
 // with the stored forward one of the opposite direction (see sn_adjoint.cu).
+#ifndef SN_GE_MINBLOCKS
+#define SN_GE_MINBLOCKS 2
+#endif
+#ifndef SN_GE_BLOCK
+#define SN_GE_BLOCK 256
+#endif
 template <typename T, bool REFINE, int XMODE = 0>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sweep_plane_ge(SweepArgs<T> a)
+__global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS : 1) sweep_plane_ge(SweepArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char red_raw[];
     T *red = reinterpret_cast<T *>(red_raw);   // [blockDim.x][9]
@@ -186,7 +192,7 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     SweepArgs<T> a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
     a.divG = FastDiv((uint32_t)h->G);
-    a.keys_per_cta = 256 / h->Do;
+    a.keys_per_cta = SN_GE_BLOCK / h->Do;
     a.sigt = (const T *)h->sigt; a.S = S; a.psi_inc = (const T *)h->psi_inc;
     a.dir = (const DirData<T> *)h->dir;
     a.fx = (Vec4<T> *)h->face;
@@ -223,7 +229,7 @@ sn_status launch_planes_adjoint(sn_handle h, const AdjPass &p, int s0, int s1, c
     SweepArgs<float> a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
     a.divG = FastDiv((uint32_t)h->G);
-    a.keys_per_cta = 256 / h->Do;
+    a.keys_per_cta = SN_GE_BLOCK / h->Do;
     a.sigt = (const float *)h->sigt; a.S = p.S; a.psi_inc = p.psi_inc;
     a.dir = (const DirData<float> *)h->dir;
     a.fx = reinterpret_cast<Vec4<float> *>(p.face);
