@@ -266,6 +266,27 @@ sn_status sn_surrogate_stats(sn_handle h, int64_t *fallbacks, int64_t *timeouts)
 sn_status sn_set_profiling(sn_handle h, int32_t enable);
 sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t reset);
 
+/* ---------------------------------------------------------------------------
+ * sn_surrogate_grad_noalloc: the loss and gradient of sn_surrogate_grad, for
+ * callers that cannot allocate device memory -- work issued while a stream is
+ * being captured in global mode (cudaMalloc is refused there), callers that own a
+ * fixed, pre-assigned pool of device memory, and latency-bound loops that must not
+ * pay the device-wide synchronisation of cudaMalloc / cudaFree.  The paper has no
+ * counterpart; this is a library convenience.
+ *   params: device [2312] FP32 weights (layout of sn_surrogate_set_weights);
+ *   feat, targ: device [n][27], [n][8] (sn_surrogate_prepare);
+ *   grad: device [2312] FP32 out; loss: device [1] FP64 out (batch mean of Eq. (19)).
+ * No handle, no allocation: the per-block partial sums live in one fixed array
+ * of the library (2.37 MB on every GPU that loads it, kept until exit), which caps
+ * n at 32768 rows (SN_EINVAL above).  The first call on a device looks the array
+ * up (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams or threads on the same device) race; calls on one stream are ordered.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * ------------------------------------------------------------------------- */
+sn_status sn_surrogate_grad_noalloc(const float *params, const float *feat, const float *targ, int64_t n,
+                                    float *grad, double *loss, void *stream);
+
 /* Status text, and the last error message recorded on a handle (h may be NULL
  * for the last error of a call without a handle, per thread). */
 const char *sn_status_string(sn_status s);

@@ -19,6 +19,7 @@
 // (stride byte offset).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "cell_problem.cuh"
@@ -893,6 +894,86 @@ static sn_status apply_cells(sn_handle h, const float *in27, float *psi, int64_t
     if (n_fallback) *n_fallback = (int64_t)c[0];
     return SN_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// Allocation-free gradient of the training loss.
+//
+// sn_surrogate_grad needs a handle (created with device allocations) and allocates a
+// temporary gradient buffer on every call.  Some callers cannot do that: code that
+// issues its work while a stream is being captured in global capture mode (where
+// cudaMalloc is refused), code whose device memory is a fixed pool handed out in
+// advance, and latency-bound loops that must not pay for the device-wide
+// synchronisation a cudaMalloc/cudaFree pair can cause.  This variant takes every
+// input and output as caller-owned device memory and keeps the per-block partial
+// gradients in the fixed array below instead of allocated scratch.
+//
+// The array lives in every GPU that loads the library until the process exits:
+// kNoAllocMaxBlocks * 2312 floats + kNoAllocMaxBlocks doubles = 2.37 MB, which caps a
+// call at kNoAllocMaxBlocks * 128 = 32768 rows.  Every call uses it from the start,
+// so calls that overlap on the GPU (different streams, or different host threads on
+// one device) race on it; calls queued on one stream are ordered and safe.  Each call
+// writes all the partials it later reads, so no part of the array has to start at
+// zero.  The first call on a device looks up the array's device address
+// (cudaGetSymbolAddress, with that device current); make that first call before any
+// stream capture begins.
+// ---------------------------------------------------------------------------------
+constexpr int kNoAllocMaxBlocks = 256;
+static __device__ __align__(256) float g_noalloc_gpart[kNoAllocMaxBlocks * kNparam];
+static __device__ __align__(256) double g_noalloc_lpart[kNoAllocMaxBlocks];
+
+static std::mutex g_noalloc_mutex;
+static float *g_noalloc_gpart_ptr[64];
+static double *g_noalloc_lpart_ptr[64];
+
+static sn_status noalloc_scratch(float **gpart, double **lpart)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(nullptr, SN_ECUDA, "sn_surrogate_grad_noalloc: device index above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_gpart_ptr[dev]) {
+        void *pg = nullptr, *pl = nullptr;
+        e = cudaGetSymbolAddress(&pg, g_noalloc_gpart);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(gradient partials)");
+        e = cudaGetSymbolAddress(&pl, g_noalloc_lpart);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(loss partials)");
+        g_noalloc_lpart_ptr[dev] = static_cast<double *>(pl);
+        g_noalloc_gpart_ptr[dev] = static_cast<float *>(pg);
+    }
+    *gpart = g_noalloc_gpart_ptr[dev];
+    *lpart = g_noalloc_lpart_ptr[dev];
+    return SN_OK;
+}
+
+}  // namespace sn
+
+extern "C" sn_status sn_surrogate_grad_noalloc(const float *params, const float *feat, const float *targ, int64_t n,
+                                                float *grad, double *loss, void *stream)
+{
+    using namespace sn;
+    if (!params || !feat || !targ || !grad || !loss)
+        return fail(nullptr, SN_EINVAL, "sn_surrogate_grad_noalloc: NULL pointer");
+    if (n < 1 || n > (int64_t)kNoAllocMaxBlocks * 128)
+        return fail(nullptr, SN_EINVAL, "sn_surrogate_grad_noalloc: n must be in 1..32768 (fixed scratch of 256 "
+                                        "blocks of 128 rows)");
+    float *gpart = nullptr;
+    double *lpart = nullptr;
+    sn_status s = noalloc_scratch(&gpart, &lpart);
+    if (s != SN_OK) return s;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int nblk = (int)((n + 127) / 128);
+    cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
+    grad_kernel<<<nblk, 128, kGradSmem, st>>>(params, feat, targ, n, 0, (int)n, 1.f / (float)n, gpart, lpart);
+    adam_kernel<<<(kNparam + 255) / 256, 256, 0, st>>>(nullptr, nullptr, nullptr, gpart, nblk, 0.f, 1.f, 1.f, grad, 0);
+    sum_kernel<<<1, 32, 0, st>>>(lpart, nblk, loss);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "sn_surrogate_grad_noalloc");
+    return SN_OK;
+}
+
+namespace sn {
 
 // Host-side uniform initialisation (SplitMix64 stream), +-1/sqrt(fan_in).
 static void init_params(std::vector<float> &p, uint64_t seed)

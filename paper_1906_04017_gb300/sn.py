@@ -89,6 +89,7 @@ _API = [
                                           ctypes.POINTER(ctypes.c_int64)]),
     ("sn_adjoint_sweep", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_double, ctypes.c_int32, _fp, _fp, _fp,
                                         _fp, ctypes.POINTER(ctypes.c_int32)]),
+    ("sn_surrogate_grad_noalloc", ctypes.c_int, [_fp, _fp, _fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
     ("sn_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sn_destroy", None, [ctypes.c_void_p]),
@@ -173,6 +174,15 @@ def surrogate_prepare(in27):
     _check(lib().sn_surrogate_prepare(_dev(in27, torch.float32, (27,)), n, _dev(feat, torch.float32, (27,)),
                                       _dev(targ, torch.float32, (8,)), _stream()))
     return feat, targ
+
+
+def surrogate_grad_noalloc(params, feat, targ, grad, loss):
+    """Loss and gradient of Eq. (19) without any device allocation by the library:
+    params [2312], feat [n, 27], targ [n, 8], grad [2312] (out) FP32 and loss [1]
+    FP64 (out) are all caller-owned CUDA tensors; n <= 32768."""
+    _check(lib().sn_surrogate_grad_noalloc(_dev(params, torch.float32), _dev(feat, torch.float32, (27,)),
+                                           _dev(targ, torch.float32, (8,)), feat.shape[0],
+                                           _dev(grad, torch.float32), _dev(loss, torch.float64), _stream()))
 
 
 def _f32p(a):
