@@ -195,7 +195,21 @@ def ann_form(P, steps):
         return res
 
     out = {"train_mae": tr, "test_mae": te, "train_s": train_s, "train_samples": 1 << 20,
-           "ge_sweep_solves_per_s": sweep_rate(sn.GE32R)[0], "ungated": run(sn.ANN, None)}
+           "ge_sweep_solves_per_s": sweep_rate(sn.GE32R)[0], "random_trained_ungated": run(sn.ANN, None)}
+    # fine-tune on one-cell problems harvested from an elimination sweep of another
+    # instance of the same family (blocked opacity field with a different seed)
+    t0 = time.perf_counter()
+    Q = sn.Problem(workloads.blocked(64, 10.0, 8, 8, 8, 16, seed=1))
+    qphi = Q.source_iterate(tol=1e-4, max_it=200, allow_noconv=True)["phi"]
+    cells = torch.cat([Q.harvest(Q.source(qphi), 1 << 19, seed=s) for s in (11, 12)])
+    Q.close()
+    feat, targ = sn.surrogate_prepare(cells)
+    P.surrogate_fit(feat, targ, steps=20000, batch=8192, lr=5e-4)
+    out["finetune"] = {"harvested_cells": int(cells.shape[0]), "mae": P.surrogate_eval(feat, targ),
+                       "seconds": time.perf_counter() - t0,
+                       "source": "GE sweep of blocked_64 with opacity seed 1 (evaluation uses seed 0)"}
+    del cells, feat, targ
+    out["ungated"] = run(sn.ANN, None)
     sweep = [run(sn.ANN_GATED, t) for t in (0.1, 0.05, 0.03, 0.02, 0.01)]
     ok = [r for r in sweep if r.get("eps_P_vs_ge") is not None and r["eps_P_vs_ge"] <= 0.03]
     best = max(ok, key=lambda r: r["sweep_solves_per_s"]) if ok else None

@@ -164,6 +164,13 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
                             void *phi, int32_t *iters, double *change_max,
                             double *change_mean, int32_t use_graph);
 
+/* One SN_SOLVE_GE32R sweep from S (device [G][ncell][8]) that also writes about cap
+ * of its solves, picked by a seeded hash, as one-cell problems (device [cap][27],
+ * layout of sn_cell_solve_batch) in the positive-octant frame the solve uses: the
+ * training data of a surrogate for this family of problems, drawn by the library's
+ * own elimination.  *n_out: how many were written (<= cap).  Synchronises. */
+sn_status sn_harvest(sn_handle h, const float *S, float *in27, int64_t cap, uint64_t seed, int64_t *n_out);
+
 /* The isotropic nodal source of the source iteration for a given flux (Eqs. (2),
  * (6), P_0 term): S_g = (sum_g' xfer[g'][g] sigs_g' phi_g' + q_g) / (4 pi);
  * phi, S: device [G][ncell][8] of the handle's element type.  Asynchronous. */

@@ -163,7 +163,8 @@ enum AccSlot {
     ACC_MEAN = 5,      // sum over (g, c) of |dphi_bar| / |phi_bar|
     ACC_MEANN = 6,     // number of terms in ACC_MEAN
     ACC_FLAG = 7,      // non-zero: a non-finite flux value was seen
-    ACC_COUNT = 8
+    ACC_HARVEST = 8,   // sn_harvest: number of solves picked (unsigned 64-bit)
+    ACC_COUNT = 9
 };
 
 }  // namespace sn

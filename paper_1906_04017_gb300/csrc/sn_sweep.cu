@@ -22,6 +22,7 @@
 // bit-reproducible run to run.
 //
 // Element type T: float (GE32R / GE32) or double (GE64, FP64 handles).
+#include <algorithm>
 #include <cmath>
 
 #include "ge8.cuh"
@@ -51,17 +52,26 @@ struct SweepArgs {
     const uint32_t *plane_pos;   // position of each primed cell within its hyperplane
     double *grad;            // PAIR: dR/dsigma_t [G][C]
     T vol216;                // V / 216
+    // harvesting (XMODE 3): a hashed sample of the solves is written out as one-cell
+    // problems in the canonical (positive-octant) frame
+    float *harvest;          // [cap][27]
+    unsigned long long *harvest_count;
+    uint32_t harvest_cap, harvest_threshold, harvest_seed, plane;
+    const float4 *dir_abs;   // |Omega| of each direction of an octant
+    T hx, hy, hz;
 };
 
 // grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
 // rounded up to whole warps.  XMODE 0: plain sweep; 1: also store each angular flux
 // (physical node order) for the adjoint; 2: adjoint pass that pairs its angular flux
 // with the stored forward one of the opposite direction (see sn_adjoint.cu).
+// 128-thread blocks, 4 per SM (128 registers a thread): measured faster on GB300 than
+// fewer, larger-register blocks -- the elimination is latency-bound, warps beat spills
 #ifndef SN_GE_MINBLOCKS
-#define SN_GE_MINBLOCKS 2
+#define SN_GE_MINBLOCKS 4
 #endif
 #ifndef SN_GE_BLOCK
-#define SN_GE_BLOCK 256
+#define SN_GE_BLOCK 128
 #endif
 template <typename T, bool REFINE, int XMODE = 0>
 __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS : 1) sweep_plane_ge(SweepArgs<T> a)
@@ -121,6 +131,30 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS 
         mirror8(S, o);
         T x[8];
         cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
+        if (XMODE == 3) {
+            // keep this solve with probability threshold / 2^32 (hash of its identity)
+            uint32_t hsh = a.harvest_seed ^ (a.plane * 0x9E3779B9u) ^ ((uint32_t)o * 0x85EBCA6Bu) ^
+                           (key * 0xC2B2AE35u) ^ ((uint32_t)d * 0x27D4EB2Fu);
+            hsh ^= hsh >> 16; hsh *= 0x7FEB352Du; hsh ^= hsh >> 15; hsh *= 0x846CA68Bu; hsh ^= hsh >> 16;
+            if (hsh < a.harvest_threshold) {
+                const unsigned long long slot = atomicAdd(a.harvest_count, 1ull);
+                if (slot < a.harvest_cap) {
+                    float *q = a.harvest + 27 * slot;
+                    const float4 ab = a.dir_abs[d];
+                    q[0] = ab.x; q[1] = ab.y; q[2] = ab.z;
+                    q[3] = (float)a.hx; q[4] = (float)a.hy; q[5] = (float)a.hz;
+                    q[6] = (float)sig;
+#pragma unroll
+                    for (int n = 0; n < 8; ++n) q[7 + n] = (float)S[n];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        q[15 + t] = (float)ux[t];
+                        q[19 + t] = (float)uy[t];
+                        q[23 + t] = (float)uz[t];
+                    }
+                }
+            }
+        }
         // outflow faces (canonical in-face order): x-face a=1, y-face b=1, z-face c=1
         if (ip < a.nx - 1) store4(a.fx + ix, x[1], x[3], x[5], x[7]);
         else leak += dd.t3x * (x[1] + x[3] + x[5] + x[7]);
@@ -261,6 +295,48 @@ sn_status launch_planes_adjoint(sn_handle h, const AdjPass &p, int s0, int s1, c
             sweep_plane_ge<float, true, 2><<<grid, block, smem, st>>>(a);
         else
             sweep_plane_ge<float, true, 0><<<grid, block, smem, st>>>(a);
+    }
+    SN_CK(h, cudaGetLastError());
+    return SN_OK;
+}
+
+// One GE32R sweep from S that also writes about `cap` randomly chosen solves as
+// canonical one-cell problems (the positive-octant frame is itself a valid physical
+// problem: Omega = |Omega|, node order as stored).
+static sn_status launch_harvest(sn_handle h, const float *S, float *out, uint32_t cap, uint64_t seed,
+                                unsigned long long *count, cudaStream_t st)
+{
+    SweepArgs<float> a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
+    a.divG = FastDiv((uint32_t)h->G);
+    a.keys_per_cta = SN_GE_BLOCK / h->Do;
+    a.sigt = (const float *)h->sigt; a.S = S; a.psi_inc = (const float *)h->psi_inc;
+    a.dir = (const DirData<float> *)h->dir;
+    a.fx = reinterpret_cast<Vec4<float> *>(h->face);
+    a.fy = a.fx + h->face_x;
+    a.fz = a.fy + h->face_y;
+    a.phi_oct = (float *)h->phi_oct;
+    a.leak = h->acc + ACC_LEAK;
+    a.vol12 = (float)(h->dx * h->dy * h->dz / 12.0);
+    a.harvest = out;
+    a.harvest_count = count;
+    a.harvest_cap = cap;
+    const double total = (double)h->ncell * h->ndir * h->G;
+    const double p = std::min(1.0, 1.05 * cap / total);
+    a.harvest_threshold = (uint32_t)std::min(4294967295.0, p * 4294967296.0);
+    a.harvest_seed = (uint32_t)(seed ^ (seed >> 32));
+    a.dir_abs = h->dir_abs;
+    a.hx = (float)h->dx; a.hy = (float)h->dy; a.hz = (float)h->dz;
+    const int block = (a.keys_per_cta * h->Do + 31) / 32 * 32;
+    const size_t smem = sizeof(float) * 9 * block;
+    for (int s = 0; s < h->nplanes; ++s) {
+        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+        a.cells = h->plane_cells + h->plane_off[s];
+        a.ncells_plane = (int)n;
+        a.plane = (uint32_t)s;
+        const int64_t nkeys = n * h->G;
+        const dim3 grid((unsigned)((nkeys + a.keys_per_cta - 1) / a.keys_per_cta), 8);
+        sweep_plane_ge<float, true, 3><<<grid, block, smem, st>>>(a);
     }
     SN_CK(h, cudaGetLastError());
     return SN_OK;
@@ -633,6 +709,23 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
     if (change_mean) *change_mean = cmean;
     if (rc == SN_ENOCONV) fail(h, SN_ENOCONV, "sn_source_iterate: max_it reached before tol");
     return rc;
+}
+
+sn_status sn_harvest(sn_handle h, const float *S, float *in27, int64_t cap, uint64_t seed, int64_t *n_out)
+{
+    if (!h || !S || !in27 || !n_out) return fail(h, SN_EINVAL, "sn_harvest: NULL argument");
+    if (h->fp64) return fail(h, SN_EINVAL, "sn_harvest: needs an FP32 handle");
+    if (cap < 1 || cap > (1LL << 31)) return fail(h, SN_EINVAL, "sn_harvest: cap must be in 1..2^31");
+    const cudaStream_t st = h->stream;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(h->acc + ACC_HARVEST);
+    SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
+    sn_status s = launch_harvest(h, S, in27, (uint32_t)cap, seed, cnt, st);
+    if (s != SN_OK) return s;
+    unsigned long long c = 0;
+    SN_CK(h, cudaMemcpyAsync(&c, cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    SN_CK(h, cudaStreamSynchronize(st));
+    *n_out = (int64_t)std::min<unsigned long long>(c, (unsigned long long)cap);
+    return SN_OK;
 }
 
 sn_status sn_source(sn_handle h, const void *phi, void *S)

@@ -69,6 +69,8 @@ _API = [
                                          _fp, ctypes.POINTER(ctypes.c_int32), _dp, _dp, ctypes.c_int32]),
     ("sn_get_balance", ctypes.c_int, [ctypes.c_void_p, _dp]),
     ("sn_source", ctypes.c_int, [ctypes.c_void_p, _fp, _fp]),
+    ("sn_harvest", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.POINTER(ctypes.c_int64)]),
     ("sn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("sn_get_profile", ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("sn_surrogate_prepare", ctypes.c_int, [_fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
@@ -287,6 +289,16 @@ class Problem:
         _check(lib().sn_source(self.h, _dev(phi, self.dtype, (self.ncell, 8)), _dev(S, self.dtype, (self.ncell, 8))),
                self.h)
         return S
+
+    def harvest(self, S, cap, seed=0):
+        """One elimination sweep from S that returns about `cap` of its solves as
+        one-cell problems in27 [n, 27] (positive-octant frame)."""
+        self._sync_stream()
+        out = torch.empty((int(cap), 27), dtype=torch.float32, device=S.device)
+        n = ctypes.c_int64(0)
+        _check(lib().sn_harvest(self.h, _dev(S, torch.float32, (self.ncell, 8)), _dev(out, torch.float32, (27,)),
+                                int(cap), int(seed), ctypes.byref(n)), self.h)
+        return out[:n.value]
 
     def set_profiling(self, on=True):
         _check(lib().sn_set_profiling(self.h, 1 if on else 0), self.h)

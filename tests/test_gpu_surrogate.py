@@ -246,3 +246,28 @@ def test_graph_replays_follow_gate_changes(sn):
     b = P.source_iterate(tol=0.0, max_it=3, mode=sn.GE32R, use_graph=True, allow_noconv=True)["phi"]
     P.close()
     assert torch.allclose(a, b, rtol=1e-6, atol=1e-7 * b.abs().max().item())
+
+
+def test_harvest_returns_the_sweeps_one_cell_problems(sn):
+    """At full rate the harvesting sweep writes every solve of the sweep as a one-cell
+    problem in the positive-octant frame: directions from the first octant of the
+    quadrature, the mesh spacing, the cell's sigma_t, inflow psi_inc on boundary
+    faces; and solving them again reproduces the same elimination."""
+    wl = W.random_small(4, 3, 5, order=4, G=2, seed=2, psi_inc=True)
+    P = sn.Problem(wl)
+    rng = np.random.default_rng(4)
+    S = cuda(rng.uniform(0.0, 1.0, (P.G, P.ncell, 8)).astype(np.float32))
+    x = P.harvest(S, cap=P.solves_per_sweep, seed=1).cpu().numpy().astype(np.float64)
+    assert x.shape[0] >= P.solves_per_sweep - 1
+    om, _ = oracle.lqn(4)
+    first = np.round(om[:3], 6)
+    assert all(any(np.allclose(r, f, atol=1e-6) for f in first) for r in x[::97, 0:3])
+    assert np.allclose(x[:, 3:6], [wl["lx"] / 4, wl["ly"] / 3, wl["lz"] / 5], rtol=1e-6)
+    assert np.isin(np.round(x[:, 6], 5), np.round(wl["sigt"].astype(np.float32), 5)).all()
+    ge = sn.cell_solve_batch(cuda(x), sn.GE32R).cpu().numpy()
+    ref = oracle.cell_solve(x)
+    assert (np.abs(ge - ref).max(axis=1) / np.abs(ref).max(axis=1)).max() < 1e-5
+    # a 10% sample
+    y = P.harvest(S, cap=P.solves_per_sweep // 10, seed=3)
+    P.close()
+    assert 0.85 * (P.solves_per_sweep // 10) <= y.shape[0] <= P.solves_per_sweep // 10
