@@ -138,7 +138,7 @@ constexpr uint32_t kW1Bytes = kNhid * kK1 * 2; // 4096
 constexpr uint32_t kW2Bytes = kN2 * kNhid * 2; // 2048
 constexpr uint32_t kXBytes = kTile * kK1 * 2;  // 8192
 constexpr uint32_t kHBytes = kTile * kNhid * 2;// 16384
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = 64;   // layer 1 uses columns 0..63, layer 2 reuses 0..15
 
 struct Net {
     float *p = nullptr;        // [kNparam] FP32 master weights
@@ -470,15 +470,23 @@ __device__ __forceinline__ bool mlp_tile(unsigned char *smem, uint32_t tbase, ui
     tc_fence_after();
     __syncwarp();
     const uint32_t lane_base = tbase + ((uint32_t)(threadIdx.x & ~31) << 16);
-    float hrow[kNhid];
+    // 16 hidden units at a time: bias, ReLU, BF16, two 16-byte stores into H
 #pragma unroll
     for (int c = 0; c < kNhid / 16; ++c) {
         float v[16];
         tmem_ld16(lane_base + 16 * c, v);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) hrow[16 * c + u] = fmaxf(v[u] + sb1[16 * c + u], 0.f);
+        for (int u = 0; u < 16; ++u) v[u] = fmaxf(v[u] + sb1[16 * c + u], 0.f);
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            uint4 q;
+            q.x = pack_bf16x2(v[8 * hf + 0], v[8 * hf + 1]);
+            q.y = pack_bf16x2(v[8 * hf + 2], v[8 * hf + 3]);
+            q.z = pack_bf16x2(v[8 * hf + 4], v[8 * hf + 5]);
+            q.w = pack_bf16x2(v[8 * hf + 6], v[8 * hf + 7]);
+            *reinterpret_cast<uint4 *>(smem + kOffH + umma_off(threadIdx.x, 16 * c + 8 * hf, kNhid)) = q;
+        }
     }
-    write_row_bf16<kNhid>(smem + kOffH, threadIdx.x, hrow);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -487,7 +495,7 @@ __device__ __forceinline__ bool mlp_tile(unsigned char *smem, uint32_t tbase, ui
         constexpr uint32_t id2 = idesc_bf16(128, kN2);
 #pragma unroll
         for (int kk = 0; kk < kNhid / 16; ++kk)
-            umma_bf16(tbase + kNhid, sdesc(sbase + kOffH + kk * 256, 128, (kNhid / 8) * 128),
+            umma_bf16(tbase, sdesc(sbase + kOffH + kk * 256, 128, (kNhid / 8) * 128),
                       sdesc(sbase + kOffW2 + kk * 256, 128, (kNhid / 8) * 128), id2, kk > 0);
         umma_commit(bar);
     }
@@ -498,7 +506,7 @@ __device__ __forceinline__ bool mlp_tile(unsigned char *smem, uint32_t tbase, ui
     tc_fence_after();
     __syncwarp();
     float v[16];
-    tmem_ld16(lane_base + kNhid, v);
+    tmem_ld16(lane_base, v);
 #pragma unroll
     for (int q = 0; q < 8; ++q) o[q] = v[q] + sb2[q];
     return true;
@@ -634,136 +642,165 @@ struct AnnSweepArgs {
     AnnArgs ann;
 };
 
-constexpr uint32_t kOffRed = kAnnSmem;                      // [128][9] floats
-constexpr uint32_t kSweepSmem = kOffRed + 4 * kTile * 9;
-constexpr int kCanon = 24;                                  // floats of a stored canonical cell
+// The sweep kernel reuses the staging area of the cell kernel for the flux reduction
+// ([128][9] floats) and the fallback results ([128][8] floats), so it needs no more
+// shared memory than the cell kernel: five CTAs fit on an SM (64 TMEM columns each).
+constexpr uint32_t kOffRed = kOffStage;
+constexpr uint32_t kOffDefer = kOffRed + 4 * kTile * 9;      // deferred rejected rows
+constexpr int kDeferCap = 1024;
+static_assert(kOffDefer + 4 * kDeferCap <= kOffBar, "sweep scratch must fit the staging area");
+constexpr uint32_t kSweepSmem = kAnnSmem;
 
+// One row of a surrogate tile: the key (cell, group) and direction of thread t, and
+// the canonical one-cell problem read from the face planes, psi_inc, S and sigma_t.
+struct AnnRow {
+    bool active;
+    int g, cell, ip, jp, kp;
+    int64_t ix, iy, iz;
+};
+
+__device__ __forceinline__ AnnRow ann_row(const AnnSweepArgs &a, int o, int tile, int t, const DirData<float> &dd,
+                                          CanonCell<float> &c)
+{
+    AnnRow r;
+    const int Do = a.Do, lk = t / Do, d = t - lk * Do;
+    const uint32_t key = (uint32_t)tile * (uint32_t)a.keys_per_tile + (uint32_t)lk;
+    r.active = lk < a.keys_per_tile && key < (uint32_t)a.ncells_plane * (uint32_t)a.G;
+    r.g = r.cell = r.ip = r.jp = r.kp = 0;
+    r.ix = r.iy = r.iz = 0;
+    if (!r.active) return r;
+    const uint32_t cidx = a.divG.div(key);
+    r.g = (int)(key - cidx * (uint32_t)a.G);
+    const uint32_t pk = a.cells[cidx];
+    r.ip = pk & 1023; r.jp = (pk >> 10) & 1023; r.kp = pk >> 20;
+    const int i = (o & 1) ? a.nx - 1 - r.ip : r.ip;
+    const int j = (o & 2) ? a.ny - 1 - r.jp : r.jp;
+    const int k = (o & 4) ? a.nz - 1 - r.kp : r.kp;
+    r.cell = i + a.nx * (j + a.ny * k);
+    const int GD = a.G * Do, gd = r.g * Do + d;
+    r.ix = (int64_t)(o * a.ny * a.nz + r.jp + a.ny * r.kp) * GD + gd;
+    r.iy = (int64_t)(o * a.nx * a.nz + r.ip + a.nx * r.kp) * GD + gd;
+    r.iz = (int64_t)(o * a.nx * a.ny + r.ip + a.nx * r.jp) * GD + gd;
+    const int g = r.g;
+    if (r.ip == 0) { const float v = a.psi_inc[6 * g + (o & 1)]; c.ux[0] = c.ux[1] = c.ux[2] = c.ux[3] = v; }
+    else load4(c.ux, a.fx + r.ix);
+    if (r.jp == 0) { const float v = a.psi_inc[6 * g + 2 + ((o >> 1) & 1)]; c.uy[0] = c.uy[1] = c.uy[2] = c.uy[3] = v; }
+    else load4(c.uy, a.fy + r.iy);
+    if (r.kp == 0) { const float v = a.psi_inc[6 * g + 4 + ((o >> 2) & 1)]; c.uz[0] = c.uz[1] = c.uz[2] = c.uz[3] = v; }
+    else load4(c.uz, a.fz + r.iz);
+    const int gc = g * a.C + r.cell;
+    c.sig = a.sigt[gc];
+    const Vec4<float> *Sp = reinterpret_cast<const Vec4<float> *>(a.S + (int64_t)gc * 8);
+    float s0[4], s1[4];
+    load4(s0, Sp);
+    load4(s1, Sp + 1);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) { c.S[n] = s0[n]; c.S[4 + n] = s1[n]; }
+    mirror8(c.S, o);
+    c.t3x = dd.t3x; c.t3y = dd.t3y; c.t3z = dd.t3z;
+    c.mask = o;
+    return r;
+}
+
+// Re-solve the deferred rejected rows of this CTA by elimination, all threads at once:
+// write their outflow faces and add w_d psi to the flux partial written by their tile.
+__device__ __forceinline__ void ann_flush_deferred(const AnnSweepArgs &a, int o, const uint32_t *defer, int n,
+                                                   float &leak)
+{
+    for (int qi = threadIdx.x; qi < n; qi += blockDim.x) {
+        const uint32_t e = defer[qi];
+        const int tile = (int)(e >> 8), row = (int)(e & 255u);
+        const int rd = row % a.Do;
+        const DirData<float> dd = a.dir[rd];
+        CanonCell<float> c;
+        const AnnRow r = ann_row(a, o, tile, row, dd, c);
+        float psi[8];
+        cell_solve_canonical<float, true>(c.t3x, c.t3y, c.t3z, c.sig, c.S, c.ux, c.uy, c.uz, psi);
+        if (r.ip < a.nx - 1) store4(a.fx + r.ix, psi[1], psi[3], psi[5], psi[7]);
+        else leak += dd.w * a.vol12 * dd.t3x * (psi[1] + psi[3] + psi[5] + psi[7]);
+        if (r.jp < a.ny - 1) store4(a.fy + r.iy, psi[2], psi[3], psi[6], psi[7]);
+        else leak += dd.w * a.vol12 * dd.t3y * (psi[2] + psi[3] + psi[6] + psi[7]);
+        if (r.kp < a.nz - 1) store4(a.fz + r.iz, psi[4], psi[5], psi[6], psi[7]);
+        else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
+        float *dst = a.phi_oct + (((int64_t)o * a.C + r.cell) * a.G + r.g) * 8;
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) atomicAdd(dst + (n2 ^ o), dd.w * psi[n2]);
+    }
+}
+
+// Rows the gate rejects are not re-solved inside their tile (that would stall the
+// whole CTA on a few lanes): they are queued and re-solved together by every thread
+// of the CTA when the queue fills and after the last tile.  Their faces are only read
+// by the next hyperplane (another launch), so the deferral is safe; their flux is
+// added to the tile's partial with atomics.
 template <bool GATED>
-__global__ void __launch_bounds__(128, 4) sweep_plane_ann(AnnSweepArgs a)
+__global__ void __launch_bounds__(128, GATED ? 4 : 5) sweep_plane_ann(AnnSweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t tbase = ann_setup(smem, a.ann);
-    float *canon = reinterpret_cast<float *>(smem + kOffStage);    // [128][24], failing rows
     float *red = reinterpret_cast<float *>(smem + kOffRed);
+    uint32_t *defer = reinterpret_cast<uint32_t *>(smem + kOffDefer);
     int *misc = reinterpret_cast<int *>(smem + kOffMisc);
-    int *queue = reinterpret_cast<int *>(smem + kOffQueue);
     const int o = blockIdx.y, t = threadIdx.x, Do = a.Do;
     const int lk = t / Do, d = t - lk * Do;
-    const bool lane_used = lk < a.keys_per_tile;
     DirData<float> dd = {0.f, 0.f, 0.f, 0.f};
     float4 dab = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (lane_used) {
+    if (lk < a.keys_per_tile) {
         dd = a.dir[d];
         dab = a.dir_abs[d];
     }
     const float lhx = (logf(a.hx) + kLogHShift) / kLogHScale;
     const float lhy = (logf(a.hy) + kLogHShift) / kLogHScale;
     const float lhz = (logf(a.hz) + kLogHShift) / kLogHScale;
-    const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
     uint32_t phase = 0;
     unsigned long long nfb = 0;
     float leak = 0.f;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const uint32_t key = (uint32_t)tile * (uint32_t)a.keys_per_tile + (uint32_t)lk;
-        const bool active = lane_used && key < nkeys;
         CanonCell<float> c;
-        float s = 0.f, xp[kK1];
+        const AnnRow r = ann_row(a, o, tile, t, dd, c);
+        float s = 0.f;
+        {
+            float xp[kK1];
 #pragma unroll
-        for (int k = 0; k < kK1; ++k) xp[k] = 0.f;
-        int g = 0, cell = 0, ip = 0, jp = 0, kp = 0;
-        int64_t ix = 0, iy = 0, iz = 0;
-        if (active) {
-            const uint32_t cidx = a.divG.div(key);
-            g = (int)(key - cidx * (uint32_t)a.G);
-            const uint32_t pk = a.cells[cidx];
-            ip = pk & 1023; jp = (pk >> 10) & 1023; kp = pk >> 20;
-            const int i = (o & 1) ? a.nx - 1 - ip : ip;
-            const int j = (o & 2) ? a.ny - 1 - jp : jp;
-            const int k = (o & 4) ? a.nz - 1 - kp : kp;
-            cell = i + a.nx * (j + a.ny * k);
-            const int GD = a.G * Do, gd = g * Do + d;
-            ix = (int64_t)(o * a.ny * a.nz + jp + a.ny * kp) * GD + gd;
-            iy = (int64_t)(o * a.nx * a.nz + ip + a.nx * kp) * GD + gd;
-            iz = (int64_t)(o * a.nx * a.ny + ip + a.nx * jp) * GD + gd;
-            if (ip == 0) { const float v = a.psi_inc[6 * g + (o & 1)]; c.ux[0] = c.ux[1] = c.ux[2] = c.ux[3] = v; }
-            else load4(c.ux, a.fx + ix);
-            if (jp == 0) { const float v = a.psi_inc[6 * g + 2 + ((o >> 1) & 1)]; c.uy[0] = c.uy[1] = c.uy[2] = c.uy[3] = v; }
-            else load4(c.uy, a.fy + iy);
-            if (kp == 0) { const float v = a.psi_inc[6 * g + 4 + ((o >> 2) & 1)]; c.uz[0] = c.uz[1] = c.uz[2] = c.uz[3] = v; }
-            else load4(c.uz, a.fz + iz);
-            const int gc = g * a.C + cell;
-            c.sig = a.sigt[gc];
-            const Vec4<float> *Sp = reinterpret_cast<const Vec4<float> *>(a.S + (int64_t)gc * 8);
-            float s0[4], s1[4];
-            load4(s0, Sp);
-            load4(s1, Sp + 1);
+            for (int k = 0; k < kK1; ++k) xp[k] = 0.f;
+            if (r.active) {
+                s = input_scale(c.S, c.ux, c.uy, c.uz);
+                float x[kNin];
+                ann_features(dab.x, dab.y, dab.z, a.hx, a.hy, a.hz, c.sig, c.S, c.ux, c.uy, c.uz,
+                             s > 0.f ? 1.f / s : 0.f, x);
+                x[3] = lhx; x[4] = lhy; x[5] = lhz;
 #pragma unroll
-            for (int n = 0; n < 4; ++n) { c.S[n] = s0[n]; c.S[4 + n] = s1[n]; }
-            mirror8(c.S, o);
-            c.t3x = dd.t3x; c.t3y = dd.t3y; c.t3z = dd.t3z;
-            c.mask = o;
-            s = input_scale(c.S, c.ux, c.uy, c.uz);
-            float x[kNin];
-            ann_features(dab.x, dab.y, dab.z, a.hx, a.hy, a.hz, c.sig, c.S, c.ux, c.uy, c.uz,
-                         s > 0.f ? 1.f / s : 0.f, x);
-            x[3] = lhx; x[4] = lhy; x[5] = lhz;
-#pragma unroll
-            for (int k = 0; k < kNin; ++k) xp[k] = x[k];
+                for (int k = 0; k < kNin; ++k) xp[k] = x[k];
+            }
+            write_row_bf16<kK1>(smem + kOffX, t, xp);
         }
-        write_row_bf16<kK1>(smem + kOffX, t, xp);
         float out[8];
         if (!mlp_tile(smem, tbase, phase, out)) break;
         float psi[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) psi[q] = s * out[q];
-        if (GATED) {
-            const bool pass = !active || s == 0.f || gate_pass(c, psi, a.ann.tau);
-            float *cr = canon + t * kCanon;
-            if (!pass) {
-                queue[atomicAdd(&misc[1], 1)] = t;
-                cr[0] = c.t3x; cr[1] = c.t3y; cr[2] = c.t3z; cr[3] = c.sig;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) cr[4 + k] = c.S[k];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) { cr[12 + q] = c.ux[q]; cr[16 + q] = c.uy[q]; cr[20 + q] = c.uz[q]; }
-            }
-            __syncthreads();
-            const int nq = misc[1];
-            for (int qi = t; qi < nq; qi += blockDim.x) {
-                float *r = canon + queue[qi] * kCanon;
-                float S2[8], u1[4], u2[4], u3[4], xs[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) S2[k] = r[4 + k];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) { u1[q] = r[12 + q]; u2[q] = r[16 + q]; u3[q] = r[20 + q]; }
-                cell_solve_canonical<float, true>(r[0], r[1], r[2], r[3], S2, u1, u2, u3, xs);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) r[k] = xs[k];
-            }
-            __syncthreads();
-            if (!pass) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) psi[k] = cr[k];
-            }
-            if (t == 0) {
-                nfb += (unsigned long long)nq;
-                misc[1] = 0;
-            }
+        bool keep = r.active;
+        if (GATED && r.active && s != 0.f && !gate_pass(c, psi, a.ann.tau)) {
+            keep = false;
+            defer[atomicAdd(&misc[1], 1)] = ((uint32_t)tile << 8) | (uint32_t)t;
         }
-        if (active) {
-            if (ip < a.nx - 1) store4(a.fx + ix, psi[1], psi[3], psi[5], psi[7]);
+        float *rr = red + t * 9;
+        if (keep) {
+            if (r.ip < a.nx - 1) store4(a.fx + r.ix, psi[1], psi[3], psi[5], psi[7]);
             else leak += dd.w * a.vol12 * dd.t3x * (psi[1] + psi[3] + psi[5] + psi[7]);
-            if (jp < a.ny - 1) store4(a.fy + iy, psi[2], psi[3], psi[6], psi[7]);
+            if (r.jp < a.ny - 1) store4(a.fy + r.iy, psi[2], psi[3], psi[6], psi[7]);
             else leak += dd.w * a.vol12 * dd.t3y * (psi[2] + psi[3] + psi[6] + psi[7]);
-            if (kp < a.nz - 1) store4(a.fz + iz, psi[4], psi[5], psi[6], psi[7]);
+            if (r.kp < a.nz - 1) store4(a.fz + r.iz, psi[4], psi[5], psi[6], psi[7]);
             else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
-            float *rr = red + t * 9;
 #pragma unroll
             for (int n = 0; n < 8; ++n) rr[n ^ o] = dd.w * psi[n];
+        } else {
+#pragma unroll
+            for (int n = 0; n < 8; ++n) rr[n] = 0.f;
         }
         __syncthreads();
-        if (active) {
-            float *dst = a.phi_oct + (((int64_t)o * a.C + cell) * a.G + g) * 8;
+        if (r.active) {
+            float *dst = a.phi_oct + (((int64_t)o * a.C + r.cell) * a.G + r.g) * 8;
             const float *base = red + (lk * Do) * 9;
             for (int n = d; n < 8; n += Do) {
                 float sum = 0.f;
@@ -772,6 +809,24 @@ __global__ void __launch_bounds__(128, 4) sweep_plane_ann(AnnSweepArgs a)
             }
         }
         __syncthreads();
+        if (GATED) {
+            const int nq = misc[1];
+            if (nq > kDeferCap - kTile) {       // room for one more tile: flush now
+                ann_flush_deferred(a, o, defer, nq, leak);
+                __syncthreads();
+                if (t == 0) {
+                    nfb += (unsigned long long)nq;
+                    misc[1] = 0;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (GATED) {
+        __syncthreads();
+        const int nq = reinterpret_cast<volatile int *>(misc)[1];
+        if (!reinterpret_cast<volatile int *>(misc)[2]) ann_flush_deferred(a, o, defer, nq, leak);
+        if (t == 0) nfb += (unsigned long long)nq;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
@@ -838,7 +893,7 @@ sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gat
         SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
     else
         SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
-    const int cap = num_sms() * 4 / 8;     // persistent CTAs per octant: 4 per SM in total
+    const int cap = num_sms() * (gated ? 4 : 5) / 8;   // persistent CTAs per octant (4 or 5 per SM in total)
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
     for (int p = 0; p < h->nplanes; ++p) {
         const int64_t n = h->plane_off[p + 1] - h->plane_off[p];
