@@ -16,6 +16,16 @@
 // the outflow form of (14) in one dimension), written per axis in the x-fastest
 // node order.  These are exactly the Gauss-integrated matrices of (12) divided by
 // V/216, so the solution psi is unchanged.
+//
+// Pivoting.  The symmetric part of Ah is the identity, so for sigma_t >= 0 the
+// symmetric part of A is positive definite (the upwind form's coercivity: half the
+// face masses of all six faces plus sigma_t M): partial pivoting then almost never
+// exchanges rows.  The elimination therefore runs first on the diagonal pivots,
+// branch-free, while it evaluates the test partial pivoting would make at each
+// step; a lane whose test fails (some entry below the pivot larger in magnitude)
+// redoes its system with the exchanges.  Every lane thus gets exactly the
+// operations of partial pivoting, and the common path keeps its instruction-level
+// parallelism.
 #pragma once
 
 namespace sn {
@@ -163,18 +173,14 @@ __device__ __forceinline__ void ge8_factor_solve(T (&A)[8][8], T (&b)[8], unsign
             if (v > best) { best = v; p = r; }
         }
         piv |= unsigned(p) << (3 * k);
-        // a warp-uniform test keeps the exchange code off the instruction stream when
-        // no lane of the warp needs it (the usual case for these matrices)
-        if (__any_sync(__activemask(), p != k)) {
 #pragma unroll
-            for (int r = k + 1; r < 8; ++r) {
-                if (p == r) {
+        for (int r = k + 1; r < 8; ++r) {
+            if (p == r) {
 #pragma unroll
-                    for (int c = k; c < 8; ++c) {
-                        const T t = A[k][c]; A[k][c] = A[r][c]; A[r][c] = t;
-                    }
-                    const T t = b[k]; b[k] = b[r]; b[r] = t;
+                for (int c = k; c < 8; ++c) {
+                    const T t = A[k][c]; A[k][c] = A[r][c]; A[r][c] = t;
                 }
+                const T t = b[k]; b[k] = b[r]; b[r] = t;
             }
         }
         rinv[k] = pivot_recip(A[k][k]);
@@ -197,6 +203,45 @@ __device__ __forceinline__ void ge8_factor_solve(T (&A)[8][8], T (&b)[8], unsign
     }
 }
 
+// Pivot rows of the identity permutation in ge8_factor_solve's encoding.
+constexpr unsigned kPivIdentity = (1u << 3) | (2u << 6) | (3u << 9) | (4u << 12) | (5u << 15) | (6u << 18);
+
+// Elimination on the diagonal pivots (multipliers in place, reciprocal pivots in
+// rinv, transformed right-hand side in b, solution in x).  Returns true when partial
+// pivoting would have exchanged rows at some step: an entry below the pivot of
+// strictly larger magnitude (ties keep the diagonal, as in ge8_factor_solve).  When
+// it returns false the results are bit-identical to ge8_factor_solve's.
+template <typename T>
+__device__ __forceinline__ bool ge8_factor_solve_diag(T (&A)[8][8], T (&b)[8], T (&rinv)[8], T (&x)[8])
+{
+    bool ex = false;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        T m = fabs(A[k + 1][k]);
+#pragma unroll
+        for (int r = k + 2; r < 8; ++r) m = fmax(m, fabs(A[r][k]));
+        ex |= m > fabs(A[k][k]);
+        rinv[k] = pivot_recip(A[k][k]);
+#pragma unroll
+        for (int r = k + 1; r < 8; ++r) {
+            const T l = A[r][k] * rinv[k];
+            A[r][k] = l;
+#pragma unroll
+            for (int c = k + 1; c < 8; ++c) A[r][c] = fma(-l, A[k][c], A[r][c]);
+            b[r] = fma(-l, b[k], b[r]);
+        }
+    }
+    rinv[7] = pivot_recip(A[7][7]);
+#pragma unroll
+    for (int r = 7; r >= 0; --r) {
+        T s = b[r];
+#pragma unroll
+        for (int c = r + 1; c < 8; ++c) s = fma(-A[r][c], x[c], s);
+        x[r] = s * rinv[r];
+    }
+    return ex;
+}
+
 // Repeat the elimination recorded by ge8_factor_solve on a new right-hand side r
 // (overwritten) and back-substitute: dx = A^{-1} r.
 template <typename T>
@@ -206,11 +251,27 @@ __device__ __forceinline__ void ge8_replay(const T (&A)[8][8], unsigned piv, con
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         const int p = (piv >> (3 * k)) & 7u;
-        if (__any_sync(__activemask(), p != k)) {
 #pragma unroll
-            for (int q = k + 1; q < 8; ++q)
-                if (p == q) { const T t = r[k]; r[k] = r[q]; r[q] = t; }
-        }
+        for (int q = k + 1; q < 8; ++q)
+            if (p == q) { const T t = r[k]; r[k] = r[q]; r[q] = t; }
+#pragma unroll
+        for (int q = k + 1; q < 8; ++q) r[q] = fma(-A[q][k], r[k], r[q]);
+    }
+#pragma unroll
+    for (int q = 7; q >= 0; --q) {
+        T s = r[q];
+#pragma unroll
+        for (int c = q + 1; c < 8; ++c) s = fma(-A[q][c], dx[c], s);
+        dx[q] = s * rinv[q];
+    }
+}
+
+// ge8_replay for the elimination of ge8_factor_solve_diag (no exchanges).
+template <typename T>
+__device__ __forceinline__ void ge8_replay_diag(const T (&A)[8][8], const T (&rinv)[8], T (&r)[8], T (&dx)[8])
+{
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
 #pragma unroll
         for (int q = k + 1; q < 8; ++q) r[q] = fma(-A[q][k], r[k], r[q]);
     }
@@ -229,22 +290,31 @@ __device__ __forceinline__ void cell_solve_canonical(T t3x, T t3y, T t3z, T sig,
                                                      const T (&ux)[4], const T (&uy)[4],
                                                      const T (&uz)[4], T (&x)[8])
 {
-    T A[8][8], b[8], rinv[8];
-    unsigned piv;
+    T A[8][8], b[8], rinv[8], b0[8];
     assemble_A(t3x, t3y, t3z, sig, A);
     build_b(T(2) * t3x, T(2) * t3y, T(2) * t3z, S, ux, uy, uz, b);
-    T b0[8];
-    if (REFINE) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) b0[k] = b[k];
+    for (int k = 0; k < 8; ++k) b0[k] = b[k];
+    const bool ex = ge8_factor_solve_diag(A, b, rinv, x);
+    // warp-uniform test: the exchange path stays off the instruction stream unless
+    // a lane of the warp needs it
+    const bool any_ex = __any_sync(__activemask(), ex);
+    unsigned piv = kPivIdentity;
+    if (any_ex && ex) {
+        assemble_A(t3x, t3y, t3z, sig, A);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = b0[k];
+        ge8_factor_solve(A, b, piv, rinv, x);
     }
-    ge8_factor_solve(A, b, piv, rinv, x);
     if (REFINE) {
         T ax[8], dx[8];
         apply_A(t3x, t3y, t3z, sig, x, ax);
 #pragma unroll
         for (int k = 0; k < 8; ++k) b0[k] -= ax[k];
-        ge8_replay(A, piv, rinv, b0, dx);
+        if (any_ex)
+            ge8_replay(A, piv, rinv, b0, dx);
+        else
+            ge8_replay_diag(A, rinv, b0, dx);
 #pragma unroll
         for (int k = 0; k < 8; ++k) x[k] += dx[k];
     }

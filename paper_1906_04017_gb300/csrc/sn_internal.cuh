@@ -140,6 +140,7 @@ void free_net(sn_handle h);
 
 // kernels launched by several translation units (element type from h->fp64)
 sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st);
+sn_status reduce_configure(sn_handle h);
 sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, bool norms,
                         cudaStream_t st);
 sn_status launch_source(sn_handle h, const void *phi, void *S, cudaStream_t st);

@@ -405,6 +405,7 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
         e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaStreamCreate"));
     }
+    SN_TRY(reduce_configure(h));
 #undef SN_TRY
     *out = h;
     return SN_OK;

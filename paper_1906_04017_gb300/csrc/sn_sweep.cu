@@ -374,58 +374,77 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v)
     atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
 }
 
-// One thread per (g, c, node): octant sum in the element type (fixed order), per-
+// Tiled over cells: a block takes TC whole cells (all groups, all nodes), sums the
+// eight octant partials in the layout the sweep writes them ([o][c][g][8], one
+// contiguous run per octant), transposes the tile through shared memory and writes
+// the scalar flux in its [g][c][8] layout (one contiguous run per group), so that
+// both sides move whole lines.  Octant sum in the element type (fixed order), per-
 // element quantities in the element type, FP64 only for the running sums and the
 // block / grid accumulation (the FP64 rate of the part is low).
 template <typename T>
 __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_oct, const T *__restrict__ phi_old,
                                                      T *__restrict__ phi_new, const T *__restrict__ S,
-                                                     const T *__restrict__ sigt, int C, int G, FastDiv divC,
-                                                     double vol8, double *acc, int norms)
+                                                     const T *__restrict__ sigt, int64_t C, int G, int TC,
+                                                     FastDiv divG8, double vol8, double *acc, int norms)
 {
+    extern __shared__ __align__(16) unsigned char red_smem[];
+    T *tile = reinterpret_cast<T *>(red_smem);   // [TC][G*8 + 8] (padded row per cell)
     __shared__ double sh[8][6];
-    const int total = G * C * 8;
-    const int stride_oct = C * G * 8;
+    const int G8 = G * 8, row = G8 + 8;
+    const int64_t stride_oct = C * G8;
+    const int64_t ntile = (C + TC - 1) / TC;
+    const int lane = threadIdx.x % 32;
     double coll = 0, src = 0, mean = 0, cnt = 0;
     T dmax = T(0), pmax = T(0);
     int bad = 0;
-    // grid-stride over whole warps so that the 8 nodes of a (g, c) stay in one warp
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e - (int)(threadIdx.x % 32) < total;
-         e += gridDim.x * blockDim.x) {
-        const bool in = e < total;
-        T nv = T(0), ov = T(0);
-        if (in) {
-            const int n = e & 7;
-            const uint32_t gc = (uint32_t)e >> 3;
-            const uint32_t g = divC.div(gc);
-            const int c = (int)(gc - g * (uint32_t)C);
-            const T *po = phi_oct + ((int64_t)c * G + g) * 8 + n;
+    for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int64_t c0 = t * TC;
+        const int nc = (int)min((int64_t)TC, C - c0);
+        const int nel = nc * G8;
+        const T *po = phi_oct + c0 * G8;
+        for (int i = threadIdx.x; i < nel; i += blockDim.x) {
             T s = T(0);
 #pragma unroll
-            for (int o = 0; o < 8; ++o) s += po[(int64_t)o * stride_oct];
-            nv = s;
-            phi_new[e] = nv;
-            if (!isfinite(nv)) bad = 1;
-            coll += (double)(sigt[gc] * nv);
-            src += (double)S[e];
-            if (norms) {
-                ov = phi_old[e];
-                dmax = fmax(dmax, fabs(nv - ov));
-                pmax = fmax(pmax, fabs(nv));
-            }
+            for (int o = 0; o < 8; ++o) s += po[(int64_t)o * stride_oct + i];
+            const int cl = (int)divG8.div((uint32_t)i);
+            tile[cl * row + (i - cl * G8)] = s;
         }
-        if (norms) {
-            T a = nv, b = ov;
+        __syncthreads();
+        const int nk = nc * 8;
+        for (int g = 0; g < G; ++g) {
+            const int64_t base = ((int64_t)g * C + c0) * 8;
+            // whole warps, so that the 8 nodes of a cell meet in one shuffle group
+            for (int k = threadIdx.x; k - lane < nk; k += blockDim.x) {
+                const bool in = k < nk;
+                T nv = T(0), ov = T(0);
+                if (in) {
+                    const int cl = k >> 3;
+                    nv = tile[cl * row + g * 8 + (k & 7)];
+                    phi_new[base + k] = nv;
+                    if (!isfinite(nv)) bad = 1;
+                    coll += (double)(sigt[(int64_t)g * C + c0 + cl] * nv);
+                    src += (double)S[base + k];
+                    if (norms) {
+                        ov = phi_old[base + k];
+                        dmax = fmax(dmax, fabs(nv - ov));
+                        pmax = fmax(pmax, fabs(nv));
+                    }
+                }
+                if (norms) {
+                    T a = nv, b = ov;
 #pragma unroll
-            for (int off = 1; off < 8; off <<= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, off);
-                b += __shfl_xor_sync(0xffffffffu, b, off);
-            }
-            if (in && (e & 7) == 0 && a != T(0)) {
-                mean += (double)(fabs(a - b) / fabs(a));
-                cnt += 1.0;
+                    for (int off = 1; off < 8; off <<= 1) {
+                        a += __shfl_xor_sync(0xffffffffu, a, off);
+                        b += __shfl_xor_sync(0xffffffffu, b, off);
+                    }
+                    if (in && (k & 7) == 0 && a != T(0)) {
+                        mean += (double)(fabs(a - b) / fabs(a));
+                        cnt += 1.0;
+                    }
+                }
             }
         }
+        __syncthreads();
     }
     // block reduction
     double v[6] = {coll * vol8, src * 4.0 * kPi * vol8, (double)dmax, (double)pmax, mean, cnt};
@@ -438,7 +457,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
         }
     }
     bad = __syncthreads_or(bad);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int warp = threadIdx.x / 32;
     if (lane == 0)
         for (int m = 0; m < 6; ++m) sh[warp][m] = v[m];
     __syncthreads();
@@ -470,22 +489,47 @@ int num_sms()
     return n;
 }
 
+static size_t reduce_tile(const sn_handle h, int *TC)
+{
+    // about 2048 elements a tile; a cell's G*8 values always stay in one tile
+    const int G8 = h->G * 8;
+    *TC = G8 >= 2048 ? 1 : 2048 / G8;
+    return (size_t)*TC * (G8 + 8) * h->esz;
+}
+
+// Opts the reduction in to more than 48 KB of dynamic shared memory where the group
+// count needs it (G*8 values of one cell, up to 1024 groups); called once by sn_setup
+// so that no attribute call falls inside a stream capture.
+sn_status reduce_configure(sn_handle h)
+{
+    int TC = 0;
+    const size_t smem = reduce_tile(h, &TC);
+    if (smem <= 48 * 1024) return SN_OK;
+    if (h->fp64)
+        SN_CK(h, cudaFuncSetAttribute(reduce_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else
+        SN_CK(h, cudaFuncSetAttribute(reduce_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return SN_OK;
+}
+
 sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, bool norms, cudaStream_t st)
 {
-    const int64_t total = (int64_t)h->G * h->ncell * 8;
-    int64_t grid = (total + 255) / 256;
+    int TC = 0;
+    const size_t smem = reduce_tile(h, &TC);
+    const int64_t ntile = (h->ncell + TC - 1) / TC;
+    int64_t grid = ntile;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (grid > cap) grid = cap;
     const double vol8 = h->dx * h->dy * h->dz / 8.0;
-    const FastDiv divC((uint32_t)h->ncell);
+    const FastDiv divG8((uint32_t)(h->G * 8));
     if (h->fp64)
-        reduce_kernel<double><<<(unsigned)grid, 256, 0, st>>>(
+        reduce_kernel<double><<<(unsigned)grid, 256, smem, st>>>(
             (const double *)h->phi_oct, (const double *)phi_old, (double *)phi_new, (const double *)S,
-            (const double *)h->sigt, (int)h->ncell, h->G, divC, vol8, h->acc, norms ? 1 : 0);
+            (const double *)h->sigt, h->ncell, h->G, TC, divG8, vol8, h->acc, norms ? 1 : 0);
     else
-        reduce_kernel<float><<<(unsigned)grid, 256, 0, st>>>(
+        reduce_kernel<float><<<(unsigned)grid, 256, smem, st>>>(
             (const float *)h->phi_oct, (const float *)phi_old, (float *)phi_new, (const float *)S,
-            (const float *)h->sigt, (int)h->ncell, h->G, divC, vol8, h->acc, norms ? 1 : 0);
+            (const float *)h->sigt, h->ncell, h->G, TC, divG8, vol8, h->acc, norms ? 1 : 0);
     SN_CK(h, cudaGetLastError());
     return SN_OK;
 }

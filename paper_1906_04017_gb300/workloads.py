@@ -183,5 +183,19 @@ def onecell_problems(n, seed=0):
     return out
 
 
+def exchange_problems(n, seed=0):
+    """One-cell problems outside the physical range, built so that elimination with
+    partial pivoting exchanges rows: flow in the first octant (canonical orientation
+    equals the physical one), sigma_t = -U[0.2, 1] * sum_a |Omega_a| / h_a < 0, so the
+    system loses its positive-definite symmetric part; other entries as in
+    onecell_problems."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    out = onecell_problems(n, seed)
+    out[:, 0:3] = np.abs(out[:, 0:3])
+    tau = (out[:, 0:3] / out[:, 3:6]).sum(axis=1)
+    out[:, 6] = -rng.uniform(0.2, 1.0, size=n) * tau
+    return out
+
+
 WORKLOADS = {"onecube_8": onecube_8, "blocked_64": blocked_64, "blocked_32": blocked_32,
              "spheres_96": spheres_96}

@@ -64,3 +64,16 @@ def test_edge_cases(sn):
 def test_empty_batch(sn):
     out = sn.cell_solve_batch(torch.zeros((0, 27), device="cuda"), sn.GE32R)
     assert out.shape == (0, 8)
+
+
+def test_exchange_path_matches_oracle(sn):
+    """sigma_t < 0: partial pivoting exchanges rows in most systems (lanes of a warp
+    mixed between the diagonal path and the exchange path); the solutions still
+    match the oracle's elimination.  The systems' condition numbers stay below ~20."""
+    x = f32_roundtrip(W.exchange_problems(50021, seed=2))
+    ref = oracle.cell_solve(x)
+    xt = torch.from_numpy(x.astype(np.float32)).cuda()
+    assert per_problem_err(sn.cell_solve_batch(xt, sn.GE32R).cpu().numpy(), ref) < 1e-5
+    assert per_problem_err(sn.cell_solve_batch(xt, sn.GE32).cpu().numpy(), ref) < 1e-4
+    got64 = sn.cell_solve_batch_f64(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert per_problem_err(got64, ref) < 1e-12
