@@ -29,10 +29,15 @@ if ROOT not in sys.path:
 
 METRIC = "Sn sweep cell*dir*group solves/s (GE form, FP32 GE + 1 refinement step)"
 UNIT = "solves/s"
-# algorithmic FP32 flops of one solve (assembly + elimination + refinement + flux), see the design doc
+# algorithmic FP32 flops of one solve: assembly 448 + right-hand side 120 + elimination
+# 372 + back substitution 64 + refinement 286 + flux 16
 FLOPS_PER_SOLVE = 1306
 # algorithmic HBM bytes of one solve: 12 inflow + 12 outflow face floats
 BYTES_PER_SOLVE = 96
+# DRAM bytes (read + write) per solve of sweep_plane_ge<float, 1, 0> measured by ncu on
+# blocked_64 hyperplane 95 (cold cache; profiles/sweep_plane_ge_blocked_64.md); None
+# once that kernel changes
+DRAM_BYTES_PER_SOLVE_NCU = 85.7
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -318,7 +323,10 @@ def run_gpu(args):
         "config": dict(workload_config(), parallelism="replicas" if ws > 1 else "single"),
         "roofline": {"bound": "alu", "kernel": "sweep_plane_ge<refine>", "achieved": achieved_tf,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                     "traffic": None,
+                     "traffic": (solves * DRAM_BYTES_PER_SOLVE_NCU / P.nplanes
+                                 if DRAM_BYTES_PER_SOLVE_NCU else None),
+                     "traffic_note": "bytes per average launch: ncu cold-cache capture of one hyperplane, "
+                                     "scaled by solves",
                      "flops_per_solve": FLOPS_PER_SOLVE,
                      "hbm_achieved_gbs": solves * BYTES_PER_SOLVE / sweep_s / 1e9,
                      "hbm_peak_gbs": hbm_peak,
@@ -340,6 +348,73 @@ def run_gpu(args):
     return 0
 
 
+def adjoint_check(args):
+    """Adjoint form at 32^3 (LQ_8, 4 groups, blocked opacity): gradients of the
+    group-summed flux integral over the 4x4x4 low corner with respect to every
+    per-cell, per-group sigma_t, sigma_s and q (393,216 parameters), by the FP32
+    adjoint sweep; 32 random parameters checked against central differences
+    (relative step 1e-6) of FP64 GPU source iterations warm-started from the
+    unperturbed flux.  Prints one JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1906_04017_gb300 import sn, workloads
+    wl = workloads.blocked_32()
+    nx = wl["nx"]
+    vol = (wl["lx"] / nx) ** 3
+    i, j, k = workloads.cell_ijk(wl)
+    G, C = wl["sigt"].shape[0], nx ** 3
+    r = np.zeros((G, C, 8))
+    r[:, (i < 4) & (j < 4) & (k < 4), :] = vol / 8.0
+    t0 = time.time()
+    P = sn.Problem(wl)
+    fwd = P.source_iterate(tol=1e-6, max_it=2000)
+    ta = time.time()
+    adj = P.adjoint(fwd["phi"], torch.from_numpy(r.astype(np.float32)).cuda(), tol=1e-6, max_it=2000)
+    torch.cuda.synchronize()
+    t_adj = time.time() - ta
+    P.close()
+    P64 = sn.Problem(wl, fp64=True)
+    base = P64.source_iterate(tol=1e-13, max_it=5000)
+    phi0 = base["phi"]
+    r64 = torch.from_numpy(r).cuda()
+    R0 = P64.response(phi0, r64)
+    P64.close()
+    rng = np.random.default_rng(2024)
+    kinds = (("sigt", "grad_sigt"), ("sigs", "grad_sigs"), ("q", "grad_q"))
+    picks = [(kinds[rng.integers(0, 3)], int(rng.integers(0, G)), int(rng.integers(0, C))) for _ in range(32)]
+    rows = []
+    iters = []
+    for (key, gkey), g, c in picks:
+        p0 = float(wl[key][g, c])
+        h = 1e-6 * (p0 if p0 > 0 else 1.0)
+        Rs = []
+        for v in (p0 + h, p0 - h):
+            w = dict(wl)
+            w[key] = wl[key].copy()
+            w[key][g, c] = v
+            Q = sn.Problem(w, fp64=True)
+            phi = phi0.clone()
+            res = Q.source_iterate(phi=phi, tol=1e-13, max_it=5000)
+            iters.append(res["iters"])
+            Rs.append(Q.response(phi, r64))
+            Q.close()
+        fd = (Rs[0] - Rs[1]) / (2 * h)
+        ga = float(adj[gkey][g, c].item())
+        gmax = float(adj[gkey].abs().max().item())
+        rows.append(dict(kind=key, g=g, c=c, adjoint=ga, fd=fd,
+                         rel=abs(ga - fd) / abs(fd) if fd != 0 else None, rel_to_max=abs(ga - fd) / gmax))
+    rel = [x["rel"] for x in rows if x["rel"] is not None]
+    big = [x["rel"] for x in rows if x["rel"] is not None and abs(x["fd"]) >= 1e-3 * abs(R0)]
+    out = {"adjoint_check": "blocked_32: 32^3 cells, LQ_8, 4 groups, corner 4^3 response",
+           "parameters": 3 * G * C, "R": R0, "adjoint_iters": adj["iters"], "adjoint_s": t_adj,
+           "checked": len(rows), "max_rel_to_max_gradient": max(x["rel_to_max"] for x in rows),
+           "max_rel": max(rel) if rel else None, "median_rel": float(np.median(rel)) if rel else None,
+           "max_rel_where_fd_ge_1e-3_R": max(big) if big else None, "n_fd_ge_1e-3_R": len(big),
+           "fd_iters_mean": float(np.mean(iters)), "wall_s": time.time() - t0, "rows": rows}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,11 +423,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ann", action="store_true")
+    ap.add_argument("--adjoint-check", action="store_true",
+                    help="adjoint gradients vs FP64 central differences at 32^3 (prints its own JSON line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_check:
+        return adjoint_check(args)
     return run_gpu(args)
 
 

@@ -195,6 +195,12 @@ sn_status sn_source(sn_handle h, const void *phi, void *S);
 sn_status sn_adjoint_sweep(sn_handle h, const float *phi, const float *resp, double tol, int32_t max_it,
                            float *Lam, double *dR_dsigt, double *dR_dsigs, double *dR_dq, int32_t *iters);
 
+/* Detector response R = sum over groups, cells and nodes of resp * phi (the
+ * functional whose gradients sn_adjoint_sweep returns; FP64 products and sum).
+ * phi, resp: device [G][ncell][8] in the handle's element type (float, or double
+ * for an FP64 handle); *R written on the host.  Synchronises the stream. */
+sn_status sn_response(sn_handle h, const void *phi, const void *resp, double *R);
+
 /* Balance tallies of the last sweep, FP64, particles per unit time:
  * tallies[0] leakage through the boundary, [1] collisions sum sigma_t int phi,
  * [2] emission 4 pi int S, [3] inflow through the boundary.  For any sweep

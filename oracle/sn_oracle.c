@@ -14,7 +14,7 @@
  *   (11) DFEM trial expansion, (12) discrete DFEM system, (13) phi = D psi,
  *   (14) the per-cell system A psi = b, (21) source-iteration change.
  *
- * Readings of the paper taken here (each one is also listed in the design doc):
+ * Readings of the paper taken here (where the text is silent or inconsistent):
  *   - Sec. 2 uses "+" for the inflow boundary (n.Omega < 0) when it defines
  *     the faces, but the per-cell system (14) puts the outflow matrix in A
  *     and the upwind matrix in b.  The oracle uses exactly that outflow form:

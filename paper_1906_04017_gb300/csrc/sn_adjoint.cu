@@ -153,11 +153,54 @@ static unsigned grid_for(int64_t n, int per)
     return (unsigned)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 
+// R = sum resp * phi over groups, cells and nodes, FP64 products and accumulation.
+template <typename T>
+__global__ void __launch_bounds__(256) response_kernel(const T *__restrict__ phi, const T *__restrict__ resp,
+                                                       int64_t n, double *out)
+{
+    __shared__ double sh[8];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s = fma((double)phi[i], (double)resp[i], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x % 32 == 0) sh[threadIdx.x / 32] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)blockDim.x / 32; ++w) s += sh[w];
+        atomicAdd(out, s);
+    }
+}
+
 }  // namespace sn
 
 using namespace sn;
 
 extern "C" {
+
+sn_status sn_response(sn_handle h, const void *phi, const void *resp, double *R)
+{
+    if (!h || !phi || !resp || !R) return fail(h, SN_EINVAL, "sn_response: NULL argument");
+    const cudaStream_t st = h->stream;
+    const int64_t n = (int64_t)h->G * h->ncell * 8;
+    int64_t grid = (n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    SN_CK(h, cudaMemsetAsync(h->acc + ACC_RESP, 0, sizeof(double), st));
+    if (h->fp64)
+        response_kernel<double><<<(unsigned)grid, 256, 0, st>>>((const double *)phi, (const double *)resp, n,
+                                                                 h->acc + ACC_RESP);
+    else
+        response_kernel<float><<<(unsigned)grid, 256, 0, st>>>((const float *)phi, (const float *)resp, n,
+                                                               h->acc + ACC_RESP);
+    SN_CK(h, cudaGetLastError());
+    SN_CK(h, cudaMemcpyAsync(h->acc_host + ACC_RESP, h->acc + ACC_RESP, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SN_CK(h, cudaStreamSynchronize(st));
+    *R = h->acc_host[ACC_RESP];
+    return SN_OK;
+}
+
 
 sn_status sn_adjoint_sweep(sn_handle h, const float *phi, const float *resp, double tol, int32_t max_it, float *Lam,
                            double *dR_dsigt, double *dR_dsigs, double *dR_dq, int32_t *iters)

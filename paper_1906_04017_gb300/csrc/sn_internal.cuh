@@ -165,7 +165,8 @@ enum AccSlot {
     ACC_MEANN = 6,     // number of terms in ACC_MEAN
     ACC_FLAG = 7,      // non-zero: a non-finite flux value was seen
     ACC_HARVEST = 8,   // sn_harvest: number of solves picked (unsigned 64-bit)
-    ACC_COUNT = 9
+    ACC_RESP = 9,      // sn_response: sum resp * phi
+    ACC_COUNT = 10
 };
 
 }  // namespace sn

@@ -91,6 +91,7 @@ _API = [
                                           ctypes.POINTER(ctypes.c_int64)]),
     ("sn_adjoint_sweep", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_double, ctypes.c_int32, _fp, _fp, _fp,
                                         _fp, ctypes.POINTER(ctypes.c_int32)]),
+    ("sn_response", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, _dp]),
     ("sn_surrogate_grad_noalloc", ctypes.c_int, [_fp, _fp, _fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
     ("sn_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
@@ -403,3 +404,53 @@ class Problem:
         if not (st == SN_ENOCONV and allow_noconv):
             _check(st, self.h)
         return dict(Lam=Lam, grad_sigt=gt, grad_sigs=gs, grad_q=gq, iters=it.value, converged=(st == SN_OK))
+
+    def response(self, phi, resp):
+        """R = sum resp * phi (device [G, ncell, 8] tensors of the handle's dtype), FP64."""
+        self._sync_stream()
+        R = ctypes.c_double(0.0)
+        _check(lib().sn_response(self.h, _dev(phi, self.dtype, (self.ncell, 8)), _dev(resp, self.dtype, (self.ncell, 8)),
+                                 ctypes.byref(R)), self.h)
+        return R.value
+
+
+class DetectorResponse(torch.autograd.Function):
+    """R(sigma_t, sigma_s, q) = sum resp * phi of the converged source iteration, as a
+    differentiable function of the per-cell, per-group cross sections and source
+    (tensors of the workload's [G, ...] shape); backward runs the discrete adjoint
+    (sn_adjoint_sweep).  The other fields (mesh, quadrature order, transfer matrix,
+    inflow) come from the workload dict ``wl``; ``resp`` is dR/dphi [G, ncell, 8].
+
+        R = DetectorResponse.apply(sigt, sigs, q, wl, resp, tol, max_it)
+    """
+
+    @staticmethod
+    def forward(ctx, sigt, sigs, q, wl, resp, tol=1e-6, max_it=500):
+        w = dict(wl)
+        for k, v in (("sigt", sigt), ("sigs", sigs), ("q", q)):
+            w[k] = v.detach().to("cpu", torch.float64).numpy()
+        P = Problem(w)
+        try:
+            fwd = P.source_iterate(tol=tol, max_it=max_it)
+            r = resp.detach().to(device="cuda", dtype=torch.float32).reshape(P.G, P.ncell, 8).contiguous()
+            R = P.response(fwd["phi"], r)
+        except Exception:
+            P.close()
+            raise
+        ctx.P, ctx.phi, ctx.r, ctx.tol, ctx.max_it = P, fwd["phi"], r, tol, max_it
+        ctx.shapes = [(t.shape, t.dtype, t.device) for t in (sigt, sigs, q)]
+        return torch.tensor(R, dtype=torch.float64, device=sigt.device)
+
+    @staticmethod
+    def backward(ctx, gR):
+        P = ctx.P
+        try:
+            adj = P.adjoint(ctx.phi, ctx.r, tol=ctx.tol, max_it=ctx.max_it)
+        finally:
+            P.close()
+            ctx.P = None
+        out = []
+        for key, (shape, dtype, device) in zip(("grad_sigt", "grad_sigs", "grad_q"), ctx.shapes):
+            g = adj[key].to(device=device) * gR.to(device=device, dtype=torch.float64)
+            out.append(g.reshape(shape).to(dtype))
+        return out[0], out[1], out[2], None, None, None, None

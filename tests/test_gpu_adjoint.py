@@ -57,3 +57,58 @@ def test_adjoint_checkpoint_blocks_cover_every_plane(sn):
     ref = O.adjoint(phi, r, tol=1e-13, maxit=5000)
     got, want = adj["grad_sigt"].cpu().numpy(), ref["grad_sigt"]
     assert np.abs(got - want).max() < 1e-4 * np.abs(want).max()
+
+
+def test_detector_response_autograd_matches_oracle(sn):
+    """DetectorResponse (torch.autograd.Function over sn_source_iterate, sn_response
+    and sn_adjoint_sweep): R and its gradients against the oracle."""
+    wl = W.random_small(6, 5, 4, order=4, G=2, seed=11, psi_inc=True)
+    r = corner_response(wl, 2)
+    sigt, sigs, q = (torch.tensor(wl[k], dtype=torch.float64, requires_grad=True) for k in ("sigt", "sigs", "q"))
+    R = sn.DetectorResponse.apply(sigt, sigs, q, wl, torch.from_numpy(r), 1e-6, 2000)
+    R.backward()
+    O = oracle.OracleProblem(wl)
+    phi = O.source_iterate(1e-13, 5000)["phi"]
+    ref = O.adjoint(phi, r, tol=1e-13, maxit=5000)
+    R_ref = float((r * phi).sum())
+    assert abs(R.item() - R_ref) < 1e-5 * abs(R_ref)
+    for t, key in ((sigt, "grad_sigt"), (sigs, "grad_sigs"), (q, "grad_q")):
+        want = ref[key]
+        assert np.abs(t.grad.numpy() - want).max() < 1e-4 * np.abs(want).max(), key
+
+
+def test_adjoint_matches_fp64_central_differences(sn):
+    """FP32 adjoint gradients against central differences (relative step 1e-6) of R
+    from FP64 GPU source iterations (SN_SOLVE_GE64), warm-started from the
+    unperturbed flux, for parameters of every kind."""
+    wl = W.random_small(5, 6, 4, order=4, G=2, seed=4, psi_inc=True)
+    r = corner_response(wl, 2)
+    P = sn.Problem(wl)
+    fwd = P.source_iterate(tol=1e-6, max_it=2000)
+    adj = P.adjoint(fwd["phi"], torch.from_numpy(r.astype(np.float32)).cuda(), tol=1e-6, max_it=2000)
+    P.close()
+    P64 = sn.Problem(wl, fp64=True)
+    base = P64.source_iterate(tol=1e-13, max_it=5000)["phi"]
+    P64.close()
+    r64 = torch.from_numpy(r).cuda()
+
+    def R_of(key, idx, val):
+        w = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in wl.items()}
+        w[key][idx] = val
+        Q = sn.Problem(w, fp64=True)
+        phi = base.clone()
+        Q.source_iterate(phi=phi, tol=1e-13, max_it=5000)
+        R = Q.response(phi, r64)
+        Q.close()
+        return R
+
+    rng = np.random.default_rng(0)
+    for key, gkey in (("sigt", "grad_sigt"), ("sigs", "grad_sigs"), ("q", "grad_q")):
+        g = adj[gkey].cpu().numpy()
+        # parameters whose gradient is at least 10% of the largest of their kind
+        cand = np.argwhere(np.abs(g) >= 0.1 * np.abs(g).max())
+        for gi, ci in cand[rng.choice(len(cand), min(4, len(cand)), replace=False)]:
+            p = wl[key][gi, ci]
+            h = 1e-6 * (p if p > 0 else 1.0)
+            fd = (R_of(key, (gi, ci), p + h) - R_of(key, (gi, ci), p - h)) / (2 * h)
+            assert abs(g[gi, ci] - fd) <= 1e-4 * abs(fd), (key, gi, ci, g[gi, ci], fd)
