@@ -6,17 +6,19 @@
 // Network: Eq. (15) with 27 inputs, 64 ReLU hidden units and 8 linear outputs.
 // Parameters (2312, FP32 masters): W1[64][27], b1[64], W2[8][64], b2[8].
 //
-// Inference (ann_cells_kernel): a CTA of 128 threads owns a 128-problem tile.  Each
-// thread builds its problem's 27 inputs, rounds them to BF16 and writes one row of
-// the A operand in shared memory; one thread issues tcgen05.mma (M=128, N=64, K=16,
-// twice) with the accumulator in tensor memory; the four warps read their 32 TMEM
-// lanes back (tcgen05.ld), add b1, apply ReLU, write the BF16 hidden tile and the
-// second layer runs the same way (N=16, only 8 columns used).
+// Inference: a CTA of 128 threads owns a 128-row tile.  Each thread builds its
+// row's 27 inputs, rounds them to BF16 and writes one row of the A operand in shared
+// memory (with two columns of ones that carry b1); one thread issues tcgen05.mma
+// (M=128, N=64, K=16, twice) with the accumulator in tensor memory; the four warps
+// read their 32 TMEM lanes back (tcgen05.ld), apply ReLU, round to BF16 and store the
+// hidden tile back into tensor memory (tcgen05.st), where the second layer reads its
+// A operand (N=16, only 8 columns used); b2 is added in FP32.
 //
 // Shared-memory operands use the no-swizzle K-major core-matrix layout: a core
 // matrix is 8 rows x 16 bytes, stored row after row; core matrices follow each other
 // along K every 128 bytes (leading byte offset) and along M/N every K/8 * 128 bytes
 // (stride byte offset).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -132,13 +134,13 @@ __host__ __device__ constexpr uint32_t umma_off(int row, int k, int kdim)
 }
 
 constexpr int kTile = 128;
-constexpr int kK1 = 32;                        // 27 inputs padded
+constexpr int kK1 = 32;                        // 27 inputs, 2 bias columns, 3 zero
 constexpr int kN2 = 16;                        // 8 outputs padded
 constexpr uint32_t kW1Bytes = kNhid * kK1 * 2; // 4096
 constexpr uint32_t kW2Bytes = kN2 * kNhid * 2; // 2048
 constexpr uint32_t kXBytes = kTile * kK1 * 2;  // 8192
 constexpr uint32_t kHBytes = kTile * kNhid * 2;// 16384
-constexpr uint32_t kTmemCols = 64;   // layer 1 uses columns 0..63, layer 2 reuses 0..15
+constexpr uint32_t kTmemCols = 64;   // layer 1: 0..63; hidden BF16 pairs: 0..31; layer 2: 32..47
 
 struct Net {
     float *p = nullptr;        // [kNparam] FP32 master weights
@@ -154,6 +156,8 @@ struct Net {
     int64_t gpart_blocks = 0;
     unsigned long long *counter = nullptr;   // [0] fallbacks, [1] error flags
     double *dacc = nullptr;    // scratch accumulator
+    uint32_t *fb_queue = nullptr;   // gated sweep: rows rejected on the current hyperplane
+    uint32_t *fb_count = nullptr;   // [nplanes] queue lengths
 };
 
 static Net *net_of(sn_handle h) { return reinterpret_cast<Net *>(h->net); }
@@ -162,7 +166,8 @@ void free_net(sn_handle h)
 {
     if (!h || !h->net) return;
     Net *n = net_of(h);
-    void *bufs[] = {n->p, n->m, n->v, n->w1p, n->w2p, n->b1, n->b2, n->gpart, n->lpart, n->counter, n->dacc};
+    void *bufs[] = {n->p, n->m, n->v, n->w1p, n->w2p, n->b1, n->b2, n->gpart, n->lpart, n->counter, n->dacc,
+                    n->fb_queue, n->fb_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete n;
@@ -187,6 +192,13 @@ static sn_status ensure_net(sn_handle h)
     SN_CK(h, cudaMemset(n->m, 0, sizeof(float) * kNparam));
     SN_CK(h, cudaMemset(n->v, 0, sizeof(float) * kNparam));
     SN_CK(h, cudaMemset(n->counter, 0, sizeof(unsigned long long) * 2));
+    // fallback queue of the gated sweep: every row of the largest hyperplane's tiles
+    int64_t max_cells = 0;
+    for (int p = 0; p < h->nplanes; ++p) max_cells = std::max(max_cells, h->plane_off[p + 1] - h->plane_off[p]);
+    const int64_t kpt = kTile / h->Do;
+    const int64_t max_tiles = (max_cells * h->G + kpt - 1) / kpt;
+    SN_CK(h, cudaMalloc(&n->fb_queue, sizeof(uint32_t) * (size_t)(8 * max_tiles * kTile)));
+    SN_CK(h, cudaMalloc(&n->fb_count, sizeof(uint32_t) * (size_t)h->nplanes));
     return SN_OK;
 }
 
@@ -384,14 +396,17 @@ __global__ void __launch_bounds__(128) mae_kernel(const float *__restrict__ P, c
     if (threadIdx.x == 0) atomicAdd(acc, sl[0] + sl[1] + sl[2] + sl[3]);
 }
 
-// FP32 masters -> BF16 operands in the tcgen05 layout, biases copied.
+// FP32 masters -> BF16 operands in the tcgen05 layout.  W1 carries b1 in two columns
+// (bf16(b1) and bf16(b1 - bf16(b1))) that meet the two columns of ones in X; b2 stays
+// FP32 (added to the layer-2 accumulator).
 __global__ void pack_kernel(const float *__restrict__ P, unsigned char *__restrict__ w1p,
                             unsigned char *__restrict__ w2p, float *__restrict__ b1, float *__restrict__ b2)
 {
     const float *W1 = P, *B1 = P + kNhid * kNin, *W2 = B1 + kNhid, *B2 = W2 + kNout * kNhid;
     for (int e = threadIdx.x; e < kNhid * kK1; e += blockDim.x) {
         const int n = e / kK1, k = e % kK1;
-        const float v = k < kNin ? W1[n * kNin + k] : 0.f;
+        const float hi = __bfloat162float(__float2bfloat16_rn(B1[n]));
+        const float v = k < kNin ? W1[n * kNin + k] : (k == kNin ? hi : (k == kNin + 1 ? B1[n] - hi : 0.f));
         *reinterpret_cast<__nv_bfloat16 *>(w1p + umma_off(n, k, kK1)) = __float2bfloat16_rn(v);
     }
     for (int e = threadIdx.x; e < kN2 * kNhid; e += blockDim.x) {
@@ -404,22 +419,24 @@ __global__ void pack_kernel(const float *__restrict__ P, unsigned char *__restri
 }
 
 // --------------------------------------------------------------------------------
-// tcgen05 inference over independent one-cell problems (+ residual gate).
+// tcgen05 inference.
+//
+// Both inference kernels run a 128-row tile as follows.  Each thread writes its row
+// of X (27 features, then two columns of ones that carry b1 = bf16(b1) +
+// bf16(b1 - bf16(b1)) through the first product, then zeros) in BF16 to shared
+// memory; one thread issues layer 1 (M=128, N=64, K=32) into TMEM columns 0..63;
+// each warp reads its 32 lanes back, applies ReLU, rounds to BF16 and writes the
+// hidden tile H back into TMEM columns 0..31 (two BF16 per column); one thread
+// issues layer 2 with A = H read from TMEM (M=128, N=16, K=64) into columns 32..47;
+// each thread reads its 8 outputs and adds b2.  Shared memory holds only W1, W2
+// and X, and TMEM 64 columns, so eight CTAs fit on an SM.
 // --------------------------------------------------------------------------------
 struct AnnArgs {
     const unsigned char *w1p, *w2p;
-    const float *b1, *b2;
+    const float *b2;
     float tau;
     unsigned long long *counter;   // [0] fallbacks, [1] timeouts
 };
-
-constexpr uint32_t kOffW1 = 0, kOffW2 = kOffW1 + kW1Bytes, kOffX = kOffW2 + kW2Bytes, kOffH = kOffX + kXBytes;
-constexpr uint32_t kOffB = kOffH + kHBytes;                   // b1[64], b2[16]
-constexpr uint32_t kOffStage = kOffB + 4 * (kNhid + kN2);      // [128][27] floats
-constexpr uint32_t kOffBar = kOffStage + 4 * kTile * 27;
-constexpr uint32_t kOffMisc = kOffBar + 8;                     // tmem slot, queue count, abort
-constexpr uint32_t kOffQueue = kOffMisc + 16;                  // [128] ints
-constexpr uint32_t kAnnSmem = kOffQueue + 4 * kTile;
 
 // Two FP32 values rounded to BF16 and packed, the first in the low half (lower address).
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
@@ -428,139 +445,176 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
     return *reinterpret_cast<const uint32_t *>(&t);
 }
 
-// Write one row of a BF16 operand tile from FP32 values (kdim multiple of 8).
-template <int KDIM>
-__device__ __forceinline__ void write_row_bf16(unsigned char *base, int row, const float *v)
+// max(a, 0), max(b, 0) rounded to BF16 and packed, a in the low half.
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(uint32_t a, uint32_t b)
 {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(b)), "f"(__uint_as_float(a)));
+    return d;
+}
+
+// The X row of thread `row` (features, bias ones, zero padding) as BF16, 4 x 16 bytes.
+__device__ __forceinline__ void write_x_row(unsigned char *sx, int row, const float (&x)[kNin], bool live)
+{
+    float v[kK1];
 #pragma unroll
-    for (int kg = 0; kg < KDIM / 8; ++kg) {
+    for (int k = 0; k < kNin; ++k) v[k] = live ? x[k] : 0.f;
+    v[kNin] = v[kNin + 1] = live ? 1.f : 0.f;
+#pragma unroll
+    for (int k = kNin + 2; k < kK1; ++k) v[k] = 0.f;
+#pragma unroll
+    for (int kg = 0; kg < kK1 / 8; ++kg) {
         uint4 u;
         u.x = pack_bf16x2(v[kg * 8 + 0], v[kg * 8 + 1]);
         u.y = pack_bf16x2(v[kg * 8 + 2], v[kg * 8 + 3]);
         u.z = pack_bf16x2(v[kg * 8 + 4], v[kg * 8 + 5]);
         u.w = pack_bf16x2(v[kg * 8 + 6], v[kg * 8 + 7]);
-        *reinterpret_cast<uint4 *>(base + umma_off(row, kg * 8, KDIM)) = u;
+        *reinterpret_cast<uint4 *>(sx + umma_off(row, kg * 8, kK1)) = u;
     }
 }
 
-// Two-layer forward of the 128 rows staged in sX; each thread gets its row's 8 outputs.
-// Returns false if a wait timed out (then the CTA must stop).
-__device__ __forceinline__ bool mlp_tile(unsigned char *smem, uint32_t tbase, uint32_t &phase, float (&o)[8])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
-    const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar = sbase + kOffBar;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kOffMisc + 8);
-    const float *sb1 = reinterpret_cast<const float *>(smem + kOffB), *sb2 = sb1 + kNhid;
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (threadIdx.x == 0) {
-        constexpr uint32_t id1 = idesc_bf16(128, kNhid);
-#pragma unroll
-        for (int kk = 0; kk < kK1 / 16; ++kk)
-            umma_bf16(tbase, sdesc(sbase + kOffX + kk * 256, 128, (kK1 / 8) * 128),
-                      sdesc(sbase + kOffW1 + kk * 256, 128, (kK1 / 8) * 128), id1, kk > 0);
-        umma_commit(bar);
-    }
-    if (!mbar_wait_bounded(bar, phase)) *abort_flag = 1;
-    phase ^= 1u;
-    __syncthreads();
-    if (*abort_flag) return false;
-    tc_fence_after();
-    __syncwarp();
-    const uint32_t lane_base = tbase + ((uint32_t)(threadIdx.x & ~31) << 16);
-    // 16 hidden units at a time: bias, ReLU, BF16, two 16-byte stores into H
-#pragma unroll
-    for (int c = 0; c < kNhid / 16; ++c) {
-        float v[16];
-        tmem_ld16(lane_base + 16 * c, v);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = fmaxf(v[u] + sb1[16 * c + u], 0.f);
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-            uint4 q;
-            q.x = pack_bf16x2(v[8 * hf + 0], v[8 * hf + 1]);
-            q.y = pack_bf16x2(v[8 * hf + 2], v[8 * hf + 3]);
-            q.z = pack_bf16x2(v[8 * hf + 4], v[8 * hf + 5]);
-            q.w = pack_bf16x2(v[8 * hf + 6], v[8 * hf + 7]);
-            *reinterpret_cast<uint4 *>(smem + kOffH + umma_off(threadIdx.x, 16 * c + 8 * hf, kNhid)) = q;
-        }
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (threadIdx.x == 0) {
-        constexpr uint32_t id2 = idesc_bf16(128, kN2);
-#pragma unroll
-        for (int kk = 0; kk < kNhid / 16; ++kk)
-            umma_bf16(tbase, sdesc(sbase + kOffH + kk * 256, 128, (kNhid / 8) * 128),
-                      sdesc(sbase + kOffW2 + kk * 256, 128, (kNhid / 8) * 128), id2, kk > 0);
-        umma_commit(bar);
-    }
-    if (!mbar_wait_bounded(bar, phase)) *abort_flag = 1;
-    phase ^= 1u;
-    __syncthreads();
-    if (*abort_flag) return false;
-    tc_fence_after();
-    __syncwarp();
-    float v[16];
-    tmem_ld16(lane_base, v);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) o[q] = v[q] + sb2[q];
-    return true;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
 }
 
-// Per-CTA set-up shared by the inference kernels: weights to shared memory, the
-// mbarrier, and 128 TMEM columns.
-__device__ __forceinline__ uint32_t ann_setup(unsigned char *smem, const AnnArgs &a)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] * B[smem]^T, BF16 inputs, FP32 accumulate, cta_group::1
+__device__ __forceinline__ void umma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// Layer 1 of the tile in X (issued by thread 0; completion arrives on the barrier).
+__device__ __forceinline__ void mma_layer1(uint32_t sbase, uint32_t offx, uint32_t offw1, uint32_t tbase, uint32_t bar)
+{
+    constexpr uint32_t id1 = idesc_bf16(128, kNhid);
+#pragma unroll
+    for (int kk = 0; kk < kK1 / 16; ++kk)
+        umma_bf16(tbase, sdesc(sbase + offx + kk * 256, 128, (kK1 / 8) * 128),
+                  sdesc(sbase + offw1 + kk * 256, 128, (kK1 / 8) * 128), id1, kk > 0);
+    umma_commit(bar);
+}
+
+// Layer 2 with A = H in TMEM columns 0..31, D in columns 32..47 (thread 0).
+__device__ __forceinline__ void mma_layer2(uint32_t sbase, uint32_t offw2, uint32_t tbase, uint32_t bar)
+{
+    constexpr uint32_t id2 = idesc_bf16(128, kN2);
+#pragma unroll
+    for (int kk = 0; kk < kNhid / 16; ++kk)
+        umma_bf16_ta(tbase + 32, tbase + 8 * kk, sdesc(sbase + offw2 + kk * 256, 128, (kNhid / 8) * 128), id2,
+                     kk > 0);
+    umma_commit(bar);
+}
+
+// This warp's lanes of the layer-1 accumulator -> ReLU -> BF16 pairs in columns 0..31.
+__device__ __forceinline__ void hidden_to_tmem(uint32_t twarp)
+{
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t v[32], h[16];
+        tmem_ld32(twarp + 32 * half, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[j] = pack_relu_bf16x2(v[2 * j], v[2 * j + 1]);
+        tmem_st16(twarp + 16 * half, h);
+    }
+    tmem_wait_st();
+}
+
+// Weights to shared memory, the mbarrier, 64 TMEM columns; returns the TMEM base.
+__device__ __forceinline__ uint32_t ann_setup(unsigned char *smem, const AnnArgs &a, uint32_t offw1, uint32_t offw2,
+                                              uint32_t offbar, int *misc)
 {
     const uint4 *g1 = reinterpret_cast<const uint4 *>(a.w1p), *g2 = reinterpret_cast<const uint4 *>(a.w2p);
-    uint4 *s1 = reinterpret_cast<uint4 *>(smem + kOffW1), *s2 = reinterpret_cast<uint4 *>(smem + kOffW2);
+    uint4 *s1 = reinterpret_cast<uint4 *>(smem + offw1), *s2 = reinterpret_cast<uint4 *>(smem + offw2);
     for (int e = threadIdx.x; e < (int)(kW1Bytes / 16); e += blockDim.x) s1[e] = g1[e];
     for (int e = threadIdx.x; e < (int)(kW2Bytes / 16); e += blockDim.x) s2[e] = g2[e];
-    float *sb = reinterpret_cast<float *>(smem + kOffB);
-    for (int e = threadIdx.x; e < kNhid; e += blockDim.x) sb[e] = a.b1[e];
-    for (int e = threadIdx.x; e < kN2; e += blockDim.x) sb[kNhid + e] = a.b2[e];
-    int *misc = reinterpret_cast<int *>(smem + kOffMisc);
     if (threadIdx.x == 0) {
         misc[1] = 0;   // queue count
         misc[2] = 0;   // abort flag
-        mbar_init(smem_u32(smem + kOffBar), 1);
+        mbar_init(smem_u32(smem + offbar), 1);
         fence_mbar_init();
     }
     __syncwarp();
     if (threadIdx.x < 32) {
-        tmem_alloc(smem_u32(smem + kOffMisc), kTmemCols);
+        tmem_alloc(smem_u32(misc), kTmemCols);
         tmem_relinquish();
     }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    return *reinterpret_cast<volatile uint32_t *>(smem + kOffMisc);
+    return *reinterpret_cast<volatile uint32_t *>(misc);
 }
 
-__device__ __forceinline__ void ann_teardown(unsigned char *smem, uint32_t tbase, const AnnArgs &a)
+__device__ __forceinline__ void ann_teardown(uint32_t tbase, const AnnArgs &a, const int *misc)
 {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x == 0 && reinterpret_cast<volatile int *>(smem + kOffMisc)[2]) atomicAdd(a.counter + 1, 1ull);
+    if (threadIdx.x == 0 && reinterpret_cast<const volatile int *>(misc)[2]) atomicAdd(a.counter + 1, 1ull);
     __syncwarp();
     if (threadIdx.x < 32) tmem_dealloc(tbase, kTmemCols);
 }
+
+// Independent one-cell problems (sn_surrogate_apply).  Rows the gate rejects are
+// queued in shared memory and re-solved by elimination by the whole CTA.
+constexpr uint32_t kCellOffW1 = 0, kCellOffW2 = kCellOffW1 + kW1Bytes, kCellOffX = kCellOffW2 + kW2Bytes;
+constexpr uint32_t kCellOffStage = kCellOffX + kXBytes;                 // [128][27] floats
+constexpr uint32_t kCellOffQueue = kCellOffStage + 4 * kTile * 27;      // [128] ints
+constexpr uint32_t kCellOffBar = kCellOffQueue + 4 * kTile;
+constexpr uint32_t kCellOffMisc = kCellOffBar + 8;                      // tmem slot, queue count, abort
+constexpr uint32_t kCellSmem = kCellOffMisc + 16;
 
 template <bool GATED>
 __global__ void __launch_bounds__(128, 4) ann_cells_kernel(const float *__restrict__ in27, float *__restrict__ out,
                                                            int64_t n, AnnArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t tbase = ann_setup(smem, a);
-    float *stage = reinterpret_cast<float *>(smem + kOffStage);
-    int *misc = reinterpret_cast<int *>(smem + kOffMisc);
-    int *queue = reinterpret_cast<int *>(smem + kOffQueue);
+    int *misc = reinterpret_cast<int *>(smem + kCellOffMisc);
+    const uint32_t tbase = ann_setup(smem, a, kCellOffW1, kCellOffW2, kCellOffBar, misc);
+    const uint32_t sbase = smem_u32(smem), bar = sbase + kCellOffBar;
+    const uint32_t twarp = tbase + ((uint32_t)(threadIdx.x & ~31) << 16);
+    float *stage = reinterpret_cast<float *>(smem + kCellOffStage);
+    int *queue = reinterpret_cast<int *>(smem + kCellOffQueue);
+    float b2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) b2[q] = a.b2[q];
     uint32_t phase = 0;
     unsigned long long nfb = 0;
     for (int64_t base = (int64_t)blockIdx.x * kTile; base < n; base += (int64_t)gridDim.x * kTile) {
@@ -576,19 +630,31 @@ __global__ void __launch_bounds__(128, 4) ann_cells_kernel(const float *__restri
             s = input_scale(c.S, c.ux, c.uy, c.uz);
             ann_features(fabsf(p[0]), fabsf(p[1]), fabsf(p[2]), p[3], p[4], p[5], c.sig, c.S, c.ux, c.uy, c.uz,
                          s > 0.f ? 1.f / s : 0.f, x);
-        } else {
-#pragma unroll
-            for (int k = 0; k < kNin; ++k) x[k] = 0.f;
         }
-        float xp[kK1];
-#pragma unroll
-        for (int k = 0; k < kK1; ++k) xp[k] = k < kNin ? x[k] : 0.f;
-        write_row_bf16<kK1>(smem + kOffX, t, xp);
-        float o[8];
-        if (!mlp_tile(smem, tbase, phase, o)) break;
+        write_x_row(smem + kCellOffX, t, x, t < cnt);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) mma_layer1(sbase, kCellOffX, kCellOffW1, tbase, bar);
+        bool late = !mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        hidden_to_tmem(twarp);
+        tc_fence_before();
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
+        tc_fence_after();
+        if (t == 0) mma_layer2(sbase, kCellOffW2, tbase, bar);
+        late = !mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t r[8];
+        tmem_ld8(twarp + 32, r);
+        tmem_wait_ld();
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
         float psi[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) psi[q] = s * o[q];
+        for (int q = 0; q < 8; ++q) psi[q] = s * (__uint_as_float(r[q]) + b2[q]);
         bool pass = true;
         if (GATED && t < cnt && s > 0.f) pass = gate_pass(c, psi, a.tau);
         if (t < cnt && pass) {
@@ -613,19 +679,24 @@ __global__ void __launch_bounds__(128, 4) ann_cells_kernel(const float *__restri
             __syncthreads();
             if (t == 0) misc[1] = 0;
         }
+        tc_fence_before();
         __syncthreads();
+        tc_fence_after();
     }
     if (GATED && threadIdx.x == 0 && nfb) atomicAdd(a.counter, nfb);
-    ann_teardown(smem, tbase, a);
+    ann_teardown(tbase, a, misc);
 }
 
 // --------------------------------------------------------------------------------
 // Surrogate sweep: one hyperplane of every octant, the per-cell elimination of the
 // wavefront replaced by the network (Sec. 4: "construction of the input vector and a
-// feed-forward evaluation"), with the residual gate and an in-CTA compacted
-// elimination pass for the cells that fail it.  Same keys, face planes and flux
-// reduction as sweep_plane_ge; a tile is one CTA of 128 threads = keys_per_tile keys x
-// Do directions (rows past that are idle MMA rows).
+// feed-forward evaluation").  Same keys, face planes and flux reduction as
+// sweep_plane_ge; a tile is 128 rows = keys_per_tile keys x Do directions (rows past
+// that are idle MMA rows).  The CTA loops over tiles; the inputs of the next tile
+// (inflow faces, source, sigma_t) are copied to shared memory with cp.async while
+// the current tile runs through the tensor cores.  With the residual gate, rejected
+// rows write nothing: they are appended to a per-hyperplane queue that
+// ann_fallback_kernel re-solves by elimination before the next hyperplane starts.
 // --------------------------------------------------------------------------------
 struct AnnSweepArgs {
     int nx, ny, nz, G, Do, ncells_plane, keys_per_tile, ntiles;   // tiles per octant
@@ -639,48 +710,59 @@ struct AnnSweepArgs {
     float *phi_oct;
     double *leak;
     float vol12, hx, hy, hz;
+    uint32_t *fb_queue;      // rejected rows: (tile << 10) | (octant << 7) | row
+    uint32_t *fb_count;      // this hyperplane's queue length
     AnnArgs ann;
 };
 
-// The sweep kernel reuses the staging area of the cell kernel for the flux reduction
-// ([128][9] floats) and the fallback results ([128][8] floats), so it needs no more
-// shared memory than the cell kernel: five CTAs fit on an SM (64 TMEM columns each).
-constexpr uint32_t kOffRed = kOffStage;
-constexpr uint32_t kOffDefer = kOffRed + 4 * kTile * 9;      // deferred rejected rows
-constexpr int kDeferCap = 1024;
-static_assert(kOffDefer + 4 * kDeferCap <= kOffBar, "sweep scratch must fit the staging area");
-constexpr uint32_t kSweepSmem = kAnnSmem;
+constexpr uint32_t kSwOffW1 = 0, kSwOffW2 = kSwOffW1 + kW1Bytes;
+constexpr uint32_t kSwOffX = kSwOffW2 + kW2Bytes;          // X tile; the flux reduction [128][9] reuses it
+constexpr uint32_t kSwOffFace = kSwOffX + kXBytes;         // [128 rows][12] inflow face values
+constexpr uint32_t kSwOffKey = kSwOffFace + kTile * 48;    // [128 keys][8] source
+constexpr uint32_t kSwOffSig = kSwOffKey + kTile * 32;     // [128 keys] sigma_t
+constexpr uint32_t kSwOffBar = kSwOffSig + kTile * 4;
+constexpr uint32_t kSwOffMisc = kSwOffBar + 8;             // tmem slot, (unused), abort
+constexpr uint32_t kSweepSmem = kSwOffMisc + 16;
+static_assert(4 * kTile * 9 <= kXBytes, "flux reduction must fit the X tile");
 
-// One row of a surrogate tile: the key (cell, group) and direction of thread t, and
-// the canonical one-cell problem read from the face planes, psi_inc, S and sigma_t.
-struct AnnRow {
-    bool active;
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Where one row of a tile sits: key (cell of the hyperplane, group) and direction d.
+struct SweepRow {
     int g, cell, ip, jp, kp;
     int64_t ix, iy, iz;
 };
 
-__device__ __forceinline__ AnnRow ann_row(const AnnSweepArgs &a, int o, int tile, int t, const DirData<float> &dd,
-                                          CanonCell<float> &c)
+__device__ __forceinline__ SweepRow sweep_row(const AnnSweepArgs &a, int o, uint32_t key, uint32_t pk, int d)
 {
-    AnnRow r;
-    const int Do = a.Do, lk = t / Do, d = t - lk * Do;
-    const uint32_t key = (uint32_t)tile * (uint32_t)a.keys_per_tile + (uint32_t)lk;
-    r.active = lk < a.keys_per_tile && key < (uint32_t)a.ncells_plane * (uint32_t)a.G;
-    r.g = r.cell = r.ip = r.jp = r.kp = 0;
-    r.ix = r.iy = r.iz = 0;
-    if (!r.active) return r;
+    SweepRow r;
     const uint32_t cidx = a.divG.div(key);
     r.g = (int)(key - cidx * (uint32_t)a.G);
-    const uint32_t pk = a.cells[cidx];
     r.ip = pk & 1023; r.jp = (pk >> 10) & 1023; r.kp = pk >> 20;
     const int i = (o & 1) ? a.nx - 1 - r.ip : r.ip;
     const int j = (o & 2) ? a.ny - 1 - r.jp : r.jp;
     const int k = (o & 4) ? a.nz - 1 - r.kp : r.kp;
     r.cell = i + a.nx * (j + a.ny * k);
-    const int GD = a.G * Do, gd = r.g * Do + d;
+    const int GD = a.G * a.Do, gd = r.g * a.Do + d;
     r.ix = (int64_t)(o * a.ny * a.nz + r.jp + a.ny * r.kp) * GD + gd;
     r.iy = (int64_t)(o * a.nx * a.nz + r.ip + a.nx * r.kp) * GD + gd;
     r.iz = (int64_t)(o * a.nx * a.ny + r.ip + a.nx * r.jp) * GD + gd;
+    return r;
+}
+
+// One row of the canonical problem read with plain loads (fallback kernel).
+__device__ __forceinline__ void load_canon(const AnnSweepArgs &a, int o, const SweepRow &r, const DirData<float> &dd,
+                                           CanonCell<float> &c)
+{
     const int g = r.g;
     if (r.ip == 0) { const float v = a.psi_inc[6 * g + (o & 1)]; c.ux[0] = c.ux[1] = c.ux[2] = c.ux[3] = v; }
     else load4(c.ux, a.fx + r.ix);
@@ -699,108 +781,172 @@ __device__ __forceinline__ AnnRow ann_row(const AnnSweepArgs &a, int o, int tile
     mirror8(c.S, o);
     c.t3x = dd.t3x; c.t3y = dd.t3y; c.t3z = dd.t3z;
     c.mask = o;
-    return r;
 }
 
-// Re-solve the deferred rejected rows of this CTA by elimination, all threads at once:
-// write their outflow faces and add w_d psi to the flux partial written by their tile.
-__device__ __forceinline__ void ann_flush_deferred(const AnnSweepArgs &a, int o, const uint32_t *defer, int n,
-                                                   float &leak)
+// Outflow faces (or leakage) of a solved row.
+__device__ __forceinline__ void store_outflow(const AnnSweepArgs &a, const SweepRow &r, const DirData<float> &dd,
+                                              const float (&psi)[8], float &leak)
 {
-    for (int qi = threadIdx.x; qi < n; qi += blockDim.x) {
-        const uint32_t e = defer[qi];
-        const int tile = (int)(e >> 8), row = (int)(e & 255u);
-        const int rd = row % a.Do;
-        const DirData<float> dd = a.dir[rd];
-        CanonCell<float> c;
-        const AnnRow r = ann_row(a, o, tile, row, dd, c);
-        float psi[8];
-        cell_solve_canonical<float, true>(c.t3x, c.t3y, c.t3z, c.sig, c.S, c.ux, c.uy, c.uz, psi);
-        if (r.ip < a.nx - 1) store4(a.fx + r.ix, psi[1], psi[3], psi[5], psi[7]);
-        else leak += dd.w * a.vol12 * dd.t3x * (psi[1] + psi[3] + psi[5] + psi[7]);
-        if (r.jp < a.ny - 1) store4(a.fy + r.iy, psi[2], psi[3], psi[6], psi[7]);
-        else leak += dd.w * a.vol12 * dd.t3y * (psi[2] + psi[3] + psi[6] + psi[7]);
-        if (r.kp < a.nz - 1) store4(a.fz + r.iz, psi[4], psi[5], psi[6], psi[7]);
-        else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
-        float *dst = a.phi_oct + (((int64_t)o * a.C + r.cell) * a.G + r.g) * 8;
-#pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2) atomicAdd(dst + (n2 ^ o), dd.w * psi[n2]);
-    }
+    if (r.ip < a.nx - 1) store4(a.fx + r.ix, psi[1], psi[3], psi[5], psi[7]);
+    else leak += dd.w * a.vol12 * dd.t3x * (psi[1] + psi[3] + psi[5] + psi[7]);
+    if (r.jp < a.ny - 1) store4(a.fy + r.iy, psi[2], psi[3], psi[6], psi[7]);
+    else leak += dd.w * a.vol12 * dd.t3y * (psi[2] + psi[3] + psi[6] + psi[7]);
+    if (r.kp < a.nz - 1) store4(a.fz + r.iz, psi[4], psi[5], psi[6], psi[7]);
+    else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
 }
 
-// Rows the gate rejects are not re-solved inside their tile (that would stall the
-// whole CTA on a few lanes): they are queued and re-solved together by every thread
-// of the CTA when the queue fills and after the last tile.  Their faces are only read
-// by the next hyperplane (another launch), so the deferral is safe; their flux is
-// added to the tile's partial with atomics.
 template <bool GATED>
-__global__ void __launch_bounds__(128, GATED ? 4 : 5) sweep_plane_ann(AnnSweepArgs a)
+__global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t tbase = ann_setup(smem, a.ann);
-    float *red = reinterpret_cast<float *>(smem + kOffRed);
-    uint32_t *defer = reinterpret_cast<uint32_t *>(smem + kOffDefer);
-    int *misc = reinterpret_cast<int *>(smem + kOffMisc);
-    const int o = blockIdx.y, t = threadIdx.x, Do = a.Do;
+    int *misc = reinterpret_cast<int *>(smem + kSwOffMisc);
+    const uint32_t tbase = ann_setup(smem, a.ann, kSwOffW1, kSwOffW2, kSwOffBar, misc);
+    const uint32_t sbase = smem_u32(smem), bar = sbase + kSwOffBar;
+    const int t = threadIdx.x;
+    const uint32_t twarp = tbase + ((uint32_t)(t & ~31) << 16);
+    float *red = reinterpret_cast<float *>(smem + kSwOffX);
+    const int o = blockIdx.y, Do = a.Do;
     const int lk = t / Do, d = t - lk * Do;
+    const bool lane_row = lk < a.keys_per_tile;
+    const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
     DirData<float> dd = {0.f, 0.f, 0.f, 0.f};
     float4 dab = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (lk < a.keys_per_tile) {
+    if (lane_row) {
         dd = a.dir[d];
         dab = a.dir_abs[d];
     }
+    float b2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) b2[q] = a.ann.b2[q];
     const float lhx = (logf(a.hx) + kLogHShift) / kLogHScale;
     const float lhy = (logf(a.hy) + kLogHShift) / kLogHScale;
     const float lhz = (logf(a.hz) + kLogHShift) / kLogHScale;
+    const uint32_t sface = sbase + kSwOffFace + 48 * t;
+    const float *fface = reinterpret_cast<const float *>(smem + kSwOffFace) + 12 * t;
+    const uint32_t skey = sbase + kSwOffKey + 32 * lk;
+    const float *fkey = reinterpret_cast<const float *>(smem + kSwOffKey) + 8 * lk;
+    const float *fsig = reinterpret_cast<const float *>(smem + kSwOffSig) + lk;
+
+    // copy a row's inputs into the stage (the key's source and sigma_t by its first
+    // directions; boundary faces are taken from psi_inc when they are used)
+    auto prefetch = [&](uint32_t key, uint32_t pk) {
+        const SweepRow r = sweep_row(a, o, key, pk, d);
+        if (r.ip > 0) cp_async16(sface, a.fx + r.ix);
+        if (r.jp > 0) cp_async16(sface + 16, a.fy + r.iy);
+        if (r.kp > 0) cp_async16(sface + 32, a.fz + r.iz);
+        const int64_t gc = (int64_t)r.g * a.C + r.cell;
+        for (int q = d; q < 3; q += Do) {
+            if (q < 2) cp_async16(skey + 16 * q, a.S + gc * 8 + 4 * q);
+            else cp_async4(sbase + kSwOffSig + 4 * lk, a.sigt + gc);
+        }
+    };
+
+    int tile = blockIdx.x;
+    uint32_t key = (uint32_t)tile * (uint32_t)a.keys_per_tile + (uint32_t)lk;
+    bool act = lane_row && key < nkeys;
+    uint32_t pk = act ? a.cells[a.divG.div(key)] : 0u;
+    if (act) prefetch(key, pk);
+    cp_async_commit();
     uint32_t phase = 0;
-    unsigned long long nfb = 0;
     float leak = 0.f;
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    unsigned long long nq_total = 0;
+    for (; tile < a.ntiles; tile += gridDim.x) {
+        // the next tile's cell index: its latency hides behind this tile's work
+        const int tn = tile + gridDim.x;
+        const uint32_t key_n = (uint32_t)tn * (uint32_t)a.keys_per_tile + (uint32_t)lk;
+        const bool act_n = lane_row && tn < a.ntiles && key_n < nkeys;
+        const uint32_t pk_n = act_n ? a.cells[a.divG.div(key_n)] : 0u;
+        cp_async_wait_all();
+        __syncthreads();
+        // features from the stage
         CanonCell<float> c;
-        const AnnRow r = ann_row(a, o, tile, t, dd, c);
         float s = 0.f;
+        int g = 0;
         {
-            float xp[kK1];
+            float x[kNin];
+            if (act) {
+                g = (int)(key - a.divG.div(key) * (uint32_t)a.G);
+                const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
 #pragma unroll
-            for (int k = 0; k < kK1; ++k) xp[k] = 0.f;
-            if (r.active) {
+                for (int q = 0; q < 4; ++q) {
+                    c.ux[q] = ip ? fface[q] : a.psi_inc[6 * g + (o & 1)];
+                    c.uy[q] = jp ? fface[4 + q] : a.psi_inc[6 * g + 2 + ((o >> 1) & 1)];
+                    c.uz[q] = kp ? fface[8 + q] : a.psi_inc[6 * g + 4 + ((o >> 2) & 1)];
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) c.S[q] = fkey[q];
+                mirror8(c.S, o);
+                c.sig = *fsig;
+                c.t3x = dd.t3x; c.t3y = dd.t3y; c.t3z = dd.t3z;
+                c.mask = o;
                 s = input_scale(c.S, c.ux, c.uy, c.uz);
-                float x[kNin];
                 ann_features(dab.x, dab.y, dab.z, a.hx, a.hy, a.hz, c.sig, c.S, c.ux, c.uy, c.uz,
                              s > 0.f ? 1.f / s : 0.f, x);
                 x[3] = lhx; x[4] = lhy; x[5] = lhz;
-#pragma unroll
-                for (int k = 0; k < kNin; ++k) xp[k] = x[k];
             }
-            write_row_bf16<kK1>(smem + kOffX, t, xp);
+            write_x_row(smem + kSwOffX, t, x, act);
         }
-        float out[8];
-        if (!mlp_tile(smem, tbase, phase, out)) break;
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) mma_layer1(sbase, kSwOffX, kSwOffW1, tbase, bar);
+        // the stage is free: fetch the next tile while this one is in the tensor cores
+        if (act_n) prefetch(key_n, pk_n);
+        cp_async_commit();
+        bool late = !mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        hidden_to_tmem(twarp);
+        tc_fence_before();
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
+        tc_fence_after();
+        if (t == 0) mma_layer2(sbase, kSwOffW2, tbase, bar);
+        late = !mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t r8[8];
+        tmem_ld8(twarp + 32, r8);
+        tmem_wait_ld();
         float psi[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) psi[q] = s * out[q];
-        bool keep = r.active;
-        if (GATED && r.active && s != 0.f && !gate_pass(c, psi, a.ann.tau)) {
-            keep = false;
-            defer[atomicAdd(&misc[1], 1)] = ((uint32_t)tile << 8) | (uint32_t)t;
+        for (int q = 0; q < 8; ++q) psi[q] = s * (__uint_as_float(r8[q]) + b2[q]);
+        bool keep = act;
+        if (GATED) {
+            const bool reject = act && s != 0.f && !gate_pass(c, psi, a.ann.tau);
+            keep = act && !reject;
+            const unsigned m = __ballot_sync(0xffffffffu, reject);
+            if (m) {
+                const int lane = t & 31, leader = __ffs(m) - 1;
+                uint32_t base = 0;
+                if (lane == leader) base = atomicAdd(a.fb_count, (uint32_t)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (reject)
+                    a.fb_queue[base + __popc(m & ((1u << lane) - 1u))] =
+                        ((uint32_t)tile << 10) | ((uint32_t)o << 7) | (uint32_t)t;
+                if (lane == 0) nq_total += (unsigned long long)__popc(m);
+            }
         }
         float *rr = red + t * 9;
         if (keep) {
-            if (r.ip < a.nx - 1) store4(a.fx + r.ix, psi[1], psi[3], psi[5], psi[7]);
-            else leak += dd.w * a.vol12 * dd.t3x * (psi[1] + psi[3] + psi[5] + psi[7]);
-            if (r.jp < a.ny - 1) store4(a.fy + r.iy, psi[2], psi[3], psi[6], psi[7]);
-            else leak += dd.w * a.vol12 * dd.t3y * (psi[2] + psi[3] + psi[6] + psi[7]);
-            if (r.kp < a.nz - 1) store4(a.fz + r.iz, psi[4], psi[5], psi[6], psi[7]);
-            else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
+            const SweepRow r = sweep_row(a, o, key, pk, d);
+            store_outflow(a, r, dd, psi, leak);
 #pragma unroll
             for (int n = 0; n < 8; ++n) rr[n ^ o] = dd.w * psi[n];
         } else {
 #pragma unroll
             for (int n = 0; n < 8; ++n) rr[n] = 0.f;
         }
-        __syncthreads();
-        if (r.active) {
-            float *dst = a.phi_oct + (((int64_t)o * a.C + r.cell) * a.G + r.g) * 8;
+        tc_fence_before();
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
+        if (act) {
+            const uint32_t cidx = a.divG.div(key);
+            const int i = (o & 1) ? a.nx - 1 - (int)(pk & 1023) : (int)(pk & 1023);
+            const int j = (o & 2) ? a.ny - 1 - (int)((pk >> 10) & 1023) : (int)((pk >> 10) & 1023);
+            const int k = (o & 4) ? a.nz - 1 - (int)(pk >> 20) : (int)(pk >> 20);
+            const int cell = i + a.nx * (j + a.ny * k);
+            g = (int)(key - cidx * (uint32_t)a.G);
+            float *dst = a.phi_oct + (((int64_t)o * a.C + cell) * a.G + g) * 8;
             const float *base = red + (lk * Do) * 9;
             for (int n = d; n < 8; n += Do) {
                 float sum = 0.f;
@@ -808,31 +954,44 @@ __global__ void __launch_bounds__(128, GATED ? 4 : 5) sweep_plane_ann(AnnSweepAr
                 dst[n] = sum;
             }
         }
-        __syncthreads();
-        if (GATED) {
-            const int nq = misc[1];
-            if (nq > kDeferCap - kTile) {       // room for one more tile: flush now
-                ann_flush_deferred(a, o, defer, nq, leak);
-                __syncthreads();
-                if (t == 0) {
-                    nfb += (unsigned long long)nq;
-                    misc[1] = 0;
-                }
-                __syncthreads();
-            }
-        }
+        key = key_n;
+        pk = pk_n;
+        act = act_n;
     }
-    if (GATED) {
-        __syncthreads();
-        const int nq = reinterpret_cast<volatile int *>(misc)[1];
-        if (!reinterpret_cast<volatile int *>(misc)[2]) ann_flush_deferred(a, o, defer, nq, leak);
-        if (t == 0) nfb += (unsigned long long)nq;
+    cp_async_wait_all();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
+    if ((t & 31) == 0 && leak != 0.f) atomicAdd(a.leak, (double)leak);
+    if (GATED && (t & 31) == 0 && nq_total) atomicAdd(a.ann.counter, nq_total);
+    ann_teardown(tbase, a.ann, misc);
+}
+
+// Elimination of the rows the gate rejected on this hyperplane: outflow faces,
+// leakage, and w_d psi added to the tile's flux partial (atomics).
+__global__ void __launch_bounds__(128, 4) ann_fallback_kernel(AnnSweepArgs a)
+{
+    const uint32_t n = *reinterpret_cast<volatile const uint32_t *>(a.fb_count);
+    float leak = 0.f;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const uint32_t qv = a.fb_queue[e];
+        const int tile = (int)(qv >> 10), o = (int)((qv >> 7) & 7u), t = (int)(qv & 127u);
+        const int lk = t / a.Do, d = t - lk * a.Do;
+        const uint32_t key = (uint32_t)tile * (uint32_t)a.keys_per_tile + (uint32_t)lk;
+        const uint32_t pk = a.cells[a.divG.div(key)];
+        const SweepRow r = sweep_row(a, o, key, pk, d);
+        const DirData<float> dd = a.dir[d];
+        CanonCell<float> c;
+        load_canon(a, o, r, dd, c);
+        float psi[8];
+        cell_solve_canonical<float, true>(c.t3x, c.t3y, c.t3z, c.sig, c.S, c.ux, c.uy, c.uz, psi);
+        store_outflow(a, r, dd, psi, leak);
+        float *dst = a.phi_oct + (((int64_t)o * a.C + r.cell) * a.G + r.g) * 8;
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) atomicAdd(dst + (n2 ^ o), dd.w * psi[n2]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
     if ((threadIdx.x & 31) == 0 && leak != 0.f) atomicAdd(a.leak, (double)leak);
-    if (GATED && threadIdx.x == 0 && nfb) atomicAdd(a.ann.counter, nfb);
-    ann_teardown(smem, tbase, a.ann);
 }
 
 static sn_status pack_if_dirty(sn_handle h, cudaStream_t st)
@@ -849,7 +1008,7 @@ static AnnArgs ann_args(sn_handle h)
 {
     Net *n = net_of(h);
     AnnArgs a;
-    a.w1p = n->w1p; a.w2p = n->w2p; a.b1 = n->b1; a.b2 = n->b2; a.tau = n->tau; a.counter = n->counter;
+    a.w1p = n->w1p; a.w2p = n->w2p; a.b2 = n->b2; a.tau = n->tau; a.counter = n->counter;
     return a;
 }
 
@@ -874,6 +1033,7 @@ sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gat
 {
     sn_status s = pack_if_dirty(h, st);
     if (s != SN_OK) return s;
+    Net *net = net_of(h);
     AnnSweepArgs a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
     a.divG = FastDiv((uint32_t)h->G);
@@ -888,23 +1048,31 @@ sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gat
     a.leak = h->acc + ACC_LEAK;
     a.vol12 = (float)(h->dx * h->dy * h->dz / 12.0);
     a.hx = (float)h->dx; a.hy = (float)h->dy; a.hz = (float)h->dz;
+    a.fb_queue = net->fb_queue;
     a.ann = ann_args(h);
-    if (gated)
+    if (gated) {
         SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
-    else
+        SN_CK(h, cudaMemsetAsync(net->fb_count, 0, sizeof(uint32_t) * (size_t)h->nplanes, st));
+    } else {
         SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
-    const int cap = num_sms() * (gated ? 4 : 5) / 8;   // persistent CTAs per octant (4 or 5 per SM in total)
+    }
+    // persistent CTAs per octant: 6 (gated) or 8 per SM in total
+    const int cap = num_sms() * (gated ? 6 : 8) / 8;
+    const int fb_grid = num_sms() * 4;
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
     for (int p = 0; p < h->nplanes; ++p) {
         const int64_t n = h->plane_off[p + 1] - h->plane_off[p];
         a.cells = h->plane_cells + h->plane_off[p];
         a.ncells_plane = (int)n;
         a.ntiles = (int)((n * h->G + a.keys_per_tile - 1) / a.keys_per_tile);
+        a.fb_count = net->fb_count + p;
         const dim3 grid((unsigned)(a.ntiles < cap ? a.ntiles : cap), 8);
-        if (gated)
+        if (gated) {
             sweep_plane_ann<true><<<grid, kTile, kSweepSmem, st>>>(a);
-        else
+            ann_fallback_kernel<<<fb_grid, 128, 0, st>>>(a);
+        } else {
             sweep_plane_ann<false><<<grid, kTile, kSweepSmem, st>>>(a);
+        }
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {
@@ -934,11 +1102,11 @@ static sn_status apply_cells(sn_handle h, const float *in27, float *psi, int64_t
         if (grid > cap) grid = cap;
         const AnnArgs a = ann_args(h);
         if (gated) {
-            SN_CK(h, cudaFuncSetAttribute(ann_cells_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAnnSmem));
-            ann_cells_kernel<true><<<(unsigned)grid, kTile, kAnnSmem, st>>>(in27, psi, n, a);
+            SN_CK(h, cudaFuncSetAttribute(ann_cells_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem));
+            ann_cells_kernel<true><<<(unsigned)grid, kTile, kCellSmem, st>>>(in27, psi, n, a);
         } else {
-            SN_CK(h, cudaFuncSetAttribute(ann_cells_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAnnSmem));
-            ann_cells_kernel<false><<<(unsigned)grid, kTile, kAnnSmem, st>>>(in27, psi, n, a);
+            SN_CK(h, cudaFuncSetAttribute(ann_cells_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem));
+            ann_cells_kernel<false><<<(unsigned)grid, kTile, kCellSmem, st>>>(in27, psi, n, a);
         }
         SN_CK(h, cudaGetLastError());
     }
