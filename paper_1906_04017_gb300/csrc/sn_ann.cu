@@ -139,7 +139,6 @@ constexpr int kN2 = 16;                        // 8 outputs padded
 constexpr uint32_t kW1Bytes = kNhid * kK1 * 2; // 4096
 constexpr uint32_t kW2Bytes = kN2 * kNhid * 2; // 2048
 constexpr uint32_t kXBytes = kTile * kK1 * 2;  // 8192
-constexpr uint32_t kHBytes = kTile * kNhid * 2;// 16384
 constexpr uint32_t kTmemCols = 64;   // layer 1: 0..63; hidden BF16 pairs: 0..31; layer 2: 32..47
 
 struct Net {
@@ -454,12 +453,14 @@ __device__ __forceinline__ uint32_t pack_relu_bf16x2(uint32_t a, uint32_t b)
 }
 
 // The X row of thread `row` (features, bias ones, zero padding) as BF16, 4 x 16 bytes.
-__device__ __forceinline__ void write_x_row(unsigned char *sx, int row, const float (&x)[kNin], bool live)
+// Rows of idle threads are left as they are: a row of the product depends only on
+// the same row of X, and idle rows' outputs are never used.
+__device__ __forceinline__ void write_x_row(unsigned char *sx, int row, const float (&x)[kNin])
 {
     float v[kK1];
 #pragma unroll
-    for (int k = 0; k < kNin; ++k) v[k] = live ? x[k] : 0.f;
-    v[kNin] = v[kNin + 1] = live ? 1.f : 0.f;
+    for (int k = 0; k < kNin; ++k) v[k] = x[k];
+    v[kNin] = v[kNin + 1] = 1.f;
 #pragma unroll
     for (int k = kNin + 2; k < kK1; ++k) v[k] = 0.f;
 #pragma unroll
@@ -631,27 +632,29 @@ __global__ void __launch_bounds__(128, 4) ann_cells_kernel(const float *__restri
             ann_features(fabsf(p[0]), fabsf(p[1]), fabsf(p[2]), p[3], p[4], p[5], c.sig, c.S, c.ux, c.uy, c.uz,
                          s > 0.f ? 1.f / s : 0.f, x);
         }
-        write_x_row(smem + kCellOffX, t, x, t < cnt);
+        if (t < cnt) write_x_row(smem + kCellOffX, t, x);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (t == 0) mma_layer1(sbase, kCellOffX, kCellOffW1, tbase, bar);
-        bool late = !mbar_wait_bounded(bar, phase);
+        // the issuing thread waits for the tensor cores; the others wait at the barrier
+        bool late = t == 0 && !mbar_wait_bounded(bar, phase);
         phase ^= 1u;
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
         tc_fence_after();
         hidden_to_tmem(twarp);
         tc_fence_before();
-        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
+        __syncthreads();
         tc_fence_after();
         if (t == 0) mma_layer2(sbase, kCellOffW2, tbase, bar);
-        late = !mbar_wait_bounded(bar, phase);
+        late = t == 0 && !mbar_wait_bounded(bar, phase);
         phase ^= 1u;
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
         tc_fence_after();
         uint32_t r[8];
         tmem_ld8(twarp + 32, r);
         tmem_wait_ld();
-        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
         float psi[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) psi[q] = s * (__uint_as_float(r[q]) + b2[q]);
@@ -714,16 +717,6 @@ struct AnnSweepArgs {
     uint32_t *fb_count;      // this hyperplane's queue length
     AnnArgs ann;
 };
-
-constexpr uint32_t kSwOffW1 = 0, kSwOffW2 = kSwOffW1 + kW1Bytes;
-constexpr uint32_t kSwOffX = kSwOffW2 + kW2Bytes;          // X tile; the flux reduction [128][9] reuses it
-constexpr uint32_t kSwOffFace = kSwOffX + kXBytes;         // [128 rows][12] inflow face values
-constexpr uint32_t kSwOffKey = kSwOffFace + kTile * 48;    // [128 keys][8] source
-constexpr uint32_t kSwOffSig = kSwOffKey + kTile * 32;     // [128 keys] sigma_t
-constexpr uint32_t kSwOffBar = kSwOffSig + kTile * 4;
-constexpr uint32_t kSwOffMisc = kSwOffBar + 8;             // tmem slot, (unused), abort
-constexpr uint32_t kSweepSmem = kSwOffMisc + 16;
-static_assert(4 * kTile * 9 <= kXBytes, "flux reduction must fit the X tile");
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
@@ -795,25 +788,118 @@ __device__ __forceinline__ void store_outflow(const AnnSweepArgs &a, const Sweep
     else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
 }
 
-template <bool GATED>
+// Shared-memory layout of the sweep kernel for kpt keys per tile.
+struct SweepSmem {
+    uint32_t w1, w2, x, face, ks, sig, rec, bar, misc, total;
+};
+__host__ __device__ inline SweepSmem sweep_smem(int kpt)
+{
+    SweepSmem m;
+    m.w1 = 0;
+    m.w2 = m.w1 + kW1Bytes;
+    m.x = m.w2 + kW2Bytes;                  // X tile; the flux reduction [128][9] reuses it
+    m.face = m.x + kXBytes;                 // [128 rows][12] inflow face values
+    m.ks = m.face + kTile * 48;             // [kpt][8] source
+    m.sig = m.ks + 32 * kpt;                // [kpt] sigma_t
+    m.rec = (m.sig + 4 * kpt + 15) & ~15u;  // two sets of [kpt] key records
+    m.bar = m.rec + 2 * 32 * kpt;
+    m.misc = m.bar + 8;                     // tmem slot, (unused), abort
+    m.total = m.misc + 16;
+    return m;
+}
+static_assert(4 * kTile * 9 <= kXBytes, "flux reduction must fit the X tile");
+
+// Per key (cell of the hyperplane, group) of a tile, written once by the key's
+// thread: face-plane slots of its direction 0 (x, y, z planes), boundary flags,
+// physical cell and group.
+struct KeyRec {
+    int bx, by, bz;
+    uint32_t flags;   // bits 0-2: inflow face on the boundary (x, y, z); 3-5: outflow
+                      // face on the boundary; 7: key exists
+    int cell, g, pad0, pad1;
+};
+
+template <int DO>
+__device__ __forceinline__ void make_key(const AnnSweepArgs &a, int o, uint32_t key, uint32_t pk, KeyRec &r)
+{
+    const int Do = DO ? DO : a.Do;
+    const uint32_t cidx = a.divG.div(key);
+    const int g = (int)(key - cidx * (uint32_t)a.G);
+    const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
+    const int i = (o & 1) ? a.nx - 1 - ip : ip;
+    const int j = (o & 2) ? a.ny - 1 - jp : jp;
+    const int k = (o & 4) ? a.nz - 1 - kp : kp;
+    r.cell = i + a.nx * (j + a.ny * k);
+    r.g = g;
+    const int GD = a.G * Do, gd = g * Do;
+    r.bx = (o * a.ny * a.nz + jp + a.ny * kp) * GD + gd;
+    r.by = (o * a.nx * a.nz + ip + a.nx * kp) * GD + gd;
+    r.bz = (o * a.nx * a.ny + ip + a.nx * jp) * GD + gd;
+    r.flags = 0x80u | (ip == 0 ? 1u : 0u) | (jp == 0 ? 2u : 0u) | (kp == 0 ? 4u : 0u) |
+              (ip == a.nx - 1 ? 8u : 0u) | (jp == a.ny - 1 ? 16u : 0u) | (kp == a.nz - 1 ? 32u : 0u);
+    r.pad0 = r.pad1 = 0;
+}
+
+__device__ __forceinline__ void put_key(unsigned char *p, const KeyRec &r)
+{
+    reinterpret_cast<int4 *>(p)[0] = make_int4(r.bx, r.by, r.bz, (int)r.flags);
+    reinterpret_cast<int4 *>(p)[1] = make_int4(r.cell, r.g, 0, 0);
+}
+
+__device__ __forceinline__ KeyRec get_key(const unsigned char *p)
+{
+    const int4 u = reinterpret_cast<const int4 *>(p)[0], v = reinterpret_cast<const int4 *>(p)[1];
+    KeyRec r;
+    r.bx = u.x; r.by = u.y; r.bz = u.z; r.flags = (uint32_t)u.w;
+    r.cell = v.x; r.g = v.y; r.pad0 = r.pad1 = 0;
+    return r;
+}
+
+__device__ __forceinline__ float lg2_approx(float v)
+{
+    float r;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float v)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Tile loop of the surrogate sweep.  Per tile: (1) wait for the staged inputs; (2)
+// every row builds its features from the stage and the key records into X; (3) one
+// thread issues layer 1, the key threads build the next tile's key records and
+// start copying its sources and opacities, and all rows then start copying its
+// inflow faces; (4) hidden layer through TMEM, layer 2; (5) outputs: gate, outflow
+// faces, w_d psi to shared memory; (6) per key and node, the sum over directions
+// to the octant's flux partial.  DO > 0 fixes the directions per octant at compile
+// time (DO = 0: the handle's value).
+template <bool GATED, int DO>
 __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    int *misc = reinterpret_cast<int *>(smem + kSwOffMisc);
-    const uint32_t tbase = ann_setup(smem, a.ann, kSwOffW1, kSwOffW2, kSwOffBar, misc);
-    const uint32_t sbase = smem_u32(smem), bar = sbase + kSwOffBar;
+    griddep_launch();
+    const int Do = DO ? DO : a.Do;
+    const int kpt = a.keys_per_tile;
+    const SweepSmem L = sweep_smem(kpt);
+    int *misc = reinterpret_cast<int *>(smem + L.misc);
+    const uint32_t tbase = ann_setup(smem, a.ann, L.w1, L.w2, L.bar, misc);
+    const uint32_t sbase = smem_u32(smem), bar = sbase + L.bar;
     const int t = threadIdx.x;
     const uint32_t twarp = tbase + ((uint32_t)(t & ~31) << 16);
-    float *red = reinterpret_cast<float *>(smem + kSwOffX);
-    const int o = blockIdx.y, Do = a.Do;
+    float *red = reinterpret_cast<float *>(smem + L.x);
+    const int o = blockIdx.y;
     const int lk = t / Do, d = t - lk * Do;
-    const bool lane_row = lk < a.keys_per_tile;
+    const bool lane_row = lk < kpt;
     const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
     DirData<float> dd = {0.f, 0.f, 0.f, 0.f};
-    float4 dab = make_float4(0.f, 0.f, 0.f, 0.f);
+    float xo0 = 0.f, xo1 = 0.f, xo2 = 0.f;
     if (lane_row) {
         dd = a.dir[d];
-        dab = a.dir_abs[d];
+        const float4 ab = a.dir_abs[d];
+        xo0 = 2.f * ab.x - 1.f; xo1 = 2.f * ab.y - 1.f; xo2 = 2.f * ab.z - 1.f;
     }
     float b2[8];
 #pragma unroll
@@ -821,90 +907,124 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
     const float lhx = (logf(a.hx) + kLogHShift) / kLogHScale;
     const float lhy = (logf(a.hy) + kLogHShift) / kLogHScale;
     const float lhz = (logf(a.hz) + kLogHShift) / kLogHScale;
-    const uint32_t sface = sbase + kSwOffFace + 48 * t;
-    const float *fface = reinterpret_cast<const float *>(smem + kSwOffFace) + 12 * t;
-    const uint32_t skey = sbase + kSwOffKey + 32 * lk;
-    const float *fkey = reinterpret_cast<const float *>(smem + kSwOffKey) + 8 * lk;
-    const float *fsig = reinterpret_cast<const float *>(smem + kSwOffSig) + lk;
+    const float lsig = 0.69314718f / kLogSigScale;      // ln 2 / 4.5: log2 -> feature
+    const uint32_t sface = sbase + L.face + 48 * t;
+    const float4 *fface = reinterpret_cast<const float4 *>(smem + L.face) + 3 * t;
+    const float *fks = reinterpret_cast<const float *>(smem + L.ks) + 8 * lk;
+    const float *fsig = reinterpret_cast<const float *>(smem + L.sig) + lk;
+    const int psi_o[3] = {o & 1, 2 + ((o >> 1) & 1), 4 + ((o >> 2) & 1)};
 
-    // copy a row's inputs into the stage (the key's source and sigma_t by its first
-    // directions; boundary faces are taken from psi_inc when they are used)
-    auto prefetch = [&](uint32_t key, uint32_t pk) {
-        const SweepRow r = sweep_row(a, o, key, pk, d);
-        if (r.ip > 0) cp_async16(sface, a.fx + r.ix);
-        if (r.jp > 0) cp_async16(sface + 16, a.fy + r.iy);
-        if (r.kp > 0) cp_async16(sface + 32, a.fz + r.iz);
-        const int64_t gc = (int64_t)r.g * a.C + r.cell;
-        for (int q = d; q < 3; q += Do) {
-            if (q < 2) cp_async16(skey + 16 * q, a.S + gc * 8 + 4 * q);
-            else cp_async4(sbase + kSwOffSig + 4 * lk, a.sigt + gc);
+    // key records of a tile (key threads only) and the copies of their sources
+    auto key_stage = [&](int tl, uint32_t pk, int parity) {
+        const uint32_t key = (uint32_t)tl * (uint32_t)kpt + (uint32_t)t;
+        KeyRec r;
+        if (tl < a.ntiles && key < nkeys) {
+            make_key<DO>(a, o, key, pk, r);
+            const int64_t gc = (int64_t)r.g * a.C + r.cell;
+            cp_async16(sbase + L.ks + 32 * t, a.S + gc * 8);
+            cp_async16(sbase + L.ks + 32 * t + 16, a.S + gc * 8 + 4);
+            cp_async4(sbase + L.sig + 4 * t, a.sigt + gc);
+        } else {
+            r.bx = r.by = r.bz = 0; r.flags = 0; r.cell = r.g = 0; r.pad0 = r.pad1 = 0;
         }
+        put_key(smem + L.rec + parity * 32 * kpt + 32 * t, r);
+    };
+    // a row's inflow faces of the tile whose key records are in `parity`
+    auto face_stage = [&](int parity) {
+        if (!lane_row) return;
+        const KeyRec r = get_key(smem + L.rec + parity * 32 * kpt + 32 * lk);
+        if (!(r.flags & 0x80u)) return;
+        if (!(r.flags & 1u)) cp_async16(sface, a.fx + r.bx + d);
+        if (!(r.flags & 2u)) cp_async16(sface + 16, a.fy + r.by + d);
+        if (!(r.flags & 4u)) cp_async16(sface + 32, a.fz + r.bz + d);
     };
 
+    // set-up above reads only what no hyperplane writes; the inputs below need the
+    // previous hyperplane (or fallback pass) complete
+    griddep_wait();
     int tile = blockIdx.x;
-    uint32_t key = (uint32_t)tile * (uint32_t)a.keys_per_tile + (uint32_t)lk;
-    bool act = lane_row && key < nkeys;
-    uint32_t pk = act ? a.cells[a.divG.div(key)] : 0u;
-    if (act) prefetch(key, pk);
+    int par = 0;
+    if (t < kpt) {
+        const uint32_t key = (uint32_t)tile * (uint32_t)kpt + (uint32_t)t;
+        const uint32_t pk = key < nkeys ? a.cells[a.divG.div(key)] : 0u;
+        key_stage(tile, pk, 0);
+    }
+    __syncthreads();
+    face_stage(0);
     cp_async_commit();
     uint32_t phase = 0;
     float leak = 0.f;
     unsigned long long nq_total = 0;
-    for (; tile < a.ntiles; tile += gridDim.x) {
-        // the next tile's cell index: its latency hides behind this tile's work
+    for (; tile < a.ntiles; tile += gridDim.x, par ^= 1) {
         const int tn = tile + gridDim.x;
-        const uint32_t key_n = (uint32_t)tn * (uint32_t)a.keys_per_tile + (uint32_t)lk;
-        const bool act_n = lane_row && tn < a.ntiles && key_n < nkeys;
-        const uint32_t pk_n = act_n ? a.cells[a.divG.div(key_n)] : 0u;
+        uint32_t pk_n = 0;
+        if (t < kpt) {
+            const uint32_t key_n = (uint32_t)tn * (uint32_t)kpt + (uint32_t)t;
+            if (tn < a.ntiles && key_n < nkeys) pk_n = a.cells[a.divG.div(key_n)];
+        }
         cp_async_wait_all();
         __syncthreads();
-        // features from the stage
+        // (2) features
+        const KeyRec kr = get_key(smem + L.rec + par * 32 * kpt + 32 * (lane_row ? lk : 0));
+        const bool act = lane_row && (kr.flags & 0x80u);
         CanonCell<float> c;
         float s = 0.f;
-        int g = 0;
         {
             float x[kNin];
             if (act) {
-                g = (int)(key - a.divG.div(key) * (uint32_t)a.G);
-                const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
+                const float4 fx4 = fface[0], fy4 = fface[1], fz4 = fface[2];
+                const float *pi = a.psi_inc + 6 * kr.g;
+                if (kr.flags & 1u) { c.ux[0] = c.ux[1] = c.ux[2] = c.ux[3] = pi[psi_o[0]]; }
+                else { c.ux[0] = fx4.x; c.ux[1] = fx4.y; c.ux[2] = fx4.z; c.ux[3] = fx4.w; }
+                if (kr.flags & 2u) { c.uy[0] = c.uy[1] = c.uy[2] = c.uy[3] = pi[psi_o[1]]; }
+                else { c.uy[0] = fy4.x; c.uy[1] = fy4.y; c.uy[2] = fy4.z; c.uy[3] = fy4.w; }
+                if (kr.flags & 4u) { c.uz[0] = c.uz[1] = c.uz[2] = c.uz[3] = pi[psi_o[2]]; }
+                else { c.uz[0] = fz4.x; c.uz[1] = fz4.y; c.uz[2] = fz4.z; c.uz[3] = fz4.w; }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    c.ux[q] = ip ? fface[q] : a.psi_inc[6 * g + (o & 1)];
-                    c.uy[q] = jp ? fface[4 + q] : a.psi_inc[6 * g + 2 + ((o >> 1) & 1)];
-                    c.uz[q] = kp ? fface[8 + q] : a.psi_inc[6 * g + 4 + ((o >> 2) & 1)];
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) c.S[q] = fkey[q];
-                mirror8(c.S, o);
+                for (int q = 0; q < 8; ++q) c.S[q] = fks[q ^ o];
                 c.sig = *fsig;
                 c.t3x = dd.t3x; c.t3y = dd.t3y; c.t3z = dd.t3z;
                 c.mask = o;
                 s = input_scale(c.S, c.ux, c.uy, c.uz);
-                ann_features(dab.x, dab.y, dab.z, a.hx, a.hy, a.hz, c.sig, c.S, c.ux, c.uy, c.uz,
-                             s > 0.f ? 1.f / s : 0.f, x);
+                const float inv = s > 0.f ? rcp_approx(s) : 0.f;
+                x[0] = xo0; x[1] = xo1; x[2] = xo2;
                 x[3] = lhx; x[4] = lhy; x[5] = lhz;
+                x[6] = lg2_approx(fmaxf(c.sig, kSigFloor)) * lsig;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) x[7 + k] = c.S[k] * inv;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    x[15 + q] = c.ux[q] * inv;
+                    x[19 + q] = c.uy[q] * inv;
+                    x[23 + q] = c.uz[q] * inv;
+                }
             }
-            write_x_row(smem + kSwOffX, t, x, act);
+            if (act) write_x_row(smem + L.x, t, x);
         }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (t == 0) mma_layer1(sbase, kSwOffX, kSwOffW1, tbase, bar);
-        // the stage is free: fetch the next tile while this one is in the tensor cores
-        if (act_n) prefetch(key_n, pk_n);
-        cp_async_commit();
-        bool late = !mbar_wait_bounded(bar, phase);
+        // (3) layer 1; the next tile's key records and source copies; its faces
+        if (t == 0) mma_layer1(sbase, L.x, L.w1, tbase, bar);
+        if (t < kpt) key_stage(tn, pk_n, par ^ 1);
+        bool late = t == 0 && !mbar_wait_bounded(bar, phase);
         phase ^= 1u;
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
+        face_stage(par ^ 1);
+        cp_async_commit();
+        // (4) hidden layer, layer 2
         tc_fence_after();
         hidden_to_tmem(twarp);
         tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) mma_layer2(sbase, L.w2, tbase, bar);
+        late = t == 0 && !mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
         if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
         tc_fence_after();
-        if (t == 0) mma_layer2(sbase, kSwOffW2, tbase, bar);
-        late = !mbar_wait_bounded(bar, phase);
-        phase ^= 1u;
-        tc_fence_after();
+        // (5) outputs
         uint32_t r8[8];
         tmem_ld8(twarp + 32, r8);
         tmem_wait_ld();
@@ -929,34 +1049,35 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
         }
         float *rr = red + t * 9;
         if (keep) {
-            const SweepRow r = sweep_row(a, o, key, pk, d);
-            store_outflow(a, r, dd, psi, leak);
+            if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, psi[1], psi[3], psi[5], psi[7]);
+            else leak += dd.w * a.vol12 * dd.t3x * (psi[1] + psi[3] + psi[5] + psi[7]);
+            if (!(kr.flags & 16u)) store4(a.fy + kr.by + d, psi[2], psi[3], psi[6], psi[7]);
+            else leak += dd.w * a.vol12 * dd.t3y * (psi[2] + psi[3] + psi[6] + psi[7]);
+            if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, psi[4], psi[5], psi[6], psi[7]);
+            else leak += dd.w * a.vol12 * dd.t3z * (psi[4] + psi[5] + psi[6] + psi[7]);
 #pragma unroll
             for (int n = 0; n < 8; ++n) rr[n ^ o] = dd.w * psi[n];
         } else {
 #pragma unroll
             for (int n = 0; n < 8; ++n) rr[n] = 0.f;
         }
-        tc_fence_before();
-        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
-        if (act) {
-            const uint32_t cidx = a.divG.div(key);
-            const int i = (o & 1) ? a.nx - 1 - (int)(pk & 1023) : (int)(pk & 1023);
-            const int j = (o & 2) ? a.ny - 1 - (int)((pk >> 10) & 1023) : (int)((pk >> 10) & 1023);
-            const int k = (o & 4) ? a.nz - 1 - (int)(pk >> 20) : (int)(pk >> 20);
-            const int cell = i + a.nx * (j + a.ny * k);
-            g = (int)(key - cidx * (uint32_t)a.G);
-            float *dst = a.phi_oct + (((int64_t)o * a.C + cell) * a.G + g) * 8;
-            const float *base = red + (lk * Do) * 9;
-            for (int n = d; n < 8; n += Do) {
+        __syncthreads();
+        // (6) flux partial: thread (key, node) sums the key's directions
+        for (int e = t; e < 8 * kpt; e += kTile) {
+            const int kk = e >> 3, n = e & 7;
+            const KeyRec r = get_key(smem + L.rec + par * 32 * kpt + 32 * kk);
+            if (r.flags & 0x80u) {
+                const float *base = red + (kk * Do) * 9 + n;
                 float sum = 0.f;
-                for (int q = 0; q < Do; ++q) sum += base[q * 9 + n];
-                dst[n] = sum;
+                if (DO) {
+#pragma unroll
+                    for (int q = 0; q < DO; ++q) sum += base[q * 9];
+                } else {
+                    for (int q = 0; q < Do; ++q) sum += base[q * 9];
+                }
+                a.phi_oct[(((int64_t)o * a.C + r.cell) * a.G + r.g) * 8 + n] = sum;
             }
         }
-        key = key_n;
-        pk = pk_n;
-        act = act_n;
     }
     cp_async_wait_all();
 #pragma unroll
@@ -970,6 +1091,8 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
 // leakage, and w_d psi added to the tile's flux partial (atomics).
 __global__ void __launch_bounds__(128, 4) ann_fallback_kernel(AnnSweepArgs a)
 {
+    griddep_launch();
+    griddep_wait();
     const uint32_t n = *reinterpret_cast<volatile const uint32_t *>(a.fb_count);
     float leak = 0.f;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -1050,14 +1173,29 @@ sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gat
     a.hx = (float)h->dx; a.hy = (float)h->dy; a.hz = (float)h->dz;
     a.fb_queue = net->fb_queue;
     a.ann = ann_args(h);
-    if (gated) {
-        SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
-        SN_CK(h, cudaMemsetAsync(net->fb_count, 0, sizeof(uint32_t) * (size_t)h->nplanes, st));
-    } else {
-        SN_CK(h, cudaFuncSetAttribute(sweep_plane_ann<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
-    }
-    // persistent CTAs per octant: 6 (gated) or 8 per SM in total
-    const int cap = num_sms() * (gated ? 6 : 8) / 8;
+    const SweepSmem L = sweep_smem(a.keys_per_tile);
+    // CTAs per SM: shared memory (plus the 1 KB the driver reserves per CTA) within the
+    // SM's 228 KB, 64 TMEM columns each (at most 8), and the kernels' register bounds
+    auto pick = [&](auto kern, int &per_sm) -> sn_status {
+        SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+        per_sm = std::min((int)((228 * 1024) / (L.total + 1024)), (int)(512 / kTmemCols));
+        if (gated) per_sm = std::min(per_sm, 6);
+        per_sm = std::max(per_sm, 1);
+        return SN_OK;
+    };
+    void (*kern)(AnnSweepArgs) = nullptr;
+    if (gated)
+        kern = h->Do == 10 ? sweep_plane_ann<true, 10> : h->Do == 21 ? sweep_plane_ann<true, 21> : sweep_plane_ann<true, 0>;
+    else
+        kern = h->Do == 10 ? sweep_plane_ann<false, 10> : h->Do == 21 ? sweep_plane_ann<false, 21> : sweep_plane_ann<false, 0>;
+    int per_sm = 1;
+    s = pick(kern, per_sm);
+    if (s != SN_OK) return s;
+    if (gated) SN_CK(h, cudaMemsetAsync(net->fb_count, 0, sizeof(uint32_t) * (size_t)h->nplanes, st));
+    // persistent CTAs per octant: as many as fit on the SMs
+    const int cap = std::max(1, num_sms() * per_sm / 8);
     const int fb_grid = num_sms() * 4;
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
     for (int p = 0; p < h->nplanes; ++p) {
@@ -1067,12 +1205,10 @@ sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gat
         a.ntiles = (int)((n * h->G + a.keys_per_tile - 1) / a.keys_per_tile);
         a.fb_count = net->fb_count + p;
         const dim3 grid((unsigned)(a.ntiles < cap ? a.ntiles : cap), 8);
-        if (gated) {
-            sweep_plane_ann<true><<<grid, kTile, kSweepSmem, st>>>(a);
-            ann_fallback_kernel<<<fb_grid, 128, 0, st>>>(a);
-        } else {
-            sweep_plane_ann<false><<<grid, kTile, kSweepSmem, st>>>(a);
-        }
+        // later hyperplanes (and the fallback passes) overlap their launch and set-up
+        // with the previous kernel's drain
+        SN_CK(h, launch_k(p > 0, kern, grid, dim3(kTile), L.total, st, a));
+        if (gated) SN_CK(h, launch_k(true, ann_fallback_kernel, dim3(fb_grid), dim3(128), 0, st, a));
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {

@@ -287,6 +287,15 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
         delete h;
         return fail(nullptr, SN_EINVAL, "sn_setup: ngroups * cells * 8 must stay below 2^31");
     }
+    {
+        // face-plane slots (4-vectors) of one plane set are indexed with 32-bit integers
+        const int64_t nxy = (int64_t)h->nx * h->ny, nxz = (int64_t)h->nx * h->nz, nyz = (int64_t)h->ny * h->nz;
+        const int64_t slots = 8 * std::max(nxy, std::max(nxz, nyz)) * G * (int64_t)(h->ndir / 8);
+        if (slots >= (1LL << 31)) {
+            delete h;
+            return fail(nullptr, SN_EINVAL, "sn_setup: 8 x face cells x groups x directions per octant must stay below 2^31");
+        }
+    }
     if (h->Do > 128) {
         delete h;
         return fail(nullptr, SN_EINVAL, "sn_setup: at most 128 directions per octant");

@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS 
 {
     extern __shared__ __align__(16) unsigned char red_raw[];
     T *red = reinterpret_cast<T *>(red_raw);   // [blockDim.x][9]
+    griddep_launch();
+    griddep_wait();
     const int Do = a.Do;
     const int o = blockIdx.y;                  // octant: sign bits of Omega
     const int lk = (int)threadIdx.x / Do;
@@ -244,10 +246,11 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
         a.ncells_plane = (int)n;
         const int64_t nkeys = n * h->G;
         const dim3 grid((unsigned)((nkeys + a.keys_per_cta - 1) / a.keys_per_cta), 8);
+        // hyperplanes after the first overlap their launch with the previous one's drain
         if (refine)
-            sweep_plane_ge<T, true><<<grid, block, smem, st>>>(a);
+            SN_CK(h, launch_k(s > 0, sweep_plane_ge<T, true, 0>, grid, dim3(block), smem, st, a));
         else
-            sweep_plane_ge<T, false><<<grid, block, smem, st>>>(a);
+            SN_CK(h, launch_k(s > 0, sweep_plane_ge<T, false, 0>, grid, dim3(block), smem, st, a));
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {
