@@ -34,10 +34,10 @@ UNIT = "solves/s"
 FLOPS_PER_SOLVE = 1306
 # algorithmic HBM bytes of one solve: 12 inflow + 12 outflow face floats
 BYTES_PER_SOLVE = 96
-# DRAM bytes (read + write) per solve of sweep_plane_ge<float, 1, 0> measured by ncu on
-# blocked_64 hyperplane 95 (cold cache; profiles/sweep_plane_ge_blocked_64.md); None
+# DRAM bytes (read + write) per solve of sweep_ge_tiles<float, 1, 10> measured by ncu on
+# blocked_64 hyperplane 95 (cold cache, full-set capture of one launch); None
 # once that kernel changes
-DRAM_BYTES_PER_SOLVE_NCU = 85.7
+DRAM_BYTES_PER_SOLVE_NCU = 85.3
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -321,7 +321,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(), parallelism="replicas" if ws > 1 else "single"),
-        "roofline": {"bound": "alu", "kernel": "sweep_plane_ge<refine>", "achieved": achieved_tf,
+        "roofline": {"bound": "alu", "kernel": "sweep_ge_tiles<float, refine, 10>", "achieved": achieved_tf,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                      "traffic": (solves * DRAM_BYTES_PER_SOLVE_NCU / P.nplanes
                                  if DRAM_BYTES_PER_SOLVE_NCU else None),

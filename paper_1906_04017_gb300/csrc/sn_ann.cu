@@ -35,7 +35,6 @@ namespace sn {
 // --------------------------------------------------------------------------------
 // tcgen05 / mbarrier helpers (inline PTX)
 // --------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
@@ -718,17 +717,6 @@ struct AnnSweepArgs {
     AnnArgs ann;
 };
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Where one row of a tile sits: key (cell of the hyperplane, group) and direction d.
 struct SweepRow {
     int g, cell, ip, jp, kp;
@@ -808,52 +796,6 @@ __host__ __device__ inline SweepSmem sweep_smem(int kpt)
     return m;
 }
 static_assert(4 * kTile * 9 <= kXBytes, "flux reduction must fit the X tile");
-
-// Per key (cell of the hyperplane, group) of a tile, written once by the key's
-// thread: face-plane slots of its direction 0 (x, y, z planes), boundary flags,
-// physical cell and group.
-struct KeyRec {
-    int bx, by, bz;
-    uint32_t flags;   // bits 0-2: inflow face on the boundary (x, y, z); 3-5: outflow
-                      // face on the boundary; 7: key exists
-    int cell, g, pad0, pad1;
-};
-
-template <int DO>
-__device__ __forceinline__ void make_key(const AnnSweepArgs &a, int o, uint32_t key, uint32_t pk, KeyRec &r)
-{
-    const int Do = DO ? DO : a.Do;
-    const uint32_t cidx = a.divG.div(key);
-    const int g = (int)(key - cidx * (uint32_t)a.G);
-    const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
-    const int i = (o & 1) ? a.nx - 1 - ip : ip;
-    const int j = (o & 2) ? a.ny - 1 - jp : jp;
-    const int k = (o & 4) ? a.nz - 1 - kp : kp;
-    r.cell = i + a.nx * (j + a.ny * k);
-    r.g = g;
-    const int GD = a.G * Do, gd = g * Do;
-    r.bx = (o * a.ny * a.nz + jp + a.ny * kp) * GD + gd;
-    r.by = (o * a.nx * a.nz + ip + a.nx * kp) * GD + gd;
-    r.bz = (o * a.nx * a.ny + ip + a.nx * jp) * GD + gd;
-    r.flags = 0x80u | (ip == 0 ? 1u : 0u) | (jp == 0 ? 2u : 0u) | (kp == 0 ? 4u : 0u) |
-              (ip == a.nx - 1 ? 8u : 0u) | (jp == a.ny - 1 ? 16u : 0u) | (kp == a.nz - 1 ? 32u : 0u);
-    r.pad0 = r.pad1 = 0;
-}
-
-__device__ __forceinline__ void put_key(unsigned char *p, const KeyRec &r)
-{
-    reinterpret_cast<int4 *>(p)[0] = make_int4(r.bx, r.by, r.bz, (int)r.flags);
-    reinterpret_cast<int4 *>(p)[1] = make_int4(r.cell, r.g, 0, 0);
-}
-
-__device__ __forceinline__ KeyRec get_key(const unsigned char *p)
-{
-    const int4 u = reinterpret_cast<const int4 *>(p)[0], v = reinterpret_cast<const int4 *>(p)[1];
-    KeyRec r;
-    r.bx = u.x; r.by = u.y; r.bz = u.z; r.flags = (uint32_t)u.w;
-    r.cell = v.x; r.g = v.y; r.pad0 = r.pad1 = 0;
-    return r;
-}
 
 __device__ __forceinline__ float lg2_approx(float v)
 {

@@ -33,7 +33,7 @@ namespace sn {
 
 template <typename T>
 struct SweepArgs {
-    int nx, ny, nz, G, Do, ncells_plane, keys_per_cta;
+    int nx, ny, nz, G, Do, ncells_plane, keys_per_cta, ntiles;
     int C;                   // cells (G * C * 8 < 2^31 is checked at set-up)
     FastDiv divG;            // key -> (cell index, group)
     const uint32_t *cells;   // packed (i',j',k') of the cells of this hyperplane
@@ -62,7 +62,8 @@ struct SweepArgs {
 };
 
 // grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
-// rounded up to whole warps.  XMODE 0: plain sweep; 1: also store each angular flux
+// rounded up to whole warps.  XMODE 0: plain sweep (the adjoint's sweeps; plain
+// forward sweeps use sweep_ge_tiles below); 1: also store each angular flux
 // (physical node order) for the adjoint; 2: adjoint pass that pairs its angular flux
 // with the stored forward one of the opposite direction (see sn_adjoint.cu).
 // 128-thread blocks, 4 per SM (128 registers a thread): measured faster on GB300 than
@@ -72,6 +73,11 @@ struct SweepArgs {
 #endif
 #ifndef SN_GE_BLOCK
 #define SN_GE_BLOCK 128
+#endif
+// the persistent form keeps a few more values live across tiles: 3 CTAs per SM (170
+// registers a thread) measured faster than 4 with spills
+#ifndef SN_GE_TILE_MINBLOCKS
+#define SN_GE_TILE_MINBLOCKS 3
 #endif
 template <typename T, bool REFINE, int XMODE = 0>
 __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS : 1) sweep_plane_ge(SweepArgs<T> a)
@@ -222,6 +228,172 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS 
     if ((threadIdx.x & 31) == 0 && leak != T(0)) atomicAdd(a.leak, (double)leak);
 }
 
+// Persistent form of the elimination sweep (plain forward sweeps, FP32 and FP64): a
+// CTA loops over tiles of keys_per_cta keys x Do directions.  Key records (face-plane
+// slots, boundary flags, cell, group) are built once per key, two tiles ahead, by
+// the first keys_per_cta threads; the sources and opacities of the next tile and
+// every row's inflow faces are copied into shared memory (cp.async) while the
+// current tile is solved, so the global-memory latency sits behind the elimination.
+// The flux reduction of a tile runs at the start of the next iteration.
+template <typename T>
+struct GeTileSmem {
+    uint32_t face, ks, sig, rec, red, total;
+};
+template <typename T>
+__host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows)
+{
+    GeTileSmem<T> m;
+    m.face = 0;                                                   // 2 x [rows][12] inflow faces
+    m.ks = m.face + 2 * rows * 12 * (uint32_t)sizeof(T);          // [kpt][8] sources
+    m.sig = m.ks + kpt * 8 * (uint32_t)sizeof(T);                 // [kpt] opacities
+    m.rec = (m.sig + kpt * (uint32_t)sizeof(T) + 15) & ~15u;      // 4 x [kpt] key records
+    m.red = m.rec + 4 * 32 * kpt;                                 // [rows][9] w_d psi
+    m.total = m.red + rows * 9 * (uint32_t)sizeof(T);
+    return m;
+}
+
+template <typename T, bool REFINE, int DO>
+__global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBLOCKS : 1) sweep_ge_tiles(SweepArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char gsm[];
+    griddep_launch();
+    const int Do = DO ? DO : a.Do;
+    const int kpt = a.keys_per_cta, rows = blockDim.x;
+    const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows);
+    const uint32_t sb = smem_u32(gsm);
+    const int t = threadIdx.x, o = blockIdx.y;
+    const int lk = t / Do, d = t - lk * Do;
+    const bool lane_row = lk < kpt;
+    const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
+    DirData<T> dd = {T(0), T(0), T(0), T(0)};
+    if (lane_row) dd = a.dir[d];
+    T *red = reinterpret_cast<T *>(gsm + L.red);
+    const T *fks = reinterpret_cast<const T *>(gsm + L.ks) + 8 * lk;
+    const T *fsig = reinterpret_cast<const T *>(gsm + L.sig) + lk;
+    auto rec_at = [&](int slot, int k) -> unsigned char * { return gsm + L.rec + (slot * kpt + k) * 32; };
+    const int psi_o[3] = {o & 1, 2 + ((o >> 1) & 1), 4 + ((o >> 2) & 1)};
+
+    // key thread t: the record of key t of tile tl into ring slot `slot`
+    auto key_pk = [&](int tl) -> uint32_t {
+        const uint32_t key = (uint32_t)tl * (uint32_t)kpt + (uint32_t)t;
+        return (tl < a.ntiles && key < nkeys) ? a.cells[a.divG.div(key)] : 0u;
+    };
+    auto key_rec = [&](int tl, uint32_t pk, int slot) {
+        const uint32_t key = (uint32_t)tl * (uint32_t)kpt + (uint32_t)t;
+        KeyRec r;
+        if (tl < a.ntiles && key < nkeys) {
+            make_key<DO>(a, o, key, pk, r);
+        } else {
+            r.bx = r.by = r.bz = 0; r.flags = 0; r.cell = r.g = 0; r.pad0 = r.pad1 = 0;
+        }
+        put_key(rec_at(slot, t), r);
+    };
+    // key thread t: copy the source and opacity of its key (record in `slot`)
+    auto key_copy = [&](int slot) {
+        const KeyRec r = get_key(rec_at(slot, t));
+        if (!(r.flags & 0x80u)) return;
+        const int64_t gc = (int64_t)r.g * a.C + r.cell;
+        cp_async_bytes(sb + L.ks + t * 8 * (uint32_t)sizeof(T), a.S + gc * 8, 8 * (int)sizeof(T));
+        if (sizeof(T) == 4) cp_async4(sb + L.sig + 4 * t, a.sigt + gc);
+        else cp_async8(sb + L.sig + 8 * t, a.sigt + gc);
+    };
+    // row: copy its inflow faces (record in `slot`) into face buffer `fb`
+    auto face_copy = [&](int slot, int fb) {
+        if (!lane_row) return;
+        const KeyRec r = get_key(rec_at(slot, lk));
+        if (!(r.flags & 0x80u)) return;
+        const uint32_t dst = sb + L.face + (uint32_t)((fb * rows + t) * 12 * (int)sizeof(T));
+        constexpr int vb = 4 * (int)sizeof(T);
+        if (!(r.flags & 1u)) cp_async_bytes(dst, a.fx + r.bx + d, vb);
+        if (!(r.flags & 2u)) cp_async_bytes(dst + vb, a.fy + r.by + d, vb);
+        if (!(r.flags & 4u)) cp_async_bytes(dst + 2 * vb, a.fz + r.bz + d, vb);
+    };
+    // flux partial of the tile whose records are in `slot` and w_d psi in red
+    auto reduce_tile = [&](int slot) {
+        for (int e = t; e < 8 * kpt; e += rows) {
+            const int kk = e >> 3, n = e & 7;
+            const KeyRec r = get_key(rec_at(slot, kk));
+            if (!(r.flags & 0x80u)) continue;
+            const T *base = red + (kk * Do) * 9 + n;
+            T sum = T(0);
+            if (DO) {
+#pragma unroll
+                for (int q = 0; q < DO; ++q) sum += base[q * 9];
+            } else {
+                for (int q = 0; q < Do; ++q) sum += base[q * 9];
+            }
+            a.phi_oct[(((int64_t)o * a.C + r.cell) * a.G + r.g) * 8 + n] = sum;
+        }
+    };
+
+    griddep_wait();
+    const int t0 = blockIdx.x, step = gridDim.x;
+    if (t < kpt) {
+        key_rec(t0, key_pk(t0), 0);
+        key_rec(t0 + step, key_pk(t0 + step), 1);
+    }
+    __syncthreads();
+    if (t < kpt) key_copy(0);
+    face_copy(0, 0);
+    cp_async_commit();
+    T leak = T(0);
+    int i = 0;
+    for (int tile = t0; tile < a.ntiles; tile += step, ++i) {
+        const int slot = i & 3;
+        // cell of this thread's key two tiles ahead (used after the next barrier)
+        const uint32_t pk2 = t < kpt ? key_pk(tile + 2 * step) : 0u;
+        cp_async_wait_all();
+        __syncthreads();
+        if (i > 0) reduce_tile((i - 1) & 3);
+        // next tile's faces (its records were built one iteration ago)
+        face_copy((i + 1) & 3, (i + 1) & 1);
+        // this tile's inputs from the stage
+        const KeyRec kr = get_key(rec_at(slot, lane_row ? lk : 0));
+        const bool act = lane_row && (kr.flags & 0x80u);
+        T S[8], ux[4], uy[4], uz[4], sig = T(0);
+        if (act) {
+            const T *ff = reinterpret_cast<const T *>(gsm + L.face) + ((i & 1) * rows + t) * 12;
+            const T *pi = a.psi_inc + 6 * kr.g;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ux[q] = (kr.flags & 1u) ? pi[psi_o[0]] : ff[q];
+                uy[q] = (kr.flags & 2u) ? pi[psi_o[1]] : ff[4 + q];
+                uz[q] = (kr.flags & 4u) ? pi[psi_o[2]] : ff[8 + q];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) S[q] = fks[q ^ o];
+            sig = *fsig;
+        }
+        __syncthreads();
+        // the stage of sources is free: records two tiles ahead, sources one tile ahead
+        if (t < kpt) {
+            key_rec(tile + 2 * step, pk2, (i + 2) & 3);
+            key_copy((i + 1) & 3);
+        }
+        cp_async_commit();
+        T *r = red + t * 9;
+        if (act) {
+            T x[8];
+            cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
+            if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, x[1], x[3], x[5], x[7]);
+            else leak += dd.t3x * (x[1] + x[3] + x[5] + x[7]);
+            if (!(kr.flags & 16u)) store4(a.fy + kr.by + d, x[2], x[3], x[6], x[7]);
+            else leak += dd.t3y * (x[2] + x[3] + x[6] + x[7]);
+            if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, x[4], x[5], x[6], x[7]);
+            else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
+#pragma unroll
+            for (int n = 0; n < 8; ++n) r[n ^ o] = dd.w * x[n];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (i > 0) reduce_tile((i - 1) & 3);
+    leak *= dd.w * a.vol12;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
+    if ((t & 31) == 0 && leak != T(0)) atomicAdd(a.leak, (double)leak);
+}
+
 template <typename T>
 static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine, cudaStream_t st)
 {
@@ -237,20 +409,28 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     a.phi_oct = phi_oct;
     a.leak = h->acc + ACC_LEAK;
     a.vol12 = (T)(h->dx * h->dy * h->dz / 12.0);
-    const int block = (a.keys_per_cta * h->Do + 31) / 32 * 32;   // whole warps (shuffles)
-    const size_t smem = sizeof(T) * 9 * block;
+    const int rows = SN_GE_BLOCK;
+    const GeTileSmem<T> L = ge_tile_smem<T>(a.keys_per_cta, rows);
+    void (*kern)(SweepArgs<T>);
+    if (refine)
+        kern = h->Do == 10 ? sweep_ge_tiles<T, true, 10> : h->Do == 21 ? sweep_ge_tiles<T, true, 21>
+                                                                     : sweep_ge_tiles<T, true, 0>;
+    else
+        kern = h->Do == 10 ? sweep_ge_tiles<T, false, 10> : h->Do == 21 ? sweep_ge_tiles<T, false, 21>
+                                                                      : sweep_ge_tiles<T, false, 0>;
+    if (L.total > 48 * 1024)
+        SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    // persistent CTAs per octant: the register-limited residency (3 a SM in FP32, 1 in FP64)
+    const int cap = std::max(1, num_sms() * (sizeof(T) == 4 ? SN_GE_TILE_MINBLOCKS : 1) / 8);
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
     for (int s = 0; s < h->nplanes; ++s) {
         const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
         a.cells = h->plane_cells + h->plane_off[s];
         a.ncells_plane = (int)n;
-        const int64_t nkeys = n * h->G;
-        const dim3 grid((unsigned)((nkeys + a.keys_per_cta - 1) / a.keys_per_cta), 8);
+        a.ntiles = (int)((n * h->G + a.keys_per_cta - 1) / a.keys_per_cta);
+        const dim3 grid((unsigned)std::min(a.ntiles, cap), 8);
         // hyperplanes after the first overlap their launch with the previous one's drain
-        if (refine)
-            SN_CK(h, launch_k(s > 0, sweep_plane_ge<T, true, 0>, grid, dim3(block), smem, st, a));
-        else
-            SN_CK(h, launch_k(s > 0, sweep_plane_ge<T, false, 0>, grid, dim3(block), smem, st, a));
+        SN_CK(h, launch_k(s > 0, kern, grid, dim3(rows), L.total, st, a));
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {
