@@ -778,24 +778,24 @@ __device__ __forceinline__ void store_outflow(const AnnSweepArgs &a, const Sweep
 
 // Shared-memory layout of the sweep kernel for kpt keys per tile.
 struct SweepSmem {
-    uint32_t w1, w2, x, face, ks, sig, rec, bar, misc, total;
+    uint32_t w1, w2, x, face, ks, sig, rec, red, bar, misc, total;
 };
 __host__ __device__ inline SweepSmem sweep_smem(int kpt)
 {
     SweepSmem m;
     m.w1 = 0;
     m.w2 = m.w1 + kW1Bytes;
-    m.x = m.w2 + kW2Bytes;                  // X tile; the flux reduction [128][9] reuses it
+    m.x = m.w2 + kW2Bytes;                  // X tile
     m.face = m.x + kXBytes;                 // [128 rows][12] inflow face values
     m.ks = m.face + kTile * 48;             // [kpt][8] source
     m.sig = m.ks + 32 * kpt;                // [kpt] sigma_t
     m.rec = (m.sig + 4 * kpt + 15) & ~15u;  // two sets of [kpt] key records
-    m.bar = m.rec + 2 * 32 * kpt;
+    m.red = m.rec + 2 * 32 * kpt;           // [128][9] w_d psi of the previous tile
+    m.bar = m.red + kTile * 9 * 4;
     m.misc = m.bar + 8;                     // tmem slot, (unused), abort
     m.total = m.misc + 16;
     return m;
 }
-static_assert(4 * kTile * 9 <= kXBytes, "flux reduction must fit the X tile");
 
 __device__ __forceinline__ float lg2_approx(float v)
 {
@@ -810,14 +810,15 @@ __device__ __forceinline__ float rcp_approx(float v)
     return r;
 }
 
-// Tile loop of the surrogate sweep.  Per tile: (1) wait for the staged inputs; (2)
-// every row builds its features from the stage and the key records into X; (3) one
-// thread issues layer 1, the key threads build the next tile's key records and
-// start copying its sources and opacities, and all rows then start copying its
-// inflow faces; (4) hidden layer through TMEM, layer 2; (5) outputs: gate, outflow
-// faces, w_d psi to shared memory; (6) per key and node, the sum over directions
-// to the octant's flux partial.  DO > 0 fixes the directions per octant at compile
-// time (DO = 0: the handle's value).
+// Tile loop of the surrogate sweep.  Per tile: (1) wait for the staged inputs and
+// reduce the previous tile's w_d psi to its octant flux partial; (2) every row builds
+// its features from the stage and the key records into X; (3) one thread issues
+// layer 1, the key threads build the next tile's key records and start copying its
+// sources and opacities; (4) each warp waits for layer 1 on its own, moves its lanes'
+// hidden layer through TMEM; after one barrier all rows start copying the next
+// tile's inflow faces and one thread issues layer 2; (5) each warp waits for layer 2
+// and writes its outputs (gate, outflow faces, w_d psi).  Three CTA barriers a tile.
+// DO > 0 fixes the directions per octant at compile time (DO = 0: the handle's value).
 template <bool GATED, int DO>
 __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepArgs a)
 {
@@ -831,7 +832,7 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
     const uint32_t sbase = smem_u32(smem), bar = sbase + L.bar;
     const int t = threadIdx.x;
     const uint32_t twarp = tbase + ((uint32_t)(t & ~31) << 16);
-    float *red = reinterpret_cast<float *>(smem + L.x);
+    float *red = reinterpret_cast<float *>(smem + L.red);
     const int o = blockIdx.y;
     const int lk = t / Do, d = t - lk * Do;
     const bool lane_row = lk < kpt;
@@ -897,6 +898,27 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
     uint32_t phase = 0;
     float leak = 0.f;
     unsigned long long nq_total = 0;
+    // flux partial of the tile whose records are in `parity`: thread (key, node) sums
+    // the key's directions
+    auto reduce_tile = [&](int parity) {
+        for (int e = t; e < 8 * kpt; e += kTile) {
+            const int kk = e >> 3, n = e & 7;
+            const KeyRec r = get_key(smem + L.rec + parity * 32 * kpt + 32 * kk);
+            if (r.flags & 0x80u) {
+                const float *base = red + (kk * Do) * 9 + n;
+                float sum = 0.f;
+                if (DO) {
+#pragma unroll
+                    for (int q = 0; q < DO; ++q) sum += base[q * 9];
+                } else {
+                    for (int q = 0; q < Do; ++q) sum += base[q * 9];
+                }
+                a.phi_oct[(((int64_t)o * a.C + r.cell) * a.G + r.g) * 8 + n] = sum;
+            }
+        }
+    };
+    bool late = false, done = true;
+    int ntile_done = 0;
     for (; tile < a.ntiles; tile += gridDim.x, par ^= 1) {
         const int tn = tile + gridDim.x;
         uint32_t pk_n = 0;
@@ -905,7 +927,8 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
             if (tn < a.ntiles && key_n < nkeys) pk_n = a.cells[a.divG.div(key_n)];
         }
         cp_async_wait_all();
-        __syncthreads();
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; done = false; break; }
+        if (ntile_done > 0) reduce_tile(par ^ 1);
         // (2) features
         const KeyRec kr = get_key(smem + L.rec + par * 32 * kpt + 32 * (lane_row ? lk : 0));
         const bool act = lane_row && (kr.flags & 0x80u);
@@ -947,26 +970,26 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        // (3) layer 1; the next tile's key records and source copies; its faces
+        // (3) layer 1; the next tile's key records and source copies
         if (t == 0) mma_layer1(sbase, L.x, L.w1, tbase, bar);
         if (t < kpt) key_stage(tn, pk_n, par ^ 1);
-        bool late = t == 0 && !mbar_wait_bounded(bar, phase);
+        // (4) each warp waits for layer 1 itself, hidden layer through TMEM
+        if ((t & 31) == 0) late = !mbar_wait_bounded(bar, phase);
+        __syncwarp();
         phase ^= 1u;
-        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
-        face_stage(par ^ 1);
-        cp_async_commit();
-        // (4) hidden layer, layer 2
         tc_fence_after();
         hidden_to_tmem(twarp);
         tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; done = false; break; }
         tc_fence_after();
         if (t == 0) mma_layer2(sbase, L.w2, tbase, bar);
-        late = t == 0 && !mbar_wait_bounded(bar, phase);
+        face_stage(par ^ 1);
+        cp_async_commit();
+        // (5) each warp waits for layer 2 itself, outputs
+        if ((t & 31) == 0) late = !mbar_wait_bounded(bar, phase);
+        __syncwarp();
         phase ^= 1u;
-        if (__syncthreads_or(late)) { if (t == 0) misc[2] = 1; break; }
         tc_fence_after();
-        // (5) outputs
         uint32_t r8[8];
         tmem_ld8(twarp + 32, r8);
         tmem_wait_ld();
@@ -1003,22 +1026,14 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
 #pragma unroll
             for (int n = 0; n < 8; ++n) rr[n] = 0.f;
         }
-        __syncthreads();
-        // (6) flux partial: thread (key, node) sums the key's directions
-        for (int e = t; e < 8 * kpt; e += kTile) {
-            const int kk = e >> 3, n = e & 7;
-            const KeyRec r = get_key(smem + L.rec + par * 32 * kpt + 32 * kk);
-            if (r.flags & 0x80u) {
-                const float *base = red + (kk * Do) * 9 + n;
-                float sum = 0.f;
-                if (DO) {
-#pragma unroll
-                    for (int q = 0; q < DO; ++q) sum += base[q * 9];
-                } else {
-                    for (int q = 0; q < Do; ++q) sum += base[q * 9];
-                }
-                a.phi_oct[(((int64_t)o * a.C + r.cell) * a.G + r.g) * 8 + n] = sum;
-            }
+        ++ntile_done;
+    }
+    if (done) {
+        cp_async_wait_all();
+        if (__syncthreads_or(late)) {
+            if (t == 0) misc[2] = 1;
+        } else if (ntile_done > 0) {
+            reduce_tile(par ^ 1);
         }
     }
     cp_async_wait_all();
