@@ -34,7 +34,7 @@ def worker(rank, world, port, out):
 
 def test_two_replicas_take_the_slowest_rank():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.start_processes(worker, args=(world, free_port(), out), nprocs=world, start_method="spawn")
     for rank in range(world):
         ms, e2e, value = out[rank]
