@@ -143,17 +143,21 @@ def run_reference(args):
     ws, rank = dist_env()
     if rank != 0:
         return 0
-    times = []
+    times, walls = [], []
     cb = None
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         r = cpu_baseline(seconds_target=float(os.environ.get("SN_REF_SECONDS", "8")))
         if i >= args.warmup:
             times.append(r["value"])
+            walls.append(time.perf_counter() - t0)
             cb = r
     value = float(np.median(times))
     cb = dict(cb, value=value)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+    # the oracle on the host cores of rank 0; n_gpus is the launch's N
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(walls)),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
