@@ -41,23 +41,29 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+// One test of an mbarrier phase; the thread may be suspended in hardware for up to
+// hint_ns nanoseconds while the phase is incomplete (it resumes when the phase
+// completes), so a waiting warp does not spend issue slots spinning.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity, uint32_t hint_ns)
 {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; false after the iteration limit.
+// Bounded wait on an mbarrier phase: false once about 2^31 SM cycles (~1 s) have
+// passed without completion.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < (1u << 22); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity, 100000u)) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols)
