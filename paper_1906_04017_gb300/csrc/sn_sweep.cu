@@ -239,16 +239,18 @@ template <typename T>
 struct GeTileSmem {
     uint32_t face, ks, sig, rec, red, total;
 };
+// Every stage a tile writes while the previous tile may still be read is doubled, so
+// one barrier a tile suffices.
 template <typename T>
 __host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows)
 {
     GeTileSmem<T> m;
     m.face = 0;                                                   // 2 x [rows][12] inflow faces
-    m.ks = m.face + 2 * rows * 12 * (uint32_t)sizeof(T);          // [kpt][8] sources
-    m.sig = m.ks + kpt * 8 * (uint32_t)sizeof(T);                 // [kpt] opacities
-    m.rec = (m.sig + kpt * (uint32_t)sizeof(T) + 15) & ~15u;      // 4 x [kpt] key records
-    m.red = m.rec + 4 * 32 * kpt;                                 // [rows][9] w_d psi
-    m.total = m.red + rows * 9 * (uint32_t)sizeof(T);
+    m.ks = m.face + 2 * rows * 12 * (uint32_t)sizeof(T);          // 2 x [kpt][8] sources
+    m.sig = m.ks + 2 * kpt * 8 * (uint32_t)sizeof(T);             // 2 x [kpt] opacities
+    m.rec = (m.sig + 2 * kpt * (uint32_t)sizeof(T) + 15) & ~15u;  // 4 x [kpt] key records
+    m.red = m.rec + 4 * 32 * kpt;                                 // 2 x [rows][9] w_d psi
+    m.total = m.red + 2 * rows * 9 * (uint32_t)sizeof(T);
     return m;
 }
 
@@ -267,9 +269,7 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
     const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
     DirData<T> dd = {T(0), T(0), T(0), T(0)};
     if (lane_row) dd = a.dir[d];
-    T *red = reinterpret_cast<T *>(gsm + L.red);
-    const T *fks = reinterpret_cast<const T *>(gsm + L.ks) + 8 * lk;
-    const T *fsig = reinterpret_cast<const T *>(gsm + L.sig) + lk;
+    auto red_at = [&](int buf) -> T * { return reinterpret_cast<T *>(gsm + L.red) + buf * rows * 9; };
     auto rec_at = [&](int slot, int k) -> unsigned char * { return gsm + L.rec + (slot * kpt + k) * 32; };
     const int psi_o[3] = {o & 1, 2 + ((o >> 1) & 1), 4 + ((o >> 2) & 1)};
 
@@ -288,14 +288,16 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
         }
         put_key(rec_at(slot, t), r);
     };
-    // key thread t: copy the source and opacity of its key (record in `slot`)
-    auto key_copy = [&](int slot) {
+    // key thread t: copy the source and opacity of its key (record in `slot`) into
+    // stage buffer `sbuf`
+    auto key_copy = [&](int slot, int sbuf) {
         const KeyRec r = get_key(rec_at(slot, t));
         if (!(r.flags & 0x80u)) return;
         const int64_t gc = (int64_t)r.g * a.C + r.cell;
-        cp_async_bytes(sb + L.ks + t * 8 * (uint32_t)sizeof(T), a.S + gc * 8, 8 * (int)sizeof(T));
-        if (sizeof(T) == 4) cp_async4(sb + L.sig + 4 * t, a.sigt + gc);
-        else cp_async8(sb + L.sig + 8 * t, a.sigt + gc);
+        const uint32_t k = (uint32_t)(sbuf * kpt + t);
+        cp_async_bytes(sb + L.ks + k * 8 * (uint32_t)sizeof(T), a.S + gc * 8, 8 * (int)sizeof(T));
+        if (sizeof(T) == 4) cp_async4(sb + L.sig + 4 * k, a.sigt + gc);
+        else cp_async8(sb + L.sig + 8 * k, a.sigt + gc);
     };
     // row: copy its inflow faces (record in `slot`) into face buffer `fb`
     auto face_copy = [&](int slot, int fb) {
@@ -308,8 +310,9 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
         if (!(r.flags & 2u)) cp_async_bytes(dst + vb, a.fy + r.by + d, vb);
         if (!(r.flags & 4u)) cp_async_bytes(dst + 2 * vb, a.fz + r.bz + d, vb);
     };
-    // flux partial of the tile whose records are in `slot` and w_d psi in red
-    auto reduce_tile = [&](int slot) {
+    // flux partial of the tile whose records are in `slot` and w_d psi in red buffer `rb`
+    auto reduce_tile = [&](int slot, int rb) {
+        const T *red = red_at(rb);
         for (int e = t; e < 8 * kpt; e += rows) {
             const int kk = e >> 3, n = e & 7;
             const KeyRec r = get_key(rec_at(slot, kk));
@@ -333,26 +336,36 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
         key_rec(t0 + step, key_pk(t0 + step), 1);
     }
     __syncthreads();
-    if (t < kpt) key_copy(0);
+    if (t < kpt) key_copy(0, 0);
     face_copy(0, 0);
     cp_async_commit();
     T leak = T(0);
     int i = 0;
     for (int tile = t0; tile < a.ntiles; tile += step, ++i) {
-        const int slot = i & 3;
-        // cell of this thread's key two tiles ahead (used after the next barrier)
+        const int slot = i & 3, cur = i & 1, nxt = cur ^ 1;
+        // cell of this thread's key two tiles ahead (used after the barrier)
         const uint32_t pk2 = t < kpt ? key_pk(tile + 2 * step) : 0u;
         cp_async_wait_all();
         __syncthreads();
-        if (i > 0) reduce_tile((i - 1) & 3);
-        // next tile's faces (its records were built one iteration ago)
-        face_copy((i + 1) & 3, (i + 1) & 1);
+        // the only barrier of the tile: this tile's stage is complete, and every buffer
+        // written below was last read before it
+        if (i > 0) reduce_tile((i - 1) & 3, nxt);
+        // next tile's faces (its records were built one iteration ago); records two
+        // tiles ahead; sources one tile ahead
+        face_copy((i + 1) & 3, nxt);
+        if (t < kpt) {
+            key_rec(tile + 2 * step, pk2, (i + 2) & 3);
+            key_copy((i + 1) & 3, nxt);
+        }
+        cp_async_commit();
         // this tile's inputs from the stage
         const KeyRec kr = get_key(rec_at(slot, lane_row ? lk : 0));
         const bool act = lane_row && (kr.flags & 0x80u);
-        T S[8], ux[4], uy[4], uz[4], sig = T(0);
         if (act) {
-            const T *ff = reinterpret_cast<const T *>(gsm + L.face) + ((i & 1) * rows + t) * 12;
+            T S[8], ux[4], uy[4], uz[4];
+            const T *ff = reinterpret_cast<const T *>(gsm + L.face) + (cur * rows + t) * 12;
+            const T *fks = reinterpret_cast<const T *>(gsm + L.ks) + (cur * kpt + lk) * 8;
+            const T sig = reinterpret_cast<const T *>(gsm + L.sig)[cur * kpt + lk];
             const T *pi = a.psi_inc + 6 * kr.g;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -362,17 +375,6 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) S[q] = fks[q ^ o];
-            sig = *fsig;
-        }
-        __syncthreads();
-        // the stage of sources is free: records two tiles ahead, sources one tile ahead
-        if (t < kpt) {
-            key_rec(tile + 2 * step, pk2, (i + 2) & 3);
-            key_copy((i + 1) & 3);
-        }
-        cp_async_commit();
-        T *r = red + t * 9;
-        if (act) {
             T x[8];
             cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
             if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, x[1], x[3], x[5], x[7]);
@@ -381,13 +383,14 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
             else leak += dd.t3y * (x[2] + x[3] + x[6] + x[7]);
             if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, x[4], x[5], x[6], x[7]);
             else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
+            T *r = red_at(cur) + t * 9;
 #pragma unroll
             for (int n = 0; n < 8; ++n) r[n ^ o] = dd.w * x[n];
         }
     }
     cp_async_wait_all();
     __syncthreads();
-    if (i > 0) reduce_tile((i - 1) & 3);
+    if (i > 0) reduce_tile((i - 1) & 3, (i - 1) & 1);
     leak *= dd.w * a.vol12;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
