@@ -74,10 +74,10 @@ struct SweepArgs {
 #ifndef SN_GE_BLOCK
 #define SN_GE_BLOCK 128
 #endif
-// the persistent form keeps a few more values live across tiles: 3 CTAs per SM (170
-// registers a thread) measured faster than 4 with spills
+// persistent form: 4 CTAs per SM (128 registers a thread, a few spills) measured faster
+// than 3 (168 registers) or 2 once a tile needed a single barrier
 #ifndef SN_GE_TILE_MINBLOCKS
-#define SN_GE_TILE_MINBLOCKS 3
+#define SN_GE_TILE_MINBLOCKS 4
 #endif
 template <typename T, bool REFINE, int XMODE = 0>
 __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS : 1) sweep_plane_ge(SweepArgs<T> a)
@@ -423,7 +423,7 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
                                                                       : sweep_ge_tiles<T, false, 0>;
     if (L.total > 48 * 1024)
         SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    // persistent CTAs per octant: the register-limited residency (3 a SM in FP32, 1 in FP64)
+    // persistent CTAs per octant: the register-limited residency (4 a SM in FP32, 1 in FP64)
     const int cap = std::max(1, num_sms() * (sizeof(T) == 4 ? SN_GE_TILE_MINBLOCKS : 1) / 8);
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
     for (int s = 0; s < h->nplanes; ++s) {
