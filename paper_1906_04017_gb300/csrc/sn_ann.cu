@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(128) grad_kernel(const float *__restrict__ P, 
     float *xr = sX + t * kXs, *hr = sH + t * kHs, *gar = sGA + t * kHs, *gor = sGO + t * kOs;
     if (i < batch) {
         const int64_t r = (row0 + i) % nrows;
-        float x[kNin], tt[8], h[kNhid], o[8];
+        float x[kNin], tt[8], h[kNhid];
 #pragma unroll
         for (int k = 0; k < kNin; ++k) { x[k] = feat[kNin * r + k]; xr[k] = x[k]; }
 #pragma unroll
@@ -279,7 +279,6 @@ __global__ void __launch_bounds__(128) grad_kernel(const float *__restrict__ P, 
             float a = b2[q];
 #pragma unroll
             for (int j = 0; j < kNhid; ++j) a = fmaf(W2[q * kNhid + j], h[j], a);
-            o[q] = a;
             d[q] = tt[q] - a;
             sd += d[q];
             st += tt[q];
