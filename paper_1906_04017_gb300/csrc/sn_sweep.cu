@@ -249,8 +249,8 @@ __host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows)
     m.ks = m.face + 2 * rows * 12 * (uint32_t)sizeof(T);          // 2 x [kpt][8] sources
     m.sig = m.ks + 2 * kpt * 8 * (uint32_t)sizeof(T);             // 2 x [kpt] opacities
     m.rec = (m.sig + 2 * kpt * (uint32_t)sizeof(T) + 15) & ~15u;  // 4 x [kpt] key records
-    m.red = m.rec + 4 * 32 * kpt;                                 // 2 x [rows][9] w_d psi
-    m.total = m.red + 2 * rows * 9 * (uint32_t)sizeof(T);
+    m.red = m.rec + 4 * 32 * kpt;                                 // 2 x [rows][8] w_d psi (canonical)
+    m.total = m.red + 2 * rows * 8 * (uint32_t)sizeof(T);
     return m;
 }
 
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
     const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
     DirData<T> dd = {T(0), T(0), T(0), T(0)};
     if (lane_row) dd = a.dir[d];
-    auto red_at = [&](int buf) -> T * { return reinterpret_cast<T *>(gsm + L.red) + buf * rows * 9; };
+    auto red_at = [&](int buf) -> T * { return reinterpret_cast<T *>(gsm + L.red) + buf * rows * 8; };
     auto rec_at = [&](int slot, int k) -> unsigned char * { return gsm + L.rec + (slot * kpt + k) * 32; };
     const int psi_o[3] = {o & 1, 2 + ((o >> 1) & 1), 4 + ((o >> 2) & 1)};
 
@@ -295,7 +295,14 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
         if (!(r.flags & 0x80u)) return;
         const int64_t gc = (int64_t)r.g * a.C + r.cell;
         const uint32_t k = (uint32_t)(sbuf * kpt + t);
-        cp_async_bytes(sb + L.ks + k * 8 * (uint32_t)sizeof(T), a.S + gc * 8, 8 * (int)sizeof(T));
+        // node by node into the canonical order of the octant (canonical n = physical n ^ o)
+        const uint32_t dst = sb + L.ks + k * 8 * (uint32_t)sizeof(T);
+        const T *src = a.S + gc * 8;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            if (sizeof(T) == 4) cp_async4(dst + 4 * (p ^ o), src + p);
+            else cp_async8(dst + 8 * (p ^ o), src + p);
+        }
         if (sizeof(T) == 4) cp_async4(sb + L.sig + 4 * k, a.sigt + gc);
         else cp_async8(sb + L.sig + 8 * k, a.sigt + gc);
     };
@@ -317,13 +324,13 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
             const int kk = e >> 3, n = e & 7;
             const KeyRec r = get_key(rec_at(slot, kk));
             if (!(r.flags & 0x80u)) continue;
-            const T *base = red + (kk * Do) * 9 + n;
+            const T *base = red + (kk * Do) * 8 + (n ^ o);   // rows hold canonical order
             T sum = T(0);
             if (DO) {
 #pragma unroll
-                for (int q = 0; q < DO; ++q) sum += base[q * 9];
+                for (int q = 0; q < DO; ++q) sum += base[q * 8];
             } else {
-                for (int q = 0; q < Do; ++q) sum += base[q * 9];
+                for (int q = 0; q < Do; ++q) sum += base[q * 8];
             }
             a.phi_oct[(((int64_t)o * a.C + r.cell) * a.G + r.g) * 8 + n] = sum;
         }
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
                 uz[q] = (kr.flags & 4u) ? pi[psi_o[2]] : ff[8 + q];
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) S[q] = fks[q ^ o];
+            for (int q = 0; q < 8; ++q) S[q] = fks[q];
             T x[8];
             cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
             if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, x[1], x[3], x[5], x[7]);
@@ -383,9 +390,9 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
             else leak += dd.t3y * (x[2] + x[3] + x[6] + x[7]);
             if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, x[4], x[5], x[6], x[7]);
             else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
-            T *r = red_at(cur) + t * 9;
-#pragma unroll
-            for (int n = 0; n < 8; ++n) r[n ^ o] = dd.w * x[n];
+            T *r = red_at(cur) + t * 8;
+            store4(reinterpret_cast<Vec4<T> *>(r), dd.w * x[0], dd.w * x[1], dd.w * x[2], dd.w * x[3]);
+            store4(reinterpret_cast<Vec4<T> *>(r) + 1, dd.w * x[4], dd.w * x[5], dd.w * x[6], dd.w * x[7]);
         }
     }
     cp_async_wait_all();
