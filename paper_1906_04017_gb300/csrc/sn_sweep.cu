@@ -595,12 +595,28 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
         const int nc = (int)min((int64_t)TC, C - c0);
         const int nel = nc * G8;
         const T *po = phi_oct + c0 * G8;
-        for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-            T s = T(0);
+        // 16-byte loads (4 floats or 2 doubles of one cell: G*8 is a multiple of 8);
+        // the same fixed octant order per value
+        constexpr int V = 16 / (int)sizeof(T);
+        for (int i = threadIdx.x * V; i < nel; i += blockDim.x * V) {
+            T s[V];
 #pragma unroll
-            for (int o = 0; o < 8; ++o) s += po[(int64_t)o * stride_oct + i];
+            for (int j = 0; j < V; ++j) s[j] = T(0);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const T *src = po + (int64_t)o * stride_oct + i;
+                if constexpr (V == 4) {
+                    const float4 f = *reinterpret_cast<const float4 *>(src);
+                    s[0] += f.x; s[1] += f.y; s[2] += f.z; s[3] += f.w;
+                } else {
+                    const double2 f = *reinterpret_cast<const double2 *>(src);
+                    s[0] += f.x; s[1] += f.y;
+                }
+            }
             const int cl = (int)divG8.div((uint32_t)i);
-            tile[cl * row + (i - cl * G8)] = s;
+            T *dst = tile + cl * row + (i - cl * G8);
+#pragma unroll
+            for (int j = 0; j < V; ++j) dst[j] = s[j];
         }
         __syncthreads();
         const int nk = nc * 8;
