@@ -134,9 +134,15 @@ def cpu_baseline(seconds_target=15.0):
     dt = time.perf_counter() - t0
     solves = P.ncell * P.G * k
     cores = min(P.G, oracle.num_threads())
+    # one group alone runs on one thread
+    k1 = max(1, k // 2)
+    t0 = time.perf_counter()
+    P.sweep(S, groups=(0, 1), dirs=(0, k1))
+    dt1 = time.perf_counter() - t0
     return {"value": solves / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": P.ncell * k1 / dt1,
             "sample": "blocked_64, one sweep of all 8 groups x %d of 80 directions (%d solves, %.1f s), "
-                      "FP64, groups in parallel" % (k, solves, dt)}
+                      "FP64, groups in parallel; single thread: group 0 x %d directions" % (k, solves, dt, k1)}
 
 
 def run_reference(args):
