@@ -234,6 +234,13 @@ def ann_form(P, steps):
     qphi = Q.source_iterate(tol=1e-4, max_it=200, allow_noconv=True)["phi"]
     cells = torch.cat([Q.harvest(Q.source(qphi), 1 << 19, seed=s) for s in (11, 12)])
     Q.close()
+    # the harvested set is fixed by its seeds but arrives in the order the GPU threads
+    # claimed their slots; sort it so that the fine-tuning, and what follows, repeats
+    # from run to run
+    host = cells.cpu().numpy()
+    order = np.lexsort((host[:, 2], host[:, 1], host[:, 0], host[:, 23], host[:, 19], host[:, 15],
+                        host[:, 6], host[:, 7]))
+    cells = torch.from_numpy(np.ascontiguousarray(host[order])).cuda()
     feat, targ = sn.surrogate_prepare(cells)
     P.surrogate_fit(feat, targ, steps=20000, batch=8192, lr=5e-4)
     out["finetune"] = {"harvested_cells": int(cells.shape[0]), "mae": P.surrogate_eval(feat, targ),
