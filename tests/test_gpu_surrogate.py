@@ -199,8 +199,11 @@ def oracle_ann_sweep(wl, p, S, predict):
     return phi
 
 
-def test_ann_sweep_matches_oracle_network_sweep(sn):
-    wl = W.random_small(3, 4, 2, order=4, G=2, seed=8, psi_inc=True)
+@pytest.mark.parametrize("order", [2, 4, 8, 12])
+def test_ann_sweep_matches_oracle_network_sweep(sn, order):
+    """The tensor-core surrogate sweep against the oracle's network swept in Python,
+    for 1, 3, 10 and 21 directions per octant (128 down to 6 keys a tile)."""
+    wl = W.random_small(3, 4, 2, order=order, G=2, seed=8, psi_inc=True)
     P = sn.Problem(wl)
     p = mlp.init_params(12) * 0.5
     P.surrogate_set_weights(p)

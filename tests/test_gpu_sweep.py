@@ -83,8 +83,12 @@ def test_source_iteration_onecube_fp32(sn):
     assert rel_err(r["phi"].cpu().numpy(), ref["phi"]) < TOL
 
 
-def test_fp64_sweep_matches_oracle(sn):
-    wl = W.random_small(7, 5, 6, order=8, G=2, seed=3, psi_inc=True)
+@pytest.mark.parametrize("order", [2, 8, 12])
+def test_fp64_sweep_matches_oracle(sn, order):
+    """FP64 elimination sweep; S2 (one direction per octant, 128 keys a tile) takes
+    the persistent kernel past 48 KB of shared memory, S8 and S12 its compiled
+    direction counts."""
+    wl = W.random_small(7, 5, 6, order=order, G=2, seed=3, psi_inc=True)
     P = sn.Problem(wl, fp64=True)
     rng = np.random.default_rng(0)
     S = rng.uniform(0.0, 1.0, (P.G, P.ncell, 8))
