@@ -863,20 +863,25 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
     const int psi_o[3] = {o & 1, 2 + ((o >> 1) & 1), 4 + ((o >> 2) & 1)};
 
     // key records of a tile (key threads only) and the copies of their sources
-    auto key_stage = [&](int tl, uint32_t pk, int parity) {
+    auto key_record = [&](int tl, uint32_t pk, int parity) -> KeyRec {
         const uint32_t key = (uint32_t)tl * (uint32_t)kpt + (uint32_t)t;
         KeyRec r;
         if (tl < a.ntiles && key < nkeys) {
             make_key<DO>(a, o, key, pk, r);
-            const int64_t gc = (int64_t)r.g * a.C + r.cell;
-            cp_async16(sbase + L.ks + 32 * t, a.S + gc * 8);
-            cp_async16(sbase + L.ks + 32 * t + 16, a.S + gc * 8 + 4);
-            cp_async4(sbase + L.sig + 4 * t, a.sigt + gc);
         } else {
             r.bx = r.by = r.bz = 0; r.flags = 0; r.cell = r.g = 0; r.pad0 = r.pad1 = 0;
         }
         put_key(smem + L.rec + parity * 32 * kpt + 32 * t, r);
+        return r;
     };
+    auto key_copy = [&](const KeyRec &r) {
+        if (!(r.flags & 0x80u)) return;
+        const int64_t gc = (int64_t)r.g * a.C + r.cell;
+        cp_async16(sbase + L.ks + 32 * t, a.S + gc * 8);
+        cp_async16(sbase + L.ks + 32 * t + 16, a.S + gc * 8 + 4);
+        cp_async4(sbase + L.sig + 4 * t, a.sigt + gc);
+    };
+    auto key_stage = [&](int tl, uint32_t pk, int parity) { key_copy(key_record(tl, pk, parity)); };
     // a row's inflow faces of the tile whose key records are in `parity`
     auto face_stage = [&](int parity) {
         if (!lane_row) return;
@@ -887,16 +892,19 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
         if (!(r.flags & 4u)) cp_async16(sface + 32, a.fz + r.bz + d);
     };
 
-    // set-up above reads only what no hyperplane writes; the inputs below need the
-    // previous hyperplane (or fallback pass) complete
-    griddep_wait();
+    // set-up above and the first tile's key records read only what no hyperplane
+    // writes; the copies of its inputs need the previous hyperplane (or fallback pass)
+    // complete
     int tile = blockIdx.x;
     int par = 0;
+    KeyRec r0 = {0, 0, 0, 0u, 0, 0, 0, 0};
     if (t < kpt) {
         const uint32_t key = (uint32_t)tile * (uint32_t)kpt + (uint32_t)t;
         const uint32_t pk = key < nkeys ? a.cells[a.divG.div(key)] : 0u;
-        key_stage(tile, pk, 0);
+        r0 = key_record(tile, pk, 0);
     }
+    griddep_wait();
+    if (t < kpt) key_copy(r0);
     __syncthreads();
     face_stage(0);
     cp_async_commit();

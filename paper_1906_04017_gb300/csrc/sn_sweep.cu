@@ -336,13 +336,15 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
         }
     };
 
-    griddep_wait();
     const int t0 = blockIdx.x, step = gridDim.x;
+    // the first two tiles' key records need only the hyperplane's cell table (written
+    // once at set-up): they are built while the previous hyperplane may still run
     if (t < kpt) {
         key_rec(t0, key_pk(t0), 0);
         key_rec(t0 + step, key_pk(t0 + step), 1);
     }
     __syncthreads();
+    griddep_wait();
     if (t < kpt) key_copy(0, 0);
     face_copy(0, 0);
     cp_async_commit();
