@@ -144,7 +144,11 @@ sn_status sn_cell_solve_batch_f64(const double *in27, double *psi, int64_t n, vo
  * density, i.e. already divided by 4 pi); writes phi (device [G][ncell][8]).
  * Hyperplane-wavefront order; all octants, directions and groups of one
  * hyperplane run in one launch.  Balance tallies of this sweep are kept for
- * sn_get_balance.  S and phi must not overlap.
+ * sn_get_balance; reading them synchronises the handle's stream before the call
+ * returns.  S and phi must not overlap.  The GE modes and SN_SOLVE_ANN give the
+ * same bits on every run; with SN_SOLVE_ANN_GATED the rows the gate rejects are
+ * re-solved by elimination between hyperplanes and added to the flux with
+ * atomics, so the last bits may differ from run to run.
  * ------------------------------------------------------------------------- */
 sn_status sn_sweep(sn_handle h, const void *S, void *phi, sn_solve_mode mode);
 
