@@ -496,6 +496,95 @@ def adjoint_check(args):
     return 0
 
 
+def paper_tables(args):
+    """The evaluation of Sec. 4 run with both solvers: Problems 1-4 (10 cm cube,
+    unit inflow on the x-, y-, z- faces) at S2-S8 on 100^3 cells and at 10^3-100^3
+    cells with S8.  For each case: the elimination solution (FP32 GE with
+    refinement) and the surrogate solution (the 27-64-8 network trained on the
+    one-cell distribution, ungated as in the paper), the mean relative error of the
+    cell-averaged flux (Eq. (20)), the solve times and the time reduction.  Problem 4
+    (scattering ratio 0.99) runs the source iteration to the mean change of Eq. (21)
+    below 1e-4 with both solvers and reports their iteration counts.  Prints one
+    JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1906_04017_gb300 import sn, workloads
+    # the network, trained once on the one-cell distribution
+    T = sn.Problem(workloads.random_small(2, 2, 2, order=2, G=1))
+    x = torch.from_numpy(workloads.onecell_problems(1 << 20, seed=0).astype(np.float32)).cuda()
+    tr, te = T.surrogate_train(x, n_test=1 << 16, steps=20000, batch=8192, lr=2e-3, seed=1)
+    weights = T.surrogate_weights()
+    T.close()
+    del x
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def solve(P, mode, iterate):
+        if not iterate:
+            S = P.source(P.flux_tensor())           # q / 4 pi: no scattering
+            P.sweep(S, mode=mode)                    # warm-up
+            phi, ms = timed(lambda: P.sweep(S, mode=mode))
+            return phi, ms, 1, "one sweep"
+        phi = P.flux_tensor()
+        P.source_iterate(phi=phi, tol=0.0, max_it=1, mode=mode, use_graph=True, allow_noconv=True)  # capture
+        phi.zero_()
+
+        hist = []
+
+        def run():
+            for it in range(1, 2001):
+                try:
+                    r = P.source_iterate(phi=phi, tol=0.0, max_it=1, mode=mode, use_graph=True, allow_noconv=True)
+                except sn.SnError as e:
+                    return it, "diverged: %s" % e
+                hist.append(r["change_mean"])
+                if r["change_mean"] < 1e-4:
+                    return it, "converged"
+            return 2000, "not converged"
+        (its, status), ms = timed(run)
+        # effective spectral radius: geometric mean ratio of the last 20 changes
+        rho = (hist[-1] / hist[-21]) ** (1.0 / 20) if len(hist) > 21 and hist[-21] > 0 else None
+        return phi, ms, its, status + ("" if rho is None else ", rho %.4f" % rho)
+
+    cases = [(k, 100, o) for k in (1, 2, 3, 4) for o in (2, 4, 6, 8)]
+    cases += [(k, n, 8) for k in (1, 2, 3, 4) for n in (10, 25, 50)]
+    rows = []
+    t0 = time.time()
+    for k, n, order in cases:
+        P = sn.Problem(workloads.paper_problem(k, n=n, order=order))
+        P.surrogate_set_weights(weights)
+        it4 = k == 4
+        ge, ms_ge, it_ge, st_ge = solve(P, sn.GE32R, it4)
+        ge = ge.clone()
+        ann, ms_ann, it_ann, st_ann = solve(P, sn.ANN, it4)
+        finite = bool(torch.isfinite(ann).all())
+        row = {"problem": k, "cells": n, "order": order, "solves_per_sweep": P.solves_per_sweep,
+               "ge_ms": ms_ge, "ann_ms": ms_ann, "ge_iters": it_ge, "ann_iters": it_ann,
+               "ge_status": st_ge, "ann_status": st_ann,
+               "eps_P": eps_p(ann, ge) if finite else None,
+               "time_reduction": 1.0 - ms_ann / ms_ge}
+        if it4:
+            # with the residual gate (not in the paper): tau = 0.01
+            P.surrogate_set_gate(0.01)
+            gt, ms_gt, it_gt, st_gt = solve(P, sn.ANN_GATED, it4)
+            row.update({"gated_ms": ms_gt, "gated_iters": it_gt, "gated_status": st_gt,
+                        "gated_eps_P": eps_p(gt, ge) if bool(torch.isfinite(gt).all()) else None,
+                        "gated_time_reduction": 1.0 - ms_gt / ms_ge})
+        rows.append(row)
+        P.close()
+    print(json.dumps({"paper_tables": "Problems 1-4 of Sec. 4, both solvers, FP32, one GPU",
+                      "network": {"train_mae": tr, "test_mae": te, "training": "2^20 one-cell problems, 20000 Adam steps"},
+                      "wall_s": time.time() - t0, "rows": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -504,6 +593,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ann", action="store_true")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="Problems 1-4 of the paper with both solvers (prints its own JSON line)")
     ap.add_argument("--adjoint-check", action="store_true",
                     help="adjoint gradients vs FP64 central differences at 32^3 (prints its own JSON line)")
     args = ap.parse_args()
@@ -513,6 +604,8 @@ def main():
         return run_reference(args)
     if args.adjoint_check:
         return adjoint_check(args)
+    if args.paper_tables:
+        return paper_tables(args)
     return run_gpu(args)
 
 

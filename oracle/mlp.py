@@ -18,7 +18,8 @@ reversed along axis a, so one network serves every octant -- and then
   x[6]    = log(max(sigma_t, SIG_FLOOR)) / LOG_SIG_SCALE
   x[7:15] = S_canonical / s,  x[15:27] = up_canonical / s,
   s = max(max|S|, max|up|)   (the "normalised by the inflow/source max" scale)
-and the network predicts psi_canonical / s.  A problem with s = 0 has psi = 0.
+and the network predicts psi_canonical / s.  A problem with s = 0 has psi = 0; a scale
+at or below 1e-30 is treated as 0 (inputs and target scaled by 0).
 
 Parameter vector (2312 values): W1[64][27] row-major, b1[64], W2[8][64], b2[8].
 """
@@ -29,6 +30,8 @@ NPARAM = NHID * NIN + NHID + NOUT * NHID + NOUT
 LAMBDA, GAMMA1, GAMMA2 = 0.2, 10.0, 0.01
 LOG_H_SHIFT, LOG_H_SCALE = 1.15, 1.15
 LOG_SIG_SCALE, SIG_FLOOR = 4.5, 1e-6
+# an input scale at or below this counts as zero (a flux that FP32 cannot hold)
+SCALE_FLOOR = 1e-30
 
 
 def unpack(p):
@@ -80,7 +83,7 @@ def features(in27):
     """(x [n,27], s [n], mask [n]) of the input construction in the module docstring."""
     aom, h, sig, S, U, mask = canonical(in27)
     s = np.maximum(np.abs(S).max(1), np.abs(U).max(1))
-    inv = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+    inv = np.where(s > SCALE_FLOOR, 1.0 / np.where(s > SCALE_FLOOR, s, 1.0), 0.0)
     x = np.empty((aom.shape[0], NIN))
     x[:, 0:3] = 2.0 * aom - 1.0
     x[:, 3:6] = (np.log(h) + LOG_H_SHIFT) / LOG_H_SCALE
@@ -95,7 +98,7 @@ def targets(psi, in27):
     _, s, mask = features(in27)
     k = np.arange(8)
     pc = np.take_along_axis(np.asarray(psi, dtype=np.float64), k[None, :] ^ mask[:, None], 1)
-    inv = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+    inv = np.where(s > SCALE_FLOOR, 1.0 / np.where(s > SCALE_FLOOR, s, 1.0), 0.0)
     return pc * inv[:, None]
 
 

@@ -60,6 +60,10 @@ __device__ __forceinline__ void solve_in27(const T *p, T (&psi)[8])
 constexpr int kNin = 27, kNhid = 64, kNout = 8;
 constexpr int kNparam = kNhid * kNin + kNhid + kNout * kNhid + kNout;   // 2312
 constexpr float kLogHShift = 1.15f, kLogHScale = 1.15f, kLogSigScale = 4.5f, kSigFloor = 1e-6f;
+// Input scales at or below this are treated as zero (inputs and target scaled by 0):
+// fluxes that underflow FP32, e.g. a hundred mean free paths into an absorber, would
+// otherwise give an infinite 1/s.
+constexpr float kScaleFloor = 1e-30f;
 
 __device__ __forceinline__ float input_scale(const float (&S)[8], const float (&ux)[4], const float (&uy)[4],
                                              const float (&uz)[4])

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(128) prepare_kernel(const float *__restrict__ 
         CanonCell<float> c;
         canonicalize(p, c);
         const float s = input_scale(c.S, c.ux, c.uy, c.uz);
-        const float inv = s > 0.f ? 1.f / s : 0.f;
+        const float inv = s > kScaleFloor ? 1.f / s : 0.f;
         float x[kNin];
         ann_features(fabsf(p[0]), fabsf(p[1]), fabsf(p[2]), p[3], p[4], p[5], c.sig, c.S, c.ux, c.uy, c.uz, inv, x);
 #pragma unroll
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(128, 4) ann_cells_kernel(const float *__restri
             canonicalize(p, c);
             s = input_scale(c.S, c.ux, c.uy, c.uz);
             ann_features(fabsf(p[0]), fabsf(p[1]), fabsf(p[2]), p[3], p[4], p[5], c.sig, c.S, c.ux, c.uy, c.uz,
-                         s > 0.f ? 1.f / s : 0.f, x);
+                         s > kScaleFloor ? 1.f / s : 0.f, x);
         }
         if (t < cnt) write_x_row(smem + kCellOffX, t, x);
         fence_async_smem();
@@ -964,7 +964,7 @@ __global__ void __launch_bounds__(128, GATED ? 6 : 8) sweep_plane_ann(AnnSweepAr
                 c.t3x = dd.t3x; c.t3y = dd.t3y; c.t3z = dd.t3z;
                 c.mask = o;
                 s = input_scale(c.S, c.ux, c.uy, c.uz);
-                const float inv = s > 0.f ? rcp_approx(s) : 0.f;
+                const float inv = s > kScaleFloor ? rcp_approx(s) : 0.f;
                 x[0] = xo0; x[1] = xo1; x[2] = xo2;
                 x[3] = lhx; x[4] = lhy; x[5] = lhz;
                 x[6] = lg2_approx(fmaxf(c.sig, kSigFloor)) * lsig;

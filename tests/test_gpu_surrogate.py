@@ -276,3 +276,19 @@ def test_harvest_returns_the_sweeps_one_cell_problems(sn):
     y = P.harvest(S, cap=P.solves_per_sweep // 10, seed=3)
     P.close()
     assert 0.85 * (P.solves_per_sweep // 10) <= y.shape[0] <= P.solves_per_sweep // 10
+
+
+def test_ann_sweep_underflowing_flux_stays_finite(sn):
+    """A hundred mean free paths of pure absorber (the paper's Problem 1 on 100^3
+    cells of one mean free path): the flux underflows FP32 deep inside, the
+    surrogate's input scale there counts as zero, and its flux stays finite
+    everywhere (like the elimination's)."""
+    wl = W.paper_problem(1, n=100, order=2)
+    P = sn.Problem(wl)
+    P.surrogate_set_weights(mlp.init_params(3))
+    S = P.source(P.flux_tensor())
+    ann = P.sweep(S, mode=sn.ANN)
+    ge = P.sweep(S, mode=sn.GE32R)
+    P.close()
+    assert torch.isfinite(ann).all() and torch.isfinite(ge).all()
+    assert (ge.abs() < 1e-30).any().item()        # the case is really there

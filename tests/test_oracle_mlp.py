@@ -109,3 +109,13 @@ def test_training_reduces_loss():
     p0 = mlp.init_params(0)
     p1 = mlp.train(p0, f, t, steps=300, batch=256, lr=2e-3)
     assert mlp.loss(p1, f, t) < 0.5 * mlp.loss(p0, f, t)
+
+
+def test_vanishing_input_scale_counts_as_zero():
+    """An input scale at or below 1e-30 (a flux FP32 cannot hold) scales inputs and
+    target by zero instead of producing an infinite 1/s."""
+    x = W.onecell_problems(4, seed=2)
+    x[:, 7:27] *= 1e-36
+    feat, s, _ = mlp.features(x)
+    assert np.all(np.isfinite(feat)) and np.all(feat[:, 7:27] == 0.0)
+    assert np.all(mlp.targets(np.ones((4, 8)), x) == 0.0)

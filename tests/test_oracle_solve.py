@@ -230,3 +230,16 @@ def test_mirror_symmetry():
     phi = r["phi"].reshape(nz, ny, nx, 2, 2, 2)          # node (c, b, a)
     mirrored = phi[:, :, ::-1, :, :, ::-1]
     assert np.allclose(phi, mirrored, rtol=1e-11, atol=1e-13)
+
+
+def test_problem4_iteration_rate_is_the_scattering_ratio():
+    """The paper's Problem 4 (sigma_s / sigma_t = 0.99 in a box a hundred mean free
+    paths wide): almost nothing leaks, so the source iteration's error shrinks by
+    about the scattering ratio each sweep (the infinite-medium rate)."""
+    O = oracle.OracleProblem(W.paper_problem(4, n=10, order=2))
+    phi, hist = None, []
+    for _ in range(80):
+        r = O.source_iterate(0.0, 1, phi0=phi)
+        phi, _ = r["phi"], hist.append(r["change_mean"])
+    rho = (hist[-1] / hist[-21]) ** (1.0 / 20)
+    assert 0.975 < rho <= 0.99
