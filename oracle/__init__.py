@@ -6,9 +6,9 @@ The product library never calls it and shares no code with it.
 
 The sweep, the per-cell assembly, the Gaussian elimination and the source
 iteration live in plain C (``sn_oracle.c``, FP64, built by ``oracle/build.py``);
-this module is the ctypes wrapper, plus the numpy FP64 oracle of the
-surrogate network (``oracle.mlp``) and of the discrete adjoint
-(``oracle.adjoint``).
+this module is the ctypes wrapper, plus the numpy FP64 oracles of the
+surrogate network (``oracle.mlp``), of the paper's per-octant networks
+(``oracle.octant_net``) and of the discrete adjoint (``oracle.adjoint``).
 """
 import ctypes
 import os
@@ -41,6 +41,10 @@ class Problem(ctypes.Structure):
     ]
 
 
+class OctNet(ctypes.Structure):
+    _fields_ = [("p", _dp), ("lo", _dp), ("hi", _dp)]
+
+
 def _declare(L):
     L.or_ge.argtypes = [ctypes.c_int, _dp, _dp, _dp]
     L.or_lqn.argtypes = [ctypes.c_int, _dp, _dp]
@@ -56,6 +60,9 @@ def _declare(L):
     L.or_source_iterate.argtypes = [P, ctypes.c_double, ctypes.c_int, _dp,
                                     ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
     L.or_num_threads.argtypes = []
+    N = ctypes.POINTER(OctNet)
+    L.or_octnet_cell_batch.argtypes = [N, ctypes.c_long, _dp, _dp]
+    L.or_sweep_octnet.argtypes = [P, N, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
     L.or_adjoint.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp,
                              ctypes.POINTER(ctypes.c_int)]
 
@@ -129,6 +136,24 @@ def cell_solve(in27):
     return out
 
 
+class _OctNetArrays:
+    """FP64 copies of per-octant network parameters [8, 288] and input ranges [8, 26]
+    kept alive beside their ctypes view."""
+
+    def __init__(self, P, lo, hi):
+        self.P, self.lo, self.hi = _f64(P).reshape(8, 288), _f64(lo).reshape(8, 26), _f64(hi).reshape(8, 26)
+        self.c = OctNet(_p(self.P), _p(self.lo), _p(self.hi))
+
+
+def octnet_cell(P, lo, hi, in27):
+    """psi [N, 8] of the per-octant networks (the C oracle's evaluation) on in27 [N, 27]."""
+    net = _OctNetArrays(P, lo, hi)
+    x = _f64(np.atleast_2d(in27))
+    out = np.zeros((x.shape[0], 8))
+    lib().or_octnet_cell_batch(ctypes.byref(net.c), x.shape[0], _p(x), _p(out))
+    return out
+
+
 class OracleProblem:
     """Holds the FP64 arrays of one problem and the ctypes view of them.
 
@@ -170,17 +195,24 @@ class OracleProblem:
             raise ZeroDivisionError("zero pivot")
         return psi, tal
 
-    def sweep(self, S, groups=None, dirs=None):
+    def sweep(self, S, groups=None, dirs=None, octnet=None):
         """phi[G,ncell,8] = sum_d w_d psi_d for the isotropic source S[G,ncell,8].
 
         ``groups`` / ``dirs`` are (begin, end) ranges; phi is zero outside them.
-        Returns (phi, tallies[4])."""
+        ``octnet`` = (P [8, 288], lo [8, 26], hi [8, 26]) replaces every per-cell
+        solve by the octant networks (oracle.octant_net).  Returns (phi, tallies[4])."""
         S = _f64(S).reshape(self.G, self.ncell, 8)
         g0, g1 = groups if groups else (0, self.G)
         d0, d1 = dirs if dirs else (0, self.ndir)
         phi = np.zeros((self.G, self.ncell, 8))
         tal = np.zeros(4)
-        if lib().or_sweep(ctypes.byref(self.c), _p(S), _p(phi), g0, g1, d0, d1, _p(tal)) != 0:
+        if octnet is None:
+            rc = lib().or_sweep(ctypes.byref(self.c), _p(S), _p(phi), g0, g1, d0, d1, _p(tal))
+        else:
+            net = _OctNetArrays(*octnet)
+            rc = lib().or_sweep_octnet(ctypes.byref(self.c), ctypes.byref(net.c), _p(S), _p(phi), g0, g1, d0, d1,
+                                       _p(tal))
+        if rc != 0:
             raise ZeroDivisionError("zero pivot")
         return phi, tal
 

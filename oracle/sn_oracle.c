@@ -313,6 +313,56 @@ int or_cell_solve_batch(long n, const double *in27, double *psi)
 }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's per-octant networks as a one-cell solver (Sec. 3, Eqs. (15)-  */
+/* (18); Sec. 4: one network per octant).  Network o serves the directions   */
+/* with octant bits (mu < 0) | (eta < 0) << 1 | (xi < 0) << 2.  Inputs, in   */
+/* the order of the list in Sec. 3: the 12 upwind face values, mu, eta, the  */
+/* 8 nodal sources, sigma_t, dx, dy, dz; each scaled by Eq. (16),            */
+/* x = (I - alpha (I_min + I_max) / 2) / |I_max - I_min|, alpha = 0.27.       */
+/* h = tanh(W1 x + b1); psi_d = z_d (z_d >= 0) or beta (e^{z_d} - 1) with     */
+/* z = W2 h + b2 and beta = 0.1 max |psi_inc| over the 12 upwind values.      */
+/* Parameters per octant (288): W1[8][26], b1[8], W2[8][8], b2[8].           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const double *p;      /* [8][288]                                       */
+    const double *lo;     /* [8][26] a-priori input minima                   */
+    const double *hi;     /* [8][26] a-priori input maxima                   */
+} or_octnet;
+
+void or_octnet_cell(const or_octnet *net, const double *in27, double *psi)
+{
+    const int o = (in27[0] < 0.0) | ((in27[1] < 0.0) << 1) | ((in27[2] < 0.0) << 2);
+    const double *P = net->p + 288 * o, *lo = net->lo + 26 * o, *hi = net->hi + 26 * o;
+    const double *W1 = P, *b1 = P + 208, *W2 = P + 216, *b2 = P + 280;
+    double I[26], x[26], h[8];
+    for (int t = 0; t < 12; ++t) I[t] = in27[15 + t];
+    I[12] = in27[0];
+    I[13] = in27[1];
+    for (int n = 0; n < 8; ++n) I[14 + n] = in27[7 + n];
+    I[22] = in27[6];
+    for (int a = 0; a < 3; ++a) I[23 + a] = in27[3 + a];
+    for (int j = 0; j < 26; ++j) x[j] = (I[j] - 0.27 * 0.5 * (lo[j] + hi[j])) / fabs(hi[j] - lo[j]);
+    double bm = 0.0;
+    for (int t = 0; t < 12; ++t) bm = fmax(bm, fabs(in27[15 + t]));
+    const double beta = 0.1 * bm;
+    for (int k = 0; k < 8; ++k) {
+        double a = b1[k];
+        for (int j = 0; j < 26; ++j) a += W1[26 * k + j] * x[j];
+        h[k] = tanh(a);
+    }
+    for (int d = 0; d < 8; ++d) {
+        double z = b2[d];
+        for (int k = 0; k < 8; ++k) z += W2[8 * d + k] * h[k];
+        psi[d] = z >= 0.0 ? z : beta * expm1(z);
+    }
+}
+
+void or_octnet_cell_batch(const or_octnet *net, long n, const double *in27, double *psi)
+{
+    for (long i = 0; i < n; ++i) or_octnet_cell(net, in27 + 27 * i, psi + 8 * i);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Problem description.                                                     */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -340,8 +390,9 @@ static long ncell_of(const or_problem *p) { return (long)p->nx * p->ny * p->nz; 
 /* or, when a pointer is NULL, from the problem's constant psi_inc (Eq. (10)) */
 /* for group g.  tallies[0..3] += leakage, collision, source, inflow.        */
 /* ------------------------------------------------------------------------ */
-static int sweep_dir(const or_problem *p, const or_elem *e, int d, int g, const double *S,
-                     const double *bx, const double *by, const double *bz, double *psi, double tal[4])
+static int sweep_dir(const or_problem *p, const or_elem *e, const or_octnet *net, int d, int g,
+                     const double *S, const double *bx, const double *by, const double *bz, double *psi,
+                     double tal[4])
 {
     const double *om = p->omega + 3 * d;
     const int nx = p->nx, ny = p->ny, nz = p->nz;
@@ -397,9 +448,21 @@ static int sweep_dir(const or_problem *p, const or_elem *e, int d, int g, const 
                         }
                     }
                 }
-                double A[64], b[8], x[8];
-                assemble(e, om, p->sigt[(long)g * nc + c], S + 8 * c, up, A, b);
-                if (or_ge(8, A, b, x) != 0) return -1;
+                double x[8];
+                if (net) {
+                    /* the cell's one-cell problem handed to the network of its octant */
+                    double in27[27];
+                    for (int a = 0; a < 3; ++a) in27[a] = om[a];
+                    in27[3] = p->dx; in27[4] = p->dy; in27[5] = p->dz;
+                    in27[6] = p->sigt[(long)g * nc + c];
+                    for (int n = 0; n < 8; ++n) in27[7 + n] = S[8 * c + n];
+                    for (int t = 0; t < 12; ++t) in27[15 + t] = up[t];
+                    or_octnet_cell(net, in27, x);
+                } else {
+                    double A[64], b[8];
+                    assemble(e, om, p->sigt[(long)g * nc + c], S + 8 * c, up, A, b);
+                    if (or_ge(8, A, b, x) != 0) return -1;
+                }
                 for (int n = 0; n < 8; ++n) psi[8 * c + n] = x[n];
                 if (tal) {
                     for (int ax = 0; ax < 3; ++ax) {
@@ -433,7 +496,7 @@ int or_sweep_dir(const or_problem *p, int d, int g, const double *S, const doubl
 {
     or_elem e;
     or_element(p->dx, p->dy, p->dz, e.M, e.L, e.G, e.F);
-    return sweep_dir(p, &e, d, g, S, bx, by, bz, psi, tal);
+    return sweep_dir(p, &e, NULL, d, g, S, bx, by, bz, psi, tal);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -444,7 +507,8 @@ int or_sweep_dir(const or_problem *p, int d, int g, const double *S, const doubl
 /* fixed order, so the result does not depend on the thread count).          */
 /* tal[4] receives the weighted balance tallies.  Returns 0 or -1.           */
 /* ------------------------------------------------------------------------ */
-int or_sweep(const or_problem *p, const double *S, double *phi, int g0, int g1, int d0, int d1, double *tal)
+static int sweep_range(const or_problem *p, const or_octnet *net, const double *S, double *phi, int g0, int g1,
+                       int d0, int d1, double *tal)
 {
     or_elem e;
     or_element(p->dx, p->dy, p->dz, e.M, e.L, e.G, e.F);
@@ -459,7 +523,7 @@ int or_sweep(const or_problem *p, const double *S, double *phi, int g0, int g1, 
         for (long i = 0; i < 8 * nc; ++i) ph[i] = 0.0;
         for (int d = d0; d < d1; ++d) {
             double t[4] = {0, 0, 0, 0};
-            if (sweep_dir(p, &e, d, g, S + (long)g * nc * 8, NULL, NULL, NULL, psi, t) != 0) bad = 1;
+            if (sweep_dir(p, &e, net, d, g, S + (long)g * nc * 8, NULL, NULL, NULL, psi, t) != 0) bad = 1;
             for (long i = 0; i < 8 * nc; ++i) ph[i] += p->w[d] * psi[i];
             for (int m = 0; m < 4; ++m) gt[g][m] += p->w[d] * t[m];
         }
@@ -469,6 +533,20 @@ int or_sweep(const or_problem *p, const double *S, double *phi, int g0, int g1, 
         for (int g = g0; g < g1; ++g)
             for (int m = 0; m < 4; ++m) tal[m] += gt[g][m];
     return bad ? -1 : 0;
+}
+
+int or_sweep(const or_problem *p, const double *S, double *phi, int g0, int g1, int d0, int d1, double *tal)
+{
+    return sweep_range(p, NULL, S, phi, g0, g1, d0, d1, tal);
+}
+
+/* The same sweep with every per-cell solve replaced by the octant networks */
+/* (Sec. 4: the assembly and solve of (14) give way to building the input   */
+/* vector and one evaluation of the network).                               */
+int or_sweep_octnet(const or_problem *p, const or_octnet *net, const double *S, double *phi, int g0, int g1,
+                    int d0, int d1, double *tal)
+{
+    return sweep_range(p, net, S, phi, g0, g1, d0, d1, tal);
 }
 
 /* Isotropic source build (Eqs. (2), (6) with the P_0 term only):           */
@@ -725,7 +803,7 @@ int or_adjoint(const or_problem *p, const double *phi, const double *resp, doubl
         for (int d = 0; d < p->ndir; ++d) {
             for (long i = 0; i < 8 * nc; ++i) rhs[i] = p->w[d] * x[(long)g * nc * 8 + i];
             if (adjoint_sweep_dir(p, &e, d, g, rhs, lam) != 0) bad = 1;
-            if (sweep_dir(p, &e, d, g, S + (long)g * nc * 8, NULL, NULL, NULL, psi, NULL) != 0) bad = 1;
+            if (sweep_dir(p, &e, NULL, d, g, S + (long)g * nc * 8, NULL, NULL, NULL, psi, NULL) != 0) bad = 1;
             for (long c = 0; c < nc; ++c) {
                 double mp[8], s = 0.0;
                 mass_apply(&e, psi + 8 * c, mp);

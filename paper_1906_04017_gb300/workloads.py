@@ -197,5 +197,51 @@ def exchange_problems(n, seed=0):
     return out
 
 
+# Sampling box of the per-octant networks' one-cell problems (Sec. 4: uniform
+# sampling of the incident fluxes, sources, total cross section, direction and cell
+# shape).  The ranges cover the paper's Problems 1-4: psi_inc <= 1 on the boundary,
+# sigma_t in {0.001, 10}, cells of 10 cm / (10..100).
+OCTANT_NET_RANGES = {"psi": (0.0, 1.0), "angle": (0.0, 1.0), "q": (0.0, 1.0),
+                     "sigt": (0.0, 10.0), "h": (0.1, 1.0)}
+
+
+def octant_net_ranges(ranges=None):
+    """(lo, hi) [8, 26] a-priori input ranges of the 8 networks, in their input
+    order: psi_x(4), psi_y(4), psi_z(4), mu, eta, q(8), sigma_t, dx, dy, dz.  The
+    angle range of octant o is mirrored to [-1, 0] on the axes where o has a
+    negative cosine (bit 0: mu, bit 1: eta)."""
+    r = dict(OCTANT_NET_RANGES if ranges is None else ranges)
+    lo = np.empty((8, 26))
+    hi = np.empty((8, 26))
+    for o in range(8):
+        spans = [r["psi"]] * 12 + [r["angle"]] * 2 + [r["q"]] * 8 + [r["sigt"]] + [r["h"]] * 3
+        for j, (a, b) in enumerate(spans):
+            if j in (12, 13) and (o >> (j - 12)) & 1:
+                a, b = -b, -a
+            lo[o, j], hi[o, j] = a, b
+    return lo, hi
+
+
+def octant_problems(m, seed=0, ranges=None):
+    """8 * m one-cell problems in27 (layout of onecell_problems), rows
+    [o * m, (o + 1) * m) in octant o (bit 0: Omega_x < 0, bit 1: Omega_y < 0,
+    bit 2: Omega_z < 0): direction uniform on the octant's part of the unit sphere,
+    every other input uniform on OCTANT_NET_RANGES."""
+    r = dict(OCTANT_NET_RANGES if ranges is None else ranges)
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    out = np.empty((8 * m, 27))
+    v = rng.normal(size=(8 * m, 3))
+    v = np.abs(v) / np.linalg.norm(v, axis=1, keepdims=True)
+    oct_ = np.repeat(np.arange(8), m)
+    for a in range(3):
+        v[:, a] *= np.where((oct_ >> a) & 1, -1.0, 1.0)
+    out[:, 0:3] = v
+    out[:, 3:6] = rng.uniform(*r["h"], size=(8 * m, 3))
+    out[:, 6] = rng.uniform(*r["sigt"], size=8 * m)
+    out[:, 7:15] = rng.uniform(*r["q"], size=(8 * m, 8))
+    out[:, 15:27] = rng.uniform(*r["psi"], size=(8 * m, 12))
+    return out
+
+
 WORKLOADS = {"onecube_8": onecube_8, "blocked_64": blocked_64, "blocked_32": blocked_32,
              "spheres_96": spheres_96}

@@ -9,6 +9,7 @@ import torch
 import oracle
 from oracle import mlp
 from paper_1906_04017_gb300 import workloads as W
+from _parity import f32_roundtrip, network_sweep
 
 pytestmark = pytest.mark.gpu
 
@@ -154,51 +155,6 @@ def test_training_reduces_error(handle):
     assert tr2 < 0.5 * tr and te2 < 0.5 * te
 
 
-def oracle_ann_sweep(wl, p, S, predict):
-    """The sweep of Sec. 2 with every per-cell solve replaced by the network
-    (Sec. 4): cells in upwind order per direction, one-cell inputs assembled from
-    the upwind neighbours' outflow nodes or psi_inc, phi = sum_d w_d psi_d.
-    Pure-Python loops: small meshes only."""
-    nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
-    h = (wl["lx"] / nx, wl["ly"] / ny, wl["lz"] / nz)
-    om, w = oracle.lqn(wl["order"])
-    G = wl["sigt"].shape[0]
-    nc = nx * ny * nz
-    phi = np.zeros((G, nc, 8))
-
-    def node(ax, side, t):
-        lo, hi = t & 1, (t >> 1) & 1
-        abc = [lo, hi]
-        abc.insert(ax, side)
-        return abc[0] + 2 * abc[1] + 4 * abc[2]
-
-    for g in range(G):
-        for d in range(len(w)):
-            o = om[d]
-            psi = np.zeros((nc, 8))
-            order = [(i, j, k) for k in range(nz) for j in range(ny) for i in range(nx)]
-            rng_axes = [range(n) if o[a] >= 0 else range(n - 1, -1, -1) for a, n in enumerate((nx, ny, nz))]
-            for k in rng_axes[2]:
-                for j in rng_axes[1]:
-                    for i in rng_axes[0]:
-                        c = i + nx * (j + ny * k)
-                        x = np.zeros(27)
-                        x[0:3], x[3:6], x[6] = o, h, wl["sigt"][g, c]
-                        x[7:15] = S[g, c]
-                        for a in range(3):
-                            fin = 0 if o[a] >= 0 else 1
-                            idx = [i, j, k]
-                            idx[a] += -1 if fin == 0 else 1
-                            if 0 <= idx[a] < (nx, ny, nz)[a]:
-                                cu = idx[0] + nx * (idx[1] + ny * idx[2])
-                                x[15 + 4 * a:19 + 4 * a] = [psi[cu, node(a, 1 - fin, t)] for t in range(4)]
-                            else:
-                                x[15 + 4 * a:19 + 4 * a] = wl["psi_inc"][g, 2 * a + fin]
-                        psi[c] = predict(p, x[None, :].astype(np.float32).astype(np.float64))[0]
-            phi[g] += w[d] * psi
-    return phi
-
-
 @pytest.mark.parametrize("order", [2, 4, 8, 12])
 def test_ann_sweep_matches_oracle_network_sweep(sn, order):
     """The tensor-core surrogate sweep against the oracle's network swept in Python,
@@ -211,10 +167,11 @@ def test_ann_sweep_matches_oracle_network_sweep(sn, order):
     S = rng.uniform(0.0, 1.0, (P.G, P.ncell, 8)).astype(np.float32)
     phi = P.sweep(cuda(S), mode=sn.ANN).cpu().numpy()
     P.close()
-    ref = oracle_ann_sweep(wl, np.asarray(p, np.float32).astype(np.float64), S.astype(np.float64), predict_bf16)
+    p64 = np.asarray(p, np.float32).astype(np.float64)
+    ref = network_sweep(wl, S.astype(np.float64), lambda x: predict_bf16(p64, f32_roundtrip(x)))
     err = np.abs(phi - ref).max() / np.abs(ref).max()
     assert err < 2e-2
-    exact = oracle_ann_sweep(wl, np.asarray(p, np.float32).astype(np.float64), S.astype(np.float64), mlp.predict)
+    exact = network_sweep(wl, S.astype(np.float64), lambda x: mlp.predict(p64, f32_roundtrip(x)))
     assert np.abs(phi - exact).max() / np.abs(exact).max() < 1e-1
 
 
