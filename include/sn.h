@@ -58,7 +58,9 @@ typedef enum {
     SN_SOLVE_ANN = 2,       /* surrogate network only (Sec. 3, Eqs. (15)-(18))        */
     SN_SOLVE_ANN_GATED = 3, /* surrogate, with cells whose residual fails the gate
                                re-solved by SN_SOLVE_GE32R                          */
-    SN_SOLVE_GE64 = 4       /* FP64 elimination with partial pivoting (FP64 handles only) */
+    SN_SOLVE_GE64 = 4,      /* FP64 elimination with partial pivoting (FP64 handles only) */
+    SN_SOLVE_OCTNET = 5     /* the paper's own per-octant networks (Sec. 3 Eqs. (15)-(18),
+                               Sec. 4), FP32 on the CUDA cores; see sn_octnet_*        */
 } sn_solve_mode;
 
 typedef struct {
@@ -282,6 +284,74 @@ sn_status sn_surrogate_stats(sn_handle h, int64_t *fallbacks, int64_t *timeouts)
  * synchronisations the library already makes. */
 sn_status sn_set_profiling(sn_handle h, int32_t enable);
 sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t reset);
+
+/* ---------------------------------------------------------------------------
+ * The paper's own surrogate: one network per octant of directions (Sec. 4),
+ * 26 inputs -> 8 tanh units -> 8 ELU outputs (Sec. 3, Eqs. (15), (17), (18)).
+ *
+ * Network o serves the directions of octant o (bit 0: mu < 0, bit 1: eta < 0,
+ * bit 2: xi < 0) and reads, in the problem's physical frame and in this order,
+ *   I[0:12]  the upwind face values up(12) of the one-cell problem (x, y, z face),
+ *   I[12:14] mu, eta (Omega_x, Omega_y),  I[14:22] the nodal sources S(8),
+ *   I[22]    sigma_t,  I[23:26] dx, dy, dz,
+ * each scaled by Eq. (16): x_j = (I_j - 0.27 (lo_j + hi_j) / 2) / |hi_j - lo_j|,
+ * with a-priori ranges lo, hi [8][26] per octant (host FP64).  Then
+ * h = tanh(W1 x + b1), z = W2 h + b2, psi_n = z_n (z_n >= 0) or
+ * beta (e^{z_n} - 1), beta = 0.1 max |up|: the angular flux itself, physical
+ * node order.  Parameters: host FP32 [8][288], per octant W1[8][26] row-major,
+ * b1[8], W2[8][8], b2[8].  mask [8][288]: 1 = connection kept, 0 = dropped
+ * (held at 0 by training); biases are not connections.
+ *
+ * Training data: in27 blocks [8][m][27] (device; rows of block o must lie in
+ * octant o, else SN_EINVAL), turned into features [8 m][27] (the 26 scaled
+ * inputs, then beta) and targets [8 m][8] (FP32 elimination, GE32R).  Loss:
+ * Eq. (19) per octant, mean over its m rows (lambda 0.2, gamma 10 and 0.01).
+ * Training is full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8), one step per
+ * epoch, all 8 networks at once.  Evaluation in sweeps (SN_SOLVE_OCTNET) and in
+ * sn_octnet_apply / sn_cell_solve_batch: FP32 on the CUDA cores; tanh(a) as
+ * 1 - 2 / (1 + e^{2a}) with the fast exponential (absolute error ~1e-6).
+ * ------------------------------------------------------------------------- */
+
+/* Glorot-uniform weights (seeded), zero biases, no dropped connection; sets the
+ * ranges; resets Adam. */
+sn_status sn_octnet_init(sn_handle h, const double *lo, const double *hi, uint64_t seed);
+
+/* Load parameters (and optionally a mask; NULL = keep every connection) and, if
+ * lo and hi are non-NULL, new ranges (else the handle's current ones).  Dropped
+ * entries are zeroed.  Resets Adam. */
+sn_status sn_octnet_set(sn_handle h, const float *params, const float *mask, const double *lo, const double *hi);
+
+/* Copy out parameters and mask (host [8][288]; either pointer may be NULL). */
+sn_status sn_octnet_get(sn_handle h, float *params, float *mask);
+
+/* Features and targets (device, layouts above) of 8 m one-cell problems. */
+sn_status sn_octnet_prepare(sn_handle h, const float *in27, int64_t m, float *feat, float *targ);
+
+/* Per-octant loss (host [8]) and gradient (host [8][288], dropped entries not
+ * zeroed) at the current parameters over all m rows of each octant. */
+sn_status sn_octnet_grad(sn_handle h, const float *feat, const float *targ, int64_t m, float *grad, double *loss);
+
+/* `steps` full-batch Adam steps (Adam state continues from the last init, set,
+ * fit or prune); loss: host [8] loss of the last step's gradient (may be NULL). */
+sn_status sn_octnet_fit(sn_handle h, const float *feat, const float *targ, int64_t m, int32_t steps, float lr,
+                        double *loss);
+
+/* Per-octant mean absolute and mean squared error over rows and outputs (host [8]
+ * each; either may be NULL). */
+sn_status sn_octnet_eval(sn_handle h, const float *feat, const float *targ, int64_t m, double *mae, double *mse);
+
+/* Connection dropping (Sec. 3), all octants in step: drop each network's remaining
+ * connection of smallest magnitude (lowest index on ties), retrain `retrain_steps`
+ * full-batch Adam steps from a fresh Adam state, keep the drop while the training
+ * MSE stays within (1 + tol) of the network's MSE before the first drop, else undo
+ * it and stop that network; at most max_drops drops a network.  dropped: host [8]
+ * drops kept (may be NULL). */
+sn_status sn_octnet_prune(sn_handle h, const float *feat, const float *targ, int64_t m, int32_t retrain_steps,
+                          float lr, double tol, int32_t max_drops, int32_t *dropped);
+
+/* psi (device [n][8], physical node order) of n one-cell problems (device in27,
+ * layout of sn_cell_solve_batch) by the network of each problem's octant. */
+sn_status sn_octnet_apply(sn_handle h, const float *in27, float *psi, int64_t n);
 
 /* ---------------------------------------------------------------------------
  * sn_surrogate_grad_noalloc: the loss and gradient of sn_surrogate_grad, for

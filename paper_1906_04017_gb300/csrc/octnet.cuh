@@ -1,0 +1,85 @@
+// octnet.cuh -- the paper's per-octant networks (Sec. 3, Eqs. (15)-(18); Sec. 4: one
+// network per octant of directions) evaluated on a one-cell problem in the canonical
+// (positive-octant) frame of the sweep.
+//
+// A network of octant o takes the 26 quantities of Sec. 3 in the problem's physical
+// frame: the upwind values of the x, y and z inflow faces (4 each), the cosines mu
+// and eta, the 8 nodal sources, sigma_t and the cell sizes, each scaled by Eq. (16)
+// x = (I - alpha m) / r (m the mean of the input's a-priori range, r its width,
+// alpha = 0.27); h = tanh(W1 x + b1); psi_d = theta(z_d), z = W2 h + b2, with
+// theta(z) = z above 0 and beta (e^z - 1) below, beta = 0.1 max |upwind value|.
+//
+// The sweep holds every cell problem mirrored into the positive octant (canonical
+// node n = physical node ^ o, face value t = physical t ^ the face's mask).  Mirroring
+// only permutes the face values, sources and outputs and flips the signs of mu and
+// eta, and Eq. (16) is affine, so each octant's network becomes a network of the
+// canonical inputs with permuted, rescaled weights and a shifted bias ("folded").
+// The folded network computes the same function as the physical one.
+#pragma once
+
+namespace sn {
+
+constexpr int kOnIn = 26, kOnHid = 8, kOnOut = 8;
+constexpr int kOnParam = kOnHid * kOnIn + kOnHid + kOnOut * kOnHid + kOnOut;   // 288 a network
+constexpr int kOnW1 = 0, kOnB1 = kOnHid * kOnIn, kOnW2 = kOnB1 + kOnHid, kOnB2 = kOnW2 + kOnOut * kOnHid;
+constexpr float kOnAlpha = 0.27f, kOnBetaFrac = 0.1f;
+
+// Folded weights of one octant (288 floats).  Hidden unit k owns 24 floats at 24 k:
+// the coefficients of the canonical ux[0..3], uy[0..3], uz[0..3], S[0..7], |mu|, |eta|,
+// sigma_t, then the bias.  Then the coefficients of the cell sizes (3 per unit), W2 in
+// canonical output order [8][8] and b2 [8].
+constexpr int kOnFold = 288;
+constexpr int kOnFoldH = 192, kOnFoldW2 = 216, kOnFoldB2 = 280;
+
+// tanh(a) = 1 - 2 / (1 + e^{2a}).  For large a the exponential overflows to +inf and
+// the quotient to 0 (tanh = 1); for very negative a it is 1 - 2 = -1.  Absolute error
+// about 1e-6 (the error of the fast exponential, damped by 2 e / (1 + e)^2 <= 1/2).
+__device__ __forceinline__ float octnet_tanh(float a)
+{
+    return 1.f - __fdividef(2.f, 1.f + __expf(2.f * a));
+}
+
+// psi (canonical node order) of the folded network at w (shared or global memory,
+// 16-byte aligned).  WITH_H: add the cell-size terms here; otherwise the bias slots
+// of w already hold them (the sweep folds the mesh's uniform cell size in once).
+template <bool WITH_H>
+__device__ __forceinline__ void octnet_forward(const float *__restrict__ w, const float (&ux)[4],
+                                               const float (&uy)[4], const float (&uz)[4], const float (&S)[8],
+                                               float amu, float aeta, float sig, float hx, float hy, float hz,
+                                               float (&psi)[8])
+{
+    float bm = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) bm = fmaxf(bm, fmaxf(fabsf(ux[t]), fmaxf(fabsf(uy[t]), fabsf(uz[t]))));
+    const float beta = kOnBetaFrac * bm;
+    float h[kOnHid];
+#pragma unroll
+    for (int k = 0; k < kOnHid; ++k) {
+        const float4 *r = reinterpret_cast<const float4 *>(w + 24 * k);
+        const float4 c0 = r[0], c1 = r[1], c2 = r[2], c3 = r[3], c4 = r[4], c5 = r[5];
+        float a = c5.w;
+        if (WITH_H) {
+            a = fmaf(w[kOnFoldH + 3 * k], hx, a);
+            a = fmaf(w[kOnFoldH + 3 * k + 1], hy, a);
+            a = fmaf(w[kOnFoldH + 3 * k + 2], hz, a);
+        }
+        a = fmaf(c0.x, ux[0], a); a = fmaf(c0.y, ux[1], a); a = fmaf(c0.z, ux[2], a); a = fmaf(c0.w, ux[3], a);
+        a = fmaf(c1.x, uy[0], a); a = fmaf(c1.y, uy[1], a); a = fmaf(c1.z, uy[2], a); a = fmaf(c1.w, uy[3], a);
+        a = fmaf(c2.x, uz[0], a); a = fmaf(c2.y, uz[1], a); a = fmaf(c2.z, uz[2], a); a = fmaf(c2.w, uz[3], a);
+        a = fmaf(c3.x, S[0], a); a = fmaf(c3.y, S[1], a); a = fmaf(c3.z, S[2], a); a = fmaf(c3.w, S[3], a);
+        a = fmaf(c4.x, S[4], a); a = fmaf(c4.y, S[5], a); a = fmaf(c4.z, S[6], a); a = fmaf(c4.w, S[7], a);
+        a = fmaf(c5.x, amu, a); a = fmaf(c5.y, aeta, a); a = fmaf(c5.z, sig, a);
+        h[k] = octnet_tanh(a);
+    }
+#pragma unroll
+    for (int t = 0; t < kOnOut; ++t) {
+        const float4 *r = reinterpret_cast<const float4 *>(w + kOnFoldW2 + 8 * t);
+        const float4 c0 = r[0], c1 = r[1];
+        float z = w[kOnFoldB2 + t];
+        z = fmaf(c0.x, h[0], z); z = fmaf(c0.y, h[1], z); z = fmaf(c0.z, h[2], z); z = fmaf(c0.w, h[3], z);
+        z = fmaf(c1.x, h[4], z); z = fmaf(c1.y, h[5], z); z = fmaf(c1.z, h[6], z); z = fmaf(c1.w, h[7], z);
+        psi[t] = z >= 0.f ? z : beta * (__expf(z) - 1.f);
+    }
+}
+
+}  // namespace sn

@@ -1571,6 +1571,12 @@ sn_status sn_cell_solve_batch(sn_handle h, const float *in27, float *psi, int64_
         if (n > 0 && (!in27 || !psi)) return fail(h, SN_EINVAL, "sn_cell_solve_batch: NULL pointer");
         return apply_cells(h, in27, psi, n, mode == SN_SOLVE_ANN_GATED, nullptr, (cudaStream_t)stream);
     }
+    if (mode == SN_SOLVE_OCTNET) {
+        if (!h) return fail(nullptr, SN_EINVAL, "sn_cell_solve_batch: SN_SOLVE_OCTNET needs a handle");
+        if (!h->has_octnet) return fail(h, SN_ESTATE, "sn_cell_solve_batch: no octant networks");
+        if (n > 0 && (!in27 || !psi)) return fail(h, SN_EINVAL, "sn_cell_solve_batch: NULL pointer");
+        return launch_octnet_cells(h, in27, psi, n, (cudaStream_t)stream);
+    }
     return fail(h, SN_EINVAL, "sn_cell_solve_batch: unknown mode");
 }
 

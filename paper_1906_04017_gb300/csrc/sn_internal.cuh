@@ -119,6 +119,10 @@ struct sn_handle_s {
     bool has_net = false;
     void *net = nullptr;
 
+    // the paper's per-octant networks (sn_octnet_init / sn_octnet_set)
+    bool has_octnet = false;
+    void *octnet = nullptr;
+
     std::string err;
 };
 
@@ -137,6 +141,11 @@ sn_status cuda_fail(sn_handle h, cudaError_t e, const char *what);
 
 // releases the surrogate network held by a handle (sn_ann.cu)
 void free_net(sn_handle h);
+// the per-octant networks (sn_octnet.cu): release, folded weights [8][288] for the
+// sweep, batch evaluation of one-cell problems
+void free_octnet(sn_handle h);
+const float *octnet_folded(sn_handle h);
+sn_status launch_octnet_cells(sn_handle h, const float *in27, float *psi, int64_t n, cudaStream_t st);
 
 // kernels launched by several translation units (element type from h->fp64)
 sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st);

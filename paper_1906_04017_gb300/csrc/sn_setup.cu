@@ -176,6 +176,7 @@ static void release(sn_handle h)
     for (int i = 0; i < 2; ++i)
         if (h->ev_sweep[i]) cudaEventDestroy(h->ev_sweep[i]);
     free_net(h);
+    free_octnet(h);
 }
 
 }  // namespace sn

@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "ge8.cuh"
+#include "octnet.cuh"
 #include "sn_internal.cuh"
 #include "sweep_common.cuh"
 
@@ -59,6 +60,7 @@ struct SweepArgs {
     uint32_t harvest_cap, harvest_threshold, harvest_seed, plane;
     const float4 *dir_abs;   // |Omega| of each direction of an octant
     T hx, hy, hz;
+    const float *onet;       // [8][288] folded octant networks (network sweeps)
 };
 
 // grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
@@ -230,38 +232,61 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS 
 
 // Persistent form of the elimination sweep (plain forward sweeps, FP32 and FP64): a
 // CTA loops over tiles of keys_per_cta keys x Do directions.  Key records (face-plane
-// slots, boundary flags, cell, group) are built once per key, two tiles ahead, by
-// the first keys_per_cta threads; the sources and opacities of the next tile and
-// every row's inflow faces are copied into shared memory (cp.async) while the
-// current tile is solved, so the global-memory latency sits behind the elimination.
-// The flux reduction of a tile runs at the start of the next iteration.
+// slots, boundary flags, cell, group) are built once per key, three tiles ahead, by
+// the first keys_per_cta threads; the sources and opacities and every row's inflow
+// faces are copied into shared memory (cp.async) two tiles ahead, so that a copy has
+// two tile solves to arrive in.  Within one hyperplane every input is ready when the
+// kernel starts (the faces were written by the previous hyperplane), so the prefetch
+// distance is free; without it a tile waits about one global-memory latency.  The
+// flux reduction of a tile runs at the start of the next iteration.
+constexpr int kTileRecs = 8;   // key-record ring (>= prefetch distance + 3 live tiles)
 template <typename T>
 struct GeTileSmem {
-    uint32_t face, ks, sig, rec, red, total;
+    uint32_t face, ks, sig, rec, red, net, total;
 };
-// Every stage a tile writes while the previous tile may still be read is doubled, so
-// one barrier a tile suffices.
+// Every stage written while an earlier tile may still be read has its own buffer
+// (PRE + 1 copy stages for a prefetch distance of PRE tiles), so one barrier a tile
+// suffices.  Network sweeps keep the octant's folded network after the stages.
 template <typename T>
-__host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows)
+__host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows, int pre, bool net)
 {
+    const uint32_t stages = (uint32_t)pre + 1;
     GeTileSmem<T> m;
-    m.face = 0;                                                   // 2 x [rows][12] inflow faces
-    m.ks = m.face + 2 * rows * 12 * (uint32_t)sizeof(T);          // 2 x [kpt][8] sources
-    m.sig = m.ks + 2 * kpt * 8 * (uint32_t)sizeof(T);             // 2 x [kpt] opacities
-    m.rec = (m.sig + 2 * kpt * (uint32_t)sizeof(T) + 15) & ~15u;  // 4 x [kpt] key records
-    m.red = m.rec + 4 * 32 * kpt;                                 // 2 x [rows][8] w_d psi (canonical)
-    m.total = m.red + 2 * rows * 8 * (uint32_t)sizeof(T);
+    m.face = 0;                                                         // stages x [rows][12] inflow faces
+    m.ks = m.face + stages * rows * 12 * (uint32_t)sizeof(T);          // stages x [kpt][8] sources
+    m.sig = m.ks + stages * kpt * 8 * (uint32_t)sizeof(T);             // stages x [kpt] opacities
+    m.rec = (m.sig + stages * kpt * (uint32_t)sizeof(T) + 15) & ~15u;  // 8 x [kpt] key records
+    m.red = m.rec + kTileRecs * 32 * kpt;                              // 2 x [rows][8] w_d psi (canonical)
+    m.net = m.red + 2 * rows * 8 * (uint32_t)sizeof(T);                // [288] folded network
+    m.total = m.net + (net ? (uint32_t)(sizeof(float) * kOnFold) : 0u);
     return m;
 }
 
-template <typename T, bool REFINE, int DO>
-__global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBLOCKS : 1) sweep_ge_tiles(SweepArgs<T> a)
+// CTAs per SM of the network sweep
+#ifndef SN_NET_TILE_MINBLOCKS
+#define SN_NET_TILE_MINBLOCKS 4
+#endif
+
+template <typename T, bool NET>
+constexpr int tile_min_blocks()
 {
+    return NET ? SN_NET_TILE_MINBLOCKS : (sizeof(T) == 4 ? SN_GE_TILE_MINBLOCKS : 1);
+}
+
+// NET: the per-cell solve is the paper's network of the CTA's octant (octnet.cuh,
+// weights in shared memory, read as broadcasts) instead of elimination; everything
+// else (staging, outflow, flux) is shared.  PRE: tiles of copies in flight.  The
+// elimination hides one tile of copy latency behind its solve (a deeper prefetch
+// measured no faster); the network's solve is shorter and gains from two.
+template <typename T, bool REFINE, int DO, bool NET>
+__device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
+{
+    constexpr int PRE = NET ? 2 : 1, STAGES = PRE + 1;
     extern __shared__ __align__(16) unsigned char gsm[];
     griddep_launch();
     const int Do = DO ? DO : a.Do;
     const int kpt = a.keys_per_cta, rows = blockDim.x;
-    const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows);
+    const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows, PRE, NET);
     const uint32_t sb = smem_u32(gsm);
     const int t = threadIdx.x, o = blockIdx.y;
     const int lk = t / Do, d = t - lk * Do;
@@ -269,6 +294,18 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
     const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
     DirData<T> dd = {T(0), T(0), T(0), T(0)};
     if (lane_row) dd = a.dir[d];
+    float *wnet = reinterpret_cast<float *>(gsm + L.net);
+    float amu = 0.f, aeta = 0.f;
+    if (NET) {
+        // the folded networks are written before the sweep's first hyperplane launch,
+        // which is not overlapped with earlier work: safe to read before griddep_wait
+        for (int e = t; e < kOnFold; e += rows) wnet[e] = a.onet[kOnFold * o + e];
+        if (lane_row) {
+            const float4 ab = a.dir_abs[d];
+            amu = ab.x;
+            aeta = ab.y;
+        }
+    }
     auto red_at = [&](int buf) -> T * { return reinterpret_cast<T *>(gsm + L.red) + buf * rows * 8; };
     auto rec_at = [&](int slot, int k) -> unsigned char * { return gsm + L.rec + (slot * kpt + k) * 32; };
     const int psi_o[3] = {o & 1, 2 + ((o >> 1) & 1), 4 + ((o >> 2) & 1)};
@@ -336,36 +373,53 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
         }
     };
 
+    // Tile i of this CTA is tile t0 + i * step of the hyperplane.  Its key record sits
+    // in ring slot i % 8 and its copies in stage buffer i % STAGES.  Iteration i waits
+    // for tile i's copies (issued in iteration i - PRE), reduces tile i - 1, issues
+    // tile i + PRE's copies and tile i + PRE + 1's records, and solves tile i.
     const int t0 = blockIdx.x, step = gridDim.x;
-    // the first two tiles' key records need only the hyperplane's cell table (written
-    // once at set-up): they are built while the previous hyperplane may still run
+    auto tile_of = [&](int i) { return t0 + i * step; };
+    // the first PRE + 1 tiles' key records need only the hyperplane's cell table
+    // (written once at set-up): they are built while the previous hyperplane may run
+    uint32_t pk_next = 0;
     if (t < kpt) {
-        key_rec(t0, key_pk(t0), 0);
-        key_rec(t0 + step, key_pk(t0 + step), 1);
+#pragma unroll
+        for (int j = 0; j <= PRE; ++j) key_rec(tile_of(j), key_pk(tile_of(j)), j);
+        pk_next = key_pk(tile_of(PRE + 1));
     }
     __syncthreads();
+    if (NET && t < kOnHid) {
+        // the uniform cell size enters every cell the same way: fold it into the bias
+        // (visible after the first barrier of the tile loop)
+        float *wk = wnet + 24 * t;
+        wk[23] = fmaf(wnet[kOnFoldH + 3 * t], (float)a.hx,
+                      fmaf(wnet[kOnFoldH + 3 * t + 1], (float)a.hy, fmaf(wnet[kOnFoldH + 3 * t + 2], (float)a.hz, wk[23])));
+    }
     griddep_wait();
-    if (t < kpt) key_copy(0, 0);
-    face_copy(0, 0);
-    cp_async_commit();
+#pragma unroll
+    for (int j = 0; j < PRE; ++j) {
+        if (t < kpt) key_copy(j, j);
+        face_copy(j, j);
+        cp_async_commit();
+    }
     T leak = T(0);
     int i = 0;
     for (int tile = t0; tile < a.ntiles; tile += step, ++i) {
-        const int slot = i & 3, cur = i & 1, nxt = cur ^ 1;
-        // cell of this thread's key two tiles ahead (used after the barrier)
-        const uint32_t pk2 = t < kpt ? key_pk(tile + 2 * step) : 0u;
-        cp_async_wait_all();
+        const int slot = i % kTileRecs, cur = i % STAGES;
+        // cell of this thread's key PRE + 2 tiles ahead (used in the next iteration)
+        const uint32_t pk_ahead = t < kpt ? key_pk(tile_of(i + PRE + 2)) : 0u;
+        cp_async_wait_pending<PRE - 1>();
         __syncthreads();
-        // the only barrier of the tile: this tile's stage is complete, and every buffer
+        // the only barrier of the tile: tile i's stage is complete, and every buffer
         // written below was last read before it
-        if (i > 0) reduce_tile((i - 1) & 3, nxt);
-        // next tile's faces (its records were built one iteration ago); records two
-        // tiles ahead; sources one tile ahead
-        face_copy((i + 1) & 3, nxt);
+        if (i > 0) reduce_tile((i - 1) % kTileRecs, (i - 1) & 1);
+        const int pre = (i + PRE) % STAGES;
+        face_copy((i + PRE) % kTileRecs, pre);
         if (t < kpt) {
-            key_rec(tile + 2 * step, pk2, (i + 2) & 3);
-            key_copy((i + 1) & 3, nxt);
+            key_rec(tile_of(i + PRE + 1), pk_next, (i + PRE + 1) % kTileRecs);
+            key_copy((i + PRE) % kTileRecs, pre);
         }
+        pk_next = pk_ahead;
         cp_async_commit();
         // this tile's inputs from the stage
         const KeyRec kr = get_key(rec_at(slot, lane_row ? lk : 0));
@@ -385,29 +439,72 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_TILE_MINBL
 #pragma unroll
             for (int q = 0; q < 8; ++q) S[q] = fks[q];
             T x[8];
-            cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
+            if constexpr (NET) {
+                octnet_forward<false>(wnet, ux, uy, uz, S, amu, aeta, sig, 0.f, 0.f, 0.f, x);
+            } else {
+                cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
+            }
             if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, x[1], x[3], x[5], x[7]);
             else leak += dd.t3x * (x[1] + x[3] + x[5] + x[7]);
             if (!(kr.flags & 16u)) store4(a.fy + kr.by + d, x[2], x[3], x[6], x[7]);
             else leak += dd.t3y * (x[2] + x[3] + x[6] + x[7]);
             if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, x[4], x[5], x[6], x[7]);
             else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
-            T *r = red_at(cur) + t * 8;
+            T *r = red_at(i & 1) + t * 8;
             store4(reinterpret_cast<Vec4<T> *>(r), dd.w * x[0], dd.w * x[1], dd.w * x[2], dd.w * x[3]);
             store4(reinterpret_cast<Vec4<T> *>(r) + 1, dd.w * x[4], dd.w * x[5], dd.w * x[6], dd.w * x[7]);
         }
     }
     cp_async_wait_all();
     __syncthreads();
-    if (i > 0) reduce_tile((i - 1) & 3, (i - 1) & 1);
+    if (i > 0) reduce_tile((i - 1) % kTileRecs, (i - 1) & 1);
     leak *= dd.w * a.vol12;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
     if ((t & 31) == 0 && leak != T(0)) atomicAdd(a.leak, (double)leak);
 }
 
+template <typename T, bool REFINE, int DO>
+__global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sweep_ge_tiles(SweepArgs<T> a)
+{
+    ge_tiles_body<T, REFINE, DO, false>(a);
+}
+
+template <int DO>
+__global__ void __launch_bounds__(SN_GE_BLOCK, SN_NET_TILE_MINBLOCKS) sweep_net_tiles(SweepArgs<float> a)
+{
+    ge_tiles_body<float, false, DO, true>(a);
+}
+
+// Hyperplane launches of a network sweep (the folded networks of the handle).
+static sn_status launch_sweep_net(sn_handle h, SweepArgs<float> &a, uint32_t smem, cudaStream_t st)
+{
+    a.onet = octnet_folded(h);
+    if (!a.onet) return fail(h, SN_ESTATE, "octant-network sweep without networks");
+    void (*kern)(SweepArgs<float>) =
+        h->Do == 10 ? sweep_net_tiles<10> : h->Do == 21 ? sweep_net_tiles<21> : sweep_net_tiles<0>;
+    if (smem > 48 * 1024)
+        SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int cap = std::max(1, num_sms() * SN_NET_TILE_MINBLOCKS / 8);
+    if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
+    for (int s = 0; s < h->nplanes; ++s) {
+        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+        a.cells = h->plane_cells + h->plane_off[s];
+        a.ncells_plane = (int)n;
+        a.ntiles = (int)((n * h->G + a.keys_per_cta - 1) / a.keys_per_cta);
+        const dim3 grid((unsigned)std::min(a.ntiles, cap), 8);
+        SN_CK(h, launch_k(s > 0, kern, grid, dim3(SN_GE_BLOCK), smem, st, a));
+    }
+    SN_CK(h, cudaGetLastError());
+    if (h->prof) {
+        SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));
+        h->prof_pending = true;
+    }
+    return SN_OK;
+}
+
 template <typename T>
-static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine, cudaStream_t st)
+static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine, bool net, cudaStream_t st)
 {
     SweepArgs<T> a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
@@ -421,17 +518,22 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     a.phi_oct = phi_oct;
     a.leak = h->acc + ACC_LEAK;
     a.vol12 = (T)(h->dx * h->dy * h->dz / 12.0);
+    a.dir_abs = h->dir_abs;
+    a.hx = (T)h->dx; a.hy = (T)h->dy; a.hz = (T)h->dz;
     const int rows = SN_GE_BLOCK;
-    const GeTileSmem<T> L = ge_tile_smem<T>(a.keys_per_cta, rows);
-    void (*kern)(SweepArgs<T>);
+    if constexpr (sizeof(T) == 4) {
+        if (net) return launch_sweep_net(h, a, ge_tile_smem<T>(a.keys_per_cta, rows, 2, true).total, st);
+    }
+    const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false).total;
+    void (*kern)(SweepArgs<T>) = nullptr;
     if (refine)
         kern = h->Do == 10 ? sweep_ge_tiles<T, true, 10> : h->Do == 21 ? sweep_ge_tiles<T, true, 21>
                                                                      : sweep_ge_tiles<T, true, 0>;
     else
         kern = h->Do == 10 ? sweep_ge_tiles<T, false, 10> : h->Do == 21 ? sweep_ge_tiles<T, false, 21>
                                                                       : sweep_ge_tiles<T, false, 0>;
-    if (L.total > 48 * 1024)
-        SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    if (smem > 48 * 1024)
+        SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // persistent CTAs per octant: the register-limited residency (4 a SM in FP32, 1 in FP64)
     const int cap = std::max(1, num_sms() * (sizeof(T) == 4 ? SN_GE_TILE_MINBLOCKS : 1) / 8);
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
@@ -442,7 +544,7 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
         a.ntiles = (int)((n * h->G + a.keys_per_cta - 1) / a.keys_per_cta);
         const dim3 grid((unsigned)std::min(a.ntiles, cap), 8);
         // hyperplanes after the first overlap their launch with the previous one's drain
-        SN_CK(h, launch_k(s > 0, kern, grid, dim3(rows), L.total, st, a));
+        SN_CK(h, launch_k(s > 0, kern, grid, dim3(rows), smem, st, a));
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {
@@ -539,10 +641,11 @@ static sn_status launch_harvest(sn_handle h, const float *S, float *out, uint32_
 
 sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st)
 {
-    if (h->fp64) return launch_sweep_t<double>(h, (const double *)S, (double *)phi_oct, false, st);
+    if (h->fp64) return launch_sweep_t<double>(h, (const double *)S, (double *)phi_oct, false, false, st);
     if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED)
         return launch_sweep_ann(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_ANN_GATED, st);
-    return launch_sweep_t<float>(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R, st);
+    return launch_sweep_t<float>(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R,
+                                 mode == SN_SOLVE_OCTNET, st);
 }
 
 // After a stream synchronisation: add the time between the sweep's first and last
@@ -826,6 +929,10 @@ static sn_status check_mode(sn_handle h, sn_solve_mode mode)
     if (mode == SN_SOLVE_GE32R || mode == SN_SOLVE_GE32) return SN_OK;
     if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
         if (!h->has_net) return fail(h, SN_ESTATE, "surrogate mode needs a trained or loaded network");
+        return SN_OK;
+    }
+    if (mode == SN_SOLVE_OCTNET) {
+        if (!h->has_octnet) return fail(h, SN_ESTATE, "octant-network mode needs initialised or loaded networks");
         return SN_OK;
     }
     if (mode == SN_SOLVE_GE64) return fail(h, SN_EINVAL, "SN_SOLVE_GE64 needs an FP64 handle");

@@ -52,6 +52,12 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// every committed group but the N most recent ones has landed
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Copy n bytes (a multiple of 16, both addresses 16-byte aligned) in 16-byte pieces.
 __device__ __forceinline__ void cp_async_bytes(uint32_t dst, const void *src, int n)

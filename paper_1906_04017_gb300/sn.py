@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsn_gb300.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ENOCONV, SN_ETIMEOUT, SN_ENAN, SN_ESTATE = range(8)
-GE32R, GE32, ANN, ANN_GATED, GE64 = 0, 1, 2, 3, 4
-MODES = {"ge32r": GE32R, "ge32": GE32, "ann": ANN, "ann_gated": ANN_GATED, "ge64": GE64}
+GE32R, GE32, ANN, ANN_GATED, GE64, OCTNET = 0, 1, 2, 3, 4, 5
+MODES = {"ge32r": GE32R, "ge32": GE32, "ann": ANN, "ann_gated": ANN_GATED, "ge64": GE64, "octnet": OCTNET}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.c_void_p
@@ -93,6 +93,17 @@ _API = [
                                         _fp, ctypes.POINTER(ctypes.c_int32)]),
     ("sn_response", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, _dp]),
     ("sn_surrogate_grad_noalloc", ctypes.c_int, [_fp, _fp, _fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
+    ("sn_octnet_init", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_uint64]),
+    ("sn_octnet_set", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                     _dp, _dp]),
+    ("sn_octnet_get", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    ("sn_octnet_prepare", ctypes.c_int, [ctypes.c_void_p, _fp, ctypes.c_int64, _fp, _fp]),
+    ("sn_octnet_grad", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float), _dp]),
+    ("sn_octnet_fit", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, _dp]),
+    ("sn_octnet_eval", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, _dp, _dp]),
+    ("sn_octnet_prune", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
+                                       ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    ("sn_octnet_apply", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64]),
     ("sn_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("sn_destroy", None, [ctypes.c_void_p]),
@@ -186,6 +197,9 @@ def surrogate_grad_noalloc(params, feat, targ, grad, loss):
     _check(lib().sn_surrogate_grad_noalloc(_dev(params, torch.float32), _dev(feat, torch.float32, (27,)),
                                            _dev(targ, torch.float32, (8,)), feat.shape[0],
                                            _dev(grad, torch.float32), _dev(loss, torch.float64), _stream()))
+
+
+OCTNET_NIN, OCTNET_NPARAM = 26, 288
 
 
 def _f32p(a):
@@ -385,6 +399,87 @@ class Problem:
         b = ctypes.c_int64(0)
         _check(lib().sn_surrogate_stats(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
         return a.value, b.value
+
+    # ---- the paper's per-octant networks (Sec. 3, Sec. 4) ----
+    def octnet_init(self, lo, hi, seed=0):
+        """Glorot-initialised networks with a-priori input ranges lo, hi [8, 26]."""
+        lo = np.ascontiguousarray(lo, dtype=np.float64).reshape(8, OCTNET_NIN)
+        hi = np.ascontiguousarray(hi, dtype=np.float64).reshape(8, OCTNET_NIN)
+        self._sync_stream()
+        _check(lib().sn_octnet_init(self.h, _dptr(lo), _dptr(hi), int(seed)), self.h)
+
+    def octnet_set(self, params, mask=None, lo=None, hi=None):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(8, OCTNET_NPARAM)
+        k = None if mask is None else np.ascontiguousarray(mask, dtype=np.float32).reshape(8, OCTNET_NPARAM)
+        r = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(8, OCTNET_NIN) for a in (lo, hi)]
+        self._sync_stream()
+        _check(lib().sn_octnet_set(self.h, _f32p(p), None if k is None else _f32p(k),
+                                   None if r[0] is None else _dptr(r[0]), None if r[1] is None else _dptr(r[1])),
+               self.h)
+
+    def octnet_get(self):
+        """(params [8, 288], mask [8, 288]) FP32."""
+        p = np.zeros((8, OCTNET_NPARAM), dtype=np.float32)
+        k = np.zeros((8, OCTNET_NPARAM), dtype=np.float32)
+        self._sync_stream()
+        _check(lib().sn_octnet_get(self.h, _f32p(p), _f32p(k)), self.h)
+        return p, k
+
+    def octnet_prepare(self, in27):
+        """(features [8m, 27], targets [8m, 8]) of octant-grouped one-cell problems in27 [8m, 27]."""
+        n = in27.shape[0]
+        if n % 8:
+            raise ValueError("in27 must hold 8 equal octant blocks")
+        feat = torch.empty((n, 27), dtype=torch.float32, device=in27.device)
+        targ = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+        self._sync_stream()
+        _check(lib().sn_octnet_prepare(self.h, _dev(in27, torch.float32, (27,)), n // 8,
+                                       _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,))), self.h)
+        return feat, targ
+
+    def octnet_grad(self, feat, targ):
+        """(loss [8], gradient [8, 288]) of Eq. (19) per octant at the current parameters."""
+        g = np.zeros((8, OCTNET_NPARAM), dtype=np.float32)
+        loss = np.zeros(8)
+        self._sync_stream()
+        _check(lib().sn_octnet_grad(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
+                                    feat.shape[0] // 8, _f32p(g), _dptr(loss)), self.h)
+        return loss, g
+
+    def octnet_fit(self, feat, targ, steps, lr):
+        loss = np.zeros(8)
+        self._sync_stream()
+        _check(lib().sn_octnet_fit(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
+                                   feat.shape[0] // 8, int(steps), float(lr), _dptr(loss)), self.h)
+        return loss
+
+    def octnet_eval(self, feat, targ):
+        """(mean absolute error [8], mean squared error [8]) per octant."""
+        mae = np.zeros(8)
+        mse = np.zeros(8)
+        self._sync_stream()
+        _check(lib().sn_octnet_eval(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
+                                    feat.shape[0] // 8, _dptr(mae), _dptr(mse)), self.h)
+        return mae, mse
+
+    def octnet_prune(self, feat, targ, retrain_steps, lr, tol=1e-3, max_drops=272):
+        """Connection dropping (Sec. 3); returns the drops kept per octant [8]."""
+        d = (ctypes.c_int32 * 8)()
+        self._sync_stream()
+        _check(lib().sn_octnet_prune(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
+                                     feat.shape[0] // 8, int(retrain_steps), float(lr), float(tol), int(max_drops), d),
+               self.h)
+        return np.array(list(d))
+
+    def octnet_apply(self, in27, out=None):
+        """psi [N, 8] of one-cell problems by the networks of their octants."""
+        n = in27.shape[0]
+        if out is None:
+            out = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+        self._sync_stream()
+        _check(lib().sn_octnet_apply(self.h, _dev(in27, torch.float32, (27,)), _dev(out, torch.float32, (8,)), n),
+               self.h)
+        return out
 
     # ---- discrete adjoint ----
     def adjoint(self, phi, resp, tol=1e-6, max_it=500, allow_noconv=False):
