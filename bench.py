@@ -271,6 +271,107 @@ def ann_form(P, steps):
     return out
 
 
+# algorithmic FP32 flops of one octant-network solve: 2 (26 x 8 + 8 x 8) multiply-adds,
+# 16 bias adds, 16 for the flux; tanh and the ELU exponential are not counted
+OCTNET_FLOPS_PER_SOLVE = 2 * (26 * 8 + 8 * 8) + 16 + 16
+
+
+def octnet_train(m_train=90000, m_test=10000, epochs=50000, lr=2e-4, retrain=500, tol=1e-3, seed=0):
+    """The paper's per-octant networks trained as in Sec. 4: 9e4 training and 1e4 test
+    one-cell problems per octant (uniform sampling of the inputs over the ranges that
+    cover Problems 1-4), elimination labels, the loss of Eq. (19), full-batch Adam for
+    5e4 epochs at lr 2e-4 (the paper's range is 5e-5..2e-4); then the connection
+    dropping of Sec. 3 (retraining `retrain` epochs after each drop, stop at +0.1 %
+    training MSE).  Returns (params [8, 288], mask, lo, hi, report)."""
+    import torch
+    from paper_1906_04017_gb300 import sn, workloads
+    lo, hi = workloads.octant_net_ranges()
+    T = sn.Problem(workloads.random_small(2, 2, 2, order=2, G=1))
+    rep = {}
+    try:
+        T.octnet_init(lo, hi, seed=seed)
+        xtr = torch.from_numpy(workloads.octant_problems(m_train, seed=seed).astype(np.float32)).cuda()
+        xte = torch.from_numpy(workloads.octant_problems(m_test, seed=seed + 1).astype(np.float32)).cuda()
+        ftr, ttr = T.octnet_prepare(xtr)
+        fte, tte = T.octnet_prepare(xte)
+        del xtr, xte
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T.octnet_fit(ftr, ttr, epochs, lr)
+        rep["train_s"] = time.perf_counter() - t0
+        rep["epoch_ms"] = rep["train_s"] * 1e3 / epochs
+        mae, mse = T.octnet_eval(ftr, ttr)
+        tmae, tmse = T.octnet_eval(fte, tte)
+        rep.update({"train_mae": mae.tolist(), "train_mse": mse.tolist(), "test_mae": tmae.tolist(),
+                    "test_mse": tmse.tolist()})
+        t0 = time.perf_counter()
+        dropped = T.octnet_prune(ftr, ttr, retrain_steps=retrain, lr=lr, tol=tol, max_drops=272)
+        rep["prune_s"] = time.perf_counter() - t0
+        pmae, pmse = T.octnet_eval(ftr, ttr)
+        ptmae, _ = T.octnet_eval(fte, tte)
+        rep.update({"dropped": dropped.tolist(), "dropped_frac": float(dropped.mean() / 272.0),
+                    "pruned_train_mae": pmae.tolist(), "pruned_train_mse": pmse.tolist(),
+                    "pruned_test_mae": ptmae.tolist(),
+                    "setup": "%d train + %d test problems per octant, %d full-batch Adam epochs at lr %g, "
+                             "%d retraining epochs per dropped connection, tol %g" % (m_train, m_test, epochs, lr,
+                                                                                     retrain, tol)})
+        params, mask = T.octnet_get()
+    finally:
+        T.close()
+    return params, mask, lo, hi, rep
+
+
+def octnet_form(P):
+    """The paper's own surrogate on the measured workload: the per-octant networks
+    (trained by octnet_train) as the cell solver of the same wavefront sweep, ungated
+    as in the paper; kernel-level solves/s, its roofline, and the error against the
+    elimination form after one sweep and at convergence."""
+    import torch
+    from paper_1906_04017_gb300 import sn
+    params, mask, lo, hi, rep = octnet_train()
+    P.octnet_set(params, mask, lo, hi)
+    ref = P.source_iterate(tol=1e-6, max_it=500, mode=sn.GE32R, use_graph=True, allow_noconv=True)["phi"].clone()
+    S_ref = P.source(ref)
+
+    def rate(mode, reps=5):
+        out_phi = P.flux_tensor()
+        P.sweep(S_ref, out_phi, mode=mode)
+        P.set_profiling(True)
+        P.profile(reset=True)
+        for _ in range(reps):
+            P.sweep(S_ref, out_phi, mode=mode)
+        ms, n = P.profile(reset=True)
+        P.set_profiling(False)
+        return P.solves_per_sweep / (ms / n / 1e3), out_phi
+
+    ge_rate, ge_phi = rate(sn.GE32R)
+    net_rate, net_phi = rate(sn.OCTNET)
+    out = {"network": rep, "value": net_rate, "unit": UNIT, "ge_sweep_solves_per_s": ge_rate,
+           "speedup_vs_ge_sweep": net_rate / ge_rate, "one_sweep_eps_P_vs_ge": eps_p(net_phi, ge_phi)}
+    phi = P.flux_tensor()
+    try:
+        r = P.source_iterate(phi=phi, tol=1e-5, max_it=300, mode=sn.OCTNET, use_graph=True, allow_noconv=True)
+        out.update({"eps_P_vs_ge": eps_p(phi, ref), "iters": r["iters"], "converged": r["converged"]})
+    except sn.SnError as e:
+        out.update({"eps_P_vs_ge": None, "converged": False, "diverged": str(e)})
+    peak_tf = N_SM * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    ach = net_rate * OCTNET_FLOPS_PER_SOLVE / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm = net_rate * BYTES_PER_SOLVE / 1e9
+    out["roofline"] = {"bound": "alu", "kernel": "sweep_net_tiles<10>", "achieved": ach, "peak": peak_tf,
+                       "unit": "TFLOP/s", "frac": ach / peak_tf, "flops_per_solve": OCTNET_FLOPS_PER_SOLVE,
+                       "hbm_achieved_gbs": hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm / hbm_peak,
+                       "peak_note": "FP32 peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock); "
+                                    "HBM peak %s" % ("measured" if "hbm_gbs" in peaks else "fallback")}
+    return out
+
+
 def e2e_pipelined(P, S_host, phi_host, steps, stream):
     """`steps` sweeps through the public API (sn_sweep) with every step's source
     copied in from pinned host memory and its flux copied back, the copies on a
@@ -370,6 +471,7 @@ def run_gpu(args):
     barrier()
 
     ann = None if args.no_ann else ann_form(P, args.steps)
+    octnet = None if args.no_octnet else octnet_form(P)
 
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, "cuda")
     P.close()
@@ -416,6 +518,8 @@ def run_gpu(args):
     }
     if ann is not None:
         line["ann"] = ann
+    if octnet is not None:
+        line["octnet"] = octnet
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -497,11 +601,12 @@ def adjoint_check(args):
 
 
 def paper_tables(args):
-    """The evaluation of Sec. 4 run with both solvers: Problems 1-4 (10 cm cube,
+    """The evaluation of Sec. 4 run with the three solvers: Problems 1-4 (10 cm cube,
     unit inflow on the x-, y-, z- faces) at S2-S8 on 100^3 cells and at 10^3-100^3
     cells with S8.  For each case: the elimination solution (FP32 GE with
-    refinement) and the surrogate solution (the 27-64-8 network trained on the
-    one-cell distribution, ungated as in the paper), the mean relative error of the
+    refinement), the tensor-core surrogate (the 27-64-8 network trained on the
+    one-cell distribution) and the paper's own per-octant networks (26-8-8, trained
+    as in Sec. 4), both ungated as in the paper: the mean relative error of the
     cell-averaged flux (Eq. (20)), the solve times and the time reduction.  Problem 4
     (scattering ratio 0.99) runs the source iteration to the mean change of Eq. (21)
     below 1e-4 with both solvers and reports their iteration counts.  Prints one
@@ -516,6 +621,8 @@ def paper_tables(args):
     weights = T.surrogate_weights()
     T.close()
     del x
+    # the paper's own per-octant networks
+    on_params, on_mask, on_lo, on_hi, on_rep = octnet_train()
 
     def timed(fn):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -560,6 +667,7 @@ def paper_tables(args):
     for k, n, order in cases:
         P = sn.Problem(workloads.paper_problem(k, n=n, order=order))
         P.surrogate_set_weights(weights)
+        P.octnet_set(on_params, on_mask, on_lo, on_hi)
         it4 = k == 4
         ge, ms_ge, it_ge, st_ge = solve(P, sn.GE32R, it4)
         ge = ge.clone()
@@ -570,6 +678,12 @@ def paper_tables(args):
                "ge_status": st_ge, "ann_status": st_ann,
                "eps_P": eps_p(ann, ge) if finite else None,
                "time_reduction": 1.0 - ms_ann / ms_ge}
+        ann = None
+        ocn, ms_ocn, it_ocn, st_ocn = solve(P, sn.OCTNET, it4)
+        row.update({"octnet_ms": ms_ocn, "octnet_iters": it_ocn, "octnet_status": st_ocn,
+                    "octnet_eps_P": eps_p(ocn, ge) if bool(torch.isfinite(ocn).all()) else None,
+                    "octnet_time_reduction": 1.0 - ms_ocn / ms_ge})
+        ocn = None
         if it4:
             # with the residual gate (not in the paper): tau = 0.01
             P.surrogate_set_gate(0.01)
@@ -581,6 +695,7 @@ def paper_tables(args):
         P.close()
     print(json.dumps({"paper_tables": "Problems 1-4 of Sec. 4, both solvers, FP32, one GPU",
                       "network": {"train_mae": tr, "test_mae": te, "training": "2^20 one-cell problems, 20000 Adam steps"},
+                      "octant_networks": on_rep,
                       "wall_s": time.time() - t0, "rows": rows}))
     return 0
 
@@ -593,6 +708,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ann", action="store_true")
+    ap.add_argument("--no-octnet", action="store_true")
     ap.add_argument("--paper-tables", action="store_true",
                     help="Problems 1-4 of the paper with both solvers (prints its own JSON line)")
     ap.add_argument("--adjoint-check", action="store_true",

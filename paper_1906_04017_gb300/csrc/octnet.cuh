@@ -82,4 +82,58 @@ __device__ __forceinline__ void octnet_forward(const float *__restrict__ w, cons
     }
 }
 
+// Two canonical one-cell problems through the same folded network (weights at w,
+// the cell-size terms already in the biases): every weight read feeds two
+// multiply-adds.  Same arithmetic, in the same order, as octnet_forward<false>.
+__device__ __forceinline__ void octnet_forward2(const float *__restrict__ w, const float (&ux)[2][4],
+                                                const float (&uy)[2][4], const float (&uz)[2][4],
+                                                const float (&S)[2][8], const float (&amu)[2], const float (&aeta)[2],
+                                                const float (&sig)[2], float (&psi)[2][8])
+{
+    float beta[2], h[2][kOnHid];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        float bm = 0.f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) bm = fmaxf(bm, fmaxf(fabsf(ux[j][t]), fmaxf(fabsf(uy[j][t]), fabsf(uz[j][t]))));
+        beta[j] = kOnBetaFrac * bm;
+    }
+#pragma unroll
+    for (int k = 0; k < kOnHid; ++k) {
+        const float4 *r = reinterpret_cast<const float4 *>(w + 24 * k);
+        const float4 c0 = r[0], c1 = r[1], c2 = r[2], c3 = r[3], c4 = r[4], c5 = r[5];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float a = c5.w;
+            a = fmaf(c0.x, ux[j][0], a); a = fmaf(c0.y, ux[j][1], a); a = fmaf(c0.z, ux[j][2], a);
+            a = fmaf(c0.w, ux[j][3], a);
+            a = fmaf(c1.x, uy[j][0], a); a = fmaf(c1.y, uy[j][1], a); a = fmaf(c1.z, uy[j][2], a);
+            a = fmaf(c1.w, uy[j][3], a);
+            a = fmaf(c2.x, uz[j][0], a); a = fmaf(c2.y, uz[j][1], a); a = fmaf(c2.z, uz[j][2], a);
+            a = fmaf(c2.w, uz[j][3], a);
+            a = fmaf(c3.x, S[j][0], a); a = fmaf(c3.y, S[j][1], a); a = fmaf(c3.z, S[j][2], a);
+            a = fmaf(c3.w, S[j][3], a);
+            a = fmaf(c4.x, S[j][4], a); a = fmaf(c4.y, S[j][5], a); a = fmaf(c4.z, S[j][6], a);
+            a = fmaf(c4.w, S[j][7], a);
+            a = fmaf(c5.x, amu[j], a); a = fmaf(c5.y, aeta[j], a); a = fmaf(c5.z, sig[j], a);
+            h[j][k] = octnet_tanh(a);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kOnOut; ++t) {
+        const float4 *r = reinterpret_cast<const float4 *>(w + kOnFoldW2 + 8 * t);
+        const float4 c0 = r[0], c1 = r[1];
+        const float b2 = w[kOnFoldB2 + t];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float z = b2;
+            z = fmaf(c0.x, h[j][0], z); z = fmaf(c0.y, h[j][1], z); z = fmaf(c0.z, h[j][2], z);
+            z = fmaf(c0.w, h[j][3], z);
+            z = fmaf(c1.x, h[j][4], z); z = fmaf(c1.y, h[j][5], z); z = fmaf(c1.z, h[j][6], z);
+            z = fmaf(c1.w, h[j][7], z);
+            psi[j][t] = z >= 0.f ? z : beta[j] * (__expf(z) - 1.f);
+        }
+    }
+}
+
 }  // namespace sn

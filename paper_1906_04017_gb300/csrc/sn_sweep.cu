@@ -262,9 +262,12 @@ __host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows, int pre
     return m;
 }
 
-// CTAs per SM of the network sweep
+// CTAs per SM of the network sweep, and its prefetch distance in tiles
 #ifndef SN_NET_TILE_MINBLOCKS
 #define SN_NET_TILE_MINBLOCKS 4
+#endif
+#ifndef SN_NET_PRE
+#define SN_NET_PRE 1
 #endif
 
 template <typename T, bool NET>
@@ -275,36 +278,46 @@ constexpr int tile_min_blocks()
 
 // NET: the per-cell solve is the paper's network of the CTA's octant (octnet.cuh,
 // weights in shared memory, read as broadcasts) instead of elimination; everything
-// else (staging, outflow, flux) is shared.  PRE: tiles of copies in flight.  The
-// elimination hides one tile of copy latency behind its solve (a deeper prefetch
-// measured no faster); the network's solve is shorter and gains from two.
+// else (staging, outflow, flux) is shared.  A network thread owns two rows (RPT = 2,
+// rows t and t + blockDim) and evaluates both with one pass over the weights: the
+// weight reads, not the arithmetic, bound a one-row network sweep.  PRE: tiles of
+// copies in flight (the elimination hides one tile of copy latency behind its
+// solve; a deeper prefetch measured no faster).
 template <typename T, bool REFINE, int DO, bool NET>
 __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
 {
-    constexpr int PRE = NET ? 2 : 1, STAGES = PRE + 1;
+    constexpr int PRE = NET ? SN_NET_PRE : 1, STAGES = PRE + 1, RPT = NET ? 2 : 1;
     extern __shared__ __align__(16) unsigned char gsm[];
     griddep_launch();
     const int Do = DO ? DO : a.Do;
-    const int kpt = a.keys_per_cta, rows = blockDim.x;
+    const int nthr = blockDim.x, kpt = a.keys_per_cta, rows = nthr * RPT;
     const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows, PRE, NET);
     const uint32_t sb = smem_u32(gsm);
     const int t = threadIdx.x, o = blockIdx.y;
-    const int lk = t / Do, d = t - lk * Do;
-    const bool lane_row = lk < kpt;
+    int lk[RPT], dr[RPT];
+    bool lane_row[RPT];
+    DirData<T> dd[RPT];
+    float amu[RPT], aeta[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int r = t + j * nthr;
+        lk[j] = r / Do;
+        dr[j] = r - lk[j] * Do;
+        lane_row[j] = lk[j] < kpt;
+        dd[j] = lane_row[j] ? a.dir[dr[j]] : DirData<T>{T(0), T(0), T(0), T(0)};
+        amu[j] = aeta[j] = 0.f;
+        if (NET && lane_row[j]) {
+            const float4 ab = a.dir_abs[dr[j]];
+            amu[j] = ab.x;
+            aeta[j] = ab.y;
+        }
+    }
     const uint32_t nkeys = (uint32_t)a.ncells_plane * (uint32_t)a.G;
-    DirData<T> dd = {T(0), T(0), T(0), T(0)};
-    if (lane_row) dd = a.dir[d];
     float *wnet = reinterpret_cast<float *>(gsm + L.net);
-    float amu = 0.f, aeta = 0.f;
     if (NET) {
         // the folded networks are written before the sweep's first hyperplane launch,
         // which is not overlapped with earlier work: safe to read before griddep_wait
-        for (int e = t; e < kOnFold; e += rows) wnet[e] = a.onet[kOnFold * o + e];
-        if (lane_row) {
-            const float4 ab = a.dir_abs[d];
-            amu = ab.x;
-            aeta = ab.y;
-        }
+        for (int e = t; e < kOnFold; e += nthr) wnet[e] = a.onet[kOnFold * o + e];
     }
     auto red_at = [&](int buf) -> T * { return reinterpret_cast<T *>(gsm + L.red) + buf * rows * 8; };
     auto rec_at = [&](int slot, int k) -> unsigned char * { return gsm + L.rec + (slot * kpt + k) * 32; };
@@ -343,21 +356,24 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
         if (sizeof(T) == 4) cp_async4(sb + L.sig + 4 * k, a.sigt + gc);
         else cp_async8(sb + L.sig + 8 * k, a.sigt + gc);
     };
-    // row: copy its inflow faces (record in `slot`) into face buffer `fb`
+    // the thread's rows: copy their inflow faces (records in `slot`) into face buffer `fb`
     auto face_copy = [&](int slot, int fb) {
-        if (!lane_row) return;
-        const KeyRec r = get_key(rec_at(slot, lk));
-        if (!(r.flags & 0x80u)) return;
-        const uint32_t dst = sb + L.face + (uint32_t)((fb * rows + t) * 12 * (int)sizeof(T));
-        constexpr int vb = 4 * (int)sizeof(T);
-        if (!(r.flags & 1u)) cp_async_bytes(dst, a.fx + r.bx + d, vb);
-        if (!(r.flags & 2u)) cp_async_bytes(dst + vb, a.fy + r.by + d, vb);
-        if (!(r.flags & 4u)) cp_async_bytes(dst + 2 * vb, a.fz + r.bz + d, vb);
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            if (!lane_row[j]) continue;
+            const KeyRec r = get_key(rec_at(slot, lk[j]));
+            if (!(r.flags & 0x80u)) continue;
+            const uint32_t dst = sb + L.face + (uint32_t)((fb * rows + t + j * nthr) * 12 * (int)sizeof(T));
+            constexpr int vb = 4 * (int)sizeof(T);
+            if (!(r.flags & 1u)) cp_async_bytes(dst, a.fx + r.bx + dr[j], vb);
+            if (!(r.flags & 2u)) cp_async_bytes(dst + vb, a.fy + r.by + dr[j], vb);
+            if (!(r.flags & 4u)) cp_async_bytes(dst + 2 * vb, a.fz + r.bz + dr[j], vb);
+        }
     };
     // flux partial of the tile whose records are in `slot` and w_d psi in red buffer `rb`
     auto reduce_tile = [&](int slot, int rb) {
         const T *red = red_at(rb);
-        for (int e = t; e < 8 * kpt; e += rows) {
+        for (int e = t; e < 8 * kpt; e += nthr) {
             const int kk = e >> 3, n = e & 7;
             const KeyRec r = get_key(rec_at(slot, kk));
             if (!(r.flags & 0x80u)) continue;
@@ -371,6 +387,23 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
             }
             a.phi_oct[(((int64_t)o * a.C + r.cell) * a.G + r.g) * 8 + n] = sum;
         }
+    };
+    // row j's solution x: outflow faces (or boundary leakage) and w_d psi
+    T leak[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) leak[j] = T(0);
+    auto emit = [&](int j, const KeyRec &kr, const T (&x)[8], int i) {
+        const int d = dr[j];
+        if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, x[1], x[3], x[5], x[7]);
+        else leak[j] += dd[j].t3x * (x[1] + x[3] + x[5] + x[7]);
+        if (!(kr.flags & 16u)) store4(a.fy + kr.by + d, x[2], x[3], x[6], x[7]);
+        else leak[j] += dd[j].t3y * (x[2] + x[3] + x[6] + x[7]);
+        if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, x[4], x[5], x[6], x[7]);
+        else leak[j] += dd[j].t3z * (x[4] + x[5] + x[6] + x[7]);
+        const T w = dd[j].w;
+        T *r = red_at(i & 1) + (t + j * nthr) * 8;
+        store4(reinterpret_cast<Vec4<T> *>(r), w * x[0], w * x[1], w * x[2], w * x[3]);
+        store4(reinterpret_cast<Vec4<T> *>(r) + 1, w * x[4], w * x[5], w * x[6], w * x[7]);
     };
 
     // Tile i of this CTA is tile t0 + i * step of the hyperplane.  Its key record sits
@@ -402,7 +435,6 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
         face_copy(j, j);
         cp_async_commit();
     }
-    T leak = T(0);
     int i = 0;
     for (int tile = t0; tile < a.ntiles; tile += step, ++i) {
         const int slot = i % kTileRecs, cur = i % STAGES;
@@ -421,47 +453,56 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
         }
         pk_next = pk_ahead;
         cp_async_commit();
-        // this tile's inputs from the stage
-        const KeyRec kr = get_key(rec_at(slot, lane_row ? lk : 0));
-        const bool act = lane_row && (kr.flags & 0x80u);
-        if (act) {
-            T S[8], ux[4], uy[4], uz[4];
-            const T *ff = reinterpret_cast<const T *>(gsm + L.face) + (cur * rows + t) * 12;
-            const T *fks = reinterpret_cast<const T *>(gsm + L.ks) + (cur * kpt + lk) * 8;
-            const T sig = reinterpret_cast<const T *>(gsm + L.sig)[cur * kpt + lk];
-            const T *pi = a.psi_inc + 6 * kr.g;
+        // this tile's inputs from the stage: inflow faces (or psi_inc on the boundary),
+        // sources and opacity of each of the thread's rows
+        KeyRec kr[RPT];
+        bool act[RPT];
+        T S[RPT][8], ux[RPT][4], uy[RPT][4], uz[RPT][4], sig[RPT];
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            kr[j] = get_key(rec_at(slot, lane_row[j] ? lk[j] : 0));
+            act[j] = lane_row[j] && (kr[j].flags & 0x80u);
+            const int kj = act[j] ? lk[j] : 0;
+            const T *ff = reinterpret_cast<const T *>(gsm + L.face) + (cur * rows + t + j * nthr) * 12;
+            const T *fks = reinterpret_cast<const T *>(gsm + L.ks) + (cur * kpt + kj) * 8;
+            sig[j] = reinterpret_cast<const T *>(gsm + L.sig)[cur * kpt + kj];
+            const T *pi = a.psi_inc + 6 * kr[j].g;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                ux[q] = (kr.flags & 1u) ? pi[psi_o[0]] : ff[q];
-                uy[q] = (kr.flags & 2u) ? pi[psi_o[1]] : ff[4 + q];
-                uz[q] = (kr.flags & 4u) ? pi[psi_o[2]] : ff[8 + q];
+                ux[j][q] = (kr[j].flags & 1u) ? pi[psi_o[0]] : ff[q];
+                uy[j][q] = (kr[j].flags & 2u) ? pi[psi_o[1]] : ff[4 + q];
+                uz[j][q] = (kr[j].flags & 4u) ? pi[psi_o[2]] : ff[8 + q];
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) S[q] = fks[q];
-            T x[8];
-            if constexpr (NET) {
-                octnet_forward<false>(wnet, ux, uy, uz, S, amu, aeta, sig, 0.f, 0.f, 0.f, x);
-            } else {
-                cell_solve_canonical<T, REFINE>(dd.t3x, dd.t3y, dd.t3z, sig, S, ux, uy, uz, x);
+            for (int q = 0; q < 8; ++q) S[j][q] = fks[q];
+        }
+        if constexpr (NET) {
+            // both rows through the network in one pass over its weights (an idle row
+            // is evaluated on whatever its stage holds and not emitted)
+            float x[RPT][8];
+            octnet_forward2(wnet, ux, uy, uz, S, amu, aeta, sig, x);
+#pragma unroll
+            for (int j = 0; j < RPT; ++j)
+                if (act[j]) emit(j, kr[j], x[j], i);
+        } else {
+            if (act[0]) {
+                T x[8];
+                cell_solve_canonical<T, REFINE>(dd[0].t3x, dd[0].t3y, dd[0].t3z, sig[0], S[0], ux[0], uy[0], uz[0],
+                                                x);
+                emit(0, kr[0], x, i);
             }
-            if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, x[1], x[3], x[5], x[7]);
-            else leak += dd.t3x * (x[1] + x[3] + x[5] + x[7]);
-            if (!(kr.flags & 16u)) store4(a.fy + kr.by + d, x[2], x[3], x[6], x[7]);
-            else leak += dd.t3y * (x[2] + x[3] + x[6] + x[7]);
-            if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, x[4], x[5], x[6], x[7]);
-            else leak += dd.t3z * (x[4] + x[5] + x[6] + x[7]);
-            T *r = red_at(i & 1) + t * 8;
-            store4(reinterpret_cast<Vec4<T> *>(r), dd.w * x[0], dd.w * x[1], dd.w * x[2], dd.w * x[3]);
-            store4(reinterpret_cast<Vec4<T> *>(r) + 1, dd.w * x[4], dd.w * x[5], dd.w * x[6], dd.w * x[7]);
         }
     }
     cp_async_wait_all();
     __syncthreads();
     if (i > 0) reduce_tile((i - 1) % kTileRecs, (i - 1) & 1);
-    leak *= dd.w * a.vol12;
+    T lsum = T(0);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) leak += __shfl_down_sync(0xffffffffu, leak, off);
-    if ((t & 31) == 0 && leak != T(0)) atomicAdd(a.leak, (double)leak);
+    for (int j = 0; j < RPT; ++j) lsum += leak[j] * dd[j].w;
+    lsum *= a.vol12;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
+    if ((t & 31) == 0 && lsum != T(0)) atomicAdd(a.leak, (double)lsum);
 }
 
 template <typename T, bool REFINE, int DO>
@@ -522,7 +563,11 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     a.hx = (T)h->dx; a.hy = (T)h->dy; a.hz = (T)h->dz;
     const int rows = SN_GE_BLOCK;
     if constexpr (sizeof(T) == 4) {
-        if (net) return launch_sweep_net(h, a, ge_tile_smem<T>(a.keys_per_cta, rows, 2, true).total, st);
+        if (net) {
+            // two rows a thread; every key needs a key thread (at most one key a thread)
+            a.keys_per_cta = std::min(2 * SN_GE_BLOCK / h->Do, SN_GE_BLOCK);
+            return launch_sweep_net(h, a, ge_tile_smem<T>(a.keys_per_cta, 2 * rows, SN_NET_PRE, true).total, st);
+        }
     }
     const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false).total;
     void (*kern)(SweepArgs<T>) = nullptr;
