@@ -346,8 +346,10 @@ def octnet_form(P):
 
     ge_rate, ge_phi = rate(sn.GE32R)
     net_rate, net_phi = rate(sn.OCTNET)
+    gmax = ge_phi.abs().amax(dim=(1, 2), keepdim=True)
     out = {"network": rep, "value": net_rate, "unit": UNIT, "ge_sweep_solves_per_s": ge_rate,
-           "speedup_vs_ge_sweep": net_rate / ge_rate, "one_sweep_eps_P_vs_ge": eps_p(net_phi, ge_phi)}
+           "speedup_vs_ge_sweep": net_rate / ge_rate, "one_sweep_eps_P_vs_ge": eps_p(net_phi, ge_phi),
+           "one_sweep_maxnorm_err_vs_ge": float(((net_phi - ge_phi).abs() / gmax).max())}
     phi = P.flux_tensor()
     try:
         r = P.source_iterate(phi=phi, tol=1e-5, max_it=300, mode=sn.OCTNET, use_graph=True, allow_noconv=True)
