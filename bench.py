@@ -37,7 +37,7 @@ BYTES_PER_SOLVE = 96
 # DRAM bytes (read + write) per solve of sweep_ge_tiles<float, 1, 10> measured by ncu on
 # blocked_64 hyperplane 95 (cold cache, full-set capture of one launch); None
 # once that kernel changes
-DRAM_BYTES_PER_SOLVE_NCU = 86.0
+DRAM_BYTES_PER_SOLVE_NCU = 86.3
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
