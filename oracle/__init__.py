@@ -8,7 +8,8 @@ The sweep, the per-cell assembly, the Gaussian elimination and the source
 iteration live in plain C (``sn_oracle.c``, FP64, built by ``oracle/build.py``);
 this module is the ctypes wrapper, plus the numpy FP64 oracles of the
 surrogate network (``oracle.mlp``), of the paper's per-octant networks
-(``oracle.octant_net``) and of the discrete adjoint (``oracle.adjoint``).
+(``oracle.octant_net``), of the discrete adjoint (``oracle.adjoint``) and the real
+spherical harmonics of the anisotropic scattering source (``oracle.harmonics``).
 """
 import ctypes
 import os
@@ -60,6 +61,10 @@ def _declare(L):
     L.or_source_iterate.argtypes = [P, ctypes.c_double, ctypes.c_int, _dp,
                                     ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
     L.or_num_threads.argtypes = []
+    L.or_source_moments.argtypes = [P, ctypes.c_int, _dp, _dp, _dp]
+    L.or_sweep_moments.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.or_source_iterate_moments.argtypes = [P, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp,
+                                            ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
     N = ctypes.POINTER(OctNet)
     L.or_octnet_cell_batch.argtypes = [N, ctypes.c_long, _dp, _dp]
     L.or_sweep_octnet.argtypes = [P, N, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
@@ -215,6 +220,50 @@ class OracleProblem:
         if rc != 0:
             raise ZeroDivisionError("zero pivot")
         return phi, tal
+
+    # ---- anisotropic scattering (Eqs. (3)-(8)); see oracle.harmonics ----
+    def _aniso(self, sigs_n):
+        """sigma_{s,n} [L+1][G][ncell] with row 0 = the problem's sigma_s; K = (L+1)^2;
+        scaled harmonics of the problem's directions [ndir][K]."""
+        from . import harmonics
+        s = _f64(sigs_n).reshape(-1, self.G, self.ncell)
+        L = s.shape[0] - 1
+        full = _f64(np.concatenate([self.sigs[None], s[1:]], 0)) if L > 0 else _f64(self.sigs[None])
+        return L, (L + 1) ** 2, full, _f64(harmonics.yhat(self.omega, L))
+
+    def source_moments(self, phi_m, sigs_n):
+        L, K, full, _ = self._aniso(sigs_n)
+        phi_m = _f64(phi_m).reshape(self.G, self.ncell, K, 8)
+        S = np.zeros_like(phi_m)
+        lib().or_source_moments(ctypes.byref(self.c), K, _p(full), _p(phi_m), _p(S))
+        return S
+
+    def sweep_moments(self, S_m, sigs_n):
+        """flux moments [G,ncell,K,8] of one sweep from source moments S_m [G,ncell,K,8]."""
+        L, K, full, Yh = self._aniso(sigs_n)
+        S_m = _f64(S_m).reshape(self.G, self.ncell, K, 8)
+        phi = np.zeros_like(S_m)
+        tal = np.zeros(4)
+        if lib().or_sweep_moments(ctypes.byref(self.c), K, _p(Yh), _p(S_m), _p(phi), _p(tal)) != 0:
+            raise ZeroDivisionError("zero pivot")
+        return phi, tal
+
+    def source_iterate_moments(self, sigs_n, tol, maxit, phi0=None):
+        """Source iteration with Legendre scattering moments sigs_n [L+1][G][ncell]
+        (row 0 is ignored: the problem's sigma_s); flux moments [G, ncell, K, 8]."""
+        L, K, full, Yh = self._aniso(sigs_n)
+        phi = (np.zeros((self.G, self.ncell, K, 8)) if phi0 is None
+               else _f64(phi0).reshape(self.G, self.ncell, K, 8).copy())
+        it = ctypes.c_int(0)
+        cmax = ctypes.c_double(0.0)
+        cmean = ctypes.c_double(0.0)
+        tal = np.zeros(4)
+        rc = lib().or_source_iterate_moments(ctypes.byref(self.c), K, _p(full), _p(Yh), tol, maxit, _p(phi),
+                                             ctypes.byref(it), ctypes.byref(cmax), ctypes.byref(cmean), _p(tal))
+        if rc < 0:
+            raise ZeroDivisionError("zero pivot")
+        return dict(phi=phi, iters=it.value, change_max=cmax.value, change_mean=cmean.value, tallies=tal,
+                    converged=(rc == 0))
 
     def source(self, phi):
         S = np.zeros((self.G, self.ncell, 8))

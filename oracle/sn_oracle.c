@@ -10,6 +10,7 @@
  *
  * Equation numbers are the paper's, counted in order of appearance:
  *   (1) transport equation, (2) total source, (6)-(7) moment form,
+ *   (3)-(5) Legendre expansion of the scattering and the addition theorem,
  *   (8)-(9) S_N discretisation, (10) inflow boundary condition,
  *   (11) DFEM trial expansion, (12) discrete DFEM system, (13) phi = D psi,
  *   (14) the per-cell system A psi = b, (21) source-iteration change.
@@ -597,6 +598,129 @@ int or_source_iterate(const or_problem *p, double tol, int maxit, double *phi, i
                 for (int k = 0; k < 8; ++k) {
                     a += pn[((long)g * nc + c) * 8 + k];
                     b += phi[((long)g * nc + c) * 8 + k];
+                }
+                if (a != 0.0) { mean += fabs(a - b) / fabs(a); ++cnt; }
+            }
+        memcpy(phi, pn, sizeof(double) * n);
+        *iters = it + 1;
+        *chg_max = pmax > 0.0 ? dmax / pmax : 0.0;
+        *chg_mean = cnt ? mean / cnt : 0.0;
+        if (tal) for (int m = 0; m < 4; ++m) tal[m] = t[m];
+        if (*chg_max <= tol) { rc = 0; break; }
+    }
+    free(S);
+    free(pn);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Anisotropic scattering (Eqs. (3)-(8)).  The differential scattering      */
+/* cross section is expanded in Legendre polynomials up to order L,          */
+/* sigma_s(mu0) = sum_n (2n+1)/(4 pi) sigma_{s,n} P_n(mu0), and by the        */
+/* addition theorem the scattering source of direction Omega is              */
+/* sum_{n,m} sigma_{s,n} Y_nm(Omega) phi_nm with the flux moments             */
+/* phi_nm = sum_d w_d Y_nm(Omega_d) psi_d (real orthonormal harmonics).       */
+/* Here the harmonics come in scaled by sqrt(4 pi), Yh = sqrt(4 pi) Y, so     */
+/* that Yh_00 = 1 and moment 0 is the scalar flux: flux moments              */
+/* phih_k = sum_d w_d Yh_k(Omega_d) psi_d, source moments                     */
+/* Sh_k = (sum_g' xfer[g'][g] sigma_{s,n(k),g'} phih_k,g' + [k = 0] q) / 4 pi,  */
+/* per-direction source S_d = sum_k Yh_k(Omega_d) Sh_k.  Moment k is (n, m)   */
+/* with k = n^2 + n + m, K = (L+1)^2 moments; n(k) = floor(sqrt(k)).           */
+/*   sigs_n: [L+1][G][ncell] Legendre moments sigma_{s,n} (row 0 = sigma_s)   */
+/*   Yh:     [ndir][K] scaled harmonics of the problem's directions           */
+/*   phi:    [G][ncell][K][8] flux moments                                    */
+/* ------------------------------------------------------------------------ */
+static int order_of(int k)
+{
+    int n = 0;
+    while ((n + 1) * (n + 1) <= k) ++n;
+    return n;
+}
+
+void or_source_moments(const or_problem *p, int K, const double *sigs_n, const double *phi, double *S)
+{
+    const long nc = ncell_of(p);
+    for (int g = 0; g < p->G; ++g)
+        for (long c = 0; c < nc; ++c)
+            for (int k = 0; k < K; ++k) {
+                const int n = order_of(k);
+                for (int q = 0; q < 8; ++q) {
+                    double s = k == 0 ? p->q[(long)g * nc + c] : 0.0;
+                    for (int gp = 0; gp < p->G; ++gp)
+                        s += p->xfer[gp * p->G + g] * sigs_n[((long)n * p->G + gp) * nc + c] *
+                             phi[(((long)gp * nc + c) * K + k) * 8 + q];
+                    S[(((long)g * nc + c) * K + k) * 8 + q] = s / (4.0 * PI);
+                }
+            }
+}
+
+/* One sweep of every direction and group from the source moments S [G][ncell]  */
+/* [K][8]; flux moments out [G][ncell][K][8]; tal[4] as or_sweep.              */
+int or_sweep_moments(const or_problem *p, int K, const double *Yh, const double *S, double *phi, double *tal)
+{
+    or_elem e;
+    or_element(p->dx, p->dy, p->dz, e.M, e.L, e.G, e.F);
+    const long nc = ncell_of(p);
+    int bad = 0;
+    double gt[64][4];
+    memset(gt, 0, sizeof(gt));
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int g = 0; g < p->G; ++g) {
+        double *psi = (double *)malloc(sizeof(double) * 8 * nc);
+        double *Sd = (double *)malloc(sizeof(double) * 8 * nc);
+        double *ph = phi + (long)g * nc * K * 8;
+        const double *Sg = S + (long)g * nc * K * 8;
+        for (long i = 0; i < nc * K * 8; ++i) ph[i] = 0.0;
+        for (int d = 0; d < p->ndir; ++d) {
+            const double *y = Yh + (long)d * K;
+            for (long c = 0; c < nc; ++c)
+                for (int q = 0; q < 8; ++q) {
+                    double s = 0.0;
+                    for (int k = 0; k < K; ++k) s += y[k] * Sg[(c * K + k) * 8 + q];
+                    Sd[c * 8 + q] = s;
+                }
+            double t[4] = {0, 0, 0, 0};
+            if (sweep_dir(p, &e, NULL, d, g, Sd, NULL, NULL, NULL, psi, t) != 0) bad = 1;
+            for (long c = 0; c < nc; ++c)
+                for (int k = 0; k < K; ++k)
+                    for (int q = 0; q < 8; ++q) ph[(c * K + k) * 8 + q] += p->w[d] * y[k] * psi[c * 8 + q];
+            for (int m = 0; m < 4; ++m) gt[g][m] += p->w[d] * t[m];
+        }
+        free(psi);
+        free(Sd);
+    }
+    if (tal)
+        for (int g = 0; g < p->G; ++g)
+            for (int m = 0; m < 4; ++m) tal[m] += gt[g][m];
+    return bad ? -1 : 0;
+}
+
+/* Source iteration with anisotropic scattering; the change norms are those of */
+/* or_source_iterate taken on moment 0 (the scalar flux).                      */
+int or_source_iterate_moments(const or_problem *p, int K, const double *sigs_n, const double *Yh, double tol,
+                              int maxit, double *phi, int *iters, double *chg_max, double *chg_mean, double *tal)
+{
+    const long nc = ncell_of(p), n = (long)p->G * nc * K * 8;
+    double *S = (double *)malloc(sizeof(double) * n);
+    double *pn = (double *)malloc(sizeof(double) * n);
+    int rc = 1;
+    *iters = 0;
+    for (int it = 0; it < maxit; ++it) {
+        or_source_moments(p, K, sigs_n, phi, S);
+        double t[4] = {0, 0, 0, 0};
+        if (or_sweep_moments(p, K, Yh, S, pn, t) != 0) { rc = -1; break; }
+        double dmax = 0.0, pmax = 0.0, mean = 0.0;
+        long cnt = 0;
+        for (int g = 0; g < p->G; ++g)
+            for (long c = 0; c < nc; ++c) {
+                double a = 0.0, b = 0.0;
+                for (int q = 0; q < 8; ++q) {
+                    const long i = (((long)g * nc + c) * K) * 8 + q;
+                    const double dd = fabs(pn[i] - phi[i]);
+                    if (dd > dmax) dmax = dd;
+                    if (fabs(pn[i]) > pmax) pmax = fabs(pn[i]);
+                    a += pn[i];
+                    b += phi[i];
                 }
                 if (a != 0.0) { mean += fabs(a - b) / fabs(a); ++cnt; }
             }
