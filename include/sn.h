@@ -286,6 +286,33 @@ sn_status sn_set_profiling(sn_handle h, int32_t enable);
 sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t reset);
 
 /* ---------------------------------------------------------------------------
+ * sn_set_scattering_order: anisotropic scattering (Sec. 2, Eqs. (3)-(8)).  The
+ * differential scattering cross section is expanded in Legendre polynomials up to
+ * order L (0..SN_MAX_SCATTERING_ORDER): sigma_s(mu0) = sum_n (2n+1)/(4 pi)
+ * sigma_{s,n} P_n(mu0), sigma_{s,0} being the handle's sigma_s.  The source of
+ * direction Omega is then sum_{n,m} sigma_{s,n} Y_nm(Omega) phi_nm (real orthonormal
+ * harmonics, flux moments phi_nm = sum_d w_d Y_nm(Omega_d) psi_d).
+ *   sigs_n: host [L][G][ncell] FP64, sigma_{s,n} for n = 1..L (NULL when L = 0);
+ *           group transfer as for sigma_s (xfer[g'][g] applies to every order).
+ * After the call every flux and source array of the handle (sn_sweep, sn_source,
+ * sn_source_iterate) holds K = (L+1)^2 moments in the layout [G][K][ncell][8]:
+ * moment k = n^2 + n + m (degree n, order m) of sqrt(4 pi) Y, so moment 0 is the
+ * scalar flux (source) of the isotropic layout and L = 0 restores it.  Real
+ * harmonics: Y_n0 = N_n0 P_n(cos theta), Y_nm = sqrt(2) N_nm P_n^m(cos theta)
+ * cos(m phi) and Y_n,-m = sqrt(2) N_nm P_n^m(cos theta) sin(m phi) for m > 0,
+ * N_nm^2 = (2n+1)/(4 pi) (n-m)!/(n+m)!, P_n^m without the Condon-Shortley sign,
+ * theta from the z axis, phi in the x-y plane.  Source moments:
+ * Sh_k = (sum_g' xfer[g'][g] sigma_{s,n(k),g'} phih_k,g' + [k = 0] q) / (4 pi).
+ * Modes: SN_SOLVE_GE32R, SN_SOLVE_GE32, SN_SOLVE_GE64; the surrogate modes, the
+ * adjoint, sn_response and sn_harvest return SN_EINVAL while L > 0.  SN_EINVAL also
+ * when the moments of a sweep tile do not fit in shared memory (few directions per
+ * octant, e.g. LQ_2 with L = 3).  Reallocates the handle's flux buffers; drops
+ * captured iteration graphs.  Synchronises the handle's stream.
+ * ------------------------------------------------------------------------- */
+#define SN_MAX_SCATTERING_ORDER 3
+sn_status sn_set_scattering_order(sn_handle h, int32_t L, const double *sigs_n);
+
+/* ---------------------------------------------------------------------------
  * The paper's own surrogate: one network per octant of directions (Sec. 4),
  * 26 inputs -> 8 tanh units -> 8 ELU outputs (Sec. 3, Eqs. (15), (17), (18)).
  *

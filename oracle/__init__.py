@@ -62,7 +62,7 @@ def _declare(L):
                                     ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
     L.or_num_threads.argtypes = []
     L.or_source_moments.argtypes = [P, ctypes.c_int, _dp, _dp, _dp]
-    L.or_sweep_moments.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.or_sweep_moments.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
     L.or_source_iterate_moments.argtypes = [P, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp,
                                             ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
     N = ctypes.POINTER(OctNet)
@@ -238,13 +238,15 @@ class OracleProblem:
         lib().or_source_moments(ctypes.byref(self.c), K, _p(full), _p(phi_m), _p(S))
         return S
 
-    def sweep_moments(self, S_m, sigs_n):
-        """flux moments [G,ncell,K,8] of one sweep from source moments S_m [G,ncell,K,8]."""
+    def sweep_moments(self, S_m, sigs_n, groups=None):
+        """flux moments [G,ncell,K,8] of one sweep from source moments S_m [G,ncell,K,8]
+        (groups: a (begin, end) range; zero outside it)."""
         L, K, full, Yh = self._aniso(sigs_n)
         S_m = _f64(S_m).reshape(self.G, self.ncell, K, 8)
         phi = np.zeros_like(S_m)
         tal = np.zeros(4)
-        if lib().or_sweep_moments(ctypes.byref(self.c), K, _p(Yh), _p(S_m), _p(phi), _p(tal)) != 0:
+        g0, g1 = groups if groups else (0, self.G)
+        if lib().or_sweep_moments(ctypes.byref(self.c), K, _p(Yh), _p(S_m), _p(phi), g0, g1, _p(tal)) != 0:
             raise ZeroDivisionError("zero pivot")
         return phi, tal
 

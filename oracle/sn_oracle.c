@@ -654,9 +654,11 @@ void or_source_moments(const or_problem *p, int K, const double *sigs_n, const d
             }
 }
 
-/* One sweep of every direction and group from the source moments S [G][ncell]  */
-/* [K][8]; flux moments out [G][ncell][K][8]; tal[4] as or_sweep.              */
-int or_sweep_moments(const or_problem *p, int K, const double *Yh, const double *S, double *phi, double *tal)
+/* One sweep of every direction of groups [g0, g1) from the source moments S     */
+/* [G][ncell][K][8]; flux moments out [G][ncell][K][8] (zero outside the        */
+/* groups); tal[4] as or_sweep.                                                 */
+int or_sweep_moments(const or_problem *p, int K, const double *Yh, const double *S, double *phi, int g0, int g1,
+                     double *tal)
 {
     or_elem e;
     or_element(p->dx, p->dy, p->dz, e.M, e.L, e.G, e.F);
@@ -665,7 +667,7 @@ int or_sweep_moments(const or_problem *p, int K, const double *Yh, const double 
     double gt[64][4];
     memset(gt, 0, sizeof(gt));
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
-    for (int g = 0; g < p->G; ++g) {
+    for (int g = g0; g < g1; ++g) {
         double *psi = (double *)malloc(sizeof(double) * 8 * nc);
         double *Sd = (double *)malloc(sizeof(double) * 8 * nc);
         double *ph = phi + (long)g * nc * K * 8;
@@ -690,7 +692,7 @@ int or_sweep_moments(const or_problem *p, int K, const double *Yh, const double 
         free(Sd);
     }
     if (tal)
-        for (int g = 0; g < p->G; ++g)
+        for (int g = g0; g < g1; ++g)
             for (int m = 0; m < 4; ++m) tal[m] += gt[g][m];
     return bad ? -1 : 0;
 }
@@ -708,7 +710,7 @@ int or_source_iterate_moments(const or_problem *p, int K, const double *sigs_n, 
     for (int it = 0; it < maxit; ++it) {
         or_source_moments(p, K, sigs_n, phi, S);
         double t[4] = {0, 0, 0, 0};
-        if (or_sweep_moments(p, K, Yh, S, pn, t) != 0) { rc = -1; break; }
+        if (or_sweep_moments(p, K, Yh, S, pn, 0, p->G, t) != 0) { rc = -1; break; }
         double dmax = 0.0, pmax = 0.0, mean = 0.0;
         long cnt = 0;
         for (int g = 0; g < p->G; ++g)

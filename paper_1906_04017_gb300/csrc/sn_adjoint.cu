@@ -181,6 +181,7 @@ extern "C" {
 sn_status sn_response(sn_handle h, const void *phi, const void *resp, double *R)
 {
     if (!h || !phi || !resp || !R) return fail(h, SN_EINVAL, "sn_response: NULL argument");
+    if (h->K > 1) return fail(h, SN_EINVAL, "sn_response: isotropic scattering only");
     const cudaStream_t st = h->stream;
     const int64_t n = (int64_t)h->G * h->ncell * 8;
     int64_t grid = (n + 255) / 256;
@@ -207,6 +208,7 @@ sn_status sn_adjoint_sweep(sn_handle h, const float *phi, const float *resp, dou
 {
     if (!h || !phi || !resp || !Lam || !dR_dsigt || !dR_dsigs || !dR_dq)
         return fail(h, SN_EINVAL, "sn_adjoint_sweep: NULL argument");
+    if (h->K > 1) return fail(h, SN_EINVAL, "sn_adjoint_sweep: isotropic scattering only");
     if (h->fp64) return fail(h, SN_EINVAL, "sn_adjoint_sweep: needs an FP32 handle");
     if (max_it < 1 || !(tol >= 0.0)) return fail(h, SN_EINVAL, "sn_adjoint_sweep: max_it >= 1, tol >= 0");
     sn_status s = ensure_adjoint(h);

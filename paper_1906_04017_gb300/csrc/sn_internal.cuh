@@ -119,6 +119,12 @@ struct sn_handle_s {
     bool has_net = false;
     void *net = nullptr;
 
+    // anisotropic scattering (sn_set_scattering_order): Legendre order L, K = (L+1)^2
+    // flux moments; sigma_s,n for n = 1..L [L][G][C] and the harmonics [8][Do][K]
+    int L = 0, K = 1;
+    void *sigs_n = nullptr;
+    void *yhat = nullptr;
+
     // the paper's per-octant networks (sn_octnet_init / sn_octnet_set)
     bool has_octnet = false;
     void *octnet = nullptr;
@@ -153,6 +159,9 @@ sn_status reduce_configure(sn_handle h);
 sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, bool norms,
                         cudaStream_t st);
 sn_status launch_source(sn_handle h, const void *phi, void *S, cudaStream_t st);
+// anisotropic scattering (sn_aniso.cu, sn_sweep.cu)
+sn_status launch_source_moments(sn_handle h, const void *phi, void *S, cudaStream_t st);
+uint32_t sweep_smem_bytes(sn_handle h, int K);
 sn_status launch_cells_f32(const float *in27, float *psi, int64_t n, bool refine, cudaStream_t st);
 // surrogate sweep (sn_ann.cu): every hyperplane of one sweep, FP32 handles only
 sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gated, cudaStream_t st);

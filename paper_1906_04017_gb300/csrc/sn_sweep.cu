@@ -61,6 +61,8 @@ struct SweepArgs {
     const float4 *dir_abs;   // |Omega| of each direction of an octant
     T hx, hy, hz;
     const float *onet;       // [8][288] folded octant networks (network sweeps)
+    int K;                   // flux / source moments (anisotropic scattering; 1 = isotropic)
+    const T *yhat;           // [8][Do][K] sqrt(4 pi) Y_k of every direction (octant-major)
 };
 
 // grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
@@ -242,23 +244,24 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS 
 constexpr int kTileRecs = 8;   // key-record ring (>= prefetch distance + 3 live tiles)
 template <typename T>
 struct GeTileSmem {
-    uint32_t face, ks, sig, rec, red, net, total;
+    uint32_t face, ks, sig, rec, red, net, yt, total;
 };
 // Every stage written while an earlier tile may still be read has its own buffer
 // (PRE + 1 copy stages for a prefetch distance of PRE tiles), so one barrier a tile
 // suffices.  Network sweeps keep the octant's folded network after the stages.
 template <typename T>
-__host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows, int pre, bool net)
+__host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows, int pre, bool net, int K = 1, int Do = 0)
 {
     const uint32_t stages = (uint32_t)pre + 1;
     GeTileSmem<T> m;
     m.face = 0;                                                         // stages x [rows][12] inflow faces
-    m.ks = m.face + stages * rows * 12 * (uint32_t)sizeof(T);          // stages x [kpt][8] sources
-    m.sig = m.ks + stages * kpt * 8 * (uint32_t)sizeof(T);             // stages x [kpt] opacities
+    m.ks = m.face + stages * rows * 12 * (uint32_t)sizeof(T);          // stages x [kpt][K][8] source moments
+    m.sig = m.ks + stages * kpt * K * 8 * (uint32_t)sizeof(T);         // stages x [kpt] opacities
     m.rec = (m.sig + stages * kpt * (uint32_t)sizeof(T) + 15) & ~15u;  // 8 x [kpt] key records
     m.red = m.rec + kTileRecs * 32 * kpt;                              // 2 x [rows][8] w_d psi (canonical)
     m.net = m.red + 2 * rows * 8 * (uint32_t)sizeof(T);                // [288] folded network
-    m.total = m.net + (net ? (uint32_t)(sizeof(float) * kOnFold) : 0u);
+    m.yt = m.net + (net ? (uint32_t)(sizeof(float) * kOnFold) : 0u);  // [Do][K] harmonics (K > 1)
+    m.total = m.yt + (K > 1 ? (uint32_t)(Do * K * sizeof(T)) : 0u);
     return m;
 }
 
@@ -283,15 +286,20 @@ constexpr int tile_min_blocks()
 // weight reads, not the arithmetic, bound a one-row network sweep.  PRE: tiles of
 // copies in flight (the elimination hides one tile of copy latency behind its
 // solve; a deeper prefetch measured no faster).
-template <typename T, bool REFINE, int DO, bool NET>
+//
+// MOM (anisotropic scattering, K = a.K moments): every key stages its K source moments,
+// a row forms its direction's source sum_k Yh_k(Omega_d) Sh_k, and the reduction of a
+// tile forms the K flux moments sum_d Yh_k(Omega_d) w_d psi_d of every key.
+template <typename T, bool REFINE, int DO, bool NET, bool MOM = false>
 __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
 {
     constexpr int PRE = NET ? SN_NET_PRE : 1, STAGES = PRE + 1, RPT = NET ? 2 : 1;
     extern __shared__ __align__(16) unsigned char gsm[];
     griddep_launch();
     const int Do = DO ? DO : a.Do;
+    const int KM = MOM ? a.K : 1;
     const int nthr = blockDim.x, kpt = a.keys_per_cta, rows = nthr * RPT;
-    const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows, PRE, NET);
+    const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows, PRE, NET, KM, Do);
     const uint32_t sb = smem_u32(gsm);
     const int t = threadIdx.x, o = blockIdx.y;
     int lk[RPT], dr[RPT];
@@ -319,6 +327,11 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
         // which is not overlapped with earlier work: safe to read before griddep_wait
         for (int e = t; e < kOnFold; e += nthr) wnet[e] = a.onet[kOnFold * o + e];
     }
+    T *yt = reinterpret_cast<T *>(gsm + L.yt);
+    if (MOM) {
+        // the octant's harmonics table (written at set-up)
+        for (int e = t; e < Do * KM; e += nthr) yt[e] = a.yhat[(int64_t)o * Do * KM + e];
+    }
     auto red_at = [&](int buf) -> T * { return reinterpret_cast<T *>(gsm + L.red) + buf * rows * 8; };
     auto rec_at = [&](int slot, int k) -> unsigned char * { return gsm + L.rec + (slot * kpt + k) * 32; };
     const int psi_o[3] = {o & 1, 2 + ((o >> 1) & 1), 4 + ((o >> 2) & 1)};
@@ -345,13 +358,16 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
         if (!(r.flags & 0x80u)) return;
         const int64_t gc = (int64_t)r.g * a.C + r.cell;
         const uint32_t k = (uint32_t)(sbuf * kpt + t);
-        // node by node into the canonical order of the octant (canonical n = physical n ^ o)
-        const uint32_t dst = sb + L.ks + k * 8 * (uint32_t)sizeof(T);
-        const T *src = a.S + gc * 8;
+        // node by node into the canonical order of the octant (canonical n = physical n ^ o);
+        // source moments in the [G][K][C][8] layout
+        for (int m = 0; m < KM; ++m) {
+            const uint32_t dst = sb + L.ks + (k * KM + m) * 8 * (uint32_t)sizeof(T);
+            const T *src = a.S + (((int64_t)r.g * KM + m) * a.C + r.cell) * 8;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            if (sizeof(T) == 4) cp_async4(dst + 4 * (p ^ o), src + p);
-            else cp_async8(dst + 8 * (p ^ o), src + p);
+            for (int p = 0; p < 8; ++p) {
+                if (sizeof(T) == 4) cp_async4(dst + 4 * (p ^ o), src + p);
+                else cp_async8(dst + 8 * (p ^ o), src + p);
+            }
         }
         if (sizeof(T) == 4) cp_async4(sb + L.sig + 4 * k, a.sigt + gc);
         else cp_async8(sb + L.sig + 8 * k, a.sigt + gc);
@@ -373,6 +389,18 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
     // flux partial of the tile whose records are in `slot` and w_d psi in red buffer `rb`
     auto reduce_tile = [&](int slot, int rb) {
         const T *red = red_at(rb);
+        if (MOM) {
+            for (int e = t; e < 8 * KM * kpt; e += nthr) {
+                const int kk = e / (8 * KM), rem = e - kk * 8 * KM, m = rem >> 3, n = rem & 7;
+                const KeyRec r = get_key(rec_at(slot, kk));
+                if (!(r.flags & 0x80u)) continue;
+                const T *base = red + (kk * Do) * 8 + (n ^ o);
+                T sum = T(0);
+                for (int q = 0; q < Do; ++q) sum += yt[q * KM + m] * base[q * 8];
+                a.phi_oct[((((int64_t)o * a.C + r.cell) * a.G + r.g) * KM + m) * 8 + n] = sum;
+            }
+            return;
+        }
         for (int e = t; e < 8 * kpt; e += nthr) {
             const int kk = e >> 3, n = e & 7;
             const KeyRec r = get_key(rec_at(slot, kk));
@@ -464,7 +492,7 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
             act[j] = lane_row[j] && (kr[j].flags & 0x80u);
             const int kj = act[j] ? lk[j] : 0;
             const T *ff = reinterpret_cast<const T *>(gsm + L.face) + (cur * rows + t + j * nthr) * 12;
-            const T *fks = reinterpret_cast<const T *>(gsm + L.ks) + (cur * kpt + kj) * 8;
+            const T *fks = reinterpret_cast<const T *>(gsm + L.ks) + (cur * kpt + kj) * KM * 8;
             sig[j] = reinterpret_cast<const T *>(gsm + L.sig)[cur * kpt + kj];
             const T *pi = a.psi_inc + 6 * kr[j].g;
 #pragma unroll
@@ -473,8 +501,20 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
                 uy[j][q] = (kr[j].flags & 2u) ? pi[psi_o[1]] : ff[4 + q];
                 uz[j][q] = (kr[j].flags & 4u) ? pi[psi_o[2]] : ff[8 + q];
             }
+            if (MOM) {
+                // this direction's source from the key's source moments
+                const T *y = yt + dr[j] * KM;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) S[j][q] = fks[q];
+                for (int q = 0; q < 8; ++q) S[j][q] = T(0);
+                for (int m = 0; m < KM; ++m) {
+                    const T ym = y[m];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) S[j][q] = fma(ym, fks[m * 8 + q], S[j][q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) S[j][q] = fks[q];
+            }
         }
         if constexpr (NET) {
             // both rows through the network in one pass over its weights (an idle row
@@ -511,10 +551,24 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sw
     ge_tiles_body<T, REFINE, DO, false>(a);
 }
 
+template <typename T, bool REFINE>
+__global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sweep_ge_moments(SweepArgs<T> a)
+{
+    ge_tiles_body<T, REFINE, 0, false, true>(a);
+}
+
 template <int DO>
 __global__ void __launch_bounds__(SN_GE_BLOCK, SN_NET_TILE_MINBLOCKS) sweep_net_tiles(SweepArgs<float> a)
 {
     ge_tiles_body<float, false, DO, true>(a);
+}
+
+// shared memory of an elimination sweep tile of this handle with K moments
+uint32_t sweep_smem_bytes(sn_handle h, int K)
+{
+    const int kpt = SN_GE_BLOCK / h->Do;
+    return h->fp64 ? ge_tile_smem<double>(kpt, SN_GE_BLOCK, 1, false, K, h->Do).total
+                   : ge_tile_smem<float>(kpt, SN_GE_BLOCK, 1, false, K, h->Do).total;
 }
 
 // Hyperplane launches of a network sweep (the folded networks of the handle).
@@ -564,14 +618,20 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     const int rows = SN_GE_BLOCK;
     if constexpr (sizeof(T) == 4) {
         if (net) {
+            a.K = 1;
+            a.yhat = nullptr;
             // two rows a thread; every key needs a key thread (at most one key a thread)
             a.keys_per_cta = std::min(2 * SN_GE_BLOCK / h->Do, SN_GE_BLOCK);
             return launch_sweep_net(h, a, ge_tile_smem<T>(a.keys_per_cta, 2 * rows, SN_NET_PRE, true).total, st);
         }
     }
-    const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false).total;
+    a.K = h->K;
+    a.yhat = (const T *)h->yhat;
+    const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false, h->K, h->Do).total;
     void (*kern)(SweepArgs<T>) = nullptr;
-    if (refine)
+    if (h->K > 1)
+        kern = refine ? sweep_ge_moments<T, true> : sweep_ge_moments<T, false>;
+    else if (refine)
         kern = h->Do == 10 ? sweep_ge_tiles<T, true, 10> : h->Do == 21 ? sweep_ge_tiles<T, true, 21>
                                                                      : sweep_ge_tiles<T, true, 0>;
     else
@@ -724,11 +784,15 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v)
 // both sides move whole lines.  Octant sum in the element type (fixed order), per-
 // element quantities in the element type, FP64 only for the running sums and the
 // block / grid accumulation (the FP64 rate of the part is low).
+//
+// With K flux moments (anisotropic scattering) the partials are [o][c][g][k][8] and the
+// flux [g][k][c][8]: the same transposition with G * K "groups"; the tallies and the
+// change measures use moment 0 (the scalar flux) only.
 template <typename T>
 __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_oct, const T *__restrict__ phi_old,
                                                      T *__restrict__ phi_new, const T *__restrict__ S,
                                                      const T *__restrict__ sigt, int64_t C, int G, int TC,
-                                                     FastDiv divG8, double vol8, double *acc, int norms)
+                                                     FastDiv divG8, double vol8, double *acc, int norms, int K)
 {
     extern __shared__ __align__(16) unsigned char red_smem[];
     T *tile = reinterpret_cast<T *>(red_smem);   // [TC][G*8 + 8] (padded row per cell)
@@ -772,6 +836,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
         const int nk = nc * 8;
         for (int g = 0; g < G; ++g) {
             const int64_t base = ((int64_t)g * C + c0) * 8;
+            const bool scalar = g % K == 0;   // moment 0 of its group
+            const int gg = g / K;
             // whole warps, so that the 8 nodes of a cell meet in one shuffle group
             for (int k = threadIdx.x; k - lane < nk; k += blockDim.x) {
                 const bool in = k < nk;
@@ -781,15 +847,17 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
                     nv = tile[cl * row + g * 8 + (k & 7)];
                     phi_new[base + k] = nv;
                     if (!isfinite(nv)) bad = 1;
-                    coll += (double)(sigt[(int64_t)g * C + c0 + cl] * nv);
-                    src += (double)S[base + k];
-                    if (norms) {
-                        ov = phi_old[base + k];
-                        dmax = fmax(dmax, fabs(nv - ov));
-                        pmax = fmax(pmax, fabs(nv));
+                    if (scalar) {
+                        coll += (double)(sigt[(int64_t)gg * C + c0 + cl] * nv);
+                        src += (double)S[base + k];
+                        if (norms) {
+                            ov = phi_old[base + k];
+                            dmax = fmax(dmax, fabs(nv - ov));
+                            pmax = fmax(pmax, fabs(nv));
+                        }
                     }
                 }
-                if (norms) {
+                if (norms && scalar) {
                     T a = nv, b = ov;
 #pragma unroll
                     for (int off = 1; off < 8; off <<= 1) {
@@ -850,8 +918,8 @@ int num_sms()
 
 static size_t reduce_tile(const sn_handle h, int *TC)
 {
-    // about 2048 elements a tile; a cell's G*8 values always stay in one tile
-    const int G8 = h->G * 8;
+    // about 2048 elements a tile; a cell's G*K*8 values always stay in one tile
+    const int G8 = h->G * h->K * 8;
     *TC = G8 >= 2048 ? 1 : 2048 / G8;
     return (size_t)*TC * (G8 + 8) * h->esz;
 }
@@ -880,15 +948,15 @@ sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const v
     const int64_t cap = (int64_t)num_sms() * 8;
     if (grid > cap) grid = cap;
     const double vol8 = h->dx * h->dy * h->dz / 8.0;
-    const FastDiv divG8((uint32_t)(h->G * 8));
+    const FastDiv divG8((uint32_t)(h->G * h->K * 8));
     if (h->fp64)
         reduce_kernel<double><<<(unsigned)grid, 256, smem, st>>>(
             (const double *)h->phi_oct, (const double *)phi_old, (double *)phi_new, (const double *)S,
-            (const double *)h->sigt, h->ncell, h->G, TC, divG8, vol8, h->acc, norms ? 1 : 0);
+            (const double *)h->sigt, h->ncell, h->G * h->K, TC, divG8, vol8, h->acc, norms ? 1 : 0, h->K);
     else
         reduce_kernel<float><<<(unsigned)grid, 256, smem, st>>>(
             (const float *)h->phi_oct, (const float *)phi_old, (float *)phi_new, (const float *)S,
-            (const float *)h->sigt, h->ncell, h->G, TC, divG8, vol8, h->acc, norms ? 1 : 0);
+            (const float *)h->sigt, h->ncell, h->G * h->K, TC, divG8, vol8, h->acc, norms ? 1 : 0, h->K);
     SN_CK(h, cudaGetLastError());
     return SN_OK;
 }
@@ -961,12 +1029,15 @@ static sn_status launch_source_t(sn_handle h, const T *phi, T *S, cudaStream_t s
 
 sn_status launch_source(sn_handle h, const void *phi, void *S, cudaStream_t st)
 {
+    if (h->K > 1) return launch_source_moments(h, phi, S, st);
     if (h->fp64) return launch_source_t<double>(h, (const double *)phi, (double *)S, st);
     return launch_source_t<float>(h, (const float *)phi, (float *)S, st);
 }
 
 static sn_status check_mode(sn_handle h, sn_solve_mode mode)
 {
+    if (h->K > 1 && mode != SN_SOLVE_GE32R && mode != SN_SOLVE_GE32 && mode != SN_SOLVE_GE64)
+        return fail(h, SN_EINVAL, "anisotropic scattering runs the elimination modes only");
     if (h->fp64) {
         if (mode == SN_SOLVE_GE64) return SN_OK;
         return fail(h, SN_EINVAL, "an FP64 handle only runs SN_SOLVE_GE64");
@@ -1109,7 +1180,7 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
         }
     }
     if (cur == 1)
-        SN_CK(h, cudaMemcpyAsync(phi, h->phi_b, h->esz * h->G * h->ncell * 8, cudaMemcpyDeviceToDevice, st));
+        SN_CK(h, cudaMemcpyAsync(phi, h->phi_b, h->esz * h->G * h->K * h->ncell * 8, cudaMemcpyDeviceToDevice, st));
     SN_CK(h, cudaStreamSynchronize(st));
     if (iters) *iters = it;
     if (change_max) *change_max = cmax;
@@ -1122,6 +1193,7 @@ sn_status sn_harvest(sn_handle h, const float *S, float *in27, int64_t cap, uint
 {
     if (!h || !S || !in27 || !n_out) return fail(h, SN_EINVAL, "sn_harvest: NULL argument");
     if (h->fp64) return fail(h, SN_EINVAL, "sn_harvest: needs an FP32 handle");
+    if (h->K > 1) return fail(h, SN_EINVAL, "sn_harvest: isotropic scattering only");
     if (cap < 1 || cap > (1LL << 31)) return fail(h, SN_EINVAL, "sn_harvest: cap must be in 1..2^31");
     const cudaStream_t st = h->stream;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(h->acc + ACC_HARVEST);

@@ -93,6 +93,7 @@ _API = [
                                         _fp, ctypes.POINTER(ctypes.c_int32)]),
     ("sn_response", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, _dp]),
     ("sn_surrogate_grad_noalloc", ctypes.c_int, [_fp, _fp, _fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
+    ("sn_set_scattering_order", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _dp]),
     ("sn_octnet_init", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_uint64]),
     ("sn_octnet_set", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                      _dp, _dp]),
@@ -245,6 +246,7 @@ class Problem:
         self.nplanes, self.dirs_per_octant = info.nplanes, info.dirs_per_octant
         self.solves_per_sweep = info.solves_per_sweep
         self.device_bytes = info.device_bytes
+        self.L, self.K = 0, 1
 
     def close(self):
         if getattr(self, "h", None):
@@ -267,7 +269,21 @@ class Problem:
         return om, w
 
     def flux_tensor(self, device="cuda"):
-        return torch.zeros((self.G, self.ncell, 8), dtype=self.dtype, device=device)
+        """Zero flux (or source) array of the handle's layout: [G, ncell, 8], or the
+        moments [G, K, ncell, 8] under anisotropic scattering."""
+        shape = (self.G, self.ncell, 8) if self.K == 1 else (self.G, self.K, self.ncell, 8)
+        return torch.zeros(shape, dtype=self.dtype, device=device)
+
+    def set_scattering_order(self, L, sigs_n=None):
+        """Anisotropic scattering to Legendre order L (Eqs. (3)-(8)); sigs_n: sigma_{s,n}
+        for n = 1..L, [L, G, ncell].  Flux and source arrays become moments
+        [G, (L+1)^2, ncell, 8]."""
+        a = None
+        if L > 0:
+            a = np.ascontiguousarray(sigs_n, dtype=np.float64).reshape(L, self.G, self.ncell)
+        self._sync_stream()
+        _check(lib().sn_set_scattering_order(self.h, int(L), None if a is None else _dptr(a)), self.h)
+        self.L, self.K = int(L), (int(L) + 1) ** 2
 
     def sweep(self, S, phi=None, mode=None):
         """One sweep: phi[G, ncell, 8] from the isotropic nodal source S[G, ncell, 8]."""
