@@ -374,6 +374,45 @@ def octnet_form(P):
     return out
 
 
+def aniso_form(steps, ge_step_ms):
+    """Anisotropic scattering (Eqs. (3)-(8)) on the same workload: Legendre order L = 1
+    and L = 3 (K = 4 and 16 flux moments), sigma_{s,n} = 0.5^n sigma_s; the graph-
+    captured source iteration's step time and the sweep kernels' solves/s.  Extra work
+    per solve against the isotropic step: the direction's source from K source moments
+    (8 K multiply-adds) and its share of the K flux moments (8 K multiply-adds)."""
+    import torch
+    from paper_1906_04017_gb300 import sn, workloads
+    out = []
+    for L in (1, 3):
+        wl = workloads.blocked_64()
+        P = sn.Problem(wl)
+        P.set_scattering_order(L, np.stack([wl["sigs"] * 0.5 ** n for n in range(1, L + 1)]))
+        phi = P.flux_tensor()
+        P.source_iterate(phi=phi, tol=0.0, max_it=3, use_graph=True, allow_noconv=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = P.source_iterate(phi=phi, tol=0.0, max_it=steps, use_graph=True, allow_noconv=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        P.set_profiling(True)
+        P.profile(reset=True)
+        P.source_iterate(phi=phi, tol=0.0, max_it=3, use_graph=False, allow_noconv=True)
+        sw_ms, n = P.profile(reset=True)
+        P.set_profiling(False)
+        K = (L + 1) ** 2
+        flops = FLOPS_PER_SOLVE - 16 + 32 * K
+        sweep_rate = P.solves_per_sweep / (sw_ms / n / 1e3)
+        out.append({"L": L, "moments": K, "step_ms": ms, "value": P.solves_per_sweep / (ms / 1e3),
+                    "unit": UNIT, "step_time_vs_isotropic": ms / ge_step_ms,
+                    "sweep_solves_per_s": sweep_rate, "flops_per_solve": flops,
+                    "sweep_tflops": sweep_rate * flops / 1e12, "iters": r["iters"]})
+        P.close()
+        del phi
+    return out
+
+
 def e2e_pipelined(P, S_host, phi_host, steps, stream):
     """`steps` sweeps through the public API (sn_sweep) with every step's source
     copied in from pinned host memory and its flux copied back, the copies on a
@@ -477,6 +516,7 @@ def run_gpu(args):
 
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, "cuda")
     P.close()
+    aniso = None if args.no_aniso else aniso_form(min(args.steps, 10), ms / args.steps)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -522,6 +562,8 @@ def run_gpu(args):
         line["ann"] = ann
     if octnet is not None:
         line["octnet"] = octnet
+    if aniso is not None:
+        line["aniso"] = aniso
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -711,6 +753,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ann", action="store_true")
     ap.add_argument("--no-octnet", action="store_true")
+    ap.add_argument("--no-aniso", action="store_true")
     ap.add_argument("--paper-tables", action="store_true",
                     help="Problems 1-4 of the paper with both solvers (prints its own JSON line)")
     ap.add_argument("--adjoint-check", action="store_true",

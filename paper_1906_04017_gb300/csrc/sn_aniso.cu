@@ -70,8 +70,9 @@ static void yhat_of(const double *om, int L, double *out)
 
 // Moment source (the generalisation of the isotropic source to K moments), flux and
 // source moments in the [G][K][C][8] layout.  One thread per (moment, cell, node),
-// all groups.
-template <typename T>
+// all groups; up to GMAX groups the scattering products sigma_{s,n,g'} phi_g' are read
+// once into registers (GMAX = 0: any group count, read per use).
+template <typename T, int GMAX>
 __global__ void __launch_bounds__(256) source_moments_kernel(const T *__restrict__ phi, const T *__restrict__ sigs,
                                                              const T *__restrict__ sigs_n, const T *__restrict__ q,
                                                              const T *__restrict__ xfer, T *__restrict__ S,
@@ -86,13 +87,41 @@ __global__ void __launch_bounds__(256) source_moments_kernel(const T *__restrict
         int n = 0;
         while ((n + 1) * (n + 1) <= k) ++n;
         const T *sn = n == 0 ? sigs : sigs_n + (int64_t)(n - 1) * G * C;
-        for (int g = 0; g < G; ++g) {
-            T acc = k == 0 ? q[(int64_t)g * C + c] : T(0);
-            for (int gp = 0; gp < G; ++gp)
-                acc = fma(xfer[gp * G + g], sn[(int64_t)gp * C + c] * phi[((int64_t)gp * K + k) * per + ce], acc);
-            S[((int64_t)g * K + k) * per + ce] = acc * inv4pi;
+        if constexpr (GMAX > 0) {
+            T sv[GMAX];
+#pragma unroll
+            for (int gp = 0; gp < GMAX; ++gp)
+                sv[gp] = gp < G ? sn[(int64_t)gp * C + c] * phi[((int64_t)gp * K + k) * per + ce] : T(0);
+#pragma unroll
+            for (int g = 0; g < GMAX; ++g) {
+                if (g >= G) break;
+                T acc = k == 0 ? q[(int64_t)g * C + c] : T(0);
+#pragma unroll
+                for (int gp = 0; gp < GMAX; ++gp)
+                    if (gp < G) acc = fma(__ldg(xfer + gp * G + g), sv[gp], acc);
+                S[((int64_t)g * K + k) * per + ce] = acc * inv4pi;
+            }
+        } else {
+            for (int g = 0; g < G; ++g) {
+                T acc = k == 0 ? q[(int64_t)g * C + c] : T(0);
+                for (int gp = 0; gp < G; ++gp)
+                    acc = fma(xfer[gp * G + g], sn[(int64_t)gp * C + c] * phi[((int64_t)gp * K + k) * per + ce], acc);
+                S[((int64_t)g * K + k) * per + ce] = acc * inv4pi;
+            }
         }
     }
+}
+
+template <typename T>
+static void launch_source_moments_t(sn_handle h, const T *phi, T *S, unsigned grid, cudaStream_t st)
+{
+    const T *sg = (const T *)h->sigs, *sn = (const T *)h->sigs_n, *q = (const T *)h->q, *xf = (const T *)h->xfer;
+    if (h->G <= 8)
+        source_moments_kernel<T, 8><<<grid, 256, 0, st>>>(phi, sg, sn, q, xf, S, h->ncell, h->G, h->K);
+    else if (h->G <= 16)
+        source_moments_kernel<T, 16><<<grid, 256, 0, st>>>(phi, sg, sn, q, xf, S, h->ncell, h->G, h->K);
+    else
+        source_moments_kernel<T, 0><<<grid, 256, 0, st>>>(phi, sg, sn, q, xf, S, h->ncell, h->G, h->K);
 }
 
 sn_status launch_source_moments(sn_handle h, const void *phi, void *S, cudaStream_t st)
@@ -102,13 +131,9 @@ sn_status launch_source_moments(sn_handle h, const void *phi, void *S, cudaStrea
     const int64_t cap = (int64_t)num_sms() * 16;
     if (grid > cap) grid = cap;
     if (h->fp64)
-        source_moments_kernel<double><<<(unsigned)grid, 256, 0, st>>>(
-            (const double *)phi, (const double *)h->sigs, (const double *)h->sigs_n, (const double *)h->q,
-            (const double *)h->xfer, (double *)S, h->ncell, h->G, h->K);
+        launch_source_moments_t<double>(h, (const double *)phi, (double *)S, (unsigned)grid, st);
     else
-        source_moments_kernel<float><<<(unsigned)grid, 256, 0, st>>>(
-            (const float *)phi, (const float *)h->sigs, (const float *)h->sigs_n, (const float *)h->q,
-            (const float *)h->xfer, (float *)S, h->ncell, h->G, h->K);
+        launch_source_moments_t<float>(h, (const float *)phi, (float *)S, (unsigned)grid, st);
     SN_CK(h, cudaGetLastError());
     return SN_OK;
 }

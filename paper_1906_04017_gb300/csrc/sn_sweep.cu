@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, sizeof(T) == 4 ? SN_GE_MINBLOCKS 
 // distance is free; without it a tile waits about one global-memory latency.  The
 // flux reduction of a tile runs at the start of the next iteration.
 constexpr int kTileRecs = 8;   // key-record ring (>= prefetch distance + 3 live tiles)
+constexpr int kMaxMoments = (SN_MAX_SCATTERING_ORDER + 1) * (SN_MAX_SCATTERING_ORDER + 1);
 template <typename T>
 struct GeTileSmem {
     uint32_t face, ks, sig, rec, red, net, yt, total;
@@ -390,14 +391,27 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
     auto reduce_tile = [&](int slot, int rb) {
         const T *red = red_at(rb);
         if (MOM) {
-            for (int e = t; e < 8 * KM * kpt; e += nthr) {
-                const int kk = e / (8 * KM), rem = e - kk * 8 * KM, m = rem >> 3, n = rem & 7;
+            // one thread per (key, node): every flux moment of that node, each w_d psi_d
+            // read once
+            for (int e = t; e < 8 * kpt; e += nthr) {
+                const int kk = e >> 3, n = e & 7;
                 const KeyRec r = get_key(rec_at(slot, kk));
                 if (!(r.flags & 0x80u)) continue;
                 const T *base = red + (kk * Do) * 8 + (n ^ o);
-                T sum = T(0);
-                for (int q = 0; q < Do; ++q) sum += yt[q * KM + m] * base[q * 8];
-                a.phi_oct[((((int64_t)o * a.C + r.cell) * a.G + r.g) * KM + m) * 8 + n] = sum;
+                T acc[kMaxMoments];
+#pragma unroll
+                for (int m = 0; m < kMaxMoments; ++m) acc[m] = T(0);
+                for (int q = 0; q < Do; ++q) {
+                    const T v = base[q * 8];
+                    const T *y = yt + q * KM;
+#pragma unroll
+                    for (int m = 0; m < kMaxMoments; ++m)
+                        if (m < KM) acc[m] = fma(y[m], v, acc[m]);
+                }
+                T *dst = a.phi_oct + (((int64_t)o * a.C + r.cell) * a.G + r.g) * KM * 8 + n;
+#pragma unroll
+                for (int m = 0; m < kMaxMoments; ++m)
+                    if (m < KM) dst[m * 8] = acc[m];
             }
             return;
         }
@@ -506,10 +520,13 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
                 const T *y = yt + dr[j] * KM;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) S[j][q] = T(0);
-                for (int m = 0; m < KM; ++m) {
-                    const T ym = y[m];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) S[j][q] = fma(ym, fks[m * 8 + q], S[j][q]);
+                for (int m = 0; m < kMaxMoments; ++m) {
+                    if (m < KM) {
+                        const T ym = y[m];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) S[j][q] = fma(ym, fks[m * 8 + q], S[j][q]);
+                    }
                 }
             } else {
 #pragma unroll
