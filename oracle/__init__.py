@@ -38,8 +38,10 @@ class Problem(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
         ("ndir", ctypes.c_int), ("omega", _dp), ("w", _dp),
         ("G", ctypes.c_int), ("sigt", _dp), ("sigs", _dp), ("q", _dp),
-        ("xfer", _dp), ("psi_inc", _dp),
+        ("xfer", _dp), ("psi_inc", _dp), ("hex", ctypes.c_void_p),
     ]
+
+HEX_DOUBLES = 64 + 3 * 64 + 6 * 3 * 64     # or_hex: M, L[3], Fv[6][3]
 
 
 class OctNet(ctypes.Structure):
@@ -61,6 +63,8 @@ def _declare(L):
     L.or_source_iterate.argtypes = [P, ctypes.c_double, ctypes.c_int, _dp,
                                     ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp]
     L.or_num_threads.argtypes = []
+    L.or_hex_element.argtypes = [_dp, _dp]
+    L.or_hex_elements.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
     L.or_source_moments.argtypes = [P, ctypes.c_int, _dp, _dp, _dp]
     L.or_sweep_moments.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
     L.or_source_iterate_moments.argtypes = [P, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp,
@@ -159,6 +163,15 @@ def octnet_cell(P, lo, hi, in27):
     return out
 
 
+def hex_element(X):
+    """(M [8,8], L [3,8,8], Fv [6,3,8,8]) of the trilinear cell with vertices X [8,3]
+    (node n = a + 2b + 4c)."""
+    X = _f64(X).reshape(8, 3)
+    out = np.zeros(HEX_DOUBLES)
+    lib().or_hex_element(_p(X), _p(out))
+    return out[:64].reshape(8, 8), out[64:256].reshape(3, 8, 8), out[256:].reshape(6, 3, 8, 8)
+
+
 class OracleProblem:
     """Holds the FP64 arrays of one problem and the ctypes view of them.
 
@@ -167,7 +180,9 @@ class OracleProblem:
     q[G,ncell], xfer[G,G], psi_inc[G,6].
     """
 
-    def __init__(self, wl, omega=None, w=None):
+    def __init__(self, wl, omega=None, w=None, xyz=None):
+        """xyz: optional vertex coordinates [(nx+1)(ny+1)(nz+1), 3] of general
+        hexahedral cells with the mesh's structured topology (box cells if None)."""
         self.nx, self.ny, self.nz = int(wl["nx"]), int(wl["ny"]), int(wl["nz"])
         self.ncell = self.nx * self.ny * self.nz
         self.dx = wl["lx"] / self.nx
@@ -184,9 +199,15 @@ class OracleProblem:
         self.q = _f64(wl["q"]).reshape(self.G, self.ncell)
         self.xfer = _f64(wl["xfer"]).reshape(self.G, self.G)
         self.psi_inc = _f64(wl["psi_inc"]).reshape(self.G, 6)
+        self.hex = None
+        if xyz is not None:
+            self.xyz = _f64(xyz).reshape(-1, 3)
+            self.hex = np.zeros(self.ncell * HEX_DOUBLES)
+            lib().or_hex_elements(self.nx, self.ny, self.nz, _p(self.xyz), _p(self.hex))
         self.c = Problem(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.ndir,
                          _p(self.omega), _p(self.w), self.G, _p(self.sigt), _p(self.sigs),
-                         _p(self.q), _p(self.xfer), _p(self.psi_inc))
+                         _p(self.q), _p(self.xfer), _p(self.psi_inc),
+                         None if self.hex is None else self.hex.ctypes.data)
 
     def sweep_dir(self, d, g, S, bx=None, by=None, bz=None):
         """psi[ncell,8] of direction d, group g, for the nodal source S[ncell,8].

@@ -364,6 +364,152 @@ void or_octnet_cell_batch(const or_octnet *net, long n, const double *in27, doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* General hexahedral cells (the shape change of the cells of Sec. 2's       */
+/* closing remarks): a trilinear map x(xi) = sum_n X_n N_n(xi) of the unit   */
+/* cube, N_n = prod over the axes of xi_a or 1 - xi_a by the bits of          */
+/* n = a + 2b + 4c, the same N_n as trial and test functions (isoparametric  */
+/* Q1).  Element matrices:                                                   */
+/*   M[k][j]       = int N_k N_j dV                                          */
+/*   L_a[k][j]     = -int N_j d_a N_k dV                                     */
+/*   Fv[f][a][k][j] = int_f n_a N_k N_j dS  (outward area vector of face f)  */
+/* With dV = det J dxi and d_a N = sum_s adj(J)[s][a] d_s N / det J, every     */
+/* integrand (det J N N, adj(J) terms, the face area vectors) is a            */
+/* polynomial of degree <= 4 per axis, so 3-point Gauss quadrature per axis  */
+/* integrates them exactly.  Face f = 2a + side (side 1: xi_a = 1); the face  */
+/* area vector is +-(dx/dxi_p x dx/dxi_q) with (a, p, q) cyclic, + on side 1. */
+/* The per-cell system is the outflow form of (14) with the faces' Omega.n   */
+/* taken from Fv; the mesh keeps the structured topology, and a face is      */
+/* inflow or outflow for a direction by the sign of Omega_a as for a box    */
+/* (meshes where Omega.n changes sign on a face are outside this reading).  */
+/* ------------------------------------------------------------------------ */
+typedef struct { double M[64], L[3][64], Fv[6][3][64]; } or_hex;
+
+static void hex_shape(const double xi[3], double N[8], double dN[8][3])
+{
+    for (int n = 0; n < 8; ++n) {
+        double f[3], df[3];
+        for (int a = 0; a < 3; ++a) {
+            const int bit = (n >> a) & 1;
+            f[a] = bit ? xi[a] : 1.0 - xi[a];
+            df[a] = bit ? 1.0 : -1.0;
+        }
+        N[n] = f[0] * f[1] * f[2];
+        dN[n][0] = df[0] * f[1] * f[2];
+        dN[n][1] = f[0] * df[1] * f[2];
+        dN[n][2] = f[0] * f[1] * df[2];
+    }
+}
+
+void or_hex_element(const double *X /* [8][3] */, or_hex *e)
+{
+    const double g[3] = {0.5 - 0.5 * sqrt(0.6), 0.5, 0.5 + 0.5 * sqrt(0.6)};
+    const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    memset(e, 0, sizeof(*e));
+    for (int i0 = 0; i0 < 3; ++i0)
+        for (int i1 = 0; i1 < 3; ++i1)
+            for (int i2 = 0; i2 < 3; ++i2) {
+                const double xi[3] = {g[i0], g[i1], g[i2]};
+                const double w = gw[i0] * gw[i1] * gw[i2];
+                double N[8], dN[8][3], J[3][3] = {{0}};
+                hex_shape(xi, N, dN);
+                for (int n = 0; n < 8; ++n)
+                    for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c) J[r][c] += X[3 * n + r] * dN[n][c];
+                /* adj(J)[s][a]: the cofactor transpose, J adj(J) = det J I */
+                double adj[3][3];
+                adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+                adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+                adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+                adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+                adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+                adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+                adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+                adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+                adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+                const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+                for (int k = 0; k < 8; ++k)
+                    for (int j = 0; j < 8; ++j) {
+                        e->M[8 * k + j] += w * det * N[k] * N[j];
+                        for (int a = 0; a < 3; ++a) {
+                            double dk = 0.0;   /* det J * d_a N_k */
+                            for (int s2 = 0; s2 < 3; ++s2) dk += adj[s2][a] * dN[k][s2];
+                            e->L[a][8 * k + j] -= w * N[j] * dk;
+                        }
+                    }
+            }
+    for (int f = 0; f < 6; ++f) {
+        const int a = f / 2, side = f % 2, p = (a + 1) % 3, q = (a + 2) % 3;
+        for (int ip = 0; ip < 3; ++ip)
+            for (int iq = 0; iq < 3; ++iq) {
+                double xi[3];
+                xi[a] = side;
+                xi[p] = g[ip];
+                xi[q] = g[iq];
+                const double w = gw[ip] * gw[iq];
+                double N[8], dN[8][3], tp[3] = {0, 0, 0}, tq[3] = {0, 0, 0};
+                hex_shape(xi, N, dN);
+                for (int n = 0; n < 8; ++n)
+                    for (int r = 0; r < 3; ++r) {
+                        tp[r] += X[3 * n + r] * dN[n][p];
+                        tq[r] += X[3 * n + r] * dN[n][q];
+                    }
+                double av[3] = {tp[1] * tq[2] - tp[2] * tq[1], tp[2] * tq[0] - tp[0] * tq[2],
+                                tp[0] * tq[1] - tp[1] * tq[0]};
+                const double sg = side ? 1.0 : -1.0;
+                for (int k = 0; k < 8; ++k)
+                    for (int j = 0; j < 8; ++j)
+                        for (int c = 0; c < 3; ++c) e->Fv[f][c][8 * k + j] += w * sg * av[c] * N[k] * N[j];
+            }
+    }
+}
+
+/* Elements of every cell of a structured mesh with vertex coordinates         */
+/* xyz [(nx+1)(ny+1)(nz+1)][3], vertex (i,j,k) at i + (nx+1)(j + (ny+1) k).     */
+void or_hex_elements(int nx, int ny, int nz, const double *xyz, or_hex *out)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double X[24];
+                for (int n = 0; n < 8; ++n) {
+                    const long v = (i + (n & 1)) + (long)(nx + 1) * ((j + ((n >> 1) & 1)) + (long)(ny + 1) * (k + (n >> 2)));
+                    for (int r = 0; r < 3; ++r) X[3 * n + r] = xyz[3 * v + r];
+                }
+                or_hex_element(X, out + i + (long)nx * (j + (long)ny * k));
+            }
+}
+
+/* Outflow form of (14) on a general cell: A = sum_a Omega_a L_a + sigma_t M  */
+/* + sum over outflow faces of Omega.Fv; b = M S + sum over inflow faces of   */
+/* (-Omega.Fv) applied to the upwind values on that face.                      */
+static void assemble_hex(const or_hex *e, const double om[3], double sigt, const double S[8],
+                         const double up[12], double A[64], double b[8])
+{
+    for (int i = 0; i < 64; ++i)
+        A[i] = om[0] * e->L[0][i] + om[1] * e->L[1][i] + om[2] * e->L[2][i] + sigt * e->M[i];
+    for (int k = 0; k < 8; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < 8; ++j) s += e->M[8 * k + j] * S[j];
+        b[k] = s;
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        if (om[ax] == 0.0) continue;
+        const int fout = 2 * ax + (om[ax] > 0.0 ? 1 : 0), fin = 2 * ax + (om[ax] > 0.0 ? 0 : 1);
+        for (int i = 0; i < 64; ++i)
+            A[i] += om[0] * e->Fv[fout][0][i] + om[1] * e->Fv[fout][1][i] + om[2] * e->Fv[fout][2][i];
+        double ext[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int t = 0; t < 4; ++t) ext[face_node(fin, t)] = up[4 * ax + t];
+        for (int k = 0; k < 8; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < 8; ++j)
+                s -= (om[0] * e->Fv[fin][0][8 * k + j] + om[1] * e->Fv[fin][1][8 * k + j] +
+                      om[2] * e->Fv[fin][2][8 * k + j]) * ext[j];
+            b[k] += s;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Problem description.                                                     */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -378,6 +524,7 @@ typedef struct {
     const double *q;        /* [G][ncell] isotropic emission density        */
     const double *xfer;     /* [G][G] fraction of g' scattering into g      */
     const double *psi_inc;  /* [G][6] isotropic inflow on x-,x+,y-,y+,z-,z+ */
+    const void *hex;        /* NULL: box cells dx x dy x dz; else or_hex [ncell] */
 } or_problem;
 
 static long ncell_of(const or_problem *p) { return (long)p->nx * p->ny * p->nz; }
@@ -459,13 +606,49 @@ static int sweep_dir(const or_problem *p, const or_elem *e, const or_octnet *net
                     for (int n = 0; n < 8; ++n) in27[7 + n] = S[8 * c + n];
                     for (int t = 0; t < 12; ++t) in27[15 + t] = up[t];
                     or_octnet_cell(net, in27, x);
+                } else if (p->hex) {
+                    double A[64], b[8];
+                    assemble_hex((const or_hex *)p->hex + c, om, p->sigt[(long)g * nc + c], S + 8 * c, up, A, b);
+                    if (or_ge(8, A, b, x) != 0) return -1;
                 } else {
                     double A[64], b[8];
                     assemble(e, om, p->sigt[(long)g * nc + c], S + 8 * c, up, A, b);
                     if (or_ge(8, A, b, x) != 0) return -1;
                 }
                 for (int n = 0; n < 8; ++n) psi[8 * c + n] = x[n];
-                if (tal) {
+                if (tal && p->hex) {
+                    /* the same tallies from the cell's own matrices: w = 1 = sum of */
+                    /* the test functions, so row sums give the face and volume     */
+                    /* integrals of psi                                              */
+                    const or_hex *h = (const or_hex *)p->hex + c;
+                    for (int ax = 0; ax < 3; ++ax) {
+                        if (om[ax] == 0.0) continue;
+                        int idx[3] = {i, j, k}, n[3] = {nx, ny, nz};
+                        int di = idx[ax] + (om[ax] >= 0.0 ? 1 : -1);
+                        for (int jn = 0; jn < 8; ++jn) {
+                            double fo = 0.0, fi = 0.0;
+                            for (int kn = 0; kn < 8; ++kn)
+                                for (int cc = 0; cc < 3; ++cc) {
+                                    fo += om[cc] * h->Fv[fout[ax]][cc][8 * kn + jn];
+                                    fi -= om[cc] * h->Fv[fin[ax]][cc][8 * kn + jn];
+                                }
+                            if (di < 0 || di >= n[ax]) tal[0] += fo * x[jn];
+                            if (onbnd[ax]) {
+                                for (int t = 0; t < 4; ++t)
+                                    if (face_node(fin[ax], t) == jn) tal[3] += fi * up[4 * ax + t];
+                            }
+                        }
+                    }
+                    double sc = 0.0, ss = 0.0;
+                    for (int jn = 0; jn < 8; ++jn) {
+                        double v = 0.0;
+                        for (int kn = 0; kn < 8; ++kn) v += h->M[8 * kn + jn];
+                        sc += v * x[jn];
+                        ss += v * S[8 * c + jn];
+                    }
+                    tal[1] += p->sigt[(long)g * nc + c] * sc;
+                    tal[2] += ss;
+                } else if (tal) {
                     for (int ax = 0; ax < 3; ++ax) {
                         if (om[ax] == 0.0) continue;
                         int idx[3] = {i, j, k}, n[3] = {nx, ny, nz};

@@ -243,5 +243,33 @@ def octant_problems(m, seed=0, ranges=None):
     return out
 
 
+def box_vertices(wl):
+    """Vertex coordinates [(nx+1)(ny+1)(nz+1), 3] of the workload's uniform box cells,
+    vertex (i, j, k) at index i + (nx+1) (j + (ny+1) k)."""
+    nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
+    x = np.linspace(0.0, wl["lx"], nx + 1)
+    y = np.linspace(0.0, wl["ly"], ny + 1)
+    z = np.linspace(0.0, wl["lz"], nz + 1)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def deformed_vertices(wl, amp, seed=0):
+    """The box vertices with every interior coordinate moved by U[-amp, amp] x the
+    cell size along its axis; a vertex on a boundary plane stays on it (the domain
+    remains the box), so the cells become general trilinear hexahedra."""
+    nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
+    v = box_vertices(wl)
+    rng = np.random.Generator(np.random.PCG64(seed + 7))
+    i = np.tile(np.arange(nx + 1), (ny + 1) * (nz + 1))
+    j = np.tile(np.repeat(np.arange(ny + 1), nx + 1), nz + 1)
+    k = np.repeat(np.arange(nz + 1), (nx + 1) * (ny + 1))
+    h = (wl["lx"] / nx, wl["ly"] / ny, wl["lz"] / nz)
+    for a, (idx, n) in enumerate(((i, nx), (j, ny), (k, nz))):
+        inner = (idx > 0) & (idx < n)
+        v[inner, a] += rng.uniform(-amp, amp, size=int(inner.sum())) * h[a]
+    return v
+
+
 WORKLOADS = {"onecube_8": onecube_8, "blocked_64": blocked_64, "blocked_32": blocked_32,
              "spheres_96": spheres_96}
