@@ -313,6 +313,24 @@ sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t
 sn_status sn_set_scattering_order(sn_handle h, int32_t L, const double *sigs_n);
 
 /* ---------------------------------------------------------------------------
+ * sn_set_geometry: general hexahedral cells (the cells' shape change of Sec. 2's
+ * closing remarks).  The mesh keeps its nx x ny x nz structured topology; xyz
+ * (host FP64 [(nx+1)(ny+1)(nz+1)][3], vertex (i,j,k) at i + (nx+1)(j + (ny+1)k))
+ * places its vertices, and cell (i,j,k) is the trilinear image of the unit cube on
+ * its 8 vertices (node n = a + 2b + 4c at vertex (i+a, j+b, k+c)), with the same
+ * trilinear functions as DFEM basis.  Element matrices (mass, streaming, face area
+ * vector matrices) are computed exactly on the device (3-point Gauss per axis).  The
+ * sweep keeps the box mesh's octant wavefront, which needs, for every quadrature
+ * direction, Omega . n to keep on each face the sign it has on a box cell; that and
+ * a positive Jacobian are checked at the quadrature points (SN_EINVAL otherwise).
+ * The balance tallies use each node's own volume.  NULL restores the box cells.
+ * Modes: SN_SOLVE_GE32R, SN_SOLVE_GE32, SN_SOLVE_GE64; not combined with
+ * anisotropic scattering, the surrogates, the adjoint or harvesting (SN_EINVAL).
+ * Drops captured iteration graphs.  Synchronises the handle's stream.
+ * ------------------------------------------------------------------------- */
+sn_status sn_set_geometry(sn_handle h, const double *xyz);
+
+/* ---------------------------------------------------------------------------
  * The paper's own surrogate: one network per octant of directions (Sec. 4),
  * 26 inputs -> 8 tanh units -> 8 ELU outputs (Sec. 3, Eqs. (15), (17), (18)).
  *

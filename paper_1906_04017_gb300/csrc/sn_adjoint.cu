@@ -208,7 +208,7 @@ sn_status sn_adjoint_sweep(sn_handle h, const float *phi, const float *resp, dou
 {
     if (!h || !phi || !resp || !Lam || !dR_dsigt || !dR_dsigs || !dR_dq)
         return fail(h, SN_EINVAL, "sn_adjoint_sweep: NULL argument");
-    if (h->K > 1) return fail(h, SN_EINVAL, "sn_adjoint_sweep: isotropic scattering only");
+    if (h->K > 1 || h->geom) return fail(h, SN_EINVAL, "sn_adjoint_sweep: isotropic scattering on box cells only");
     if (h->fp64) return fail(h, SN_EINVAL, "sn_adjoint_sweep: needs an FP32 handle");
     if (max_it < 1 || !(tol >= 0.0)) return fail(h, SN_EINVAL, "sn_adjoint_sweep: max_it >= 1, tol >= 0");
     sn_status s = ensure_adjoint(h);

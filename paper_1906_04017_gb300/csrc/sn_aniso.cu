@@ -159,6 +159,7 @@ sn_status sn_set_scattering_order(sn_handle h, int32_t L, const double *sigs_n)
     if (L < 0 || L > SN_MAX_SCATTERING_ORDER)
         return fail(h, SN_EINVAL, "sn_set_scattering_order: L must be in 0..3");
     if (L > 0 && !sigs_n) return fail(h, SN_EINVAL, "sn_set_scattering_order: NULL sigs_n");
+    if (L > 0 && h->geom) return fail(h, SN_EINVAL, "sn_set_scattering_order: not with general hexahedral cells");
     const int64_t GC = (int64_t)h->G * h->ncell;
     std::vector<double> sn((size_t)L * GC);
     for (size_t i = 0; i < sn.size(); ++i) {

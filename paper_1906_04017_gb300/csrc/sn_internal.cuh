@@ -99,6 +99,7 @@ struct sn_handle_s {
     int64_t device_bytes = 0;
 
     double inflow = 0.0;         // boundary inflow of one sweep (host, exact)
+    double inflow_box = 0.0;     // the same for the box cells of sn_setup
     double tallies[4] = {0, 0, 0, 0};
     bool tallies_valid = false;
 
@@ -118,6 +119,12 @@ struct sn_handle_s {
     uint64_t net_gen = 1;        // bumped whenever weights or gate change (graphs bake both in)
     bool has_net = false;
     void *net = nullptr;
+
+    // general hexahedral cells (sn_set_geometry): element records [C][544], node
+    // volumes [C][8] and |Omega| of the octant's directions [Do][3], element type T
+    void *geom = nullptr;
+    void *vnode = nullptr;
+    void *omabs = nullptr;
 
     // anisotropic scattering (sn_set_scattering_order): Legendre order L, K = (L+1)^2
     // flux moments; sigma_s,n for n = 1..L [L][G][C] and the harmonics [8][Do][K]

@@ -168,7 +168,7 @@ static void release(sn_handle h)
         if (h->graphs.exec[i]) cudaGraphExecDestroy(h->graphs.exec[i]);
     free_adjoint(h);
     void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->dir_abs, h->plane_cells, h->plane_pos,
-                    h->face, h->phi_oct, h->S, h->phi_b, h->acc, h->sigs_n, h->yhat};
+                    h->face, h->phi_oct, h->S, h->phi_b, h->acc, h->sigs_n, h->yhat, h->geom, h->vnode, h->omabs};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->acc_host) cudaFreeHost(h->acc_host);
@@ -367,6 +367,7 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
                 }
             }
         h->inflow = tot;
+        h->inflow_box = tot;
     }
 
     // hyperplane table: cells (i',j',k') with i'+j'+k' = s, packed 10 bits per index

@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "ge8.cuh"
+#include "hex.cuh"
 #include "octnet.cuh"
 #include "sn_internal.cuh"
 #include "sweep_common.cuh"
@@ -63,6 +64,8 @@ struct SweepArgs {
     const float *onet;       // [8][288] folded octant networks (network sweeps)
     int K;                   // flux / source moments (anisotropic scattering; 1 = isotropic)
     const T *yhat;           // [8][Do][K] sqrt(4 pi) Y_k of every direction (octant-major)
+    const T *geom;           // general hexahedral cells: element records [C][544] (hex.cuh)
+    const T *omabs;          // |Omega| of the octant's directions [Do][3]
 };
 
 // grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
@@ -291,7 +294,14 @@ constexpr int tile_min_blocks()
 // MOM (anisotropic scattering, K = a.K moments): every key stages its K source moments,
 // a row forms its direction's source sum_k Yh_k(Omega_d) Sh_k, and the reduction of a
 // tile forms the K flux moments sum_d Yh_k(Omega_d) w_d psi_d of every key.
-template <typename T, bool REFINE, int DO, bool NET, bool MOM = false>
+//
+// GEOM (general hexahedral cells): each row assembles its cell's system (14) in the
+// physical frame from the cell's element record (hex.cuh; the rows of a key read the
+// same record, so the loads are broadcasts), with the canonical staged sources and
+// inflow faces permuted back to physical order, solves it by elimination with partial
+// pivoting (and one refinement step), and takes the boundary leakage from the outflow
+// faces' own matrices.
+template <typename T, bool REFINE, int DO, bool NET, bool MOM = false, bool GEOM = false>
 __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
 {
     constexpr int PRE = NET ? SN_NET_PRE : 1, STAGES = PRE + 1, RPT = NET ? 2 : 1;
@@ -432,16 +442,17 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
     };
     // row j's solution x: outflow faces (or boundary leakage) and w_d psi
     T leak[RPT];
+    T leak_exact = T(0);   // GEOM: boundary leakage already weighted by w_d
 #pragma unroll
     for (int j = 0; j < RPT; ++j) leak[j] = T(0);
     auto emit = [&](int j, const KeyRec &kr, const T (&x)[8], int i) {
         const int d = dr[j];
         if (!(kr.flags & 8u)) store4(a.fx + kr.bx + d, x[1], x[3], x[5], x[7]);
-        else leak[j] += dd[j].t3x * (x[1] + x[3] + x[5] + x[7]);
+        else if (!GEOM) leak[j] += dd[j].t3x * (x[1] + x[3] + x[5] + x[7]);
         if (!(kr.flags & 16u)) store4(a.fy + kr.by + d, x[2], x[3], x[6], x[7]);
-        else leak[j] += dd[j].t3y * (x[2] + x[3] + x[6] + x[7]);
+        else if (!GEOM) leak[j] += dd[j].t3y * (x[2] + x[3] + x[6] + x[7]);
         if (!(kr.flags & 32u)) store4(a.fz + kr.bz + d, x[4], x[5], x[6], x[7]);
-        else leak[j] += dd[j].t3z * (x[4] + x[5] + x[6] + x[7]);
+        else if (!GEOM) leak[j] += dd[j].t3z * (x[4] + x[5] + x[6] + x[7]);
         const T w = dd[j].w;
         T *r = red_at(i & 1) + (t + j * nthr) * 8;
         store4(reinterpret_cast<Vec4<T> *>(r), w * x[0], w * x[1], w * x[2], w * x[3]);
@@ -541,6 +552,48 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
 #pragma unroll
             for (int j = 0; j < RPT; ++j)
                 if (act[j]) emit(j, kr[j], x[j], i);
+        } else if constexpr (GEOM) {
+            if (act[0]) {
+                const T *gc = a.geom + (int64_t)kr[0].cell * kHexRec;
+                const int fx = o & 1, fy = (o >> 1) & 1, fz = (o >> 2) & 1;
+                const T *oa = a.omabs + 3 * dr[0];
+                const T om[3] = {fx ? -oa[0] : oa[0], fy ? -oa[1] : oa[1], fz ? -oa[2] : oa[2]};
+                const int out[3] = {1 - fx, 1 - fy, 1 - fz};   // outflow side of each axis
+                // physical order: node n = canonical n ^ o; face value t = canonical t ^ face mask
+                T Sp[8], upx[4], upy[4], upz[4];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) Sp[q] = S[0][q];
+                mirror8(Sp, o);
+#pragma unroll
+                for (int t4 = 0; t4 < 4; ++t4) { upx[t4] = ux[0][t4]; upy[t4] = uy[0][t4]; upz[t4] = uz[0][t4]; }
+                mirror4(upx, fy | (fz << 1));
+                mirror4(upy, fx | (fz << 1));
+                mirror4(upz, fx | (fy << 1));
+                T A[8][8], b[8], b0[8], rinv[8], xp[8];
+                hex_assemble_A(gc, om, sig[0], out, A);
+                hex_build_b(gc, om, out, Sp, upx, upy, upz, b);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) b0[q] = b[q];
+                unsigned piv;
+                ge8_factor_solve(A, b, piv, rinv, xp);
+                if (REFINE) {
+                    T y[8], r[8], dx[8];
+                    hex_apply_A(gc, om, sig[0], out, xp, y);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) r[q] = b0[q] - y[q];
+                    ge8_replay(A, piv, rinv, r, dx);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) xp[q] += dx[q];
+                }
+                if (kr[0].flags & 8u) leak_exact += dd[0].w * hex_out_flux<T, 0>(gc, om, out[0], xp);
+                if (kr[0].flags & 16u) leak_exact += dd[0].w * hex_out_flux<T, 1>(gc, om, out[1], xp);
+                if (kr[0].flags & 32u) leak_exact += dd[0].w * hex_out_flux<T, 2>(gc, om, out[2], xp);
+                T x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = xp[q];
+                mirror8(x, o);
+                emit(0, kr[0], x, i);
+            }
         } else {
             if (act[0]) {
                 T x[8];
@@ -557,6 +610,7 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
 #pragma unroll
     for (int j = 0; j < RPT; ++j) lsum += leak[j] * dd[j].w;
     lsum *= a.vol12;
+    lsum += leak_exact;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
     if ((t & 31) == 0 && lsum != T(0)) atomicAdd(a.leak, (double)lsum);
@@ -572,6 +626,12 @@ template <typename T, bool REFINE>
 __global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sweep_ge_moments(SweepArgs<T> a)
 {
     ge_tiles_body<T, REFINE, 0, false, true>(a);
+}
+
+template <typename T, bool REFINE>
+__global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sweep_ge_hex(SweepArgs<T> a)
+{
+    ge_tiles_body<T, REFINE, 0, false, false, true>(a);
 }
 
 template <int DO>
@@ -644,9 +704,13 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     }
     a.K = h->K;
     a.yhat = (const T *)h->yhat;
+    a.geom = (const T *)h->geom;
+    a.omabs = (const T *)h->omabs;
     const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false, h->K, h->Do).total;
     void (*kern)(SweepArgs<T>) = nullptr;
-    if (h->K > 1)
+    if (h->geom)
+        kern = refine ? sweep_ge_hex<T, true> : sweep_ge_hex<T, false>;
+    else if (h->K > 1)
         kern = refine ? sweep_ge_moments<T, true> : sweep_ge_moments<T, false>;
     else if (refine)
         kern = h->Do == 10 ? sweep_ge_tiles<T, true, 10> : h->Do == 21 ? sweep_ge_tiles<T, true, 21>
@@ -809,7 +873,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_oct, const T *__restrict__ phi_old,
                                                      T *__restrict__ phi_new, const T *__restrict__ S,
                                                      const T *__restrict__ sigt, int64_t C, int G, int TC,
-                                                     FastDiv divG8, double vol8, double *acc, int norms, int K)
+                                                     FastDiv divG8, double vol8, double *acc, int norms, int K,
+                                                     const T *__restrict__ vnode)
 {
     extern __shared__ __align__(16) unsigned char red_smem[];
     T *tile = reinterpret_cast<T *>(red_smem);   // [TC][G*8 + 8] (padded row per cell)
@@ -865,8 +930,10 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
                     phi_new[base + k] = nv;
                     if (!isfinite(nv)) bad = 1;
                     if (scalar) {
-                        coll += (double)(sigt[(int64_t)gg * C + c0 + cl] * nv);
-                        src += (double)S[base + k];
+                        // general cells: the node's own volume (column sum of M)
+                        const T wv = vnode ? vnode[(c0 + cl) * 8 + (k & 7)] : T(1);
+                        coll += (double)(sigt[(int64_t)gg * C + c0 + cl] * nv * wv);
+                        src += (double)(S[base + k] * wv);
                         if (norms) {
                             ov = phi_old[base + k];
                             dmax = fmax(dmax, fabs(nv - ov));
@@ -964,16 +1031,18 @@ sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const v
     int64_t grid = ntile;
     const int64_t cap = (int64_t)num_sms() * 8;
     if (grid > cap) grid = cap;
-    const double vol8 = h->dx * h->dy * h->dz / 8.0;
+    const double vol8 = h->vnode ? 1.0 : h->dx * h->dy * h->dz / 8.0;
     const FastDiv divG8((uint32_t)(h->G * h->K * 8));
     if (h->fp64)
         reduce_kernel<double><<<(unsigned)grid, 256, smem, st>>>(
             (const double *)h->phi_oct, (const double *)phi_old, (double *)phi_new, (const double *)S,
-            (const double *)h->sigt, h->ncell, h->G * h->K, TC, divG8, vol8, h->acc, norms ? 1 : 0, h->K);
+            (const double *)h->sigt, h->ncell, h->G * h->K, TC, divG8, vol8, h->acc, norms ? 1 : 0, h->K,
+            (const double *)h->vnode);
     else
         reduce_kernel<float><<<(unsigned)grid, 256, smem, st>>>(
             (const float *)h->phi_oct, (const float *)phi_old, (float *)phi_new, (const float *)S,
-            (const float *)h->sigt, h->ncell, h->G * h->K, TC, divG8, vol8, h->acc, norms ? 1 : 0, h->K);
+            (const float *)h->sigt, h->ncell, h->G * h->K, TC, divG8, vol8, h->acc, norms ? 1 : 0, h->K,
+            (const float *)h->vnode);
     SN_CK(h, cudaGetLastError());
     return SN_OK;
 }
@@ -1055,6 +1124,8 @@ static sn_status check_mode(sn_handle h, sn_solve_mode mode)
 {
     if (h->K > 1 && mode != SN_SOLVE_GE32R && mode != SN_SOLVE_GE32 && mode != SN_SOLVE_GE64)
         return fail(h, SN_EINVAL, "anisotropic scattering runs the elimination modes only");
+    if (h->geom && mode != SN_SOLVE_GE32R && mode != SN_SOLVE_GE32 && mode != SN_SOLVE_GE64)
+        return fail(h, SN_EINVAL, "general hexahedral cells run the elimination modes only");
     if (h->fp64) {
         if (mode == SN_SOLVE_GE64) return SN_OK;
         return fail(h, SN_EINVAL, "an FP64 handle only runs SN_SOLVE_GE64");
@@ -1210,7 +1281,7 @@ sn_status sn_harvest(sn_handle h, const float *S, float *in27, int64_t cap, uint
 {
     if (!h || !S || !in27 || !n_out) return fail(h, SN_EINVAL, "sn_harvest: NULL argument");
     if (h->fp64) return fail(h, SN_EINVAL, "sn_harvest: needs an FP32 handle");
-    if (h->K > 1) return fail(h, SN_EINVAL, "sn_harvest: isotropic scattering only");
+    if (h->K > 1 || h->geom) return fail(h, SN_EINVAL, "sn_harvest: isotropic scattering on box cells only");
     if (cap < 1 || cap > (1LL << 31)) return fail(h, SN_EINVAL, "sn_harvest: cap must be in 1..2^31");
     const cudaStream_t st = h->stream;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(h->acc + ACC_HARVEST);

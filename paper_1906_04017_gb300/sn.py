@@ -94,6 +94,7 @@ _API = [
     ("sn_response", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, _dp]),
     ("sn_surrogate_grad_noalloc", ctypes.c_int, [_fp, _fp, _fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
     ("sn_set_scattering_order", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _dp]),
+    ("sn_set_geometry", ctypes.c_int, [ctypes.c_void_p, _dp]),
     ("sn_octnet_init", ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_uint64]),
     ("sn_octnet_set", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                      _dp, _dp]),
@@ -273,6 +274,13 @@ class Problem:
         moments [G, K, ncell, 8] under anisotropic scattering."""
         shape = (self.G, self.ncell, 8) if self.K == 1 else (self.G, self.K, self.ncell, 8)
         return torch.zeros(shape, dtype=self.dtype, device=device)
+
+    def set_geometry(self, xyz=None):
+        """General hexahedral cells: vertex coordinates [(nx+1)(ny+1)(nz+1), 3] (see
+        workloads.deformed_vertices); None restores the box cells."""
+        a = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        self._sync_stream()
+        _check(lib().sn_set_geometry(self.h, None if a is None else _dptr(a)), self.h)
 
     def set_scattering_order(self, L, sigs_n=None):
         """Anisotropic scattering to Legendre order L (Eqs. (3)-(8)); sigs_n: sigma_{s,n}
