@@ -413,6 +413,47 @@ def aniso_form(steps, ge_step_ms):
     return out
 
 
+# counted FP32 flops of one solve on a general hexahedral cell: the assembly of A from
+# the cell's matrices (4 x 64 multiply-adds plus 3 outflow face blocks of 16 x 3), the
+# right-hand side (64 + 3 x 64), elimination 372, back substitution 64, the refinement
+# residual without forming A (64 x 4 + 64 + 3 x 64) and replay 128, flux 16
+GEOM_FLOPS_PER_SOLVE = 2 * (256 + 144 + 64 + 192 + 256 + 64 + 192) + 372 + 64 + 128 + 16
+
+
+def geom_form(steps, ge_step_ms):
+    """General hexahedral cells on the same workload: every interior vertex moved by up
+    to 3% of a cell (the largest deformation the LQ_8 directions allow everywhere), the
+    graph-captured source iteration's step time and the sweep kernels' solves/s."""
+    import torch
+    from paper_1906_04017_gb300 import sn, workloads
+    wl = workloads.blocked_64()
+    P = sn.Problem(wl)
+    P.set_geometry(workloads.deformed_vertices(wl, 0.03, seed=0))
+    phi = P.flux_tensor()
+    P.source_iterate(phi=phi, tol=0.0, max_it=3, use_graph=True, allow_noconv=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = P.source_iterate(phi=phi, tol=0.0, max_it=steps, use_graph=True, allow_noconv=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    P.set_profiling(True)
+    P.profile(reset=True)
+    P.source_iterate(phi=phi, tol=0.0, max_it=3, use_graph=False, allow_noconv=True)
+    sw_ms, n = P.profile(reset=True)
+    P.set_profiling(False)
+    bal = P.balance()
+    rate = P.solves_per_sweep / (sw_ms / n / 1e3)
+    out = {"deformation": "interior vertices moved by U[-0.03, 0.03] cell sizes per axis", "step_ms": ms,
+           "value": P.solves_per_sweep / (ms / 1e3), "unit": UNIT, "step_time_vs_box": ms / ge_step_ms,
+           "sweep_solves_per_s": rate, "flops_per_solve": GEOM_FLOPS_PER_SOLVE,
+           "sweep_tflops": rate * GEOM_FLOPS_PER_SOLVE / 1e12, "iters": r["iters"],
+           "balance_rel": abs(bal[0] + bal[1] - bal[2] - bal[3]) / (bal[2] + bal[3])}
+    P.close()
+    return out
+
+
 def e2e_pipelined(P, S_host, phi_host, steps, stream):
     """`steps` sweeps through the public API (sn_sweep) with every step's source
     copied in from pinned host memory and its flux copied back, the copies on a
@@ -517,6 +558,7 @@ def run_gpu(args):
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, "cuda")
     P.close()
     aniso = None if args.no_aniso else aniso_form(min(args.steps, 10), ms / args.steps)
+    geom = None if args.no_geom else geom_form(min(args.steps, 10), ms / args.steps)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -564,6 +606,8 @@ def run_gpu(args):
         line["octnet"] = octnet
     if aniso is not None:
         line["aniso"] = aniso
+    if geom is not None:
+        line["geom"] = geom
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -754,6 +798,7 @@ def main():
     ap.add_argument("--no-ann", action="store_true")
     ap.add_argument("--no-octnet", action="store_true")
     ap.add_argument("--no-aniso", action="store_true")
+    ap.add_argument("--no-geom", action="store_true")
     ap.add_argument("--paper-tables", action="store_true",
                     help="Problems 1-4 of the paper with both solvers (prints its own JSON line)")
     ap.add_argument("--adjoint-check", action="store_true",
