@@ -37,7 +37,7 @@ BYTES_PER_SOLVE = 96
 # DRAM bytes (read + write) per solve of sweep_ge_tiles<float, 1, 10> measured by ncu on
 # blocked_64 hyperplane 95 (cold cache, full-set capture of one launch); None
 # once that kernel changes
-DRAM_BYTES_PER_SOLVE_NCU = 86.3
+DRAM_BYTES_PER_SOLVE_NCU = 86.0
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -261,7 +261,7 @@ def ann_form(P, steps):
     out["roofline_ungated"] = {"bound": "alu", "tensor_achieved": tach, "tensor_peak": tpeak, "unit": "TFLOP/s",
                                "tensor_frac": tach / tpeak,
                                "peak_note": "measured bf16 burst" if "bf16_tflops" in peaks else "fallback"}
-    sweep = [run(sn.ANN_GATED, t) for t in (0.1, 0.05, 0.03, 0.02, 0.01)]
+    sweep = [run(sn.ANN_GATED, t) for t in (0.1, 0.05, 0.03, 0.02, 0.01, 0.005)]
     ok = [r for r in sweep if r.get("eps_P_vs_ge") is not None and r["eps_P_vs_ge"] <= 0.03]
     best = max(ok, key=lambda r: r["sweep_solves_per_s"]) if ok else None
     out.update({"gated_sweep": sweep, "value": best["sweep_solves_per_s"] if best else None,
