@@ -34,8 +34,7 @@ struct OctNet {
     int64_t part_blocks = 0;
     double *loss = nullptr;    // [8] Eq. (19) of the last gradient
     int *flag = nullptr;       // rows found outside their octant by prepare
-    bool ranges = false, params = false;
-    std::vector<double> lo, hi;
+    bool ranges = false;       // input ranges set
 };
 
 static OctNet *onet_of(sn_handle h) { return reinterpret_cast<OctNet *>(h->octnet); }
@@ -492,8 +491,6 @@ static sn_status set_ranges(sn_handle h, const double *lo, const double *hi, cud
     SN_CK(h, cudaMemcpyAsync(n->shift, sh.data(), sizeof(float) * sh.size(), cudaMemcpyHostToDevice, st));
     SN_CK(h, cudaMemcpyAsync(n->inv_r, ir.data(), sizeof(float) * ir.size(), cudaMemcpyHostToDevice, st));
     SN_CK(h, cudaStreamSynchronize(st));
-    n->lo.assign(lo, lo + 8 * kOnIn);
-    n->hi.assign(hi, hi + 8 * kOnIn);
     n->ranges = true;
     return SN_OK;
 }
@@ -579,7 +576,6 @@ sn_status sn_octnet_init(sn_handle h, const double *lo, const double *hi, uint64
     if (s == SN_OK) s = refold(h, st);
     if (s != SN_OK) return s;
     SN_CK(h, cudaStreamSynchronize(st));
-    onet_of(h)->params = true;
     h->has_octnet = true;
     return SN_OK;
 }
@@ -612,7 +608,6 @@ sn_status sn_octnet_set(sn_handle h, const float *params, const float *mask, con
     if (s == SN_OK) s = refold(h, st);
     if (s != SN_OK) return s;
     SN_CK(h, cudaStreamSynchronize(st));
-    onet_of(h)->params = true;
     h->has_octnet = true;
     return SN_OK;
 }

@@ -628,8 +628,13 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sw
     ge_tiles_body<T, REFINE, 0, false, true>(a);
 }
 
+// CTAs per SM of the general-cell sweep: at 4 (128 registers, with spills) it measured
+// as fast as at 3 (168) and faster than at 2 (254, no spills)
+#ifndef SN_GEOM_MINBLOCKS
+#define SN_GEOM_MINBLOCKS 4
+#endif
 template <typename T, bool REFINE>
-__global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sweep_ge_hex(SweepArgs<T> a)
+__global__ void __launch_bounds__(SN_GE_BLOCK, (sizeof(T) == 4 ? SN_GEOM_MINBLOCKS : 1)) sweep_ge_hex(SweepArgs<T> a)
 {
     ge_tiles_body<T, REFINE, 0, false, false, true>(a);
 }
@@ -721,7 +726,8 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     if (smem > 48 * 1024)
         SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // persistent CTAs per octant: the register-limited residency (4 a SM in FP32, 1 in FP64)
-    const int cap = std::max(1, num_sms() * (sizeof(T) == 4 ? SN_GE_TILE_MINBLOCKS : 1) / 8);
+    const int per_sm = sizeof(T) != 4 ? 1 : (h->geom ? SN_GEOM_MINBLOCKS : SN_GE_TILE_MINBLOCKS);
+    const int cap = std::max(1, num_sms() * per_sm / 8);
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
     for (int s = 0; s < h->nplanes; ++s) {
         const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
