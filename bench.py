@@ -226,6 +226,7 @@ def ann_form(P, steps):
         return res
 
     out = {"train_mae": tr, "test_mae": te, "train_s": train_s, "train_samples": 1 << 20,
+           "train_samples_per_s": 20000 * 8192 / train_s,
            "ge_sweep_solves_per_s": sweep_rate(sn.GE32R)[0], "random_trained_ungated": run(sn.ANN, None)}
     # fine-tune on one-cell problems harvested from an elimination sweep of another
     # instance of the same family (blocked opacity field with a different seed)
@@ -300,6 +301,7 @@ def octnet_train(m_train=90000, m_test=10000, epochs=50000, lr=2e-4, retrain=500
         T.octnet_fit(ftr, ttr, epochs, lr)
         rep["train_s"] = time.perf_counter() - t0
         rep["epoch_ms"] = rep["train_s"] * 1e3 / epochs
+        rep["train_samples_per_s"] = 8 * m_train * epochs / rep["train_s"]
         mae, mse = T.octnet_eval(ftr, ttr)
         tmae, tmse = T.octnet_eval(fte, tte)
         rep.update({"train_mae": mae.tolist(), "train_mse": mse.tolist(), "test_mae": tmae.tolist(),
