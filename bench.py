@@ -416,10 +416,10 @@ def aniso_form(steps, ge_step_ms):
 
 
 # counted FP32 flops of one solve on a general hexahedral cell: the assembly of A from
-# the cell's matrices (4 x 64 multiply-adds plus 3 outflow face blocks of 16 x 3), the
-# right-hand side (64 + 3 x 64), elimination 372, back substitution 64, the refinement
-# residual without forming A (64 x 4 + 64 + 3 x 64) and replay 128, flux 16
-GEOM_FLOPS_PER_SOLVE = 2 * (256 + 144 + 64 + 192 + 256 + 64 + 192) + 372 + 64 + 128 + 16
+# the octant's folded streaming matrices and the mass matrix (4 x 64 multiply-adds), the
+# right-hand side (64 + 3 inflow faces x 64), elimination 372, back substitution 64, the
+# refinement residual without forming A (4 x 64 + 64) and replay 128, flux 16
+GEOM_FLOPS_PER_SOLVE = 2 * (256 + 64 + 192 + 256 + 64) + 372 + 64 + 128 + 16
 
 
 def geom_form(steps, ge_step_ms):

@@ -8,6 +8,7 @@
 // (x-face: b + 2c, y-face: a + 2c, z-face: a + 2b).  The system, in the physical
 // frame of the cell:
 //   A = sum_a Omega_a L_a + sigma_t M + sum over outflow faces of Omega . F
+//     = sum_c Omega_c B_c + sigma_t M  (B: per cell and octant, outflow faces folded in)
 //   b = M S + sum over inflow faces of (-Omega . F) up
 // where the inflow face of axis a is side 0 when Omega_a > 0 (structured wavefront).
 #pragma once
@@ -37,17 +38,6 @@ __device__ __forceinline__ void hex_face_block(const T *__restrict__ g, const T 
 }
 
 template <typename T, int A, int SIDE>
-__device__ __forceinline__ void hex_add_outflow(const T *__restrict__ g, const T (&om)[3], T (&M)[8][8])
-{
-    T B[4][4];
-    hex_face_block<T, A, SIDE>(g, om, B);
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) M[hex_face_node<A, SIDE>(t)][hex_face_node<A, SIDE>(u)] += B[t][u];
-}
-
-template <typename T, int A, int SIDE>
 __device__ __forceinline__ void hex_add_inflow(const T *__restrict__ g, const T (&om)[3], const T (&up)[4],
                                                T (&b)[8])
 {
@@ -59,21 +49,6 @@ __device__ __forceinline__ void hex_add_inflow(const T *__restrict__ g, const T 
 #pragma unroll
         for (int u = 0; u < 4; ++u) s = fma(B[t][u], up[u], s);
         b[hex_face_node<A, SIDE>(t)] -= s;
-    }
-}
-
-// y += (Omega . F of face (A, SIDE)) x on the face's nodes
-template <typename T, int A, int SIDE>
-__device__ __forceinline__ void hex_apply_face(const T *__restrict__ g, const T (&om)[3], const T (&x)[8], T (&y)[8])
-{
-    T B[4][4];
-    hex_face_block<T, A, SIDE>(g, om, B);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        T s = T(0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) s = fma(B[t][u], x[hex_face_node<A, SIDE>(u)], s);
-        y[hex_face_node<A, SIDE>(t)] += s;
     }
 }
 
@@ -91,14 +66,7 @@ __device__ __forceinline__ T hex_face_flux(const T *__restrict__ g, const T (&om
     return s;
 }
 
-// out[0] = sum over the outflow face of axis A (side out_side), dispatched to the
-// compile-time face so that register arrays are indexed by constants only
-template <typename T, int A>
-__device__ __forceinline__ void hex_outflow(const T *g, const T (&om)[3], int out_side, T (&M)[8][8])
-{
-    if (out_side) hex_add_outflow<T, A, 1>(g, om, M);
-    else hex_add_outflow<T, A, 0>(g, om, M);
-}
+// dispatch to the compile-time face (register arrays indexed by constants only)
 template <typename T, int A>
 __device__ __forceinline__ void hex_inflow(const T *g, const T (&om)[3], int in_side, const T (&up)[4], T (&b)[8])
 {
@@ -106,33 +74,29 @@ __device__ __forceinline__ void hex_inflow(const T *g, const T (&om)[3], int in_
     else hex_add_inflow<T, A, 0>(g, om, up, b);
 }
 template <typename T, int A>
-__device__ __forceinline__ void hex_apply_out(const T *g, const T (&om)[3], int out_side, const T (&x)[8], T (&y)[8])
-{
-    if (out_side) hex_apply_face<T, A, 1>(g, om, x, y);
-    else hex_apply_face<T, A, 0>(g, om, x, y);
-}
-template <typename T, int A>
 __device__ __forceinline__ T hex_out_flux(const T *g, const T (&om)[3], int out_side, const T (&x)[8])
 {
     return out_side ? hex_face_flux<T, A, 1>(g, om, x) : hex_face_flux<T, A, 0>(g, om, x);
 }
 
-// A (physical frame) of one cell and direction; out[a]: outflow side of axis a
+// Per (cell, octant) the streaming matrices with the octant's outflow faces folded in,
+// B_c = L_c + sum over the outflow faces of F_f^c, so that A = sum_c Omega_c B_c + sigma_t M
+// (the outflow side of every axis is fixed within an octant).
+constexpr int kHexB = 192;   // values a (cell, octant): B_0, B_1, B_2 [8][8]
+
+// A (physical frame) of one cell and direction from its octant's B and the cell's M
 template <typename T>
-__device__ __forceinline__ void hex_assemble_A(const T *__restrict__ g, const T (&om)[3], T sig, const int (&out)[3],
-                                               T (&A)[8][8])
+__device__ __forceinline__ void hex_assemble_A(const T *__restrict__ g, const T *__restrict__ B, const T (&om)[3],
+                                               T sig, T (&A)[8][8])
 {
 #pragma unroll
     for (int k = 0; k < 8; ++k)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int e = 8 * k + j;
-            A[k][j] = om[0] * __ldg(g + kHexL + e) + om[1] * __ldg(g + kHexL + 64 + e) +
-                      om[2] * __ldg(g + kHexL + 128 + e) + sig * __ldg(g + kHexM + e);
+            A[k][j] = om[0] * __ldg(B + e) + om[1] * __ldg(B + 64 + e) + om[2] * __ldg(B + 128 + e) +
+                      sig * __ldg(g + kHexM + e);
         }
-    hex_outflow<T, 0>(g, om, out[0], A);
-    hex_outflow<T, 1>(g, om, out[1], A);
-    hex_outflow<T, 2>(g, om, out[2], A);
 }
 
 template <typename T>
@@ -154,8 +118,8 @@ __device__ __forceinline__ void hex_build_b(const T *__restrict__ g, const T (&o
 
 // y = A x without forming A
 template <typename T>
-__device__ __forceinline__ void hex_apply_A(const T *__restrict__ g, const T (&om)[3], T sig, const int (&out)[3],
-                                            const T (&x)[8], T (&y)[8])
+__device__ __forceinline__ void hex_apply_A(const T *__restrict__ g, const T *__restrict__ B, const T (&om)[3],
+                                            T sig, const T (&x)[8], T (&y)[8])
 {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -163,15 +127,12 @@ __device__ __forceinline__ void hex_apply_A(const T *__restrict__ g, const T (&o
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int e = 8 * k + j;
-            const T a = om[0] * __ldg(g + kHexL + e) + om[1] * __ldg(g + kHexL + 64 + e) +
-                        om[2] * __ldg(g + kHexL + 128 + e) + sig * __ldg(g + kHexM + e);
+            const T a = om[0] * __ldg(B + e) + om[1] * __ldg(B + 64 + e) + om[2] * __ldg(B + 128 + e) +
+                        sig * __ldg(g + kHexM + e);
             s = fma(a, x[j], s);
         }
         y[k] = s;
     }
-    hex_apply_out<T, 0>(g, om, out[0], x, y);
-    hex_apply_out<T, 1>(g, om, out[1], x, y);
-    hex_apply_out<T, 2>(g, om, out[2], x, y);
 }
 
 }  // namespace sn

@@ -48,7 +48,7 @@ template <typename T>
 __global__ void __launch_bounds__(64) hex_elements_kernel(const double *__restrict__ xyz, int nx, int ny, int nz,
                                                           const double *__restrict__ omabs, int Do,
                                                           T *__restrict__ geom, T *__restrict__ vnode,
-                                                          int *__restrict__ flag)
+                                                          T *__restrict__ geomB, int *__restrict__ flag)
 {
     const int64_t C = (int64_t)nx * ny * nz;
     const double g[3] = {0.5 - 0.5 * sqrt(0.6), 0.5, 0.5 + 0.5 * sqrt(0.6)};
@@ -99,6 +99,11 @@ __global__ void __launch_bounds__(64) hex_elements_kernel(const double *__restri
         T *out = geom + c * kHexRec;
         for (int e = 0; e < 64; ++e) out[kHexM + e] = (T)M[e];
         for (int e = 0; e < 192; ++e) out[kHexL + e] = (T)L[e];
+        // B of every octant starts from L (the outflow faces are added below)
+        double Bo[8][kHexB];
+        for (int o = 0; o < 8; ++o)
+            for (int e = 0; e < kHexB; ++e) Bo[o][e] = L[e];
+        auto L2B = [&](int o, int cc, int k2, int j2) -> double & { return Bo[o][64 * cc + 8 * k2 + j2]; };
         for (int n = 0; n < 8; ++n) {
             double s = 0.0;
             for (int kk = 0; kk < 8; ++kk) s += M[8 * kk + n];
@@ -145,13 +150,24 @@ __global__ void __launch_bounds__(64) hex_elements_kernel(const double *__restri
                 }
             for (int cc = 0; cc < 3; ++cc)
                 for (int e = 0; e < 16; ++e) out[kHexF + f * 48 + cc * 16 + e] = (T)F[cc][e];
+            // this face is the outflow face of axis a in the octants whose bit a is
+            // 1 - side: add it into their B (from the FP64 values)
+            for (int o = 0; o < 8; ++o) {
+                if (((o >> a) & 1) != 1 - side) continue;
+                for (int cc = 0; cc < 3; ++cc)
+                    for (int t = 0; t < 4; ++t)
+                        for (int u = 0; u < 4; ++u) L2B(o, cc, fn[t], fn[u]) += F[cc][4 * t + u];
+            }
         }
+        for (int o = 0; o < 8; ++o)
+            for (int e = 0; e < kHexB; ++e) geomB[(c * 8 + o) * kHexB + e] = (T)Bo[o][e];
         if (bad) atomicOr(flag, bad);
     }
 }
 
 template <typename T>
-static sn_status build_geometry(sn_handle h, const double *xyz_host, void **geom, void **vnode, void **omabs)
+static sn_status build_geometry(sn_handle h, const double *xyz_host, void **geom, void **vnode, void **omabs,
+                                void **geomB)
 {
     const int64_t C = h->ncell, NV = (int64_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
     double *dxyz = nullptr, *dom = nullptr;
@@ -166,6 +182,7 @@ static sn_status build_geometry(sn_handle h, const double *xyz_host, void **geom
     if (e == cudaSuccess) e = cudaMalloc(geom, sizeof(T) * C * kHexRec);
     if (e == cudaSuccess) e = cudaMalloc(vnode, sizeof(T) * C * 8);
     if (e == cudaSuccess) e = cudaMalloc(omabs, sizeof(T) * omT.size());
+    if (e == cudaSuccess) e = cudaMalloc(geomB, sizeof(T) * C * 8 * kHexB);
     if (e == cudaSuccess) e = cudaMemcpy(dxyz, xyz_host, sizeof(double) * 3 * NV, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dom, om.data(), sizeof(double) * om.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(*omabs, omT.data(), sizeof(T) * omT.size(), cudaMemcpyHostToDevice);
@@ -175,7 +192,7 @@ static sn_status build_geometry(sn_handle h, const double *xyz_host, void **geom
         int64_t grid = (C + 63) / 64;
         if (grid > (int64_t)num_sms() * 32) grid = (int64_t)num_sms() * 32;
         hex_elements_kernel<T><<<(unsigned)grid, 64>>>(dxyz, h->nx, h->ny, h->nz, dom, h->Do, (T *)*geom, (T *)*vnode,
-                                                       dflag);
+                                                       (T *)*geomB, dflag);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpy(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost);
     }
@@ -202,10 +219,10 @@ sn_status sn_set_geometry(sn_handle h, const double *xyz)
     if (h->K > 1) return fail(h, SN_EINVAL, "sn_set_geometry: not with anisotropic scattering");
     SN_CK(h, cudaStreamSynchronize(h->stream));
     auto release = [h]() {
-        void *b[] = {h->geom, h->vnode, h->omabs};
+        void *b[] = {h->geom, h->vnode, h->omabs, h->geomB};
         for (void *p : b)
             if (p) cudaFree(p);
-        h->geom = h->vnode = h->omabs = nullptr;
+        h->geom = h->vnode = h->omabs = h->geomB = nullptr;
     };
     if (!xyz) {
         release();
@@ -215,19 +232,20 @@ sn_status sn_set_geometry(sn_handle h, const double *xyz)
     const int64_t NV = (int64_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
     for (int64_t i = 0; i < 3 * NV; ++i)
         if (!std::isfinite(xyz[i])) return fail(h, SN_EINVAL, "sn_set_geometry: non-finite vertex coordinate");
-    void *geom = nullptr, *vnode = nullptr, *omabs = nullptr;
-    sn_status s = h->fp64 ? build_geometry<double>(h, xyz, &geom, &vnode, &omabs)
-                          : build_geometry<float>(h, xyz, &geom, &vnode, &omabs);
+    void *geom = nullptr, *vnode = nullptr, *omabs = nullptr, *geomB = nullptr;
+    sn_status s = h->fp64 ? build_geometry<double>(h, xyz, &geom, &vnode, &omabs, &geomB)
+                          : build_geometry<float>(h, xyz, &geom, &vnode, &omabs, &geomB);
     if (s != SN_OK) {
-        if (geom) cudaFree(geom);
-        if (vnode) cudaFree(vnode);
-        if (omabs) cudaFree(omabs);
+        void *b[] = {geom, vnode, omabs, geomB};
+        for (void *p : b)
+            if (p) cudaFree(p);
         return s;
     }
     release();
     h->geom = geom;
     h->vnode = vnode;
     h->omabs = omabs;
+    h->geomB = geomB;
     // boundary inflow of one sweep: the inflow planes' outward area vectors (sum of
     // the boundary faces' bilinear patches, half the cross product of the diagonals)
     const int nx = h->nx, ny = h->ny, nz = h->nz;

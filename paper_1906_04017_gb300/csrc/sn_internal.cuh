@@ -125,6 +125,7 @@ struct sn_handle_s {
     void *geom = nullptr;
     void *vnode = nullptr;
     void *omabs = nullptr;
+    void *geomB = nullptr;   // [C][8][192] streaming + outflow-face matrices per octant
 
     // anisotropic scattering (sn_set_scattering_order): Legendre order L, K = (L+1)^2
     // flux moments; sigma_s,n for n = 1..L [L][G][C] and the harmonics [8][Do][K]

@@ -168,7 +168,7 @@ static void release(sn_handle h)
         if (h->graphs.exec[i]) cudaGraphExecDestroy(h->graphs.exec[i]);
     free_adjoint(h);
     void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->dir_abs, h->plane_cells, h->plane_pos,
-                    h->face, h->phi_oct, h->S, h->phi_b, h->acc, h->sigs_n, h->yhat, h->geom, h->vnode, h->omabs};
+                    h->face, h->phi_oct, h->S, h->phi_b, h->acc, h->sigs_n, h->yhat, h->geom, h->vnode, h->omabs, h->geomB};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->acc_host) cudaFreeHost(h->acc_host);

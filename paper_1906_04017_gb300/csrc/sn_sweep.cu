@@ -66,6 +66,7 @@ struct SweepArgs {
     const T *yhat;           // [8][Do][K] sqrt(4 pi) Y_k of every direction (octant-major)
     const T *geom;           // general hexahedral cells: element records [C][544] (hex.cuh)
     const T *omabs;          // |Omega| of the octant's directions [Do][3]
+    const T *geomB;          // [C][8][192] per-octant streaming + outflow-face matrices
 };
 
 // grid = (blocks per octant, 8 octants); block = keys_per_cta keys x Do directions,
@@ -570,7 +571,8 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
                 mirror4(upy, fx | (fz << 1));
                 mirror4(upz, fx | (fy << 1));
                 T A[8][8], b[8], b0[8], rinv[8], xp[8];
-                hex_assemble_A(gc, om, sig[0], out, A);
+                const T *gB = a.geomB + ((int64_t)kr[0].cell * 8 + o) * kHexB;
+                hex_assemble_A(gc, gB, om, sig[0], A);
                 hex_build_b(gc, om, out, Sp, upx, upy, upz, b);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) b0[q] = b[q];
@@ -578,7 +580,7 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
                 ge8_factor_solve(A, b, piv, rinv, xp);
                 if (REFINE) {
                     T y[8], r[8], dx[8];
-                    hex_apply_A(gc, om, sig[0], out, xp, y);
+                    hex_apply_A(gc, gB, om, sig[0], xp, y);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) r[q] = b0[q] - y[q];
                     ge8_replay(A, piv, rinv, r, dx);
@@ -711,6 +713,7 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     a.yhat = (const T *)h->yhat;
     a.geom = (const T *)h->geom;
     a.omabs = (const T *)h->omabs;
+    a.geomB = (const T *)h->geomB;
     const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false, h->K, h->Do).total;
     void (*kern)(SweepArgs<T>) = nullptr;
     if (h->geom)
