@@ -370,11 +370,18 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
         if (!(r.flags & 0x80u)) return;
         const int64_t gc = (int64_t)r.g * a.C + r.cell;
         const uint32_t k = (uint32_t)(sbuf * kpt + t);
-        // node by node into the canonical order of the octant (canonical n = physical n ^ o);
-        // source moments in the [G][K][C][8] layout
-        for (int m = 0; m < KM; ++m) {
-            const uint32_t dst = sb + L.ks + (k * KM + m) * 8 * (uint32_t)sizeof(T);
-            const T *src = a.S + (((int64_t)r.g * KM + m) * a.C + r.cell) * 8;
+        if (MOM) {
+            // source moments ([G][K][C][8] layout) as whole 16-byte pieces, in physical
+            // node order (the row reads node n of the canonical frame at n ^ o)
+            for (int m = 0; m < KM; ++m) {
+                const uint32_t dst = sb + L.ks + (k * KM + m) * 8 * (uint32_t)sizeof(T);
+                const T *src = a.S + (((int64_t)r.g * KM + m) * a.C + r.cell) * 8;
+                cp_async_bytes(dst, src, 8 * (int)sizeof(T));
+            }
+        } else {
+            // node by node into the canonical order of the octant (canonical n = physical n ^ o)
+            const uint32_t dst = sb + L.ks + k * 8 * (uint32_t)sizeof(T);
+            const T *src = a.S + gc * 8;
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
                 if (sizeof(T) == 4) cp_async4(dst + 4 * (p ^ o), src + p);
@@ -537,7 +544,7 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
                     if (m < KM) {
                         const T ym = y[m];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) S[j][q] = fma(ym, fks[m * 8 + q], S[j][q]);
+                        for (int q = 0; q < 8; ++q) S[j][q] = fma(ym, fks[m * 8 + (q ^ o)], S[j][q]);
                     }
                 }
             } else {
