@@ -84,23 +84,23 @@ __device__ __forceinline__ T hex_out_flux(const T *g, const T (&om)[3], int out_
 // (the outflow side of every axis is fixed within an octant).
 constexpr int kHexB = 192;   // values a (cell, octant): B_0, B_1, B_2 [8][8]
 
-// A (physical frame) of one cell and direction from its octant's B and the cell's M
+// A (physical frame) of one cell and direction from its octant's B and the cell's mass
+// matrix M (both [8][8] row-major, in shared memory)
 template <typename T>
-__device__ __forceinline__ void hex_assemble_A(const T *__restrict__ g, const T *__restrict__ B, const T (&om)[3],
-                                               T sig, T (&A)[8][8])
+__device__ __forceinline__ void hex_assemble_A(const T *M, const T *B, const T (&om)[3], T sig, T (&A)[8][8])
 {
 #pragma unroll
     for (int k = 0; k < 8; ++k)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int e = 8 * k + j;
-            A[k][j] = om[0] * __ldg(B + e) + om[1] * __ldg(B + 64 + e) + om[2] * __ldg(B + 128 + e) +
-                      sig * __ldg(g + kHexM + e);
+            A[k][j] = om[0] * B[e] + om[1] * B[64 + e] + om[2] * B[128 + e] + sig * M[e];
         }
 }
 
+// b (physical frame): M S plus the inflow faces' terms (face blocks from the cell record g)
 template <typename T>
-__device__ __forceinline__ void hex_build_b(const T *__restrict__ g, const T (&om)[3], const int (&out)[3],
+__device__ __forceinline__ void hex_build_b(const T *__restrict__ g, const T *M, const T (&om)[3], const int (&out)[3],
                                             const T (&S)[8], const T (&ux)[4], const T (&uy)[4], const T (&uz)[4],
                                             T (&b)[8])
 {
@@ -108,7 +108,7 @@ __device__ __forceinline__ void hex_build_b(const T *__restrict__ g, const T (&o
     for (int k = 0; k < 8; ++k) {
         T s = T(0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) s = fma(__ldg(g + kHexM + 8 * k + j), S[j], s);
+        for (int j = 0; j < 8; ++j) s = fma(M[8 * k + j], S[j], s);
         b[k] = s;
     }
     hex_inflow<T, 0>(g, om, 1 - out[0], ux, b);
@@ -116,10 +116,10 @@ __device__ __forceinline__ void hex_build_b(const T *__restrict__ g, const T (&o
     hex_inflow<T, 2>(g, om, 1 - out[2], uz, b);
 }
 
-// y = A x without forming A
+// y = A x without forming A (M, B as for hex_assemble_A)
 template <typename T>
-__device__ __forceinline__ void hex_apply_A(const T *__restrict__ g, const T *__restrict__ B, const T (&om)[3],
-                                            T sig, const T (&x)[8], T (&y)[8])
+__device__ __forceinline__ void hex_apply_A(const T *M, const T *B, const T (&om)[3], T sig, const T (&x)[8],
+                                            T (&y)[8])
 {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -127,8 +127,7 @@ __device__ __forceinline__ void hex_apply_A(const T *__restrict__ g, const T *__
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int e = 8 * k + j;
-            const T a = om[0] * __ldg(B + e) + om[1] * __ldg(B + 64 + e) + om[2] * __ldg(B + 128 + e) +
-                        sig * __ldg(g + kHexM + e);
+            const T a = om[0] * B[e] + om[1] * B[64 + e] + om[2] * B[128 + e] + sig * M[e];
             s = fma(a, x[j], s);
         }
         y[k] = s;

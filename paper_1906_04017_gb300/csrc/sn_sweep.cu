@@ -249,13 +249,17 @@ constexpr int kTileRecs = 8;   // key-record ring (>= prefetch distance + 3 live
 constexpr int kMaxMoments = (SN_MAX_SCATTERING_ORDER + 1) * (SN_MAX_SCATTERING_ORDER + 1);
 template <typename T>
 struct GeTileSmem {
-    uint32_t face, ks, sig, rec, red, net, yt, total;
+    uint32_t face, ks, sig, rec, red, net, yt, geo, total;
 };
 // Every stage written while an earlier tile may still be read has its own buffer
 // (PRE + 1 copy stages for a prefetch distance of PRE tiles), so one barrier a tile
 // suffices.  Network sweeps keep the octant's folded network after the stages.
+// general cells: a key's staged mass matrix and folded streaming matrices (256 values,
+// padded so that the keys of a warp fall in different banks)
+constexpr int kGeoKey = 260;
 template <typename T>
-__host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows, int pre, bool net, int K = 1, int Do = 0)
+__host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows, int pre, bool net, int K = 1, int Do = 0,
+                                                      bool geo = false)
 {
     const uint32_t stages = (uint32_t)pre + 1;
     GeTileSmem<T> m;
@@ -266,7 +270,8 @@ __host__ __device__ inline GeTileSmem<T> ge_tile_smem(int kpt, int rows, int pre
     m.red = m.rec + kTileRecs * 32 * kpt;                              // 2 x [rows][8] w_d psi (canonical)
     m.net = m.red + 2 * rows * 8 * (uint32_t)sizeof(T);                // [288] folded network
     m.yt = m.net + (net ? (uint32_t)(sizeof(float) * kOnFold) : 0u);  // [Do][K] harmonics (K > 1)
-    m.total = m.yt + (K > 1 ? (uint32_t)(Do * K * sizeof(T)) : 0u);
+    m.geo = (m.yt + (K > 1 ? (uint32_t)(Do * K * sizeof(T)) : 0u) + 15) & ~15u;   // 2 x [kpt][260] M, B
+    m.total = m.geo + (geo ? 2u * kpt * kGeoKey * (uint32_t)sizeof(T) : 0u);
     return m;
 }
 
@@ -311,7 +316,7 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
     const int Do = DO ? DO : a.Do;
     const int KM = MOM ? a.K : 1;
     const int nthr = blockDim.x, kpt = a.keys_per_cta, rows = nthr * RPT;
-    const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows, PRE, NET, KM, Do);
+    const GeTileSmem<T> L = ge_tile_smem<T>(kpt, rows, PRE, NET, KM, Do, GEOM);
     const uint32_t sb = smem_u32(gsm);
     const int t = threadIdx.x, o = blockIdx.y;
     int lk[RPT], dr[RPT];
@@ -405,6 +410,22 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
             if (!(r.flags & 4u)) cp_async_bytes(dst + 2 * vb, a.fz + r.bz + dr[j], vb);
         }
     };
+    // GEOM: every key's mass matrix and its octant's folded streaming matrices (records
+    // in `slot`) into geometry stage `gb`, 16-byte pieces spread over the whole CTA
+    auto geo_copy = [&](int slot, int gb) {
+        if (!GEOM) return;
+        constexpr int per = 16 / (int)sizeof(T);   // values a 16-byte piece
+        const int npiece = 256 / per;
+        for (int c = t; c < kpt * npiece; c += nthr) {
+            const int kk = c / npiece, pc = c - kk * npiece;
+            const KeyRec r = get_key(rec_at(slot, kk));
+            if (!(r.flags & 0x80u)) continue;
+            const int v = pc * per;   // value index within [M (64) | B (192)]
+            const T *src = v < 64 ? a.geom + (int64_t)r.cell * kHexRec + kHexM + v
+                                  : a.geomB + ((int64_t)r.cell * 8 + o) * kHexB + (v - 64);
+            cp_async16(sb + L.geo + (uint32_t)(((gb * kpt + kk) * kGeoKey + v) * (int)sizeof(T)), src);
+        }
+    };
     // flux partial of the tile whose records are in `slot` and w_d psi in red buffer `rb`
     auto reduce_tile = [&](int slot, int rb) {
         const T *red = red_at(rb);
@@ -494,6 +515,7 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
     for (int j = 0; j < PRE; ++j) {
         if (t < kpt) key_copy(j, j);
         face_copy(j, j);
+        geo_copy(j, j);
         cp_async_commit();
     }
     int i = 0;
@@ -508,6 +530,7 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
         if (i > 0) reduce_tile((i - 1) % kTileRecs, (i - 1) & 1);
         const int pre = (i + PRE) % STAGES;
         face_copy((i + PRE) % kTileRecs, pre);
+        geo_copy((i + PRE) % kTileRecs, pre);
         if (t < kpt) {
             key_rec(tile_of(i + PRE + 1), pk_next, (i + PRE + 1) % kTileRecs);
             key_copy((i + PRE) % kTileRecs, pre);
@@ -578,16 +601,18 @@ __device__ __forceinline__ void ge_tiles_body(const SweepArgs<T> &a)
                 mirror4(upy, fx | (fz << 1));
                 mirror4(upz, fx | (fy << 1));
                 T A[8][8], b[8], b0[8], rinv[8], xp[8];
-                const T *gB = a.geomB + ((int64_t)kr[0].cell * 8 + o) * kHexB;
-                hex_assemble_A(gc, gB, om, sig[0], A);
-                hex_build_b(gc, om, out, Sp, upx, upy, upz, b);
+                // the key's staged mass matrix and folded streaming matrices
+                const T *Mk = reinterpret_cast<const T *>(gsm + L.geo) + (cur * kpt + lk[0]) * kGeoKey;
+                const T *Bk = Mk + 64;
+                hex_assemble_A(Mk, Bk, om, sig[0], A);
+                hex_build_b(gc, Mk, om, out, Sp, upx, upy, upz, b);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) b0[q] = b[q];
                 unsigned piv;
                 ge8_factor_solve(A, b, piv, rinv, xp);
                 if (REFINE) {
                     T y[8], r[8], dx[8];
-                    hex_apply_A(gc, gB, om, sig[0], xp, y);
+                    hex_apply_A(Mk, Bk, om, sig[0], xp, y);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) r[q] = b0[q] - y[q];
                     ge8_replay(A, piv, rinv, r, dx);
@@ -721,7 +746,9 @@ static sn_status launch_sweep_t(sn_handle h, const T *S, T *phi_oct, bool refine
     a.geom = (const T *)h->geom;
     a.omabs = (const T *)h->omabs;
     a.geomB = (const T *)h->geomB;
-    const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false, h->K, h->Do).total;
+    // general cells stage 1 KB (FP32) of matrices a key: at most 24 keys a tile
+    if (h->geom) a.keys_per_cta = std::min(a.keys_per_cta, 24);
+    const uint32_t smem = ge_tile_smem<T>(a.keys_per_cta, rows, 1, false, h->K, h->Do, h->geom != nullptr).total;
     void (*kern)(SweepArgs<T>) = nullptr;
     if (h->geom)
         kern = refine ? sweep_ge_hex<T, true> : sweep_ge_hex<T, false>;
