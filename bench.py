@@ -505,6 +505,10 @@ def run_gpu(args):
     ws, rank = dist_env()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if ws > 1:
+        # the other forms and the CPU baseline are single-GPU reports: replicas would only
+        # hold the GPUs longer
+        args.no_ann = args.no_octnet = args.no_aniso = args.no_geom = args.no_cpu_baseline = True
     dist = None
     if ws > 1:
         import torch.distributed as dist
