@@ -22,7 +22,10 @@
  *    buffer it allocates and frees it in sn_destroy.
  *  - Work is queued on the handle's CUDA stream (sn_setup / sn_set_stream; the
  *    library never synchronises the whole device).  Calls that return host
- *    scalars synchronise that stream before returning.
+ *    scalars synchronise that stream before returning, and so do the set-up
+ *    calls that copy host arrays (sn_setup, sn_set_geometry,
+ *    sn_set_scattering_order, the weight setters): they return with their
+ *    copies complete.
  *  - Inputs are validated on the host; a rejected call returns SN_EINVAL and
  *    queues nothing.  sn_last_error() gives the message.  There is no CPU
  *    fallback: without a usable CUDA device calls return SN_ECUDA.
@@ -111,7 +114,9 @@ typedef struct {
 sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *quad,
                    const sn_xs *xs, const sn_options *opts, void *stream);
 
-/* Replace the stream later calls are queued on. */
+/* Replace the stream later calls are queued on.  When the stream changes, the
+ * work already queued on the old one is waited for first (a host wait on that
+ * stream), so later calls see its results. */
 sn_status sn_set_stream(sn_handle h, void *stream);
 
 sn_status sn_get_info(sn_handle h, sn_info *info);

@@ -59,7 +59,7 @@ static sn_status ensure_adjoint(sn_handle h)
     SN_CK(h, cudaMalloc(&a->Sfwd, sizeof(float) * GC8));
     SN_CK(h, cudaMalloc(&a->lam_b, sizeof(float) * GC8));
     SN_CK(h, cudaMalloc(&a->zero_inc, sizeof(float) * 6 * h->G));
-    SN_CK(h, cudaMemset(a->zero_inc, 0, sizeof(float) * 6 * h->G));
+    SN_CK(h, cudaMemsetAsync(a->zero_inc, 0, sizeof(float) * 6 * h->G, h->stream));
     SN_CK(h, cudaMalloc(&a->acc2, sizeof(double) * ACC_COUNT));
     a->face_bytes = sizeof(float4) * (size_t)(h->face_x + h->face_y + h->face_z);
     SN_CK(h, cudaMalloc(&a->face2, a->face_bytes));

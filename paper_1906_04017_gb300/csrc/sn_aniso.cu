@@ -143,7 +143,8 @@ static sn_status upload_as(sn_handle h, void **dst, const std::vector<double> &v
 {
     std::vector<T> t(v.begin(), v.end());
     SN_CK(h, cudaMalloc(dst, sizeof(T) * (t.empty() ? 1 : t.size())));
-    if (!t.empty()) SN_CK(h, cudaMemcpy(*dst, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice));
+    if (!t.empty())
+        SN_CK(h, cudaMemcpyAsync(*dst, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice, h->stream));
     return SN_OK;
 }
 
@@ -187,6 +188,7 @@ sn_status sn_set_scattering_order(sn_handle h, int32_t L, const double *sigs_n)
     if (s == SN_OK) e = cudaMalloc(&new_oct, esz * 8 * (size_t)GC * K * 8);
     if (s == SN_OK && e == cudaSuccess) e = cudaMalloc(&new_S, esz * (size_t)GC * K * 8);
     if (s == SN_OK && e == cudaSuccess) e = cudaMalloc(&new_b, esz * (size_t)GC * K * 8);
+    if (s == SN_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // the uploads have landed
     if (s != SN_OK || e != cudaSuccess) {
         cleanup();
         return s != SN_OK ? s : cuda_fail(h, e, "sn_set_scattering_order: cudaMalloc");

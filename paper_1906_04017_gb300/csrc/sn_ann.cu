@@ -193,9 +193,9 @@ static sn_status ensure_net(sn_handle h)
     SN_CK(h, cudaMalloc(&n->b2, sizeof(float) * kN2));
     SN_CK(h, cudaMalloc(&n->counter, sizeof(unsigned long long) * 2));
     SN_CK(h, cudaMalloc(&n->dacc, sizeof(double) * 4));
-    SN_CK(h, cudaMemset(n->m, 0, sizeof(float) * kNparam));
-    SN_CK(h, cudaMemset(n->v, 0, sizeof(float) * kNparam));
-    SN_CK(h, cudaMemset(n->counter, 0, sizeof(unsigned long long) * 2));
+    SN_CK(h, cudaMemsetAsync(n->m, 0, sizeof(float) * kNparam, h->stream));
+    SN_CK(h, cudaMemsetAsync(n->v, 0, sizeof(float) * kNparam, h->stream));
+    SN_CK(h, cudaMemsetAsync(n->counter, 0, sizeof(unsigned long long) * 2, h->stream));
     // fallback queue of the gated sweep: every row of the largest hyperplane's tiles
     int64_t max_cells = 0;
     for (int p = 0; p < h->nplanes; ++p) max_cells = std::max(max_cells, h->plane_off[p + 1] - h->plane_off[p]);
@@ -1110,7 +1110,8 @@ sn_status check_ann_timeouts(sn_handle h)
 {
     if (!h->net) return SN_OK;
     unsigned long long c[2] = {0, 0};
-    SN_CK(h, cudaMemcpy(c, net_of(h)->counter, sizeof(c), cudaMemcpyDeviceToHost));
+    SN_CK(h, cudaMemcpyAsync(c, net_of(h)->counter, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    SN_CK(h, cudaStreamSynchronize(h->stream));
     if (c[1]) return fail(h, SN_ETIMEOUT, "surrogate sweep: a tensor-core completion wait timed out");
     return SN_OK;
 }
@@ -1327,9 +1328,10 @@ static sn_status upload_params(sn_handle h, const float *host)
     sn_status s = ensure_net(h);
     if (s != SN_OK) return s;
     Net *n = net_of(h);
-    SN_CK(h, cudaMemcpy(n->p, host, sizeof(float) * kNparam, cudaMemcpyHostToDevice));
-    SN_CK(h, cudaMemset(n->m, 0, sizeof(float) * kNparam));
-    SN_CK(h, cudaMemset(n->v, 0, sizeof(float) * kNparam));
+    SN_CK(h, cudaMemcpyAsync(n->p, host, sizeof(float) * kNparam, cudaMemcpyHostToDevice, h->stream));
+    SN_CK(h, cudaMemsetAsync(n->m, 0, sizeof(float) * kNparam, h->stream));
+    SN_CK(h, cudaMemsetAsync(n->v, 0, sizeof(float) * kNparam, h->stream));
+    SN_CK(h, cudaStreamSynchronize(h->stream));
     n->t = 0;
     n->dirty = true;
     h->has_net = true;
@@ -1456,7 +1458,8 @@ sn_status sn_surrogate_get_weights(sn_handle h, float *params)
     sn_status s = need_net(h, "sn_surrogate_get_weights");
     if (s != SN_OK) return s;
     if (!params) return fail(h, SN_EINVAL, "sn_surrogate_get_weights: NULL argument");
-    SN_CK(h, cudaMemcpy(params, net_of(h)->p, sizeof(float) * kNparam, cudaMemcpyDeviceToHost));
+    SN_CK(h, cudaMemcpyAsync(params, net_of(h)->p, sizeof(float) * kNparam, cudaMemcpyDeviceToHost, h->stream));
+    SN_CK(h, cudaStreamSynchronize(h->stream));
     return SN_OK;
 }
 

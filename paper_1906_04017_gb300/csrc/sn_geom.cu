@@ -183,18 +183,24 @@ static sn_status build_geometry(sn_handle h, const double *xyz_host, void **geom
     if (e == cudaSuccess) e = cudaMalloc(vnode, sizeof(T) * C * 8);
     if (e == cudaSuccess) e = cudaMalloc(omabs, sizeof(T) * omT.size());
     if (e == cudaSuccess) e = cudaMalloc(geomB, sizeof(T) * C * 8 * kHexB);
-    if (e == cudaSuccess) e = cudaMemcpy(dxyz, xyz_host, sizeof(double) * 3 * NV, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(dom, om.data(), sizeof(double) * om.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(*omabs, omT.data(), sizeof(T) * omT.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(dflag, 0, sizeof(int));
+    cudaStream_t st = h->stream;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dxyz, xyz_host, sizeof(double) * 3 * NV, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dom, om.data(), sizeof(double) * om.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*omabs, omT.data(), sizeof(T) * omT.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(int), st);
     int flag = 0;
     if (e == cudaSuccess) {
         int64_t grid = (C + 63) / 64;
         if (grid > (int64_t)num_sms() * 32) grid = (int64_t)num_sms() * 32;
-        hex_elements_kernel<T><<<(unsigned)grid, 64>>>(dxyz, h->nx, h->ny, h->nz, dom, h->Do, (T *)*geom, (T *)*vnode,
-                                                       (T *)*geomB, dflag);
+        hex_elements_kernel<T><<<(unsigned)grid, 64, 0, st>>>(dxyz, h->nx, h->ny, h->nz, dom, h->Do, (T *)*geom,
+                                                              (T *)*vnode, (T *)*geomB, dflag);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpy(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    }
+    // the element kernel and the flag are complete before the scratch buffers go
+    {
+        const cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
     }
     cudaFree(dxyz);
     cudaFree(dom);
@@ -272,10 +278,12 @@ sn_status sn_set_geometry(sn_handle h, const double *xyz)
     }
     std::vector<double> inc(6 * (size_t)h->G);
     if (h->fp64) {
-        SN_CK(h, cudaMemcpy(inc.data(), h->psi_inc, sizeof(double) * inc.size(), cudaMemcpyDeviceToHost));
+        SN_CK(h, cudaMemcpyAsync(inc.data(), h->psi_inc, sizeof(double) * inc.size(), cudaMemcpyDeviceToHost, h->stream));
+        SN_CK(h, cudaStreamSynchronize(h->stream));
     } else {
         std::vector<float> f32(inc.size());
-        SN_CK(h, cudaMemcpy(f32.data(), h->psi_inc, sizeof(float) * f32.size(), cudaMemcpyDeviceToHost));
+        SN_CK(h, cudaMemcpyAsync(f32.data(), h->psi_inc, sizeof(float) * f32.size(), cudaMemcpyDeviceToHost, h->stream));
+        SN_CK(h, cudaStreamSynchronize(h->stream));
         for (size_t i = 0; i < f32.size(); ++i) inc[i] = f32[i];
     }
     double tot = 0.0;

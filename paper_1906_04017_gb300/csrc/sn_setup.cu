@@ -136,12 +136,12 @@ static sn_status dalloc(sn_handle h, void **p, size_t n) { return dalloc_bytes(h
 static sn_status upload(sn_handle h, void *dst, const double *src, size_t n)
 {
     if (h->fp64) {
-        SN_CK(h, cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyHostToDevice));
+        SN_CK(h, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         return SN_OK;
     }
     std::vector<float> tmp(n);
     for (size_t i = 0; i < n; ++i) tmp[i] = (float)src[i];
-    SN_CK(h, cudaMemcpy(dst, tmp.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    SN_CK(h, cudaMemcpyAsync(dst, tmp.data(), n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     return SN_OK;
 }
 
@@ -157,7 +157,7 @@ static sn_status upload_dirs(sn_handle h)
     }
     sn_status s = dalloc_bytes(h, &h->dir, sizeof(DirData<T>) * h->Do);
     if (s != SN_OK) return s;
-    SN_CK(h, cudaMemcpy(h->dir, dd.data(), sizeof(DirData<T>) * h->Do, cudaMemcpyHostToDevice));
+    SN_CK(h, cudaMemcpyAsync(h->dir, dd.data(), sizeof(DirData<T>) * h->Do, cudaMemcpyHostToDevice, h->stream));
     return SN_OK;
 }
 
@@ -347,8 +347,8 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
             da[d] = make_float4((float)std::fabs(h->omega[3 * d]), (float)std::fabs(h->omega[3 * d + 1]),
                                 (float)std::fabs(h->omega[3 * d + 2]), 0.f);
         SN_TRY(dalloc_bytes(h, (void **)&h->dir_abs, sizeof(float4) * h->Do));
-        cudaError_t e = cudaMemcpy(h->dir_abs, da.data(), sizeof(float4) * h->Do, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(dir_abs)"));
+        cudaError_t e = cudaMemcpyAsync(h->dir_abs, da.data(), sizeof(float4) * h->Do, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpyAsync(dir_abs)"));
     }
 
     // boundary inflow of one sweep: sum over faces, groups and inflowing directions
@@ -385,8 +385,9 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
                 for (int i = 0; i < h->nx; ++i)
                     cells[fill[i + j + k]++] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
         SN_TRY(dalloc_bytes(h, (void **)&h->plane_cells, sizeof(uint32_t) * (size_t)C));
-        cudaError_t e = cudaMemcpy(h->plane_cells, cells.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(plane_cells)"));
+        cudaError_t e = cudaMemcpyAsync(h->plane_cells, cells.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpyAsync(plane_cells)"));
         std::vector<uint32_t> pos(C);
         for (int s2 = 0; s2 < h->nplanes; ++s2)
             for (int64_t q = count[s2]; q < count[s2 + 1]; ++q) {
@@ -395,8 +396,8 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
                 pos[lin] = (uint32_t)(q - count[s2]);
             }
         SN_TRY(dalloc_bytes(h, (void **)&h->plane_pos, sizeof(uint32_t) * (size_t)C));
-        e = cudaMemcpy(h->plane_pos, pos.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpy(plane_pos)"));
+        e = cudaMemcpyAsync(h->plane_pos, pos.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpyAsync(plane_pos)"));
     }
 
     // face planes: per octant, per (j',k') / (i',k') / (i',j'), per (group, direction):
@@ -417,6 +418,12 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaStreamCreate"));
     }
     SN_TRY(reduce_configure(h));
+    {
+        // the uploads above are queued on the handle's stream (from pageable host
+        // memory: staged before each call returns); the handle is complete once they land
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "sn_setup: cudaStreamSynchronize"));
+    }
 #undef SN_TRY
     *out = h;
     return SN_OK;
@@ -425,6 +432,8 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
 sn_status sn_set_stream(sn_handle h, void *stream)
 {
     if (!h) return fail(nullptr, SN_EINVAL, "sn_set_stream: NULL handle");
+    // work queued on the old stream is ordered before anything on the new one
+    if (h->stream != (cudaStream_t)stream) SN_CK(h, cudaStreamSynchronize(h->stream));
     h->stream = (cudaStream_t)stream;
     return SN_OK;
 }
