@@ -1,0 +1,62 @@
+"""Pin of the oracle's DFEM discretisation against the transport equation itself:
+for a smooth, non-polynomial solution psi*(x) = exp(a . x) of Omega . grad psi +
+sigma_t psi = Q (Eq. (1) for one direction, no scattering), with Q = (Omega . a +
+sigma_t) psi* interpolated at the nodes and psi* as inflow (Eq. (10)), the sweep's
+nodal error falls at second order in the cell size (the Q1 elements of the
+discretisation of Sec. 2).  A mis-scaled face term, mass or streaming matrix would stop the
+convergence or its rate."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1906_04017_gb300 import workloads as W
+from test_oracle_solve import face_points
+
+A_VEC = np.array([0.9, -0.6, 0.7])
+SIGMA_T = 2.0
+
+
+def psi_star(x, y, z):
+    return float(np.exp(A_VEC @ np.array([x, y, z])))
+
+
+def smooth_error(n, d, order=4):
+    """Max nodal |psi - psi*| / max psi* of direction d on an n^3 mesh of the unit cube."""
+    wl = W.random_small(n, n, n, order=order, G=1, seed=3, lengths=(1.0, 1.0, 1.0))
+    wl["sigt"][:] = SIGMA_T
+    wl["sigs"][:] = 0.0
+    P = oracle.OracleProblem(wl)
+    h = (P.dx, P.dy, P.dz)
+    om = P.omega[d]
+    rate = float(om @ A_VEC) + SIGMA_T
+    i, j, k = W.cell_ijk(wl)
+    exact = np.zeros((P.ncell, 8))
+    for m in range(8):
+        x = np.stack([(i + (m & 1)) * h[0], (j + ((m >> 1) & 1)) * h[1], (k + (m >> 2)) * h[2]], axis=1)
+        exact[:, m] = np.exp(x @ A_VEC)
+    S = rate * exact
+    bnd = []
+    for ax in range(3):
+        side = 0 if om[ax] >= 0 else 1
+        t = [a for a in range(3) if a != ax]
+        arr = np.zeros((n * n, 4))
+        for q in range(n):
+            for p in range(n):
+                o = [0.0, 0.0, 0.0]
+                o[ax] = (n - 1) * h[ax] if side else 0.0
+                o[t[0]] = p * h[t[0]]
+                o[t[1]] = q * h[t[1]]
+                arr[p + n * q] = [psi_star(*pt) for pt in face_points(ax, side, h, o)]
+        bnd.append(arr)
+    psi, _ = P.sweep_dir(d, 0, S, *bnd)
+    return float(np.abs(psi - exact).max() / np.abs(exact).max())
+
+
+@pytest.mark.parametrize("d", [0, 7, 13, 23])
+def test_second_order_convergence_to_a_smooth_solution(d):
+    """Errors on 8^3, 16^3 and 32^3 cells: each halving of the cell size divides the
+    error by more than 2^1.65 (measured 1.7-1.95, approaching 2 from below)."""
+    e = [smooth_error(n, d) for n in (8, 16, 32)]
+    assert e[0] < 0.01
+    rates = [np.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert all(r > 1.65 for r in rates), (e, rates)
