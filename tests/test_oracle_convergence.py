@@ -60,3 +60,34 @@ def test_second_order_convergence_to_a_smooth_solution(d):
     assert e[0] < 0.01
     rates = [np.log2(e[i] / e[i + 1]) for i in range(2)]
     assert all(r > 1.65 for r in rates), (e, rates)
+
+
+def smooth_error_hex(n, d, amp, order=4):
+    """As smooth_error on a mesh of trilinear cells: every interior vertex of the unit
+    cube's n^3 grid moved by up to amp cell sizes per axis (a fresh seeded pattern at
+    every n with the same relative amplitude, so the cells keep their shape quality as
+    they shrink)."""
+    from test_oracle_hex import cell_vertex_values, face_values
+    wl = W.random_small(n, n, n, order=order, G=1, seed=3, lengths=(1.0, 1.0, 1.0))
+    wl["sigt"][:] = SIGMA_T
+    wl["sigs"][:] = 0.0
+    xyz = W.deformed_vertices(wl, amp, seed=11)
+    P = oracle.OracleProblem(wl, xyz=xyz)
+    om = P.omega[d]
+    rate = float(om @ A_VEC) + SIGMA_T
+    f = lambda x: float(np.exp(A_VEC @ x))
+    exact = cell_vertex_values(f, xyz, wl)
+    bnd = [face_values(f, xyz, wl, a, 0 if om[a] >= 0 else 1) for a in range(3)]
+    psi, _ = P.sweep_dir(d, 0, rate * exact, *bnd)
+    return float(np.abs(psi - exact).max() / np.abs(exact).max())
+
+
+@pytest.mark.parametrize("d", [0, 23])
+def test_second_order_convergence_on_deformed_cells(d):
+    """The same on trilinear cells (vertices moved by up to 10% of a cell): the
+    isoparametric element matrices keep the second order (measured rates 1.66-1.84;
+    the meshes are not nested, so the rate is less regular than on box cells)."""
+    e = [smooth_error_hex(n, d, 0.1) for n in (8, 16, 32)]
+    assert e[0] < 0.01
+    rates = [np.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert all(r > 1.5 for r in rates), (e, rates)
