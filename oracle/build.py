@@ -1,6 +1,6 @@
 """Compile the FP64 oracle (test infrastructure) into oracle/_build/libsn_oracle.so.
 
-Plain gcc, no CUDA: the oracle is the checker, never part of the product path.
+Plain gcc, no CUDA: the oracle is test infrastructure, never part of the product path.
 """
 import os
 import subprocess
