@@ -48,6 +48,10 @@ class OctNet(ctypes.Structure):
     _fields_ = [("p", _dp), ("lo", _dp), ("hi", _dp)]
 
 
+class Mlp(ctypes.Structure):
+    _fields_ = [("p", _dp), ("bf16", ctypes.c_int)]
+
+
 def _declare(L):
     L.or_ge.argtypes = [ctypes.c_int, _dp, _dp, _dp]
     L.or_lqn.argtypes = [ctypes.c_int, _dp, _dp]
@@ -72,6 +76,9 @@ def _declare(L):
     N = ctypes.POINTER(OctNet)
     L.or_octnet_cell_batch.argtypes = [N, ctypes.c_long, _dp, _dp]
     L.or_sweep_octnet.argtypes = [P, N, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    Mp = ctypes.POINTER(Mlp)
+    L.or_mlp_cell_batch.argtypes = [Mp, ctypes.c_long, _dp, _dp]
+    L.or_sweep_mlp.argtypes = [P, Mp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
     L.or_adjoint.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp,
                              ctypes.POINTER(ctypes.c_int)]
 
@@ -163,6 +170,25 @@ def octnet_cell(P, lo, hi, in27):
     return out
 
 
+class _MlpArrays:
+    """An FP64 copy of the surrogate's parameters [2312] kept alive beside its ctypes view."""
+
+    def __init__(self, p, bf16):
+        self.p = _f64(p).reshape(-1)
+        assert self.p.size == 2312
+        self.c = Mlp(_p(self.p), 1 if bf16 else 0)
+
+
+def mlp_cell(p, in27, bf16=False):
+    """psi [N, 8] of the surrogate network p [2312] (the C oracle's evaluation) on in27
+    [N, 27]; bf16 applies the rounding steps of the tensor-core path."""
+    net = _MlpArrays(p, bf16)
+    x = _f64(np.atleast_2d(in27))
+    out = np.zeros((x.shape[0], 8))
+    lib().or_mlp_cell_batch(ctypes.byref(net.c), x.shape[0], _p(x), _p(out))
+    return out
+
+
 def hex_element(X):
     """(M [8,8], L [3,8,8], Fv [6,3,8,8]) of the trilinear cell with vertices X [8,3]
     (node n = a + 2b + 4c)."""
@@ -221,18 +247,24 @@ class OracleProblem:
             raise ZeroDivisionError("zero pivot")
         return psi, tal
 
-    def sweep(self, S, groups=None, dirs=None, octnet=None):
+    def sweep(self, S, groups=None, dirs=None, octnet=None, mlp=None):
         """phi[G,ncell,8] = sum_d w_d psi_d for the isotropic source S[G,ncell,8].
 
         ``groups`` / ``dirs`` are (begin, end) ranges; phi is zero outside them.
         ``octnet`` = (P [8, 288], lo [8, 26], hi [8, 26]) replaces every per-cell
-        solve by the octant networks (oracle.octant_net).  Returns (phi, tallies[4])."""
+        solve by the octant networks (oracle.octant_net); ``mlp`` = (p [2312], bf16)
+        by the workload's surrogate network (oracle.mlp, with the BF16 rounding steps
+        if bf16).  Returns (phi, tallies[4])."""
         S = _f64(S).reshape(self.G, self.ncell, 8)
         g0, g1 = groups if groups else (0, self.G)
         d0, d1 = dirs if dirs else (0, self.ndir)
         phi = np.zeros((self.G, self.ncell, 8))
         tal = np.zeros(4)
-        if octnet is None:
+        if mlp is not None:
+            net = _MlpArrays(*mlp)
+            rc = lib().or_sweep_mlp(ctypes.byref(self.c), ctypes.byref(net.c), _p(S), _p(phi), g0, g1, d0, d1,
+                                    _p(tal))
+        elif octnet is None:
             rc = lib().or_sweep(ctypes.byref(self.c), _p(S), _p(phi), g0, g1, d0, d1, _p(tal))
         else:
             net = _OctNetArrays(*octnet)

@@ -36,6 +36,7 @@
  */
 #include <math.h>
 #include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -364,6 +365,128 @@ void or_octnet_cell_batch(const or_octnet *net, long n, const double *in27, doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* The workload's surrogate network as a one-cell solver: 27 inputs -> 64    */
+/* ReLU -> 8 linear outputs (one hidden layer, Eq. (15)), one network for    */
+/* every octant through the mirror symmetry of the DFEM system.  The input   */
+/* construction (the counterpart of the scaling of Eq. (16)) follows the     */
+/* Python oracle (oracle/mlp.py) term by term:                               */
+/*   mirror into the positive octant: node k of the canonical cell is node   */
+/*   k ^ m, m = (mu<0) | (eta<0)<<1 | (xi<0)<<2, in-face t of the x-face is   */
+/*   t ^ ((eta<0) | (xi<0)<<1) (y-, z-faces alike);                          */
+/*   s = max(max |S_c|, max |up_c|), 1/s taken as 0 for s <= 1e-30;          */
+/*   x = [2|Omega| - 1, (log h + 1.15) / 1.15, log(max(sigma_t, 1e-6)) / 4.5, */
+/*        S_c / s, up_c / s];                                                */
+/*   psi (physical node k) = s * o[k ^ m].                                    */
+/* With bf16 set, the rounding steps of the tensor-core path are applied:    */
+/* the one-cell inputs and the parameters to FP32, the features, W1, W2 and  */
+/* the hidden activations to BF16 (round to nearest, ties to even), sums and */
+/* biases otherwise exact.  Parameters (2312): W1[64][27], b1[64], W2[8][64], */
+/* b2[8].                                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const double *p;
+    int bf16;
+} or_mlp;
+
+static double to_f32(double v) { return (double)(float)v; }
+
+static double to_bf16(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    uint64_t w = u;
+    w = ((w + 0x7FFFu + ((w >> 16) & 1u)) >> 16) << 16;
+    u = (uint32_t)w;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* parameters as the network uses them: rounded to FP32, W1 and W2 further to */
+/* BF16, when bf16 is set; unchanged otherwise                                */
+static void mlp_params(const or_mlp *net, double *q)
+{
+    for (int i = 0; i < 2312; ++i) {
+        const int is_w = i < 64 * 27 || (i >= 64 * 27 + 64 && i < 64 * 27 + 64 + 8 * 64);
+        q[i] = !net->bf16 ? net->p[i] : (is_w ? to_bf16(to_f32(net->p[i])) : to_f32(net->p[i]));
+    }
+}
+
+/* one cell with the parameters q of mlp_params */
+static void mlp_cell(const double *q, int rb, const double *in27_, double *psi)
+{
+    double in27[27];
+    for (int i = 0; i < 27; ++i) in27[i] = rb ? to_f32(in27_[i]) : in27_[i];
+    const int fx = in27[0] < 0.0, fy = in27[1] < 0.0, fz = in27[2] < 0.0;
+    const int m = fx | (fy << 1) | (fz << 2);
+    double Sc[8], Uc[12];
+    for (int k = 0; k < 8; ++k) Sc[k] = in27[7 + (k ^ m)];
+    for (int t = 0; t < 4; ++t) {
+        Uc[t] = in27[15 + (t ^ (fy | (fz << 1)))];
+        Uc[4 + t] = in27[19 + (t ^ (fx | (fz << 1)))];
+        Uc[8 + t] = in27[23 + (t ^ (fx | (fy << 1)))];
+    }
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s = fmax(s, fabs(Sc[k]));
+    for (int t = 0; t < 12; ++t) s = fmax(s, fabs(Uc[t]));
+    const double inv = s > 1e-30 ? 1.0 / s : 0.0;
+    double x[27];
+    for (int a = 0; a < 3; ++a) {
+        x[a] = 2.0 * fabs(in27[a]) - 1.0;
+        x[3 + a] = (log(in27[3 + a]) + 1.15) / 1.15;
+    }
+    x[6] = log(fmax(in27[6], 1e-6)) / 4.5;
+    for (int k = 0; k < 8; ++k) x[7 + k] = Sc[k] * inv;
+    for (int t = 0; t < 12; ++t) x[15 + t] = Uc[t] * inv;
+    if (rb)
+        for (int i = 0; i < 27; ++i) x[i] = to_bf16(x[i]);
+    const double *W1 = q, *b1 = W1 + 64 * 27, *W2 = b1 + 64, *b2 = W2 + 8 * 64;
+    double h[64], o[8];
+    for (int j = 0; j < 64; ++j) {
+        double a = b1[j];
+        for (int i = 0; i < 27; ++i) a += W1[27 * j + i] * x[i];
+        h[j] = a > 0.0 ? a : 0.0;
+        if (rb) h[j] = to_bf16(h[j]);
+    }
+    for (int d = 0; d < 8; ++d) {
+        double z = b2[d];
+        for (int j = 0; j < 64; ++j) z += W2[64 * d + j] * h[j];
+        o[d] = z;
+    }
+    for (int k = 0; k < 8; ++k) psi[k] = s * o[k ^ m];
+}
+
+void or_mlp_cell_batch(const or_mlp *net, long n, const double *in27, double *psi)
+{
+    double q[2312];
+    mlp_params(net, q);
+    for (long i = 0; i < n; ++i) mlp_cell(q, net->bf16, in27 + 27 * i, psi + 8 * i);
+}
+
+/* a one-cell solver handed to the sweep in place of assembly and elimination */
+typedef struct {
+    void (*cell)(const void *ctx, const double *in27, double *psi);
+    const void *ctx;
+} or_cellnet;
+
+static void octnet_cb(const void *ctx, const double *in27, double *psi)
+{
+    or_octnet_cell((const or_octnet *)ctx, in27, psi);
+}
+
+/* the surrogate prepared for a sweep: its parameters as used, and the mode */
+typedef struct {
+    double q[2312];
+    int bf16;
+} or_mlp_prepared;
+
+static void mlp_cb(const void *ctx, const double *in27, double *psi)
+{
+    const or_mlp_prepared *m = (const or_mlp_prepared *)ctx;
+    mlp_cell(m->q, m->bf16, in27, psi);
+}
+
+/* ------------------------------------------------------------------------ */
 /* General hexahedral cells (the shape change of the cells of Sec. 2's       */
 /* closing remarks): a trilinear map x(xi) = sum_n X_n N_n(xi) of the unit   */
 /* cube, N_n = prod over the axes of xi_a or 1 - xi_a by the bits of          */
@@ -538,7 +661,7 @@ static long ncell_of(const or_problem *p) { return (long)p->nx * p->ny * p->nz; 
 /* or, when a pointer is NULL, from the problem's constant psi_inc (Eq. (10)) */
 /* for group g.  tallies[0..3] += leakage, collision, source, inflow.        */
 /* ------------------------------------------------------------------------ */
-static int sweep_dir(const or_problem *p, const or_elem *e, const or_octnet *net, int d, int g,
+static int sweep_dir(const or_problem *p, const or_elem *e, const or_cellnet *net, int d, int g,
                      const double *S, const double *bx, const double *by, const double *bz, double *psi,
                      double tal[4])
 {
@@ -598,14 +721,14 @@ static int sweep_dir(const or_problem *p, const or_elem *e, const or_octnet *net
                 }
                 double x[8];
                 if (net) {
-                    /* the cell's one-cell problem handed to the network of its octant */
+                    /* the cell's one-cell problem handed to the network */
                     double in27[27];
                     for (int a = 0; a < 3; ++a) in27[a] = om[a];
                     in27[3] = p->dx; in27[4] = p->dy; in27[5] = p->dz;
                     in27[6] = p->sigt[(long)g * nc + c];
                     for (int n = 0; n < 8; ++n) in27[7 + n] = S[8 * c + n];
                     for (int t = 0; t < 12; ++t) in27[15 + t] = up[t];
-                    or_octnet_cell(net, in27, x);
+                    net->cell(net->ctx, in27, x);
                 } else if (p->hex) {
                     double A[64], b[8];
                     assemble_hex((const or_hex *)p->hex + c, om, p->sigt[(long)g * nc + c], S + 8 * c, up, A, b);
@@ -691,7 +814,7 @@ int or_sweep_dir(const or_problem *p, int d, int g, const double *S, const doubl
 /* fixed order, so the result does not depend on the thread count).          */
 /* tal[4] receives the weighted balance tallies.  Returns 0 or -1.           */
 /* ------------------------------------------------------------------------ */
-static int sweep_range(const or_problem *p, const or_octnet *net, const double *S, double *phi, int g0, int g1,
+static int sweep_range(const or_problem *p, const or_cellnet *net, const double *S, double *phi, int g0, int g1,
                        int d0, int d1, double *tal)
 {
     or_elem e;
@@ -730,7 +853,22 @@ int or_sweep(const or_problem *p, const double *S, double *phi, int g0, int g1, 
 int or_sweep_octnet(const or_problem *p, const or_octnet *net, const double *S, double *phi, int g0, int g1,
                     int d0, int d1, double *tal)
 {
-    return sweep_range(p, net, S, phi, g0, g1, d0, d1, tal);
+    const or_cellnet cn = {octnet_cb, net};
+    return sweep_range(p, &cn, S, phi, g0, g1, d0, d1, tal);
+}
+
+/* The same with the workload's surrogate network as the cell solver.      */
+int or_sweep_mlp(const or_problem *p, const or_mlp *net, const double *S, double *phi, int g0, int g1, int d0,
+                 int d1, double *tal)
+{
+    or_mlp_prepared *m = (or_mlp_prepared *)malloc(sizeof(or_mlp_prepared));
+    if (!m) return -1;
+    mlp_params(net, m->q);
+    m->bf16 = net->bf16;
+    const or_cellnet cn = {mlp_cb, m};
+    const int rc = sweep_range(p, &cn, S, phi, g0, g1, d0, d1, tal);
+    free(m);
+    return rc;
 }
 
 /* Isotropic source build (Eqs. (2), (6) with the P_0 term only):           */

@@ -119,3 +119,50 @@ def test_vanishing_input_scale_counts_as_zero():
     feat, s, _ = mlp.features(x)
     assert np.all(np.isfinite(feat)) and np.all(feat[:, 7:27] == 0.0)
     assert np.all(mlp.targets(np.ones((4, 8)), x) == 0.0)
+
+
+def bf16_ref(p, in27):
+    """The numpy oracle with the BF16 path's rounding steps (shared with the GPU
+    parity tests)."""
+    from _parity import f32_roundtrip
+    from test_gpu_surrogate import predict_bf16
+    return predict_bf16(p, f32_roundtrip(in27))
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_c_and_numpy_evaluations_agree(bf16):
+    """The C oracle's surrogate cell (used by the whole-mesh sweeps) equals the numpy
+    oracle on every octant, with and without the BF16 rounding steps; an input scale
+    at or below 1e-30 zeroes the flux features, so psi = s o stays of the order of s
+    in both."""
+    x = W.onecell_problems(3000, seed=5)
+    x[:3, 7:27] *= 1e-36
+    p = mlp.init_params(3)
+    got = oracle.mlp_cell(p, x, bf16=bf16)
+    want = bf16_ref(p, x) if bf16 else mlp.predict(p, x)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+    assert np.all(np.isfinite(got)) and np.abs(got[:3]).max() < 1e-30
+    assert len(np.unique(mlp.mirror_masks(x)[0] | (mlp.mirror_masks(x)[1] << 1) | (mlp.mirror_masks(x)[2] << 2))) == 8
+
+
+@pytest.mark.parametrize("order, bf16", [(2, False), (4, True), (8, True)])
+def test_c_network_sweep_matches_the_python_sweep(order, bf16):
+    """The C oracle's sweep with the surrogate as cell solver against the pure-Python
+    upwind sweep calling the numpy network (both FP64 sweeps)."""
+    from _parity import network_sweep
+    wl = W.random_small(3, 4, 2, order=order, G=2, seed=8, psi_inc=True)
+    p = mlp.init_params(12) * 0.5
+    S = np.random.default_rng(2).uniform(0.0, 1.0, (2, 24, 8))
+    phi, _ = oracle.OracleProblem(wl).sweep(S, mlp=(p, bf16))
+    ref = network_sweep(wl, S, (lambda z: bf16_ref(p, z)) if bf16 else (lambda z: mlp.predict(p, z)))
+    assert np.abs(phi - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_bf16_rounding_is_nearest_even():
+    """The rounding step itself: values exactly halfway between two BF16 numbers go
+    to the even one, others to the nearest."""
+    from test_gpu_surrogate import bf16
+    one = 1.0
+    ulp = 2.0 ** -7                      # BF16 spacing in [1, 2)
+    v = np.array([one + ulp / 2, one + 1.5 * ulp, one + 0.26 * ulp, one + 0.74 * ulp, -3.0])
+    assert list(bf16(v)) == [one, one + 2 * ulp, one, one + ulp, -3.0]
