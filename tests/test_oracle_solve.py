@@ -243,3 +243,29 @@ def test_problem4_iteration_rate_is_the_scattering_ratio():
         phi, _ = r["phi"], hist.append(r["change_mean"])
     rho = (hist[-1] / hist[-21]) ** (1.0 / 20)
     assert 0.975 < rho <= 0.99
+
+
+def test_per_cell_balance_with_closed_form_integrals():
+    """Testing the cell's weak form with w = 1 (the sum of its basis functions) gives
+    the cell's particle balance: outflow + sigma_t int psi = int S + inflow.  Each
+    integral is written here in closed form for the box cell (a trilinear function
+    integrates to V/8 times its nodal sum, a bilinear face trace to A/4 times its
+    four values), independently of the oracle's matrices."""
+    x = W.onecell_problems(2000, seed=13)
+    psi = oracle.cell_solve(x)
+    worst = 0.0
+    for r in range(x.shape[0]):
+        om, h, sig = x[r, 0:3], x[r, 3:6], x[r, 6]
+        S, up = x[r, 7:15], x[r, 15:27]
+        V = h[0] * h[1] * h[2]
+        area = (h[1] * h[2], h[0] * h[2], h[0] * h[1])
+        out = inflow = 0.0
+        for a in range(3):
+            side = 1 if om[a] >= 0 else 0
+            on_face = [n for n in range(8) if (n >> a) & 1 == side]
+            out += abs(om[a]) * area[a] / 4 * psi[r, on_face].sum()
+            inflow += abs(om[a]) * area[a] / 4 * up[4 * a:4 * a + 4].sum()
+        lhs = out + sig * V / 8 * psi[r].sum()
+        rhs = V / 8 * S.sum() + inflow
+        worst = max(worst, abs(lhs - rhs) / (abs(rhs) + abs(lhs)))
+    assert worst < 1e-13
