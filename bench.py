@@ -181,6 +181,16 @@ def run_reference(args):
     return 0
 
 
+def guarded(form, *args):
+    """One of the secondary reports (surrogate, networks, anisotropic, general cells):
+    an exception in it becomes an "error" entry of its object instead of costing the
+    step's JSON line."""
+    try:
+        return form(*args)
+    except Exception as e:  # noqa: BLE001 -- reported in the line, not swallowed
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
 def eps_p(phi, ref):
     """Eq. (20)-style mean relative error of the cell-averaged scalar flux (all groups), m = 1e-8."""
     a = phi.view(phi.shape[0], -1, 8).mean(-1).double()
@@ -568,13 +578,13 @@ def run_gpu(args):
     e2e_ms = e2e_pipelined(P, S_host, phi_host, args.steps, stream)
     barrier()
 
-    ann = None if args.no_ann else ann_form(P, args.steps)
-    octnet = None if args.no_octnet else octnet_form(P)
+    ann = None if args.no_ann else guarded(ann_form, P, args.steps)
+    octnet = None if args.no_octnet else guarded(octnet_form, P)
 
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, "cuda")
     P.close()
-    aniso = None if args.no_aniso else aniso_form(min(args.steps, 10), ms / args.steps)
-    geom = None if args.no_geom else geom_form(min(args.steps, 10), ms / args.steps)
+    aniso = None if args.no_aniso else guarded(aniso_form, min(args.steps, 10), ms / args.steps)
+    geom = None if args.no_geom else guarded(geom_form, min(args.steps, 10), ms / args.steps)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -625,7 +635,7 @@ def run_gpu(args):
     if geom is not None:
         line["geom"] = geom
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = guarded(cpu_baseline)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

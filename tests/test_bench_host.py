@@ -68,3 +68,10 @@ def test_clocks_stop_reads_the_sampler_output_and_cleans_up():
     name = c.f.name
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
     assert not os.path.exists(name)
+
+
+def test_a_failing_secondary_report_keeps_the_line():
+    def boom(x):
+        raise RuntimeError("no network (%d)" % x)
+    assert bench.guarded(boom, 3) == {"error": "RuntimeError: no network (3)"}
+    assert bench.guarded(lambda a, b: {"v": a + b}, 1, 2) == {"v": 3}
