@@ -38,3 +38,51 @@ def test_octant_problems_lie_in_their_octants():
         assert np.allclose(np.linalg.norm(rows[:, 0:3], axis=1), 1.0)
         for j, col in ((12, 0), (13, 1)):
             assert np.all(rows[:, col] >= lo[o, j]) and np.all(rows[:, col] <= hi[o, j])
+
+
+def test_blocked_64_follows_its_recipe():
+    """64^3 cells on a 10^3 box, LQ_8, 8 groups; sigma_t constant on each 8^3 block and
+    lognormal(0, 1) over the blocks; scattering ratio U[0.3, 0.9] per block, the same in
+    every group; downscatter-only transfer; q = 1 in group 0 on one 16^3 box only."""
+    wl = W.blocked_64()
+    assert (wl["nx"], wl["ny"], wl["nz"], wl["lx"], wl["order"]) == (64, 64, 64, 10.0, 8)
+    G = wl["sigt"].shape[0]
+    assert G == 8
+    sig = wl["sigt"].reshape(G, 8, 8, 8, 8, 8, 8)      # [g][bk][k][bj][j][bi][i]
+    blocks = sig[:, :, 0, :, 0, :, 0]
+    assert np.all(sig == blocks[:, :, None, :, None, :, None])
+    logs = np.log(blocks).ravel()                        # 8 groups x 512 blocks
+    assert abs(logs.mean()) < 0.1 and abs(logs.std() - 1.0) < 0.05
+    ratio = wl["sigs"] / wl["sigt"]
+    assert np.allclose(ratio, ratio[0][None, :]) and ratio.min() >= 0.3 and ratio.max() <= 0.9
+    x = wl["xfer"]
+    # row g' holds where group g' scatters to: only g >= g' (downscatter), all of it
+    assert np.all(x[np.tril_indices(G, -1)] == 0.0) and np.allclose(x.sum(axis=1), 1.0)
+    src = wl["q"][0].reshape(64, 64, 64) > 0
+    assert src.sum() == 16 ** 3 and np.all(wl["q"][1:] == 0.0) and np.all(wl["q"][0][wl["q"][0] > 0] == 1.0)
+    k, j, i = np.nonzero(src)
+    assert (i.max() - i.min(), j.max() - j.min(), k.max() - k.min()) == (15, 15, 15)
+
+
+def test_spheres_96_background_and_sources():
+    """Background sigma_t = 0.1 with scattering ratio 0.5; sources (q = 1, group 0 only)
+    lie inside spheres, never in the background."""
+    wl = W.spheres_96()
+    assert (wl["nx"], wl["order"], wl["sigt"].shape[0]) == (96, 12, 16)
+    bg = np.all(wl["sigt"] == 0.1, axis=0)
+    assert bg.mean() > 0.2
+    assert np.allclose(wl["sigs"][:, bg], 0.05)
+    src = wl["q"][0] > 0
+    assert src.any() and not np.any(src & bg) and np.all(wl["q"][1:] == 0.0)
+
+
+def test_onecell_problems_follow_the_training_distribution():
+    """Directions on the unit sphere, cell sizes in [0.1, 1], sigma_t lognormal(0, 1.5),
+    sources and upwind values in [0, 1]."""
+    x = W.onecell_problems(20000, seed=9)
+    assert np.allclose(np.linalg.norm(x[:, 0:3], axis=1), 1.0)
+    assert np.all(np.abs(np.sign(x[:, 0:3]).mean(axis=0)) < 0.05)
+    assert x[:, 3:6].min() >= 0.1 and x[:, 3:6].max() <= 1.0
+    ls = np.log(x[:, 6])
+    assert abs(ls.mean()) < 0.05 and abs(ls.std() - 1.5) < 0.05
+    assert x[:, 7:27].min() >= 0.0 and x[:, 7:27].max() <= 1.0
