@@ -274,6 +274,15 @@ sn_status sn_surrogate_train(sn_handle h, const float *in27, int64_t n, int64_t 
 sn_status sn_surrogate_apply(sn_handle h, const float *in27, float *psi, int64_t n, int32_t gated,
                              int64_t *n_fallback);
 
+/* Self-test of the failure path of the bounded device waits (not in the paper):
+ * one CTA sets up like a surrogate kernel (an mbarrier and tensor-memory columns)
+ * and waits, for at most limit_cycles SM cycles (1..2^31), on an mbarrier phase
+ * that nothing completes.  The wait gives up, the CTA raises its abort flag, frees
+ * its tensor memory and is counted as timed out, as a surrogate sweep's CTA would
+ * be; the call then returns SN_ETIMEOUT, and the handle and the CUDA context stay
+ * usable.  Synchronises the handle's stream.  (The waits of the sweeps use 2^31.) */
+sn_status sn_selftest_wait(sn_handle h, int64_t limit_cycles);
+
 /* Surrogate counters of the last sweep (sn_sweep) or of the last iteration of
  * sn_source_iterate in an ANN mode, or of the last sn_surrogate_apply: cells sent
  * back to elimination by the gate, and CTAs that gave up a bounded tensor-core
@@ -417,7 +426,9 @@ sn_status sn_octnet_apply(sn_handle h, const float *in27, float *psi, int64_t n)
  * of the library (2.37 MB on every GPU that loads it, kept until exit), which caps
  * n at 32768 rows (SN_EINVAL above).  The first call on a device looks the array
  * up (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (other
+ * capture.  The address is kept until the process exits: after a device reset
+ * (cudaDeviceReset or a primary-context reset) it is stale, and this entry point
+ * must not be called again in that process.  All calls share the array: calls that overlap on the GPU (other
  * streams or threads on the same device) race; calls on one stream are ordered.
  * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).
  * ------------------------------------------------------------------------- */

@@ -430,6 +430,141 @@ __device__ __forceinline__ void cell_solve_canonical(T t3x, T t3y, T t3z, T sig,
     }
 }
 
+// ---------------------------------------------------------------------------------
+// The canonical solve of the key sweep (one thread per key, every direction of the
+// octant in turn): the source part (Mh x Mh x Mh) S of the right-hand side is formed
+// once per key, A is built from its 27 distinct values, and the refinement residual
+// is formed from the Kronecker factors with the subtraction folded into the products.
+// The elimination, its partial-pivoting test and the exchange path are those above.
+// ---------------------------------------------------------------------------------
+
+// Per-axis state of an entry (k, j) of A: both node bits equal (0), k's bit 0 and j's
+// bit 1 (1), k's bit 1 and j's bit 0 (2).
+__host__ __device__ constexpr int ax_state(int a, int b) { return a == b ? 0 : (a == 0 ? 1 : 2); }
+
+// 216/V * A in canonical orientation: entry (k, j) = 2^(axes in state 0) *
+// (sigma_t + sum_a t3a * c_a), c = 1/2, 1, -1 for the states 0, 1, 2 -- the same
+// matrix as assemble_A, written through its 27 distinct values.
+__device__ __forceinline__ void assemble_A27(float t3x, float t3y, float t3z, float sig, float (&A)[8][8])
+{
+    const float vx[3] = {0.5f * t3x, t3x, -t3x};
+    const float vy[3] = {0.5f * t3y, t3y, -t3y};
+    const float vz[3] = {0.5f * t3z, t3z, -t3z};
+    float v[3][3][3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const float sx = sig + vx[p];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float sxy = sx + vy[q];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                v[p][q][r] = (sxy + vz[r]) * (float)((p == 0 ? 2 : 1) * (q == 0 ? 2 : 1) * (r == 0 ? 2 : 1));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            A[k][j] = v[ax_state(k & 1, j & 1)][ax_state((k >> 1) & 1, (j >> 1) & 1)][ax_state(k >> 2, j >> 2)];
+    }
+}
+
+// 216/V * b from the key's Sm = (Mh x Mh x Mh) S and the inflow faces (t6a = 6 tau_a);
+// face in-face order as in build_b.
+__device__ __forceinline__ void build_b_msrc(float t6x, float t6y, float t6z, const float (&Sm)[8],
+                                             const float (&ux)[4], const float (&uy)[4], const float (&uz)[4],
+                                             float (&b)[8])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = Sm[k];
+    float v[4];
+    mh_face(ux, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) b[2 * t] = fmaf(t6x, v[t], b[2 * t]);
+    mh_face(uy, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) b[(t & 1) + 4 * (t >> 1)] = fmaf(t6y, v[t], b[(t & 1) + 4 * (t >> 1)]);
+    mh_face(uz, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) b[t] = fmaf(t6z, v[t], b[t]);
+}
+
+// r = b0 - (216/V * A) x from the Kronecker factors (apply_A's terms): the x-streaming
+// and mass terms share Mh along y and z and combine as alpha = t3x + 2 sigma,
+// beta = t3x + sigma, gamma = sigma - t3x per x-pair.
+__device__ __forceinline__ void residual_A(float t3x, float t3y, float t3z, float sig, const float (&x)[8],
+                                           const float (&b0)[8], float (&r)[8])
+{
+    float u[8], v[8], w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u[k] = x[k];
+    mh_axis<2>(u);                      // Mh_z x
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = u[k];
+    mh_axis<1>(v);                      // Mh_y Mh_z x
+    const float al = fmaf(2.f, sig, t3x), be = t3x + sig, ga = sig - t3x;
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        const float v0 = v[k], v1 = v[k + 1];
+        r[k] = fmaf(-be, v1, fmaf(-al, v0, b0[k]));
+        r[k + 1] = fmaf(-al, v1, fmaf(-ga, v0, b0[k + 1]));
+    }
+    mh_axis<0>(u);                      // Mh_x Mh_z x
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k & 2) continue;
+        const float w0 = u[k], w1 = u[k | 2];
+        r[k] = fmaf(-t3y, w0 + w1, r[k]);
+        r[k | 2] = fmaf(-t3y, w1 - w0, r[k | 2]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = x[k];
+    mh_axis<0>(w);
+    mh_axis<1>(w);                      // Mh_x Mh_y x
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float w0 = w[k], w1 = w[k | 4];
+        r[k] = fmaf(-t3z, w0 + w1, r[k]);
+        r[k | 4] = fmaf(-t3z, w1 - w0, r[k | 4]);
+    }
+}
+
+// The key sweep's solve: GE with partial pivoting (diagonal pivots first, exchange
+// path where the pivoting test fails) and, with REFINE, one FP32 refinement step.
+template <bool REFINE>
+__device__ __forceinline__ void cell_solve_key(float t3x, float t3y, float t3z, float sig, const float (&Sm)[8],
+                                               const float (&ux)[4], const float (&uy)[4], const float (&uz)[4],
+                                               float (&x)[8])
+{
+    float A[8][8], b[8], b0[8], rinv[8];
+    assemble_A27(t3x, t3y, t3z, sig, A);
+    build_b_msrc(2.f * t3x, 2.f * t3y, 2.f * t3z, Sm, ux, uy, uz, b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b0[k] = b[k];
+    const bool ex = ge8_factor_solve_diag(A, b, rinv, x);
+    // warp-uniform test: the exchange path stays off the instruction stream unless a
+    // lane of the warp needs it
+    const bool any_ex = __any_sync(__activemask(), ex);
+    unsigned piv = kPivIdentity;
+    if (any_ex && ex) {
+        assemble_A27(t3x, t3y, t3z, sig, A);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = b0[k];
+        ge8_factor_solve(A, b, piv, rinv, x);
+    }
+    if (REFINE) {
+        float r[8], dx[8];
+        residual_A(t3x, t3y, t3z, sig, x, b0, r);
+        if (any_ex)
+            ge8_replay(A, piv, rinv, r, dx);
+        else
+            ge8_replay_diag(A, rinv, r, dx);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] += dx[k];
+    }
+}
+
 // Swap the halves of an 8-vector along node bit BIT when flag is set (x[k] <-> x[k ^ 2^BIT]).
 template <int BIT, typename T>
 __device__ __forceinline__ void cswap_axis(T (&x)[8], bool flag)

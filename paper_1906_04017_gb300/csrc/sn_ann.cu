@@ -55,14 +55,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity, uin
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase: false once about 2^31 SM cycles (~1 s) have
-// passed without completion.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+// Bounded wait on an mbarrier phase: false once `limit` SM cycles (by default 2^31,
+// about 1 s) have passed without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit = (1LL << 31))
 {
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity, 100000u)) return true;
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -595,6 +595,35 @@ __device__ __forceinline__ void ann_teardown(uint32_t tbase, const AnnArgs &a, c
     if (threadIdx.x == 0 && reinterpret_cast<const volatile int *>(misc)[2]) atomicAdd(a.counter + 1, 1ull);
     __syncwarp();
     if (threadIdx.x < 32) tmem_dealloc(tbase, kTmemCols);
+}
+
+// Self-test of the bounded tensor-core waits (not in the paper): the set-up of a
+// surrogate kernel (mbarrier, TMEM columns), then thread 0 waits on phase 0 of the
+// mbarrier, which expects one arrival that nothing makes, for at most `limit` SM
+// cycles.  It gives up, raises the CTA's abort flag, and the teardown counts the
+// timed-out CTA and frees the TMEM exactly as after a failed wait in a sweep.
+__global__ void __launch_bounds__(128) wait_selftest_kernel(AnnArgs a, long long limit)
+{
+    __shared__ __align__(8) unsigned long long bar_word;
+    __shared__ __align__(16) int misc[4];
+    const uint32_t bar = smem_u32(&bar_word);
+    if (threadIdx.x == 0) {
+        misc[2] = 0;
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (threadIdx.x < 32) {
+        tmem_alloc(smem_u32(misc), kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t *>(misc);
+    const bool late = threadIdx.x == 0 && !mbar_wait_bounded(bar, 0u, limit);
+    if (__syncthreads_or(late) && threadIdx.x == 0) misc[2] = 1;
+    ann_teardown(tbase, a, misc);
 }
 
 // Independent one-cell problems (sn_surrogate_apply).  Rows the gate rejects are
@@ -1244,8 +1273,11 @@ static sn_status apply_cells(sn_handle h, const float *in27, float *psi, int64_t
 // one device) race on it; calls queued on one stream are ordered and safe.  Each call
 // writes all the partials it later reads, so no part of the array has to start at
 // zero.  The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress, with that device current); make that first call before any
-// stream capture begins.
+// (cudaGetSymbolAddress, with that device current) and sets the gradient kernel's
+// shared-memory attribute; make that first call before any stream capture begins.
+// The address is kept for the life of the process: a device reset (cudaDeviceReset,
+// or a reset of the primary context) reloads the module and invalidates it, so after
+// a reset this entry point must not be called again in the same process.
 // ---------------------------------------------------------------------------------
 constexpr int kNoAllocMaxBlocks = 256;
 static __device__ __align__(256) float g_noalloc_gpart[kNoAllocMaxBlocks * kNparam];
@@ -1268,6 +1300,8 @@ static sn_status noalloc_scratch(float **gpart, double **lpart)
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(gradient partials)");
         e = cudaGetSymbolAddress(&pl, g_noalloc_lpart);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(loss partials)");
+        e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
         g_noalloc_lpart_ptr[dev] = static_cast<double *>(pl);
         g_noalloc_gpart_ptr[dev] = static_cast<float *>(pg);
     }
@@ -1293,12 +1327,10 @@ extern "C" sn_status sn_surrogate_grad_noalloc(const float *params, const float 
     if (s != SN_OK) return s;
     const cudaStream_t st = (cudaStream_t)stream;
     const int nblk = (int)((n + 127) / 128);
-    cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
     grad_kernel<<<nblk, 128, kGradSmem, st>>>(params, feat, targ, n, 0, (int)n, 1.f / (float)n, gpart, lpart);
     adam_kernel<<<(kNparam + 255) / 256, 256, 0, st>>>(nullptr, nullptr, nullptr, gpart, nblk, 0.f, 1.f, 1.f, grad, 0);
     sum_kernel<<<1, 32, 0, st>>>(lpart, nblk, loss);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "sn_surrogate_grad_noalloc");
     return SN_OK;
 }
@@ -1544,6 +1576,23 @@ sn_status sn_surrogate_apply(sn_handle h, const float *in27, float *psi, int64_t
     if (s != SN_OK) return s;
     if (n < 0 || (n > 0 && (!in27 || !psi))) return fail(h, SN_EINVAL, "sn_surrogate_apply: bad argument");
     return apply_cells(h, in27, psi, n, gated != 0, n_fallback, h->stream);
+}
+
+sn_status sn_selftest_wait(sn_handle h, int64_t limit_cycles)
+{
+    if (!h) return fail(nullptr, SN_EINVAL, "sn_selftest_wait: NULL handle");
+    if (limit_cycles < 1 || limit_cycles > (1LL << 31))
+        return fail(h, SN_EINVAL, "sn_selftest_wait: limit_cycles must be in 1..2^31");
+    sn_status s = ensure_net(h);
+    if (s != SN_OK) return s;
+    Net *n = net_of(h);
+    AnnArgs a;
+    a.w1p = n->w1p; a.w2p = n->w2p; a.b2 = n->b2; a.tau = n->tau; a.counter = n->counter;
+    s = reset_ann_counters(h, h->stream);
+    if (s != SN_OK) return s;
+    wait_selftest_kernel<<<1, 128, 0, h->stream>>>(a, (long long)limit_cycles);
+    SN_CK(h, cudaGetLastError());
+    return check_ann_timeouts(h);
 }
 
 sn_status sn_surrogate_stats(sn_handle h, int64_t *fallbacks, int64_t *timeouts)

@@ -91,6 +91,7 @@ struct sn_handle_s {
     uint32_t *plane_pos = nullptr;    // [C] position of primed cell i'+nx(j'+ny k') within its hyperplane
     void *face = nullptr;        // face planes: 4-vectors of T, see sn_sweep.cu
     int64_t face_x = 0, face_y = 0, face_z = 0;  // 4-vector count of each plane set
+    int64_t face_in = 0;         // 4-vector offset of the inflow vectors [G][6] after the planes
     void *phi_oct = nullptr;     // T[8][C][G][8] per-octant partial scalar flux
     void *S = nullptr;           // T[G][C][8]
     void *phi_b = nullptr;       // T[G][C][8] iteration scratch
@@ -173,6 +174,9 @@ uint32_t sweep_smem_bytes(sn_handle h, int K);
 sn_status launch_cells_f32(const float *in27, float *psi, int64_t n, bool refine, cudaStream_t st);
 // surrogate sweep (sn_ann.cu): every hyperplane of one sweep, FP32 handles only
 sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gated, cudaStream_t st);
+// the key sweep (sn_sweep_keys.cu): FP32 elimination on box cells, isotropic scattering
+bool key_sweep_ok(sn_handle h);
+sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st);
 // zero the surrogate's fallback / timeout counters (stream-ordered)
 sn_status reset_ann_counters(sn_handle h, cudaStream_t st);
 sn_status check_ann_timeouts(sn_handle h);

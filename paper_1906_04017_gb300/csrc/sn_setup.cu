@@ -406,7 +406,17 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
     h->face_x = 8LL * h->ny * h->nz * GD;
     h->face_y = 8LL * h->nx * h->nz * GD;
     h->face_z = 8LL * h->nx * h->ny * GD;
-    SN_TRY(dalloc(h, &h->face, 4 * (size_t)(h->face_x + h->face_y + h->face_z)));
+    // after the planes: psi_inc of every (group, face) as a 4-vector, read by the key
+    // sweep's inflow-boundary cells in place of a face slot
+    h->face_in = h->face_x + h->face_y + h->face_z;
+    SN_TRY(dalloc(h, &h->face, 4 * (size_t)(h->face_in + 6 * G)));
+    if (!h->fp64) {
+        std::vector<float> in4(24 * (size_t)G);
+        for (size_t e = 0; e < in4.size(); ++e) in4[e] = (float)inc[e / 4];
+        cudaError_t e = cudaMemcpyAsync(static_cast<float *>(h->face) + 4 * h->face_in, in4.data(),
+                                        sizeof(float) * in4.size(), cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpyAsync(inflow vectors)"));
+    }
     SN_TRY(dalloc(h, &h->phi_oct, (size_t)8 * GC * 8));
     SN_TRY(dalloc(h, &h->S, GC * 8));
     SN_TRY(dalloc(h, &h->phi_b, GC * 8));

@@ -873,6 +873,8 @@ sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode 
     if (h->fp64) return launch_sweep_t<double>(h, (const double *)S, (double *)phi_oct, false, false, st);
     if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED)
         return launch_sweep_ann(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_ANN_GATED, st);
+    if ((mode == SN_SOLVE_GE32R || mode == SN_SOLVE_GE32) && key_sweep_ok(h))
+        return launch_sweep_keys(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R, st);
     return launch_sweep_t<float>(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R,
                                  mode == SN_SOLVE_OCTNET, st);
 }

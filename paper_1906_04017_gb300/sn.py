@@ -87,6 +87,7 @@ _API = [
                                           ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _dp, _dp]),
     ("sn_surrogate_apply", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int64)]),
+    ("sn_selftest_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     ("sn_surrogate_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]),
     ("sn_adjoint_sweep", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_double, ctypes.c_int32, _fp, _fp, _fp,
@@ -192,12 +193,37 @@ def surrogate_prepare(in27):
     return feat, targ
 
 
+def _rows(feat, targ):
+    """Row count of a (features [n, 27], targets [n, 8]) pair; ValueError unless both
+    are 2-D with those widths and the same n."""
+    if feat.dim() != 2 or feat.shape[1] != 27 or targ.dim() != 2 or targ.shape[1] != 8:
+        raise ValueError("features must be [n, 27] and targets [n, 8], got %s and %s"
+                         % (tuple(feat.shape), tuple(targ.shape)))
+    if feat.shape[0] != targ.shape[0]:
+        raise ValueError("features have %d rows, targets %d" % (feat.shape[0], targ.shape[0]))
+    return int(feat.shape[0])
+
+
 def surrogate_grad_noalloc(params, feat, targ, grad, loss):
     """Loss and gradient of Eq. (19) without any device allocation by the library:
     params [2312], feat [n, 27], targ [n, 8], grad [2312] (out) FP32 and loss [1]
-    FP64 (out) are all caller-owned CUDA tensors; n <= 32768."""
+    FP64 (out) are all caller-owned CUDA tensors on the current device; n <= 32768.
+    The C entry point sees only pointers, so every size and the device are checked
+    here, before anything is launched (ValueError / TypeError)."""
+    n = _rows(feat, targ)
+    if params.numel() != NPARAM or grad.numel() != NPARAM:
+        raise ValueError("params and grad must hold %d values, got %d and %d"
+                         % (NPARAM, params.numel(), grad.numel()))
+    if loss.numel() < 1:
+        raise ValueError("loss must hold at least one value")
+    tensors = (params, feat, targ, grad, loss)
+    if not all(isinstance(t, torch.Tensor) and t.is_cuda for t in tensors):
+        raise TypeError("expected CUDA tensors")
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in tensors):
+        raise ValueError("every tensor must be on the current CUDA device (cuda:%d)" % dev)
     _check(lib().sn_surrogate_grad_noalloc(_dev(params, torch.float32), _dev(feat, torch.float32, (27,)),
-                                           _dev(targ, torch.float32, (8,)), feat.shape[0],
+                                           _dev(targ, torch.float32, (8,)), n,
                                            _dev(grad, torch.float32), _dev(loss, torch.float64), _stream()))
 
 
@@ -375,25 +401,28 @@ class Problem:
 
     def surrogate_grad(self, feat, targ):
         """(loss, gradient [2312]) of Eq. (19) at the current weights over all rows."""
+        n = _rows(feat, targ)
         self._sync_stream()
         g = np.zeros(NPARAM, dtype=np.float32)
         loss = ctypes.c_double(0)
         _check(lib().sn_surrogate_grad(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
-                                       feat.shape[0], _f32p(g), ctypes.byref(loss)), self.h)
+                                       n, _f32p(g), ctypes.byref(loss)), self.h)
         return loss.value, g
 
     def surrogate_fit(self, feat, targ, steps, batch, lr):
+        n = _rows(feat, targ)
         self._sync_stream()
         loss = ctypes.c_double(0)
         _check(lib().sn_surrogate_fit(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
-                                      feat.shape[0], int(steps), int(batch), float(lr), ctypes.byref(loss)), self.h)
+                                      n, int(steps), int(batch), float(lr), ctypes.byref(loss)), self.h)
         return loss.value
 
     def surrogate_eval(self, feat, targ):
+        n = _rows(feat, targ)
         self._sync_stream()
         mae = ctypes.c_double(0)
         _check(lib().sn_surrogate_eval(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
-                                       feat.shape[0], ctypes.byref(mae)), self.h)
+                                       n, ctypes.byref(mae)), self.h)
         return mae.value
 
     def surrogate_train(self, in27, n_test, steps, batch, lr, seed=0):
@@ -423,6 +452,12 @@ class Problem:
         b = ctypes.c_int64(0)
         _check(lib().sn_surrogate_stats(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
         return a.value, b.value
+
+    def selftest_wait(self, limit_cycles=100000):
+        """Run the bounded-wait self-test (sn_selftest_wait); returns its status code
+        (SN_ETIMEOUT when the withheld wait gave up as designed)."""
+        self._sync_stream()
+        return int(lib().sn_selftest_wait(self.h, int(limit_cycles)))
 
     # ---- the paper's per-octant networks (Sec. 3, Sec. 4) ----
     def octnet_init(self, lo, hi, seed=0):

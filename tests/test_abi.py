@@ -106,3 +106,40 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(sn, "_LIB", None)
     with pytest.raises(RuntimeError):
         sn.lib()
+
+
+@pytest.mark.parametrize("case", ["targ_rows", "feat_width", "targ_width", "params_len", "grad_len", "loss_empty"])
+def test_noalloc_wrapper_refuses_bad_sizes_before_launch(case, monkeypatch):
+    """The allocation-free gradient's C entry point sees only pointers, so its
+    binding checks every size first: a short target, gradient or parameter array
+    would otherwise become an out-of-bounds access on the device.  Each bad size is
+    refused with ValueError before the library is even loaded."""
+    import torch
+    from paper_1906_04017_gb300 import sn
+
+    def no_launch():
+        raise AssertionError("the library was reached")
+    monkeypatch.setattr(sn, "lib", no_launch)
+    n = 64
+    t = {"params": torch.zeros(sn.NPARAM), "feat": torch.zeros(n, 27), "targ": torch.zeros(n, 8),
+         "grad": torch.zeros(sn.NPARAM), "loss": torch.zeros(1, dtype=torch.float64)}
+    bad = {"targ_rows": ("targ", torch.zeros(n - 1, 8)), "feat_width": ("feat", torch.zeros(n, 26)),
+           "targ_width": ("targ", torch.zeros(n, 9)), "params_len": ("params", torch.zeros(sn.NPARAM - 1)),
+           "grad_len": ("grad", torch.zeros(100)), "loss_empty": ("loss", torch.zeros(0, dtype=torch.float64))}
+    k, v = bad[case]
+    t[k] = v
+    with pytest.raises(ValueError):
+        sn.surrogate_grad_noalloc(t["params"], t["feat"], t["targ"], t["grad"], t["loss"])
+
+
+def test_noalloc_wrapper_refuses_host_tensors(monkeypatch):
+    """Right sizes, but host tensors: refused (TypeError) before the library is reached."""
+    import torch
+    from paper_1906_04017_gb300 import sn
+
+    def no_launch():
+        raise AssertionError("the library was reached")
+    monkeypatch.setattr(sn, "lib", no_launch)
+    with pytest.raises(TypeError):
+        sn.surrogate_grad_noalloc(torch.zeros(sn.NPARAM), torch.zeros(8, 27), torch.zeros(8, 8),
+                                  torch.zeros(sn.NPARAM), torch.zeros(1, dtype=torch.float64))

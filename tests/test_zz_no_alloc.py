@@ -23,8 +23,8 @@ def test_noalloc_gradient_matches_allocating_entry_point(sn):
     params = torch.from_numpy(p).cuda()
     grad = torch.empty(sn.NPARAM, dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
-    # two calls in a row, the second one smaller, so stale partials of the first
-    # call would show up in the second if they were read
+    # two calls in a row of different sizes: each call writes every partial it
+    # reads, and this pins equality with the allocating path across call sizes
     for n, seed in ((20000, 1), (3000, 2)):
         x = torch.from_numpy(W.onecell_problems(n, seed=seed).astype(np.float32)).cuda()
         feat, targ = sn.surrogate_prepare(x)
