@@ -79,6 +79,8 @@ def _declare(L):
     Mp = ctypes.POINTER(Mlp)
     L.or_mlp_cell_batch.argtypes = [Mp, ctypes.c_long, _dp, _dp]
     L.or_sweep_mlp.argtypes = [P, Mp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    L.or_sweep_mlp_gated.argtypes = [P, Mp, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_long)]
     L.or_adjoint.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp,
                              ctypes.POINTER(ctypes.c_int)]
 
@@ -247,20 +249,29 @@ class OracleProblem:
             raise ZeroDivisionError("zero pivot")
         return psi, tal
 
-    def sweep(self, S, groups=None, dirs=None, octnet=None, mlp=None):
+    def sweep(self, S, groups=None, dirs=None, octnet=None, mlp=None, gate=None):
         """phi[G,ncell,8] = sum_d w_d psi_d for the isotropic source S[G,ncell,8].
 
         ``groups`` / ``dirs`` are (begin, end) ranges; phi is zero outside them.
         ``octnet`` = (P [8, 288], lo [8, 26], hi [8, 26]) replaces every per-cell
         solve by the octant networks (oracle.octant_net); ``mlp`` = (p [2312], bf16)
         by the workload's surrogate network (oracle.mlp, with the BF16 rounding steps
-        if bf16).  Returns (phi, tallies[4])."""
+        if bf16); with ``gate`` = tau as well, a cell keeps the network's prediction
+        only where its residual passes ||b - A psi|| <= tau ||b|| and is solved by
+        elimination otherwise (the count is left in ``self.last_fallbacks``).
+        Returns (phi, tallies[4])."""
         S = _f64(S).reshape(self.G, self.ncell, 8)
         g0, g1 = groups if groups else (0, self.G)
         d0, d1 = dirs if dirs else (0, self.ndir)
         phi = np.zeros((self.G, self.ncell, 8))
         tal = np.zeros(4)
-        if mlp is not None:
+        if mlp is not None and gate is not None:
+            net = _MlpArrays(*mlp)
+            nfb = ctypes.c_long(0)
+            rc = lib().or_sweep_mlp_gated(ctypes.byref(self.c), ctypes.byref(net.c), float(gate), _p(S), _p(phi),
+                                          g0, g1, d0, d1, _p(tal), ctypes.byref(nfb))
+            self.last_fallbacks = int(nfb.value)
+        elif mlp is not None:
             net = _MlpArrays(*mlp)
             rc = lib().or_sweep_mlp(ctypes.byref(self.c), ctypes.byref(net.c), _p(S), _p(phi), g0, g1, d0, d1,
                                     _p(tal))

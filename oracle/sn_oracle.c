@@ -871,6 +871,60 @@ int or_sweep_mlp(const or_problem *p, const or_mlp *net, const double *S, double
     return rc;
 }
 
+/* The same with the residual gate of the surrogate form: the network's     */
+/* prediction psi of a cell is kept when ||b - A psi||_2 <= tau ||b||_2 for */
+/* the cell's own system (14) (FP64, assembled as above), else the cell is */
+/* solved by elimination.  *fallbacks (may be NULL) receives the number of */
+/* cells sent to elimination.  tau = 0 gives or_sweep's flux, a tau above  */
+/* every residual or_sweep_mlp's.                                          */
+typedef struct {
+    or_mlp_prepared m;
+    or_elem e;
+    double tau;
+    long fallbacks;
+} or_mlp_gated;
+
+static void mlp_gated_cb(const void *ctx, const double *in27, double *psi)
+{
+    or_mlp_gated *m = (or_mlp_gated *)ctx;
+    mlp_cell(m->m.q, m->m.bf16, in27, psi);
+    double A[64], b[8];
+    assemble(&m->e, in27, in27[6], in27 + 7, in27 + 15, A, b);
+    double rr = 0.0, bb = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        double r = b[k];
+        for (int j = 0; j < 8; ++j) r -= A[8 * k + j] * psi[j];
+        rr += r * r;
+        bb += b[k] * b[k];
+    }
+    if (!(rr <= m->tau * m->tau * bb)) {
+        double x[8];
+        if (or_ge(8, A, b, x) == 0)
+            for (int k = 0; k < 8; ++k) psi[k] = x[k];
+        else
+            for (int k = 0; k < 8; ++k) psi[k] = NAN;
+#pragma omp atomic
+        m->fallbacks += 1;
+    }
+}
+
+int or_sweep_mlp_gated(const or_problem *p, const or_mlp *net, double tau, const double *S, double *phi, int g0,
+                       int g1, int d0, int d1, double *tal, long *fallbacks)
+{
+    or_mlp_gated *m = (or_mlp_gated *)malloc(sizeof(or_mlp_gated));
+    if (!m) return -1;
+    mlp_params(net, m->m.q);
+    m->m.bf16 = net->bf16;
+    or_element(p->dx, p->dy, p->dz, m->e.M, m->e.L, m->e.G, m->e.F);
+    m->tau = tau;
+    m->fallbacks = 0;
+    const or_cellnet cn = {mlp_gated_cb, m};
+    const int rc = sweep_range(p, &cn, S, phi, g0, g1, d0, d1, tal);
+    if (fallbacks) *fallbacks = m->fallbacks;
+    free(m);
+    return rc;
+}
+
 /* Isotropic source build (Eqs. (2), (6) with the P_0 term only):           */
 /* S_g = (sum_g' xfer[g'][g] sigs_g' phi_g' + q_g) / (4 pi), nodal.           */
 void or_source(const or_problem *p, const double *phi, double *S)

@@ -530,6 +530,102 @@ __device__ __forceinline__ void residual_A(float t3x, float t3y, float t3z, floa
     }
 }
 
+#ifndef SN_KEY_F32X2
+#define SN_KEY_F32X2 1
+#endif
+
+// The key sweep's solve with the matrix held as column pairs: the trailing-row
+// updates of the diagonal elimination are two-lane fused multiply-adds
+// (fma.rn.f32x2, each lane rounded as fmaf), so the results are those of the scalar
+// form bit for bit with about half the update instructions.  Same pivoting test,
+// exchange path and refinement step as cell_solve_key below.
+template <bool REFINE>
+__device__ __forceinline__ void cell_solve_key_x2(float t3x, float t3y, float t3z, float sig, const float (&Sm)[8],
+                                                  const float (&ux)[4], const float (&uy)[4], const float (&uz)[4],
+                                                  float (&x)[8])
+{
+    float2 A[8][4];
+    {
+        float As[8][8];
+        assemble_A27(t3x, t3y, t3z, sig, As);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) A[k][q] = make_float2(As[k][2 * q], As[k][2 * q + 1]);
+        }
+    }
+    float b[8], b0[8], rinv[8];
+    build_b_msrc(2.f * t3x, 2.f * t3y, 2.f * t3z, Sm, ux, uy, uz, b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b0[k] = b[k];
+    bool ex = false;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int kq = k >> 1, kl = k & 1;
+        float m = fabsf(pel(A[k + 1][kq], kl));
+#pragma unroll
+        for (int r = k + 2; r < 8; ++r) m = fmaxf(m, fabsf(pel(A[r][kq], kl)));
+        ex |= m > fabsf(pel(A[k][kq], kl));
+        rinv[k] = pivot_recip(pel(A[k][kq], kl));
+#pragma unroll
+        for (int r = k + 1; r < 8; ++r) {
+            const float l = pel(A[r][kq], kl) * rinv[k];
+            const float2 nl = make_float2(-l, -l);
+#pragma unroll
+            for (int q = kq; q < 4; ++q) {
+                if (2 * q + 1 <= k) continue;          // both columns at or left of k
+                A[r][q] = __ffma2_rn(nl, A[k][q], A[r][q]);
+            }
+            pel(A[r][kq], kl) = l;                     // multiplier in place
+            b[r] = fmaf(-l, b[k], b[r]);
+        }
+    }
+    rinv[7] = pivot_recip(A[7][3].y);
+#pragma unroll
+    for (int r = 7; r >= 0; --r) {
+        float sum = b[r];
+#pragma unroll
+        for (int c = r + 1; c < 8; ++c) sum = fmaf(-pel(A[r][c >> 1], c & 1), x[c], sum);
+        x[r] = sum * rinv[r];
+    }
+    // warp-uniform test: the exchange path stays off the instruction stream unless a
+    // lane of the warp needs it
+    if (__any_sync(__activemask(), ex) && ex) {
+        float As[8][8], bb[8], rp[8];
+        assemble_A27(t3x, t3y, t3z, sig, As);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) bb[k] = b0[k];
+        unsigned piv;
+        ge8_factor_solve(As, bb, piv, rp, x);
+        if (REFINE) {
+            float r[8], dx[8];
+            residual_A(t3x, t3y, t3z, sig, x, b0, r);
+            ge8_replay(As, piv, rp, r, dx);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] += dx[k];
+        }
+        return;
+    }
+    if (REFINE) {
+        float r[8], dx[8];
+        residual_A(t3x, t3y, t3z, sig, x, b0, r);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+#pragma unroll
+            for (int q = k + 1; q < 8; ++q) r[q] = fmaf(-pel(A[q][k >> 1], k & 1), r[k], r[q]);
+        }
+#pragma unroll
+        for (int q = 7; q >= 0; --q) {
+            float sum = r[q];
+#pragma unroll
+            for (int c = q + 1; c < 8; ++c) sum = fmaf(-pel(A[q][c >> 1], c & 1), dx[c], sum);
+            dx[q] = sum * rinv[q];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] += dx[k];
+    }
+}
+
 // The key sweep's solve: GE with partial pivoting (diagonal pivots first, exchange
 // path where the pivoting test fails) and, with REFINE, one FP32 refinement step.
 template <bool REFINE>
@@ -537,6 +633,10 @@ __device__ __forceinline__ void cell_solve_key(float t3x, float t3y, float t3z, 
                                                const float (&ux)[4], const float (&uy)[4], const float (&uz)[4],
                                                float (&x)[8])
 {
+    if constexpr (SN_KEY_F32X2) {
+        cell_solve_key_x2<REFINE>(t3x, t3y, t3z, sig, Sm, ux, uy, uz, x);
+        return;
+    }
     float A[8][8], b[8], b0[8], rinv[8];
     assemble_A27(t3x, t3y, t3z, sig, A);
     build_b_msrc(2.f * t3x, 2.f * t3y, 2.f * t3z, Sm, ux, uy, uz, b);

@@ -134,6 +134,9 @@ struct sn_handle_s {
     void *sigs_n = nullptr;
     void *yhat = nullptr;
 
+    // unit tables of the wavefront kernel of the key sweep (sn_sweep_keys.cu)
+    void *wave = nullptr;
+
     // the paper's per-octant networks (sn_octnet_init / sn_octnet_set)
     bool has_octnet = false;
     void *octnet = nullptr;
@@ -177,6 +180,8 @@ sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gat
 // the key sweep (sn_sweep_keys.cu): FP32 elimination on box cells, isotropic scattering
 bool key_sweep_ok(sn_handle h);
 sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st);
+sn_status build_wave(sn_handle h);
+void free_wave(sn_handle h);
 // zero the surrogate's fallback / timeout counters (stream-ordered)
 sn_status reset_ann_counters(sn_handle h, cudaStream_t st);
 sn_status check_ann_timeouts(sn_handle h);
@@ -196,7 +201,8 @@ enum AccSlot {
     ACC_FLAG = 7,      // non-zero: a non-finite flux value was seen
     ACC_HARVEST = 8,   // sn_harvest: number of solves picked (unsigned 64-bit)
     ACC_RESP = 9,      // sn_response: sum resp * phi
-    ACC_COUNT = 10
+    ACC_ABORT = 10,    // non-zero: a bounded wait of the wavefront sweep gave up
+    ACC_COUNT = 11
 };
 
 }  // namespace sn

@@ -167,6 +167,7 @@ static void release(sn_handle h)
     for (int i = 0; i < 2; ++i)
         if (h->graphs.exec[i]) cudaGraphExecDestroy(h->graphs.exec[i]);
     free_adjoint(h);
+    free_wave(h);
     void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->dir_abs, h->plane_cells, h->plane_pos,
                     h->face, h->phi_oct, h->S, h->phi_b, h->acc, h->sigs_n, h->yhat, h->geom, h->vnode, h->omabs, h->geomB};
     for (void *b : bufs)
@@ -428,6 +429,7 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaStreamCreate"));
     }
     SN_TRY(reduce_configure(h));
+    SN_TRY(build_wave(h));
     {
         // the uploads above are queued on the handle's stream (from pageable host
         // memory: staged before each call returns); the handle is complete once they land

@@ -1229,6 +1229,7 @@ sn_status sn_sweep(sn_handle h, const void *S, void *phi, sn_solve_mode mode)
     SN_CK(h, cudaStreamSynchronize(st));
     prof_collect(h);
     take_tallies(h);
+    if (h->acc_host[ACC_ABORT] != 0.0) return fail(h, SN_ETIMEOUT, "sn_sweep: a bounded wait of the sweep gave up");
     if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) return check_ann_timeouts(h);
     return SN_OK;
 }
@@ -1297,6 +1298,7 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
         cmax = a[ACC_PMAX] > 0 ? a[ACC_DMAX] / a[ACC_PMAX] : 0.0;
         cmean = a[ACC_MEANN] > 0 ? a[ACC_MEAN] / a[ACC_MEANN] : 0.0;
         take_tallies(h);
+        if (a[ACC_ABORT] != 0.0) return fail(h, SN_ETIMEOUT, "sn_source_iterate: a bounded wait of the sweep gave up");
         if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
             s = check_ann_timeouts(h);
             if (s != SN_OK) return s;

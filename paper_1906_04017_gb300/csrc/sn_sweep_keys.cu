@@ -6,7 +6,7 @@
 // cell's system (14) for a chunk of the octant's directions in turn (all of them
 // where the hyperplane has enough keys to fill the GPU; on the small hyperplanes at
 // the two ends of the wavefront the directions are split over NCH threads so that
-// the launch still has enough threads).  Everything a key's directions share is
+// the work still spreads over the GPU).  Everything a key's directions share is
 // done once per key: the cell, its opacity, the source term (Mh x Mh x Mh) S of the
 // right-hand side (ge8.cuh), the face-plane offsets; the scalar-flux partial
 // sum_d w_d psi_d of Eqs. (9), (13) accumulates in registers in a fixed direction
@@ -18,20 +18,35 @@
 // are whole 128-byte lines.  A cell reads its inflow slot and overwrites it with its
 // outflow (within one hyperplane every slot belongs to one cell).  On the inflow
 // boundary the key reads a 4-vector holding psi_inc of its group and face, stored
-// after the planes, with a direction stride of zero, so the direction loop has no
-// boundary test; on the outflow boundary the outflow is stored like any other, and
-// after the last hyperplane every slot holds the outflow of the last cell of its
-// column: the leakage kernel below sums the boundary leakage from them.
+// after the planes, in place of the slot, so the direction loop has no boundary
+// test; on the outflow boundary the outflow is stored like any other, and after the
+// last hyperplane every slot holds the outflow of the last cell of its column: the
+// leakage kernel below sums the boundary leakage from them.
 //
 // Prefetch.  The next direction's three inflow faces are copied into a per-thread
-// shared-memory stage (cp.async) while the current direction is solved.  A key's
-// cell, opacity and source are read before the kernel waits for the previous
-// hyperplane (programmatic dependent launch): none of them is written by the sweep.
+// shared-memory stage (cp.async, L2 only) while the current direction is solved.  A
+// key's cell, opacity and source are read before the key waits for its upwind
+// neighbours: none of them is written by the sweep.
+//
+// Scheduling.  Two forms share the per-key work:
+//  * the wavefront kernel (sweep_ge_wave), one persistent launch per sweep: work
+//    units (hyperplane s, octant o, a tile of keys) are handed out in wavefront order
+//    by an atomic counter; a unit waits only for the units of hyperplane s - 1 that
+//    hold its cells' upwind neighbours (a done flag per unit, release / acquire at GPU
+//    scope), so a unit starts as soon as its own inputs exist and no hyperplane waits
+//    for the slowest tile of the previous one.  A unit waits only for units handed
+//    out before it, to CTAs that are already running, so the wait always ends; every
+//    wait is bounded all the same (2^31 SM cycles, about 1 s), after which the CTA
+//    raises the sweep's abort flag, every CTA stops, and the call returns SN_ETIMEOUT;
+//  * the per-hyperplane kernel (sweep_ge_keys), one launch per hyperplane ordered by
+//    programmatic dependent launch, used when the unit tables are absent.
 //
 // The flux partials go to phi_oct[o][c][g][8] (physical node order); the reduction
-// kernel of sn_sweep.cu sums the eight octants in a fixed order.  Nothing is atomic:
-// the flux is bit-reproducible run to run.
+// kernel of sn_sweep.cu sums the eight octants in a fixed order.  Nothing is atomic
+// but the hand-out of units: the flux is bit-reproducible run to run.
 #include <algorithm>
+#include <climits>
+#include <vector>
 
 #include "ge8.cuh"
 #include "sn_internal.cuh"
@@ -39,8 +54,11 @@
 
 namespace sn {
 
-constexpr int kKeyBlock = 128;   // threads a CTA
-constexpr int kKeyMaxDo = 64;    // directions per octant the kernel takes
+#ifndef SN_KEY_BLOCK
+#define SN_KEY_BLOCK 128
+#endif
+constexpr int kKeyBlock = SN_KEY_BLOCK;   // threads a CTA
+constexpr int kKeyMaxDo = 64;             // directions per octant the kernels take
 // CTAs per SM: 3 (168 registers a thread) measured faster on blocked_64 than 4
 // (128 registers, with spills of the refined solve): 5.55 against 5.91 ms a sweep
 #ifndef SN_KEY_MINBLOCKS
@@ -49,37 +67,51 @@ constexpr int kKeyMaxDo = 64;    // directions per octant the kernel takes
 
 struct KeyArgs {
     int nx, ny, nz, G, Do, C;
-    int nkeys;                   // keys of one octant on this hyperplane (cells x G)
+    int nkeys;                   // per-hyperplane kernel: keys of one octant (cells x G)
     FastDiv divG;                // key -> (cell of the hyperplane, group)
-    const uint32_t *cells;       // packed (i',j',k') of the hyperplane's cells
+    const uint32_t *cells;       // per-hyperplane kernel: packed (i',j',k') of its cells
     const float *sigt;           // [G][C]
     const float *S;              // [G][C][8]
     const float4 *dir;           // [Do] (3|Omega_x|/dx, 3|Omega_y|/dy, 3|Omega_z|/dz, w)
     float4 *face;                // x-planes | y-planes | z-planes | inflow vectors [G][6]
     uint32_t off_y, off_z, off_in;
     float *phi_oct;              // [8][C][G][8]
+    // wavefront kernel
+    const uint32_t *all_cells;   // the hyperplane table (h->plane_cells)
+    const uint32_t *plane_off;   // [nplanes + 1] offsets into it
+    const int4 *units;           // [nunits] see sweep_ge_wave
+    uint32_t *flags;             // [nunits] done flags (zeroed before the sweep)
+    uint32_t *next;              // hand-out counter (zeroed before the sweep)
+    double *abort;               // the sweep's abort flag (an accumulator slot, zeroed)
+    int nunits;
 };
 
-template <bool REFINE, int NCH>
-__global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(KeyArgs a)
-{
-    constexpr int KB = kKeyBlock / NCH;                       // keys a CTA
-    __shared__ __align__(16) float4 stage[2][3][kKeyBlock];  // per-thread inflow stages
-    __shared__ __align__(16) float4 msrc[2][kKeyBlock];      // per-thread (Mh x Mh x Mh) S
-    __shared__ __align__(16) float4 dsm[kKeyMaxDo];
-    __shared__ __align__(16) float red[NCH > 1 ? NCH * KB * 8 : 4];
-    __shared__ int kdst[kKeyBlock];
-    griddep_launch();
-    const int t = threadIdx.x, o = blockIdx.y;
-    const int chunk = t / KB, lk = t - chunk * KB;
-    const int key = (int)blockIdx.x * KB + lk;
-    const bool act = key < a.nkeys;
-    const int Do = a.Do, G = a.G;
-    const int d0 = chunk * Do / NCH, d1 = (chunk + 1) * Do / NCH;
-    for (int e = t; e < Do; e += kKeyBlock) dsm[e] = a.dir[e];
+struct KeySmem {
+    float4 stage[2][3][kKeyBlock];   // per-thread inflow stages
+    float4 msrc[2][kKeyBlock];       // per-thread (Mh x Mh x Mh) S
+    float4 dsm[kKeyMaxDo];           // direction table
+    float red[8 * kKeyBlock];        // chunk partials of the flux (more than one chunk)
+    int kdst[kKeyBlock];             // flux-partial index of each thread's key
+};
 
-    // the key: set-up tables and the sweep's inputs only, so this runs while the
-    // previous hyperplane may still be running
+// Work of one CTA on one tile of keys: keys key0 .. key0 + KB - 1 of octant o on a
+// hyperplane with `cells` and nkeys keys an octant, its directions split in 2^lch
+// chunks (KB = kKeyBlock >> lch keys a tile).  wait() runs after the keys' set-up,
+// must contain a CTA barrier, and returns once the upwind faces are complete (false:
+// give the tile up).  Returns false if the tile was given up.
+template <bool REFINE, typename Wait>
+__device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem &sm, int o, const uint32_t *cells, int nkeys,
+                                         int key0, int lch, Wait wait)
+{
+    const int t = threadIdx.x;
+    const int KB = kKeyBlock >> lch;
+    const int chunk = t >> (31 - __clz(KB)), lk = t & (KB - 1);
+    const int key = key0 + lk;
+    const bool act = key < nkeys;
+    const int Do = a.Do, G = a.G;
+    const int nch = 1 << lch;
+    const int d0 = chunk * Do / nch, d1 = (chunk + 1) * Do / nch;
+
     float sig = 0.f;
     uint32_t ou0 = 0, ou1 = 0, ou2 = 0;   // this direction's slots
     uint32_t inb = 0, bnd = 0;            // inflow vectors of the key's group; inflow-boundary axes
@@ -87,7 +119,7 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
     if (act) {
         const uint32_t cidx = a.divG.div((uint32_t)key);
         const int g = key - (int)cidx * G;
-        const uint32_t pk = a.cells[cidx];
+        const uint32_t pk = cells[cidx];
         const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
         const int i = (o & 1) ? a.nx - 1 - ip : ip;
         const int j = (o & 2) ? a.ny - 1 - jp : jp;
@@ -102,8 +134,8 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
         mh_axis<0>(Sm);
         mh_axis<1>(Sm);
         mh_axis<2>(Sm);
-        msrc[0][t] = make_float4(Sm[0], Sm[1], Sm[2], Sm[3]);
-        msrc[1][t] = make_float4(Sm[4], Sm[5], Sm[6], Sm[7]);
+        sm.msrc[0][t] = make_float4(Sm[0], Sm[1], Sm[2], Sm[3]);
+        sm.msrc[1][t] = make_float4(Sm[4], Sm[5], Sm[6], Sm[7]);
         const uint32_t DG = (uint32_t)(Do * G), first = (uint32_t)(d0 * G + g);
         ou0 = (uint32_t)(o * a.ny * a.nz + jp + a.ny * kp) * DG + first;
         ou1 = a.off_y + (uint32_t)(o * a.nx * a.nz + ip + a.nx * kp) * DG + first;
@@ -112,9 +144,8 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
         bnd = (ip == 0 ? 1u : 0u) | (jp == 0 ? 2u : 0u) | (kp == 0 ? 4u : 0u);
         dst = (o * a.C + c) * G + g;
     }
-    kdst[t] = dst;
-    __syncthreads();   // direction table
-    griddep_wait();    // the previous hyperplane's outflow faces are complete
+    sm.kdst[t] = dst;
+    if (!wait()) return false;
 
     float phi[8];
 #pragma unroll
@@ -122,7 +153,7 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
     if (act && d0 < d1) {
         constexpr uint32_t AX = kKeyBlock * 16;   // bytes between the faces of a stage
         constexpr uint32_t SP = 3 * AX;           // bytes between the two stages
-        const uint32_t sb = smem_u32(&stage[0][0][t]);
+        const uint32_t sb = smem_u32(&sm.stage[0][0][t]);
         // inflow slot of direction d: the outflow slot (in place), or on the inflow
         // boundary the group's psi_inc vector of that face (every direction)
         auto issue = [&](uint32_t buf, uint32_t s0, uint32_t s1, uint32_t s2) {
@@ -138,9 +169,9 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
             if (d + 1 < d1) issue((uint32_t)(cur ^ 1), ou0 + (uint32_t)G, ou1 + (uint32_t)G, ou2 + (uint32_t)G);
             cp_async_commit();
             cp_async_wait_pending<1>();   // this direction's faces have landed
-            const float4 fx = stage[cur][0][t], fy = stage[cur][1][t], fz = stage[cur][2][t];
-            const float4 m0 = msrc[0][t], m1 = msrc[1][t];
-            const float4 dd = dsm[d];
+            const float4 fx = sm.stage[cur][0][t], fy = sm.stage[cur][1][t], fz = sm.stage[cur][2][t];
+            const float4 m0 = sm.msrc[0][t], m1 = sm.msrc[1][t];
+            const float4 dd = sm.dsm[d];
             const float ux[4] = {fx.x, fx.y, fx.z, fx.w};
             const float uy[4] = {fy.x, fy.y, fy.z, fy.w};
             const float uz[4] = {fz.x, fz.y, fz.z, fz.w};
@@ -159,28 +190,108 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
         }
     }
     mirror8(phi, o);   // physical node order
-    if constexpr (NCH == 1) {
+    if (lch == 0) {
         if (act) {
-            float4 *p = reinterpret_cast<float4 *>(a.phi_oct) + 2 * (int64_t)kdst[t];
+            float4 *p = reinterpret_cast<float4 *>(a.phi_oct) + 2 * (int64_t)dst;
             p[0] = make_float4(phi[0], phi[1], phi[2], phi[3]);
             p[1] = make_float4(phi[4], phi[5], phi[6], phi[7]);
         }
     } else {
         // the chunks of a key add their partials in chunk order
-        float4 *r = reinterpret_cast<float4 *>(red + (chunk * KB + lk) * 8);
+        float4 *r = reinterpret_cast<float4 *>(sm.red + (chunk * KB + lk) * 8);
         r[0] = make_float4(phi[0], phi[1], phi[2], phi[3]);
         r[1] = make_float4(phi[4], phi[5], phi[6], phi[7]);
         __syncthreads();
         for (int e = t; e < KB * 8; e += kKeyBlock) {
             const int kk = e >> 3, n = e & 7;
-            const int dk = kdst[kk];   // chunk 0's thread of key kk
+            const int dk = sm.kdst[kk];   // chunk 0's thread of key kk
             if (dk < 0) continue;
-            float s = red[kk * 8 + n];
-#pragma unroll
-            for (int q = 1; q < NCH; ++q) s += red[(q * KB + kk) * 8 + n];
+            float s = sm.red[kk * 8 + n];
+            for (int q = 1; q < nch; ++q) s += sm.red[(q * KB + kk) * 8 + n];
             a.phi_oct[(int64_t)dk * 8 + n] = s;
         }
     }
+    return true;
+}
+
+// One launch per hyperplane (grid: tiles of one octant x 8 octants), ordered by
+// programmatic dependent launch.
+template <bool REFINE, int LCH>
+__global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(KeyArgs a)
+{
+    __shared__ __align__(16) KeySmem sm;
+    griddep_launch();
+    for (int e = threadIdx.x; e < a.Do; e += kKeyBlock) sm.dsm[e] = a.dir[e];
+    key_tile<REFINE>(a, sm, (int)blockIdx.y, a.cells, a.nkeys, (int)blockIdx.x * (kKeyBlock >> LCH), LCH, [] {
+        __syncthreads();   // direction table, key records
+        griddep_wait();    // the previous hyperplane's outflow faces are complete
+        return true;
+    });
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The persistent wavefront kernel (see the file header).  units[u] = (first key of
+// the tile within its hyperplane and octant, s | o << 12 | lch << 15, first unit of
+// hyperplane s - 1 it depends on, how many).  Thread 0 fetches the next unit's index
+// while the CTA works on the current one, and alone waits for the dependencies.
+template <bool REFINE>
+__global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(KeyArgs a)
+{
+    __shared__ __align__(16) KeySmem sm;
+    __shared__ int s_next, s_stop;
+    const int t = threadIdx.x;
+    for (int e = t; e < a.Do; e += kKeyBlock) sm.dsm[e] = a.dir[e];
+    if (t == 0) s_next = (int)atomicAdd(a.next, 1u);
+    __syncthreads();
+    for (;;) {
+        const int u = s_next;
+        if (u >= a.nunits) break;
+        __syncthreads();   // every thread has read s_next
+        const int4 ud = a.units[u];
+        if (t == 0) s_next = (int)atomicAdd(a.next, 1u);
+        const int s = ud.y & 4095, o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
+        const uint32_t c0 = a.plane_off[s], c1 = a.plane_off[s + 1];
+        const bool ok = key_tile<REFINE>(a, sm, o, a.all_cells + c0, (int)(c1 - c0) * a.G, ud.x, lch, [&] {
+            if (t == 0) {
+                int stop = 0;
+                const long long t0 = clock64();
+                for (int v = ud.z; v < ud.z + ud.w && !stop; ++v) {
+                    while (ld_acquire_u32(a.flags + v) == 0u) {
+                        if (*reinterpret_cast<volatile double *>(a.abort) != 0.0) {
+                            stop = 1;
+                            break;
+                        }
+                        if (clock64() - t0 > (1LL << 31)) {
+                            *reinterpret_cast<volatile double *>(a.abort) = 1.0;
+                            stop = 1;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                s_stop = stop;
+            }
+            __syncthreads();
+            return s_stop == 0;
+        });
+        if (!ok) break;
+        __syncthreads();   // every store of this unit has been issued
+        if (t == 0) {
+            __threadfence();
+            st_release_u32(a.flags + u, 1u);
+        }
+    }
+    cp_async_wait_all();
 }
 
 // Boundary leakage of a key sweep: after the last hyperplane every face slot holds
@@ -220,39 +331,146 @@ bool key_sweep_ok(sn_handle h)
            (uint64_t)h->face_in + 6ull * (uint64_t)h->G < (1ull << 32);
 }
 
-// Directions split over NCH threads a key on a hyperplane with `keys` keys (all
-// octants): the fewest chunks that still give the launch about one resident
-// thread per SM slot, and no more chunks than directions.
-static int key_chunks(int64_t keys, int Do)
+// log2 of the chunks a key's directions are split in on a hyperplane with `keys`
+// keys (all octants): the fewest that still give about one thread per resident
+// thread slot of the GPU, at most 8 chunks and no more chunks than directions.
+static int key_chunks_log2(int64_t keys, int Do)
 {
     const int64_t slots = (int64_t)num_sms() * SN_KEY_MINBLOCKS * kKeyBlock;
-    int nch = 1;
-    while (nch < 8 && 2 * nch <= Do && keys * nch < slots) nch *= 2;
-    return nch;
+    int l = 0;
+    while (l < 3 && (2 << l) <= Do && keys * (1 << l) < slots) ++l;
+    return l;
 }
 
-template <bool REFINE, int NCH>
+// Unit tables of the wavefront kernel (built once by sn_setup).
+struct WaveTables {
+    int4 *units = nullptr;
+    uint32_t *flags = nullptr;     // [nunits] done flags, then the hand-out counter
+    uint32_t *plane_off = nullptr;
+    int nunits = 0;
+    int grid = 0;
+};
+
+void free_wave(sn_handle h)
+{
+    if (!h || !h->wave) return;
+    WaveTables *w = static_cast<WaveTables *>(h->wave);
+    cudaFree(w->units);
+    cudaFree(w->flags);
+    cudaFree(w->plane_off);
+    delete w;
+    h->wave = nullptr;
+}
+
+// Units in wavefront order: hyperplane, octant, tile.  A tile covers kKeyBlock >> lch
+// consecutive keys (key = position of the cell within the hyperplane x G + g); it
+// depends on the tiles of hyperplane s - 1 of the same octant (the octants are
+// independent) that hold the upwind neighbours (i'-1,j',k'), (i',j'-1,k'),
+// (i',j',k'-1) of its cells: a contiguous range, since a hyperplane's cells are
+// listed by (k', j').
+// SN_KEY_WAVE=0 keeps the per-hyperplane launches (the form the wavefront kernel is
+// measured against)
+#ifndef SN_KEY_WAVE
+#define SN_KEY_WAVE 1
+#endif
+sn_status build_wave(sn_handle h)
+{
+    free_wave(h);
+    if (!SN_KEY_WAVE || !key_sweep_ok(h)) return SN_OK;
+    const int np = h->nplanes, G = h->G;
+    std::vector<uint32_t> cells(h->ncell), pos(h->ncell);
+    SN_CK(h, cudaMemcpyAsync(cells.data(), h->plane_cells, sizeof(uint32_t) * h->ncell, cudaMemcpyDeviceToHost,
+                             h->stream));
+    SN_CK(h, cudaMemcpyAsync(pos.data(), h->plane_pos, sizeof(uint32_t) * h->ncell, cudaMemcpyDeviceToHost, h->stream));
+    SN_CK(h, cudaStreamSynchronize(h->stream));
+    std::vector<int> lch(np), ntile(np);
+    std::vector<int64_t> first(np + 1);   // first unit of each hyperplane
+    first[0] = 0;
+    for (int s = 0; s < np; ++s) {
+        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+        lch[s] = key_chunks_log2(8 * n * G, h->Do);
+        const int64_t kb = kKeyBlock >> lch[s];
+        ntile[s] = (int)((n * G + kb - 1) / kb);
+        first[s + 1] = first[s] + 8 * (int64_t)ntile[s];
+    }
+    if (first[np] >= (1LL << 30) || np > 4095) return SN_OK;   // the per-hyperplane kernel serves it
+    std::vector<int4> units((size_t)first[np]);
+    for (int s = 0; s < np; ++s) {
+        const int64_t kb = kKeyBlock >> lch[s];
+        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+        const int64_t kbp = s > 0 ? (kKeyBlock >> lch[s - 1]) : 1;
+        for (int tl = 0; tl < ntile[s]; ++tl) {
+            int64_t dlo = 0, dn = 0;
+            if (s > 0) {
+                const int64_t p0 = tl * kb / G, p1 = std::min<int64_t>(n - 1, (tl * kb + kb - 1) / G);
+                int64_t lo = INT64_MAX, hi = -1;
+                for (int64_t q = p0; q <= p1; ++q) {
+                    const uint32_t pk = cells[h->plane_off[s] + q];
+                    const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
+                    const int nb[3][3] = {{ip - 1, jp, kp}, {ip, jp - 1, kp}, {ip, jp, kp - 1}};
+                    for (int m = 0; m < 3; ++m) {
+                        if (nb[m][0] < 0 || nb[m][1] < 0 || nb[m][2] < 0) continue;
+                        const int64_t lin = nb[m][0] + (int64_t)h->nx * (nb[m][1] + (int64_t)h->ny * nb[m][2]);
+                        const int64_t pp = pos[lin];
+                        lo = std::min(lo, pp);
+                        hi = std::max(hi, pp);
+                    }
+                }
+                if (hi >= 0) {
+                    dlo = lo * G / kbp;
+                    dn = (hi * G + G - 1) / kbp - dlo + 1;
+                }
+            }
+            for (int o = 0; o < 8; ++o) {
+                const int64_t u = first[s] + (int64_t)o * ntile[s] + tl;
+                units[u] = make_int4((int)(tl * kb), s | (o << 12) | (lch[s] << 15),
+                                     s > 0 ? (int)(first[s - 1] + (int64_t)o * ntile[s - 1] + dlo) : 0, (int)dn);
+            }
+        }
+    }
+    WaveTables *w = new WaveTables();
+    h->wave = w;
+    w->nunits = (int)first[np];
+    std::vector<uint32_t> poff(np + 1);
+    for (int s = 0; s <= np; ++s) poff[s] = (uint32_t)h->plane_off[s];
+    SN_CK(h, cudaMalloc(&w->units, sizeof(int4) * units.size()));
+    SN_CK(h, cudaMalloc(&w->flags, sizeof(uint32_t) * (units.size() + 1)));
+    SN_CK(h, cudaMalloc(&w->plane_off, sizeof(uint32_t) * poff.size()));
+    h->device_bytes += (int64_t)(sizeof(int4) * units.size() + sizeof(uint32_t) * (units.size() + 1 + poff.size()));
+    SN_CK(h, cudaMemcpyAsync(w->units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, h->stream));
+    SN_CK(h, cudaMemcpyAsync(w->plane_off, poff.data(), sizeof(uint32_t) * poff.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    int per_sm = 0;
+    SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_ge_wave<true>, kKeyBlock, 0));
+    int per_sm2 = 0;
+    SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, sweep_ge_wave<false>, kKeyBlock, 0));
+    w->grid = std::max(1, std::min(std::min(per_sm, per_sm2), SN_KEY_MINBLOCKS) * num_sms());
+    SN_CK(h, cudaStreamSynchronize(h->stream));
+    return SN_OK;
+}
+
+template <bool REFINE, int LCH>
 static cudaError_t launch_keys_plane(bool pdl, const KeyArgs &a, cudaStream_t st)
 {
-    constexpr int KB = kKeyBlock / NCH;
+    constexpr int KB = kKeyBlock >> LCH;
     const dim3 grid((unsigned)((a.nkeys + KB - 1) / KB), 8);
-    return launch_k(pdl, sweep_ge_keys<REFINE, NCH>, grid, dim3(kKeyBlock), 0, st, a);
+    return launch_k(pdl, sweep_ge_keys<REFINE, LCH>, grid, dim3(kKeyBlock), 0, st, a);
 }
 
 template <bool REFINE>
-static cudaError_t launch_keys_nch(int nch, bool pdl, const KeyArgs &a, cudaStream_t st)
+static cudaError_t launch_keys_lch(int lch, bool pdl, const KeyArgs &a, cudaStream_t st)
 {
-    switch (nch) {
+    switch (lch) {
+    case 0: return launch_keys_plane<REFINE, 0>(pdl, a, st);
     case 1: return launch_keys_plane<REFINE, 1>(pdl, a, st);
     case 2: return launch_keys_plane<REFINE, 2>(pdl, a, st);
-    case 4: return launch_keys_plane<REFINE, 4>(pdl, a, st);
-    default: return launch_keys_plane<REFINE, 8>(pdl, a, st);
+    default: return launch_keys_plane<REFINE, 3>(pdl, a, st);
     }
 }
 
 sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st)
 {
-    KeyArgs a;
+    KeyArgs a = {};
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
     a.divG = FastDiv((uint32_t)h->G);
     a.sigt = (const float *)h->sigt;
@@ -263,14 +481,32 @@ sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool re
     a.off_z = (uint32_t)(h->face_x + h->face_y);
     a.off_in = (uint32_t)h->face_in;
     a.phi_oct = phi_oct;
+    const WaveTables *w = static_cast<const WaveTables *>(h->wave);
+    if (w) {
+        a.all_cells = h->plane_cells;
+        a.plane_off = w->plane_off;
+        a.units = w->units;
+        a.flags = w->flags;
+        a.next = w->flags + w->nunits;
+        a.abort = h->acc + ACC_ABORT;
+        a.nunits = w->nunits;
+        SN_CK(h, cudaMemsetAsync(w->flags, 0, sizeof(uint32_t) * (size_t)(w->nunits + 1), st));
+    }
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
-    for (int s = 0; s < h->nplanes; ++s) {
-        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
-        a.cells = h->plane_cells + h->plane_off[s];
-        a.nkeys = (int)(n * h->G);
-        const int nch = key_chunks(8 * n * h->G, h->Do);
-        // hyperplanes after the first overlap their launch with the previous one's drain
-        SN_CK(h, refine ? launch_keys_nch<true>(nch, s > 0, a, st) : launch_keys_nch<false>(nch, s > 0, a, st));
+    if (w) {
+        if (refine)
+            sweep_ge_wave<true><<<w->grid, kKeyBlock, 0, st>>>(a);
+        else
+            sweep_ge_wave<false><<<w->grid, kKeyBlock, 0, st>>>(a);
+    } else {
+        for (int s = 0; s < h->nplanes; ++s) {
+            const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+            a.cells = h->plane_cells + h->plane_off[s];
+            a.nkeys = (int)(n * h->G);
+            const int lch = key_chunks_log2(8 * n * h->G, h->Do);
+            // hyperplanes after the first overlap their launch with the previous one's drain
+            SN_CK(h, refine ? launch_keys_lch<true>(lch, s > 0, a, st) : launch_keys_lch<false>(lch, s > 0, a, st));
+        }
     }
     SN_CK(h, cudaGetLastError());
     if (h->prof) {

@@ -158,6 +158,48 @@ def test_c_network_sweep_matches_the_python_sweep(order, bf16):
     assert np.abs(phi - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_c_gated_network_sweep_matches_the_python_sweep():
+    """The residual gate in the C oracle's network sweep (keep the network's psi where
+    ||b - A psi|| <= tau ||b|| for the cell's own system (14), else eliminate) against
+    the pure-Python upwind sweep that applies the same test with numpy and solves the
+    rejected cells with LAPACK: at a threshold that sends part of the cells to
+    elimination the fluxes agree to round-off and the fallback counts are equal; tau
+    = 0 gives the elimination sweep and a huge tau the ungated network sweep, bit for
+    bit."""
+    from _parity import network_sweep
+    wl = W.random_small(3, 4, 2, order=4, G=2, seed=8, psi_inc=True)
+    p = mlp.init_params(12) * 0.5
+    S = np.random.default_rng(2).uniform(0.0, 1.0, (2, 24, 8))
+
+    def gated(tau, record):
+        def predict(x):
+            psi = mlp.predict(p, x)
+            A, b = oracle.assemble(x[0])
+            r = np.linalg.norm(b - A @ psi[0]) / np.linalg.norm(b)
+            record.append(r)
+            return np.linalg.solve(A, b)[None] if r > tau else psi
+        return predict
+
+    first = []
+    network_sweep(wl, S, gated(np.inf, first))
+    tau = float(np.median(first))
+    ratios = []
+    ref = network_sweep(wl, S, gated(tau, ratios))
+    rejected = int(sum(r > tau for r in ratios))
+    assert 0.2 < rejected / len(ratios) < 0.8
+    assert min(abs(r / tau - 1.0) for r in ratios) > 1e-9      # no decision at the threshold
+    O = oracle.OracleProblem(wl)
+    phi, _ = O.sweep(S, mlp=(p, False), gate=tau)
+    assert O.last_fallbacks == rejected
+    assert np.abs(phi - ref).max() <= 1e-11 * np.abs(ref).max()
+    ge, _ = O.sweep(S)
+    g0, _ = O.sweep(S, mlp=(p, False), gate=0.0)
+    assert np.array_equal(g0, ge) and O.last_fallbacks == len(ratios)
+    un, _ = O.sweep(S, mlp=(p, True))
+    ginf, _ = O.sweep(S, mlp=(p, True), gate=1e300)
+    assert np.array_equal(ginf, un) and O.last_fallbacks == 0
+
+
 def test_bf16_rounding_is_nearest_even():
     """The rounding step itself: values exactly halfway between two BF16 numbers go
     to the even one, others to the nearest."""
