@@ -29,17 +29,22 @@ if ROOT not in sys.path:
 
 METRIC = "Sn sweep cell*dir*group solves/s (GE form, FP32 GE + 1 refinement step)"
 UNIT = "solves/s"
-# algorithmic FP32 flops of one solve: assembly 448 + right-hand side 120 + elimination
-# 372 + back substitution 64 + refinement 286 + flux 16
-FLOPS_PER_SOLVE = 1306
+# algorithmic FP32 flops of one solve, the fixed count of the GE form: assembly of A
+# (64 entries x 4 terms x 2) 512 + right-hand side (M S and three inflow faces) 224 +
+# LU with partial pivoting sum_{m=1..7} (m + 2 m^2) = 308 + two triangular solves 128 +
+# one refinement step (residual 128, solves 128, update 8) 264 + flux accumulation 16
+FLOPS_PER_SOLVE = 1450
 # algorithmic HBM bytes of one solve: 12 inflow + 12 outflow face floats
 BYTES_PER_SOLVE = 96
-# DRAM bytes (read + write) per solve of sweep_ge_tiles<float, 1, 10> measured by ncu on
-# blocked_64 hyperplane 95 (cold cache, full-set capture of one launch); None
+# DRAM bytes (read + write) per solve of the key sweep (sweep_ge_keys<true, 1>) measured
+# by ncu on blocked_64 hyperplane 95 (cold cache, full-set capture of one launch); None
 # once that kernel changes
-DRAM_BYTES_PER_SOLVE_NCU = 86.0
+DRAM_BYTES_PER_SOLVE_NCU = None
 FP32_LANES_PER_SM = 128
 N_SM = 152
+# this library's kernels in one source-iteration step: source build, the sweep kernel,
+# the boundary-leakage sum, the octant reduction
+LAUNCHES_PER_STEP = 4
 
 
 def workload_config():
@@ -126,33 +131,85 @@ def clock_summary(lines):
             "reasons": reasons, "samples": len(rows)}
 
 
+def oracle_sweep_timed(k_dirs=None):
+    """One FP64 oracle sweep of blocked_64 from the seeded source of the parity check
+    (uniform [0, 1], rounded to FP32 as the device sees it), all 8 groups in parallel on
+    the host cores, over the first k_dirs directions (all 80 by default).  Returns
+    (S [G, C, 8] FP32, phi [G, C, 8] FP64, seconds, solves)."""
+    import oracle
+    from paper_1906_04017_gb300 import workloads
+    wl = workloads.blocked_64()
+    P = oracle.OracleProblem(wl)
+    S = np.random.default_rng(0).uniform(0.0, 1.0, (P.G, P.ncell, 8)).astype(np.float32)
+    k = P.ndir if k_dirs is None else k_dirs
+    t0 = time.perf_counter()
+    phi, _ = P.sweep(S.astype(np.float64), dirs=(0, k))
+    dt = time.perf_counter() - t0
+    return S, phi, dt, P.ncell * P.G * k
+
+
+def single_thread_rate(seconds=2.0):
+    """Solves/s of the FP64 oracle on one thread: one group, the first directions."""
+    import oracle
+    from paper_1906_04017_gb300 import workloads
+    P = oracle.OracleProblem(workloads.blocked_64())
+    S = np.random.default_rng(0).uniform(0.0, 1.0, (P.G, P.ncell, 8))
+    t0 = time.perf_counter()
+    P.sweep(S, groups=(0, 1), dirs=(0, 1))
+    t1 = time.perf_counter() - t0
+    k = int(max(1, min(P.ndir, seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    P.sweep(S, groups=(0, 1), dirs=(0, k))
+    return P.ncell * k / (time.perf_counter() - t0), k
+
+
+def cpu_baseline_from(dt, solves, k_dirs):
+    import oracle
+    st, k1 = single_thread_rate()
+    return {"value": solves / dt, "unit": UNIT, "cores": min(8, oracle.num_threads()), "kind": "oracle",
+            "single_thread_value": st,
+            "sample": "blocked_64, one sweep of all 8 groups x %d of 80 directions (%d solves, %.1f s), FP64, "
+                      "groups in parallel; single thread: group 0 x %d directions" % (k_dirs, solves, dt, k1)}
+
+
+def parity_report(phi, ref):
+    """Element-by-element comparison of the device flux with the FP64 oracle's
+    (arrays [G, C, 8]): the per-group max-norm relative error, the pointwise relative
+    error where |ref| >= 1% of the group maximum, and the pointwise error floored at
+    1e-8 and 1e-6 of the group maximum (max and mean)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    out = {"maxnorm_rel": 0.0, "point_rel_at_1pct": 0.0, "point_rel_floored_1e-8max": 0.0,
+           "point_rel_floored_1e-6max": 0.0, "mean_rel_floored_1e-8max": 0.0}
+    means = []
+    for g in range(ref.shape[0]):
+        m = np.abs(ref[g]).max()
+        d = np.abs(phi[g] - ref[g])
+        a = np.abs(ref[g])
+        out["maxnorm_rel"] = max(out["maxnorm_rel"], float(d.max() / m))
+        sel = a >= 1e-2 * m
+        out["point_rel_at_1pct"] = max(out["point_rel_at_1pct"], float((d[sel] / a[sel]).max()))
+        r8 = d / (a + 1e-8 * m)
+        out["point_rel_floored_1e-8max"] = max(out["point_rel_floored_1e-8max"], float(r8.max()))
+        out["point_rel_floored_1e-6max"] = max(out["point_rel_floored_1e-6max"], float((d / (a + 1e-6 * m)).max()))
+        means.append(float(r8.mean()))
+    out["mean_rel_floored_1e-8max"] = float(np.mean(means))
+    return out
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle timed on a bounded sample of the same workload (all groups,
     the first k directions of one sweep from a fixed source) on the host cores."""
     import oracle
     from paper_1906_04017_gb300 import workloads
-    wl = workloads.blocked_64()
-    P = oracle.OracleProblem(wl)
-    rng = np.random.default_rng(0)
-    S = rng.uniform(0.0, 1.0, (P.G, P.ncell, 8))
+    P = oracle.OracleProblem(workloads.blocked_64())
+    S = np.random.default_rng(0).uniform(0.0, 1.0, (P.G, P.ncell, 8))
     t0 = time.perf_counter()
     P.sweep(S, dirs=(0, 1))
     t1 = time.perf_counter() - t0
     k = int(max(1, min(P.ndir, seconds_target / max(t1, 1e-3))))
-    t0 = time.perf_counter()
-    P.sweep(S, dirs=(0, k))
-    dt = time.perf_counter() - t0
-    solves = P.ncell * P.G * k
-    cores = min(P.G, oracle.num_threads())
-    # one group alone runs on one thread
-    k1 = max(1, k // 2)
-    t0 = time.perf_counter()
-    P.sweep(S, groups=(0, 1), dirs=(0, k1))
-    dt1 = time.perf_counter() - t0
-    return {"value": solves / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "single_thread_value": P.ncell * k1 / dt1,
-            "sample": "blocked_64, one sweep of all 8 groups x %d of 80 directions (%d solves, %.1f s), "
-                      "FP64, groups in parallel; single thread: group 0 x %d directions" % (k, solves, dt, k1)}
+    _, _, dt, solves = oracle_sweep_timed(k)
+    return cpu_baseline_from(dt, solves, k)
 
 
 def run_reference(args):
@@ -476,19 +533,25 @@ def geom_form(steps, ge_step_ms):
     return out
 
 
-def e2e_pipelined(P, S_host, phi_host, steps, stream):
-    """`steps` sweeps through the public API (sn_sweep) with every step's source
-    copied in from pinned host memory and its flux copied back, the copies on a
-    second stream with double buffers so that step i+1's source and step i's flux
-    move while a sweep runs.  Returns the milliseconds from the first copy's start
-    to the last copy's end (CUDA events)."""
+def e2e_pipelined(P, phi_in_host, phi_out_host, steps, stream):
+    """`steps` source-iteration steps through the public API (sn_source_iterate, one
+    iteration a call: source build, sweep, octant reduction with FP64 norms), each
+    starting from the flux copied in from pinned host memory and ending with its new
+    flux copied back to pinned host memory.  The host copies run on a second stream
+    into and out of two staging buffers, so step i+1's input and step i's result move
+    while a step runs; the step itself reads and writes one device flux buffer (the
+    one its captured graph was made for) through two device-to-device copies.
+    Returns the milliseconds from the first copy's start to the last copy's end (CUDA
+    events)."""
     import torch
     xs = torch.cuda.Stream()
-    S_dev = [torch.empty_like(S_host, device="cuda") for _ in range(2)]
-    phi_dev = [torch.empty_like(S_dev[0]) for _ in range(2)]
+    phi = P.flux_tensor()
+    inb = [torch.empty_like(phi) for _ in range(2)]
+    outb = [torch.empty_like(phi) for _ in range(2)]
     ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_used = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_res = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     xs.wait_event(e0)
@@ -496,8 +559,8 @@ def e2e_pipelined(P, S_host, phi_host, steps, stream):
     def copy_in(b, i):
         with torch.cuda.stream(xs):
             if i >= 2:
-                xs.wait_event(ev_done[b])       # the sweep that read this buffer is done
-            S_dev[b].copy_(S_host, non_blocking=True)
+                xs.wait_event(ev_used[b])       # the step that read this buffer has copied it
+            inb[b].copy_(phi_in_host, non_blocking=True)
             ev_in[b].record(xs)
 
     copy_in(0, 0)
@@ -506,13 +569,16 @@ def e2e_pipelined(P, S_host, phi_host, steps, stream):
         if i + 1 < steps:
             copy_in(1 - b, i + 1)
         stream.wait_event(ev_in[b])
+        phi.copy_(inb[b], non_blocking=True)
+        ev_used[b].record(stream)
+        P.source_iterate(phi=phi, tol=0.0, max_it=1, use_graph=True, allow_noconv=True)
         if i >= 2:
-            stream.wait_event(ev_out[b])        # the flux copy out of this buffer is done
-        P.sweep(S_dev[b], phi_dev[b])
-        ev_done[b].record(stream)
+            stream.wait_event(ev_out[b])        # the host copy out of this buffer is done
+        outb[b].copy_(phi, non_blocking=True)
+        ev_res[b].record(stream)
         with torch.cuda.stream(xs):
-            xs.wait_event(ev_done[b])
-            phi_host.copy_(phi_dev[b], non_blocking=True)
+            xs.wait_event(ev_res[b])
+            phi_out_host.copy_(outb[b], non_blocking=True)
             ev_out[b].record(xs)
     stream.wait_event(ev_out[(steps - 1) % 2])
     e1.record(stream)
@@ -561,7 +627,7 @@ def run_gpu(args):
     clk = clocks.stop()
     assert r["iters"] == args.steps
 
-    # the dominant kernel alone: CUDA events around each sweep's hyperplane launches
+    # the dominant kernel alone: CUDA events around each sweep's kernel
     P.set_profiling(True)
     P.source_iterate(phi=phi, tol=0.0, max_it=2, use_graph=False, allow_noconv=True)
     P.profile(reset=True)
@@ -569,14 +635,31 @@ def run_gpu(args):
     sweep_ms, nsw = P.profile(reset=True)
     P.set_profiling(False)
 
-    # end to end through the public API with host buffers: pinned S in, phi out
-    rng = np.random.default_rng(0)
-    S_host = torch.from_numpy(rng.uniform(0, 1, (P.G, P.ncell, 8)).astype(np.float32)).pin_memory()
-    phi_host = torch.empty_like(S_host).pin_memory()
-    e2e_pipelined(P, S_host, phi_host, 2, stream)
+    # end to end through the public API with host buffers: pinned flux in, flux out,
+    # every step one source iteration (the work `value` times)
+    phi_in_host = phi.cpu().pin_memory()
+    phi_out_host = torch.empty_like(phi_in_host).pin_memory()
+    e2e_pipelined(P, phi_in_host, phi_out_host, 2, stream)
     barrier()
-    e2e_ms = e2e_pipelined(P, S_host, phi_host, args.steps, stream)
+    e2e_ms = e2e_pipelined(P, phi_in_host, phi_out_host, args.steps, stream)
     barrier()
+
+    # parity of the measured kernel against the FP64 oracle: one sweep of the same
+    # seeded source on the device and in the oracle (whose timing is the CPU baseline)
+    parity = cb = None
+    if not args.no_cpu_baseline:
+        def parity_and_baseline():
+            S32, ref, dt, ns = oracle_sweep_timed()
+            got = P.sweep(torch.from_numpy(S32).cuda(), mode=sn.GE32R).cpu().numpy()
+            rep = parity_report(got, ref)
+            rep["what"] = ("one GE32R sweep of blocked_64 (all 8 groups, 80 directions, uniform [0, 1] source, "
+                           "seed 0) against the FP64 oracle's sweep of the same FP32-rounded source")
+            return rep, cpu_baseline_from(dt, ns, 80)
+        res = guarded(parity_and_baseline)
+        if isinstance(res, tuple):
+            parity, cb = res
+        else:
+            parity = cb = res
 
     ann = None if args.no_ann else guarded(ann_form, P, args.steps)
     octnet = None if args.no_octnet else guarded(octnet_form, P)
@@ -607,25 +690,30 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(), parallelism="replicas" if ws > 1 else "single"),
-        "roofline": {"bound": "alu", "kernel": "sweep_ge_tiles<float, refine, 10>", "achieved": achieved_tf,
+        "config": workload_config(),
+        "roofline": {"bound": "alu", "kernel": "sweep_ge_wave<true>", "achieved": achieved_tf,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                     "traffic": (solves * DRAM_BYTES_PER_SOLVE_NCU / P.nplanes
-                                 if DRAM_BYTES_PER_SOLVE_NCU else None),
-                     "traffic_note": "bytes per average launch: ncu cold-cache capture of one hyperplane, "
-                                     "scaled by solves",
+                     "traffic": (solves * DRAM_BYTES_PER_SOLVE_NCU if DRAM_BYTES_PER_SOLVE_NCU else None),
+                     "traffic_note": "DRAM bytes of one sweep kernel launch (ncu), null until captured for this "
+                                     "kernel",
                      "flops_per_solve": FLOPS_PER_SOLVE,
                      "hbm_achieved_gbs": solves * BYTES_PER_SOLVE / sweep_s / 1e9,
                      "hbm_peak_gbs": hbm_peak,
-                     "peak_note": "FP32 peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
+                     "peak_note": "FP32 peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock); "
+                                  "HBM peak %s" % ("measured" if "hbm_gbs" in peaks else "fallback"),
                      "sweep_ms": sweep_s * 1e3},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(S_host.numel() * 4),
-                "d2h_bytes_per_step": int(phi_host.numel() * 4),
-                "what": "sn_sweep through the public API, pinned host source in and host flux out every step, "
-                        "copies on a second stream overlapping the neighbouring steps' sweeps"},
-        "gpu_launches": int(args.steps * (P.nplanes + 2)),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(phi_in_host.numel() * 4),
+                "d2h_bytes_per_step": int(phi_out_host.numel() * 4),
+                "what": "one source iteration a step through sn_source_iterate, the flux copied in from pinned "
+                        "host memory and the new flux copied back every step (copies on a second stream, "
+                        "overlapping the neighbouring steps)"},
+        "gpu_launches": int(args.steps * LAUNCHES_PER_STEP),
         "clocks": clk,
     }
+    if ws > 1:
+        line["replicas"] = ws
+    if parity is not None:
+        line["parity"] = parity
     if ann is not None:
         line["ann"] = ann
     if octnet is not None:
@@ -634,8 +722,8 @@ def run_gpu(args):
         line["aniso"] = aniso
     if geom is not None:
         line["geom"] = geom
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = guarded(cpu_baseline)
+    if cb is not None:
+        line["cpu_baseline"] = cb
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

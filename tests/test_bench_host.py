@@ -75,3 +75,23 @@ def test_a_failing_secondary_report_keeps_the_line():
         raise RuntimeError("no network (%d)" % x)
     assert bench.guarded(boom, 3) == {"error": "RuntimeError: no network (3)"}
     assert bench.guarded(lambda a, b: {"v": a + b}, 1, 2) == {"v": 3}
+
+
+def test_parity_report_on_known_arrays():
+    """The parity object of the bench line: a planted error of 1e-6 on a node of
+    value 1 (group max 1) and of 1e-12 on a node of value 1e-9 (group max 2)."""
+    import numpy as np
+    ref = np.ones((2, 3, 8))
+    ref[1] *= 2.0
+    ref[1, 0, 0] = 1e-9
+    phi = ref.copy()
+    phi[0, 1, 2] += 1e-6
+    phi[1, 0, 0] += 1e-12
+    r = bench.parity_report(phi, ref)
+    assert r["maxnorm_rel"] == pytest.approx(1e-6)
+    assert r["point_rel_at_1pct"] == pytest.approx(1e-6)
+    # the tiny node: 1e-12 / (1e-9 + 2e-8) under the 1e-8 floor (larger than the other
+    # node's 1e-6), 1e-12 / (1e-9 + 2e-6) under 1e-6 (smaller)
+    assert r["point_rel_floored_1e-8max"] == pytest.approx(1e-12 / 2.1e-8)
+    assert r["point_rel_floored_1e-6max"] == pytest.approx(1e-6 / (1 + 1e-6))
+    assert r["mean_rel_floored_1e-8max"] == pytest.approx(0.5 * (1e-6 / (1 + 1e-8) / 24 + 1e-12 / 2.1e-8 / 24))

@@ -118,11 +118,12 @@ def test_adjoint_blocked_32_against_central_differences(sn):
     """The adjoint form at its stated size: blocked_32 (32^3 cells, LQ_8, 4 groups),
     R = group-summed scalar flux over the 4x4x4 low corner, gradients with respect to
     all 393,216 per-cell, per-group sigma_t, sigma_s and q by the FP32 adjoint; 32
-    parameters drawn uniformly over every kind, group and cell, each checked against
-    FP64 central differences with relative step 1e-6 (absolute 1e-6 where the
-    parameter is 0).  Both perturbed FP64 source iterations start from the converged
-    unperturbed flux and take the same 120 iterations (spectral radius <= 0.9, so the
-    difference is converged to ~1e-6 of itself).
+    parameters drawn uniformly over every kind, group and cell, and 8 more from the
+    cells within 6 cells of the detector's corner, each checked against FP64 central
+    differences with relative step 1e-6 (absolute 1e-6 where the parameter is 0).
+    Both perturbed FP64 source iterations start from the converged unperturbed flux
+    and take the same 120 iterations (spectral radius <= 0.9, so the difference is
+    converged to ~1e-6 of itself).
 
     Bar: |adjoint - FD| <= 1e-4 |FD| + 1e-5 max|g| + 1e-14 |R| / h, max|g| the largest
     adjoint gradient of the parameter's kind.  The second term is the accuracy of the
@@ -130,8 +131,8 @@ def test_adjoint_blocked_32_against_central_differences(sn):
     so every entry carries an absolute error of about tol / (1 - rho) <= 1e-5 of the
     largest one (far from the detector that is more than 1e-4 of the entry).  The
     third is the resolution of the difference: two FP64 values of R carry ~1e-15 R of
-    rounding each, divided by the step h.  Parameters with |FD| >= 0.1 max|g| are held
-    to 1e-4 relative by the first term alone (at least three of the 32 here)."""
+    rounding each, divided by the step h.  Parameters with |FD| >= 0.1 max|g| (those
+    near the detector) are held to 1e-4 relative by the first term alone."""
     wl = W.blocked_32()
     nx = wl["nx"]
     G, C = wl["sigt"].shape[0], nx ** 3
@@ -149,10 +150,13 @@ def test_adjoint_blocked_32_against_central_differences(sn):
     rng = np.random.default_rng(2024)
     kinds = (("sigt", "grad_sigt"), ("sigs", "grad_sigs"), ("q", "grad_q"))
     gmax = {gk: float(adj[gk].abs().max().item()) for _, gk in kinds}
+    i, j, k = W.cell_ijk(wl)
+    near = np.flatnonzero((i < 6) & (j < 6) & (k < 6))
     worst, rows, strict = 0.0, [], 0
-    for _ in range(32):
+    for n in range(40):
         key, gkey = kinds[rng.integers(0, 3)]
-        g, c = int(rng.integers(0, G)), int(rng.integers(0, C))
+        g = int(rng.integers(0, G))
+        c = int(rng.integers(0, C)) if n < 32 else int(near[rng.integers(0, len(near))])
         p0 = float(wl[key][g, c])
         h = 1e-6 * (p0 if p0 > 0 else 1.0)
         Rs = []
