@@ -62,8 +62,12 @@ typedef enum {
     SN_SOLVE_ANN_GATED = 3, /* surrogate, with cells whose residual fails the gate
                                re-solved by SN_SOLVE_GE32R                          */
     SN_SOLVE_GE64 = 4,      /* FP64 elimination with partial pivoting (FP64 handles only) */
-    SN_SOLVE_OCTNET = 5     /* the paper's own per-octant networks (Sec. 3 Eqs. (15)-(18),
+    SN_SOLVE_OCTNET = 5,    /* the paper's own per-octant networks (Sec. 3 Eqs. (15)-(18),
                                Sec. 4), FP32 on the CUDA cores; see sn_octnet_*        */
+    SN_SOLVE_ANN_FROZEN = 6 /* surrogate with the gate decisions frozen by
+                               sn_surrogate_freeze_gate: each (octant, cell, group,
+                               direction) keeps the solver the gated sweep chose there,
+                               so the source iteration is a fixed linear map          */
 } sn_solve_mode;
 
 typedef struct {
@@ -282,6 +286,19 @@ sn_status sn_surrogate_apply(sn_handle h, const float *in27, float *psi, int64_t
  * be; the call then returns SN_ETIMEOUT, and the handle and the CUDA context stay
  * usable.  Synchronises the handle's stream.  (The waits of the sweeps use 2^31.) */
 sn_status sn_selftest_wait(sn_handle h, int64_t limit_cycles);
+
+/* Freeze the residual gate (not in the paper; the gate routes cells the network
+ * fails back to elimination): one SN_SOLVE_ANN_GATED sweep from S (device
+ * [G][ncell][8]) records, for every (octant, cell, group, direction), whether the
+ * network's prediction passed the gate; later SN_SOLVE_ANN_FROZEN sweeps and source
+ * iterations take the network there and elimination elsewhere without testing the
+ * residual again.  Rows decided the same way give the same flux as the gated sweep
+ * from the same source.  A change of the weights or of the threshold drops the
+ * frozen decisions (SN_ESTATE for SN_SOLVE_ANN_FROZEN until the next freeze).  The
+ * decisions take one bit a row (8 ncell G ndir/8 bits, allocated on first use; more
+ * than 2^32 rows: SN_EINVAL).  FP32 handles on box cells with isotropic scattering.
+ * Synchronises; sn_surrogate_stats then gives the number of rows sent to elimination. */
+sn_status sn_surrogate_freeze_gate(sn_handle h, const float *S);
 
 /* Surrogate counters of the last sweep (sn_sweep) or of the last iteration of
  * sn_source_iterate in an ANN mode, or of the last sn_surrogate_apply: cells sent

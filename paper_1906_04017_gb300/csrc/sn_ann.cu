@@ -27,6 +27,7 @@
 #include "cell_problem.cuh"
 #include "sn_internal.cuh"
 #include "sweep_common.cuh"
+#include "wave.cuh"
 
 #include <cuda_bf16.h>
 
@@ -162,6 +163,9 @@ struct Net {
     double *dacc = nullptr;    // scratch accumulator
     uint32_t *fb_queue = nullptr;   // gated sweep: rows rejected on the current hyperplane
     uint32_t *fb_count = nullptr;   // [nplanes] queue lengths
+    uint32_t *mask = nullptr;       // frozen gate: one bit a row ((o C + c) G + g) Do + d, 1 = network
+    int64_t mask_words = 0;
+    uint64_t frozen_gen = 0;        // net_gen of the handle when the mask was recorded (0: none)
 };
 
 static Net *net_of(sn_handle h) { return reinterpret_cast<Net *>(h->net); }
@@ -171,7 +175,7 @@ void free_net(sn_handle h)
     if (!h || !h->net) return;
     Net *n = net_of(h);
     void *bufs[] = {n->p, n->m, n->v, n->w1p, n->w2p, n->b1, n->b2, n->gpart, n->lpart, n->counter, n->dacc,
-                    n->fb_queue, n->fb_count};
+                    n->fb_queue, n->fb_count, n->mask};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete n;
@@ -1152,10 +1156,390 @@ sn_status reset_ann_counters(sn_handle h, cudaStream_t st)
     return SN_OK;
 }
 
-sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gated, cudaStream_t st)
+
+// --------------------------------------------------------------------------------
+// Surrogate key sweep: the schedule of the elimination key sweep (sn_sweep_keys.cu:
+// one thread per key (octant, cell of the hyperplane, group) and chunk of directions,
+// wavefront units, face planes [o][column][d][g], inflow vectors on the boundary)
+// with the per-cell solve of (14) replaced by the network (Sec. 4: build the input
+// vector, one feed-forward evaluation).  For each direction step the CTA's 128 rows
+// (one a thread, TMEM lane = thread) go through the two tcgen05 layers together.
+//   ANN_UNGATED  every row takes the network's output;
+//   ANN_GATED    a row keeps it when ||b - A psi|| <= tau ||b|| for its system (14),
+//                and with `record` the decision goes to the gate mask;
+//   ANN_FROZEN   the gate mask decides (the decisions of a recorded gated sweep).
+// The rows a step rejects are compacted, in thread order, to the first threads of
+// the CTA and solved there by elimination (GE32R, the key sweep's solve), so only
+// ceil(rejected / 32) warps run it; their outflow faces are stored by the solving
+// thread and w_d psi_d handed back to the key's thread, which adds the network's and
+// the elimination's rows to its flux partial in direction order: the flux is
+// bit-reproducible for a given set of decisions.
+// --------------------------------------------------------------------------------
+enum { ANN_UNGATED = 0, ANN_GATED = 1, ANN_FROZEN = 2 };
+
+struct AnnKeyArgs {
+    int nx, ny, nz, G, Do, C;
+    FastDiv divG;
+    const float *sigt, *S;
+    const float4 *dir;        // [Do] (3|Omega_x|/dx, 3|Omega_y|/dy, 3|Omega_z|/dz, w)
+    const float4 *dir_abs;    // [Do] |Omega|
+    float4 *face;             // x-planes | y-planes | z-planes | inflow vectors [G][6]
+    uint32_t off_y, off_z, off_in;
+    float *phi_oct;           // [8][C][G][8]
+    float lhx, lhy, lhz;      // the cell-size inputs of the network
+    AnnArgs ann;
+    uint32_t *mask;           // gate decisions (ANN_GATED with record, ANN_FROZEN)
+    int record;
+    WaveCtl w;
+};
+
+// shared memory (bytes)
+constexpr uint32_t kAkW1 = 0, kAkW2 = kAkW1 + kW1Bytes, kAkX = kAkW2 + kW2Bytes;
+constexpr uint32_t kAkStage = kAkX + kXBytes;           // [2][3][128] float4 inflow stages
+constexpr uint32_t kAkSrc = kAkStage + 2 * 3 * kTile * 16;   // [128][8] canonical source of each key
+constexpr uint32_t kAkKey = kAkSrc + kTile * 32;        // [128] sigma_t of each key
+constexpr uint32_t kAkOff = kAkKey + kTile * 4;         // [128] uint4 (slots of d0, d0)
+constexpr uint32_t kAkDir = kAkOff + kTile * 16;        // [64] float4 directions
+constexpr uint32_t kAkDab = kAkDir + 64 * 16;           // [64] float4 |Omega|
+constexpr uint32_t kAkQ = kAkDab + 64 * 16;             // [128] rejected rows: 12 faces, owner, d
+constexpr uint32_t kAkRes = kAkQ + kTile * 64;          // [128][8] w_d psi of the rejected rows, by owner
+constexpr uint32_t kAkRed = kAkRes + kTile * 32;        // [128][8] chunk partials of the flux
+constexpr uint32_t kAkDst = kAkRed + kTile * 32;        // [128] flux-partial index of each key
+constexpr uint32_t kAkCnt = kAkDst + kTile * 4;         // [8] ints: warp counts, next unit, stop
+constexpr uint32_t kAkBar = kAkCnt + 32;                // mbarrier
+constexpr uint32_t kAkMisc = kAkBar + 8;                // tmem slot, (unused), abort
+constexpr uint32_t kAkSmem = kAkMisc + 16;
+
+template <int MODE>
+__global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_wave(AnnKeyArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    int *misc = reinterpret_cast<int *>(smem + kAkMisc);
+    const uint32_t tbase = ann_setup(smem, a.ann, kAkW1, kAkW2, kAkBar, misc);
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const uint32_t sbase = smem_u32(smem), bar = sbase + kAkBar;
+    const uint32_t twarp = tbase + ((uint32_t)(t & ~31) << 16);
+    float4 *sdir = reinterpret_cast<float4 *>(smem + kAkDir), *sdab = reinterpret_cast<float4 *>(smem + kAkDab);
+    float *ssrc = reinterpret_cast<float *>(smem + kAkSrc), *ssig = reinterpret_cast<float *>(smem + kAkKey);
+    uint4 *soff = reinterpret_cast<uint4 *>(smem + kAkOff);
+    float *sq = reinterpret_cast<float *>(smem + kAkQ), *sres = reinterpret_cast<float *>(smem + kAkRes);
+    float *sred = reinterpret_cast<float *>(smem + kAkRed);
+    int *sdst = reinterpret_cast<int *>(smem + kAkDst), *cnt = reinterpret_cast<int *>(smem + kAkCnt);
+    const int Do = a.Do, G = a.G;
+    for (int e = t; e < Do; e += kTile) {
+        sdir[e] = a.dir[e];
+        sdab[e] = a.dir_abs[e];
+    }
+    float b2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) b2[q] = a.ann.b2[q];
+    const float lsig_scale = 0.69314718f / kLogSigScale;   // log2 -> the sigma_t input
+    uint32_t phase = 0;
+    unsigned long long nfb = 0;
+    bool late = false, stop = false;
+    if (t == 0) cnt[4] = (int)atomicAdd(a.w.next, 1u);
+    __syncthreads();
+    while (!stop) {
+        const int u = cnt[4];
+        if (u >= a.w.nunits) break;
+        __syncthreads();   // every thread has read the unit index
+        const int4 ud = a.w.units[u];
+        if (t == 0) cnt[4] = (int)atomicAdd(a.w.next, 1u);
+        const int s = ud.y & 4095, o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
+        const uint32_t c0 = a.w.plane_off[s];
+        const int nkeys = (int)(a.w.plane_off[s + 1] - c0) * G;
+        const int KB = kTile >> lch, nch = 1 << lch;
+        const int chunk = t >> (31 - __clz(KB)), lk = t & (KB - 1);
+        const int key = ud.x + lk;
+        const bool act = key < nkeys;
+        const int d0 = chunk * Do / nch, d1 = (chunk + 1) * Do / nch;
+        const int nsteps = (Do + nch - 1) / nch;
+
+        // the key (inputs of the sweep and set-up tables only: before the wait)
+        float sig = 0.f, smax = 0.f, lsig = 0.f;
+        uint32_t ou0 = 0, ou1 = 0, ou2 = 0, inb = 0, bnd = 0, row0 = 0;
+        int dst = -1;
+        if (act) {
+            const uint32_t cidx = a.divG.div((uint32_t)key);
+            const int g = key - (int)cidx * G;
+            const uint32_t pk = a.w.all_cells[c0 + cidx];
+            const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
+            const int i = (o & 1) ? a.nx - 1 - ip : ip;
+            const int j = (o & 2) ? a.ny - 1 - jp : jp;
+            const int k = (o & 4) ? a.nz - 1 - kp : kp;
+            const int c = i + a.nx * (j + a.ny * k);
+            const int gc = g * a.C + c;
+            sig = __ldg(a.sigt + gc);
+            const float4 s0 = __ldg(reinterpret_cast<const float4 *>(a.S) + 2 * (int64_t)gc);
+            const float4 s1 = __ldg(reinterpret_cast<const float4 *>(a.S) + 2 * (int64_t)gc + 1);
+            float Sc[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+            mirror8(Sc, o);      // canonical node n = physical n ^ o
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                ssrc[t * 8 + n] = Sc[n];
+                smax = fmaxf(smax, fabsf(Sc[n]));
+            }
+            lsig = lg2_approx(fmaxf(sig, kSigFloor)) * lsig_scale;
+            const uint32_t DG = (uint32_t)(Do * G), first = (uint32_t)(d0 * G + g);
+            ou0 = (uint32_t)(o * a.ny * a.nz + jp + a.ny * kp) * DG + first;
+            ou1 = a.off_y + (uint32_t)(o * a.nx * a.nz + ip + a.nx * kp) * DG + first;
+            ou2 = a.off_z + (uint32_t)(o * a.nx * a.ny + ip + a.nx * jp) * DG + first;
+            inb = a.off_in + 6u * (uint32_t)g;
+            bnd = (ip == 0 ? 1u : 0u) | (jp == 0 ? 2u : 0u) | (kp == 0 ? 4u : 0u);
+            dst = (o * a.C + c) * G + g;
+            row0 = (uint32_t)dst * (uint32_t)Do + (uint32_t)d0;
+        }
+        ssig[t] = sig;
+        soff[t] = make_uint4(ou0, ou1, ou2, (uint32_t)d0);
+        sdst[t] = dst;
+        if (t == 0) cnt[5] = wave_wait_deps(a.w, ud.z, ud.w) ? 0 : 1;
+        __syncthreads();
+        if (cnt[5]) break;
+
+        constexpr uint32_t AX = kTile * 16, SP = 3 * AX;
+        const uint32_t sb = sbase + kAkStage + 16 * t;
+        auto issue = [&](uint32_t buf, uint32_t f0, uint32_t f1, uint32_t f2) {
+            const uint32_t nb = sb + buf * SP;
+            cp_async16(nb, a.face + ((bnd & 1u) ? inb + (uint32_t)(o & 1) : f0));
+            cp_async16(nb + AX, a.face + ((bnd & 2u) ? inb + 2u + (uint32_t)((o >> 1) & 1) : f1));
+            cp_async16(nb + 2 * AX, a.face + ((bnd & 4u) ? inb + 4u + (uint32_t)((o >> 2) & 1) : f2));
+        };
+        if (act && d0 < d1) issue(0u, ou0, ou1, ou2);
+        cp_async_commit();
+        float phi[8];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) phi[n] = 0.f;
+        for (int jst = 0; jst < nsteps; ++jst) {
+            const int d = d0 + jst;
+            const bool valid = act && d < d1;
+            const int cur = jst & 1;
+            if (valid && d + 1 < d1) issue((uint32_t)(cur ^ 1), ou0 + (uint32_t)G, ou1 + (uint32_t)G, ou2 + (uint32_t)G);
+            cp_async_commit();
+            cp_async_wait_pending<1>();
+            const float4 *stg = reinterpret_cast<const float4 *>(smem + kAkStage) + cur * 3 * kTile + t;
+            const float4 fx = stg[0], fy = stg[kTile], fz = stg[2 * kTile];
+            const float ux[4] = {fx.x, fx.y, fx.z, fx.w};
+            const float uy[4] = {fy.x, fy.y, fy.z, fy.w};
+            const float uz[4] = {fz.x, fz.y, fz.z, fz.w};
+            float sc = 0.f;
+            float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) {
+                dd = sdir[d];
+                sc = smax;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sc = fmaxf(sc, fmaxf(fabsf(ux[q]), fmaxf(fabsf(uy[q]), fabsf(uz[q]))));
+                const float inv = sc > kScaleFloor ? rcp_approx(sc) : 0.f;
+                const float4 ab = sdab[d];
+                float x[kNin];
+                x[0] = 2.f * ab.x - 1.f; x[1] = 2.f * ab.y - 1.f; x[2] = 2.f * ab.z - 1.f;
+                x[3] = a.lhx; x[4] = a.lhy; x[5] = a.lhz;
+                x[6] = lsig;
+#pragma unroll
+                for (int n = 0; n < 8; ++n) x[7 + n] = ssrc[t * 8 + n] * inv;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    x[15 + q] = ux[q] * inv;
+                    x[19 + q] = uy[q] * inv;
+                    x[23 + q] = uz[q] * inv;
+                }
+                write_x_row(smem + kAkX, t, x);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (t == 0) mma_layer1(sbase, kAkX, kAkW1, tbase, bar);
+            if (lane == 0) late = !mbar_wait_bounded(bar, phase);
+            __syncwarp();
+            phase ^= 1u;
+            tc_fence_after();
+            hidden_to_tmem(twarp);
+            tc_fence_before();
+            if (__syncthreads_or(late)) { stop = true; break; }
+            tc_fence_after();
+            if (t == 0) mma_layer2(sbase, kAkW2, tbase, bar);
+            if (lane == 0) late = !mbar_wait_bounded(bar, phase);
+            __syncwarp();
+            phase ^= 1u;
+            tc_fence_after();
+            uint32_t r8[8];
+            tmem_ld8(twarp + 32, r8);
+            tmem_wait_ld();
+            if (__syncthreads_or(late)) { stop = true; break; }
+            float psi[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) psi[q] = sc * (__uint_as_float(r8[q]) + b2[q]);
+            bool keep = valid;
+            if (MODE == ANN_GATED && valid && sc != 0.f) {
+                CanonCell<float> cc;
+                cc.t3x = dd.x; cc.t3y = dd.y; cc.t3z = dd.z; cc.sig = sig; cc.mask = o;
+#pragma unroll
+                for (int n = 0; n < 8; ++n) cc.S[n] = ssrc[t * 8 + n];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { cc.ux[q] = ux[q]; cc.uy[q] = uy[q]; cc.uz[q] = uz[q]; }
+                keep = gate_pass(cc, psi, a.ann.tau);
+            }
+            if (MODE == ANN_GATED && valid && a.record && keep) {
+                const uint32_t r = row0 + (uint32_t)jst;
+                atomicOr(a.mask + (r >> 5), 1u << (r & 31));
+            }
+            if (MODE == ANN_FROZEN && valid) {
+                const uint32_t r = row0 + (uint32_t)jst;
+                keep = (__ldg(a.mask + (r >> 5)) >> (r & 31)) & 1u;
+            }
+            if (keep) {
+                a.face[ou0] = make_float4(psi[1], psi[3], psi[5], psi[7]);
+                a.face[ou1] = make_float4(psi[2], psi[3], psi[6], psi[7]);
+                a.face[ou2] = make_float4(psi[4], psi[5], psi[6], psi[7]);
+#pragma unroll
+                for (int n = 0; n < 8; ++n) phi[n] = fmaf(dd.w, psi[n], phi[n]);
+            }
+            if (MODE != ANN_UNGATED) {
+                // rejected rows to the first threads of the CTA, in thread order
+                const bool rej = valid && !keep;
+                const unsigned m = __ballot_sync(0xffffffffu, rej);
+                if (lane == 0) cnt[wid] = __popc(m);
+                __syncthreads();
+                int base = 0, total = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < kTile / 32; ++w2) {
+                    base += w2 < wid ? cnt[w2] : 0;
+                    total += cnt[w2];
+                }
+                if (rej) {
+                    float *e = sq + 16 * (base + __popc(m & ((1u << lane) - 1u)));
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { e[q] = ux[q]; e[4 + q] = uy[q]; e[8 + q] = uz[q]; }
+                    e[12] = __int_as_float(t);
+                    e[13] = __int_as_float(d);
+                }
+                __syncthreads();
+                if (t < total) {
+                    const float *e = sq + 16 * t;
+                    const int ow = __float_as_int(e[12]), de = __float_as_int(e[13]);
+                    const float4 de4 = sdir[de];
+                    float Sm[8];
+#pragma unroll
+                    for (int n = 0; n < 8; ++n) Sm[n] = ssrc[ow * 8 + n];
+                    mh_axis<0>(Sm);
+                    mh_axis<1>(Sm);
+                    mh_axis<2>(Sm);
+                    const float gx[4] = {e[0], e[1], e[2], e[3]}, gy[4] = {e[4], e[5], e[6], e[7]},
+                                gz[4] = {e[8], e[9], e[10], e[11]};
+                    float xg[8];
+                    cell_solve_key<true>(de4.x, de4.y, de4.z, ssig[ow], Sm, gx, gy, gz, xg);
+                    const uint4 of = soff[ow];
+                    const uint32_t dG = (uint32_t)(de - (int)of.w) * (uint32_t)G;
+                    a.face[of.x + dG] = make_float4(xg[1], xg[3], xg[5], xg[7]);
+                    a.face[of.y + dG] = make_float4(xg[2], xg[3], xg[6], xg[7]);
+                    a.face[of.z + dG] = make_float4(xg[4], xg[5], xg[6], xg[7]);
+#pragma unroll
+                    for (int n = 0; n < 8; ++n) sres[ow * 8 + n] = de4.w * xg[n];
+                }
+                if (t == 0) nfb += (unsigned long long)total;
+                __syncthreads();
+                if (rej) {
+#pragma unroll
+                    for (int n = 0; n < 8; ++n) phi[n] += sres[t * 8 + n];
+                }
+            }
+            ou0 += (uint32_t)G;
+            ou1 += (uint32_t)G;
+            ou2 += (uint32_t)G;
+        }
+        if (stop) {
+            if (t == 0) {
+                misc[2] = 1;   // counted as a timed-out CTA by the teardown
+                *reinterpret_cast<volatile double *>(a.w.abort) = 1.0;
+            }
+            break;
+        }
+        mirror8(phi, o);   // physical node order
+        if (lch == 0) {
+            if (act) {
+                float4 *p = reinterpret_cast<float4 *>(a.phi_oct) + 2 * (int64_t)dst;
+                p[0] = make_float4(phi[0], phi[1], phi[2], phi[3]);
+                p[1] = make_float4(phi[4], phi[5], phi[6], phi[7]);
+            }
+        } else {
+            float4 *r = reinterpret_cast<float4 *>(sred + (chunk * KB + lk) * 8);
+            r[0] = make_float4(phi[0], phi[1], phi[2], phi[3]);
+            r[1] = make_float4(phi[4], phi[5], phi[6], phi[7]);
+            __syncthreads();
+            for (int e = t; e < KB * 8; e += kTile) {
+                const int kk = e >> 3, n = e & 7;
+                const int dk = sdst[kk];
+                if (dk < 0) continue;
+                float sum = sred[kk * 8 + n];
+                for (int q = 1; q < nch; ++q) sum += sred[(q * KB + kk) * 8 + n];
+                a.phi_oct[(int64_t)dk * 8 + n] = sum;
+            }
+        }
+        __syncthreads();   // every store of this unit has been issued
+        if (t == 0) wave_done(a.w, u);
+    }
+    cp_async_wait_all();
+    if (MODE != ANN_UNGATED && t == 0 && nfb) atomicAdd(a.ann.counter, nfb);
+    ann_teardown(tbase, a.ann, misc);
+}
+
+// The surrogate key sweep of every hyperplane (one persistent launch) and the
+// boundary-leakage sum; false if the handle has no unit tables.
+static sn_status launch_sweep_ann_keys(sn_handle h, const float *S, float *phi_oct, int mode, bool record,
+                                       cudaStream_t st)
+{
+    Net *net = net_of(h);
+    const WaveTables *wt = static_cast<const WaveTables *>(h->wave);
+    AnnKeyArgs a = {};
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
+    a.divG = FastDiv((uint32_t)h->G);
+    a.sigt = (const float *)h->sigt;
+    a.S = S;
+    a.dir = reinterpret_cast<const float4 *>(h->dir);
+    a.dir_abs = h->dir_abs;
+    a.face = reinterpret_cast<float4 *>(h->face);
+    a.off_y = (uint32_t)h->face_x;
+    a.off_z = (uint32_t)(h->face_x + h->face_y);
+    a.off_in = (uint32_t)h->face_in;
+    a.phi_oct = phi_oct;
+    a.lhx = (logf((float)h->dx) + kLogHShift) / kLogHScale;
+    a.lhy = (logf((float)h->dy) + kLogHShift) / kLogHScale;
+    a.lhz = (logf((float)h->dz) + kLogHShift) / kLogHScale;
+    a.ann = ann_args(h);
+    a.mask = net->mask;
+    a.record = record ? 1 : 0;
+    a.w = wave_ctl(h);
+    void (*kern)(AnnKeyArgs) = mode == ANN_UNGATED ? sweep_ann_wave<ANN_UNGATED>
+                               : mode == ANN_GATED ? sweep_ann_wave<ANN_GATED> : sweep_ann_wave<ANN_FROZEN>;
+    SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAkSmem));
+    int per_sm = 0;
+    SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTile, kAkSmem));
+    per_sm = std::max(1, std::min(per_sm, (int)(512 / kTmemCols)));
+    SN_CK(h, cudaMemsetAsync(wt->flags, 0, sizeof(uint32_t) * (size_t)(wt->nunits + 1), st));
+    if (record) SN_CK(h, cudaMemsetAsync(net->mask, 0, sizeof(uint32_t) * (size_t)net->mask_words, st));
+    if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
+    kern<<<per_sm * num_sms(), kTile, kAkSmem, st>>>(a);
+    SN_CK(h, cudaGetLastError());
+    if (h->prof) {
+        SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));
+        h->prof_pending = true;
+    }
+    return launch_leak_keys(h, st);
+}
+
+bool ann_frozen(sn_handle h)
+{
+    return h->net && net_of(h)->mask && net_of(h)->frozen_gen == h->net_gen;
+}
+
+sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, int ann_mode, cudaStream_t st)
 {
     sn_status s = pack_if_dirty(h, st);
     if (s != SN_OK) return s;
+    if (key_sweep_ok(h) && h->wave)
+        return launch_sweep_ann_keys(h, S, phi_oct, ann_mode, false, st);
+    if (ann_mode == ANN_FROZEN) return fail(h, SN_EINVAL, "frozen gate: needs the key sweep");
+    const bool gated = ann_mode == ANN_GATED;
     Net *net = net_of(h);
     AnnSweepArgs a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
@@ -1593,6 +1977,39 @@ sn_status sn_selftest_wait(sn_handle h, int64_t limit_cycles)
     wait_selftest_kernel<<<1, 128, 0, h->stream>>>(a, (long long)limit_cycles);
     SN_CK(h, cudaGetLastError());
     return check_ann_timeouts(h);
+}
+
+sn_status sn_surrogate_freeze_gate(sn_handle h, const float *S)
+{
+    sn_status s = need_net(h, "sn_surrogate_freeze_gate");
+    if (s != SN_OK) return s;
+    if (!S) return fail(h, SN_EINVAL, "sn_surrogate_freeze_gate: NULL source");
+    if (!key_sweep_ok(h) || !h->wave)
+        return fail(h, SN_EINVAL, "sn_surrogate_freeze_gate: needs an FP32 handle on box cells with isotropic "
+                                  "scattering (the key sweep)");
+    const uint64_t rows = 8ull * (uint64_t)h->ncell * (uint64_t)h->G * (uint64_t)h->Do;
+    if (rows >= (1ull << 32)) return fail(h, SN_EINVAL, "sn_surrogate_freeze_gate: more than 2^32 rows");
+    Net *n = net_of(h);
+    if (!n->mask) {
+        n->mask_words = (int64_t)((rows + 31) / 32);
+        SN_CK(h, cudaMalloc(&n->mask, sizeof(uint32_t) * (size_t)n->mask_words));
+        h->device_bytes += (int64_t)sizeof(uint32_t) * n->mask_words;
+    }
+    const cudaStream_t st = h->stream;
+    s = pack_if_dirty(h, st);
+    if (s != SN_OK) return s;
+    SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
+    s = reset_ann_counters(h, st);
+    if (s != SN_OK) return s;
+    s = launch_sweep_ann_keys(h, S, static_cast<float *>(h->phi_oct), ANN_GATED, true, st);
+    if (s != SN_OK) return s;
+    SN_CK(h, cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT, cudaMemcpyDeviceToHost, st));
+    SN_CK(h, cudaStreamSynchronize(st));
+    if (h->acc_host[ACC_ABORT] != 0.0) return fail(h, SN_ETIMEOUT, "sn_surrogate_freeze_gate: a bounded wait gave up");
+    s = check_ann_timeouts(h);
+    if (s != SN_OK) return s;
+    n->frozen_gen = h->net_gen;
+    return SN_OK;
 }
 
 sn_status sn_surrogate_stats(sn_handle h, int64_t *fallbacks, int64_t *timeouts)

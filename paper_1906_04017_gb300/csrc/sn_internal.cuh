@@ -176,12 +176,17 @@ sn_status launch_source_moments(sn_handle h, const void *phi, void *S, cudaStrea
 uint32_t sweep_smem_bytes(sn_handle h, int K);
 sn_status launch_cells_f32(const float *in27, float *psi, int64_t n, bool refine, cudaStream_t st);
 // surrogate sweep (sn_ann.cu): every hyperplane of one sweep, FP32 handles only
-sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, bool gated, cudaStream_t st);
+// ann_mode: 0 network only, 1 residual gate, 2 frozen gate (ANN_* of sn_ann.cu)
+sn_status launch_sweep_ann(sn_handle h, const float *S, float *phi_oct, int ann_mode, cudaStream_t st);
+bool ann_frozen(sn_handle h);
 // the key sweep (sn_sweep_keys.cu): FP32 elimination on box cells, isotropic scattering
 bool key_sweep_ok(sn_handle h);
 sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st);
 sn_status build_wave(sn_handle h);
+sn_status launch_leak_keys(sn_handle h, cudaStream_t st);
 void free_wave(sn_handle h);
+struct WaveCtl;
+WaveCtl wave_ctl(sn_handle h);
 // zero the surrogate's fallback / timeout counters (stream-ordered)
 sn_status reset_ann_counters(sn_handle h, cudaStream_t st);
 sn_status check_ann_timeouts(sn_handle h);

@@ -871,8 +871,9 @@ static sn_status launch_harvest(sn_handle h, const float *S, float *out, uint32_
 sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st)
 {
     if (h->fp64) return launch_sweep_t<double>(h, (const double *)S, (double *)phi_oct, false, false, st);
-    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED)
-        return launch_sweep_ann(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_ANN_GATED, st);
+    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED || mode == SN_SOLVE_ANN_FROZEN)
+        return launch_sweep_ann(h, (const float *)S, (float *)phi_oct,
+                                mode == SN_SOLVE_ANN ? 0 : (mode == SN_SOLVE_ANN_GATED ? 1 : 2), st);
     if ((mode == SN_SOLVE_GE32R || mode == SN_SOLVE_GE32) && key_sweep_ok(h))
         return launch_sweep_keys(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R, st);
     return launch_sweep_t<float>(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R,
@@ -961,6 +962,10 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
         }
         __syncthreads();
         const int nk = nc * 8;
+        // this tile's tallies in the element type, added to the FP64 sums once a tile
+        // (the FP64 pipe of the GPU is a small fraction of the FP32 one)
+        T coll_t = T(0), src_t = T(0), mean_t = T(0);
+        int cnt_t = 0;
         for (int g = 0; g < G; ++g) {
             const int64_t base = ((int64_t)g * C + c0) * 8;
             const bool scalar = g % K == 0;   // moment 0 of its group
@@ -977,8 +982,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
                     if (scalar) {
                         // general cells: the node's own volume (column sum of M)
                         const T wv = vnode ? vnode[(c0 + cl) * 8 + (k & 7)] : T(1);
-                        coll += (double)(sigt[(int64_t)gg * C + c0 + cl] * nv * wv);
-                        src += (double)(S[base + k] * wv);
+                        coll_t = fma(sigt[(int64_t)gg * C + c0 + cl] * nv, wv, coll_t);
+                        src_t = fma(S[base + k], wv, src_t);
                         if (norms) {
                             ov = phi_old[base + k];
                             dmax = fmax(dmax, fabs(nv - ov));
@@ -994,12 +999,16 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
                         b += __shfl_xor_sync(0xffffffffu, b, off);
                     }
                     if (in && (k & 7) == 0 && a != T(0)) {
-                        mean += (double)(fabs(a - b) / fabs(a));
-                        cnt += 1.0;
+                        mean_t += fabs(a - b) / fabs(a);
+                        cnt_t += 1;
                     }
                 }
             }
         }
+        coll += (double)coll_t;
+        src += (double)src_t;
+        mean += (double)mean_t;
+        cnt += (double)cnt_t;
         __syncthreads();
     }
     // block reduction
@@ -1180,6 +1189,13 @@ static sn_status check_mode(sn_handle h, sn_solve_mode mode)
         if (!h->has_net) return fail(h, SN_ESTATE, "surrogate mode needs a trained or loaded network");
         return SN_OK;
     }
+    if (mode == SN_SOLVE_ANN_FROZEN) {
+        if (!h->has_net) return fail(h, SN_ESTATE, "surrogate mode needs a trained or loaded network");
+        if (!ann_frozen(h))
+            return fail(h, SN_ESTATE, "SN_SOLVE_ANN_FROZEN needs sn_surrogate_freeze_gate at the current weights "
+                                      "and threshold");
+        return SN_OK;
+    }
     if (mode == SN_SOLVE_OCTNET) {
         if (!h->has_octnet) return fail(h, SN_ESTATE, "octant-network mode needs initialised or loaded networks");
         return SN_OK;
@@ -1193,7 +1209,7 @@ static sn_status sweep_once(sn_handle h, const void *S, void *phi_out, const voi
                             cudaStream_t st)
 {
     SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
-    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
+    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED || mode == SN_SOLVE_ANN_FROZEN) {
         sn_status r = reset_ann_counters(h, st);
         if (r != SN_OK) return r;
     }
@@ -1230,7 +1246,7 @@ sn_status sn_sweep(sn_handle h, const void *S, void *phi, sn_solve_mode mode)
     prof_collect(h);
     take_tallies(h);
     if (h->acc_host[ACC_ABORT] != 0.0) return fail(h, SN_ETIMEOUT, "sn_sweep: a bounded wait of the sweep gave up");
-    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) return check_ann_timeouts(h);
+    if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED || mode == SN_SOLVE_ANN_FROZEN) return check_ann_timeouts(h);
     return SN_OK;
 }
 
@@ -1299,7 +1315,7 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
         cmean = a[ACC_MEANN] > 0 ? a[ACC_MEAN] / a[ACC_MEANN] : 0.0;
         take_tallies(h);
         if (a[ACC_ABORT] != 0.0) return fail(h, SN_ETIMEOUT, "sn_source_iterate: a bounded wait of the sweep gave up");
-        if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED) {
+        if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED || mode == SN_SOLVE_ANN_FROZEN) {
             s = check_ann_timeouts(h);
             if (s != SN_OK) return s;
         }

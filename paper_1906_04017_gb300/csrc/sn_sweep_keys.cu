@@ -51,6 +51,7 @@
 #include "ge8.cuh"
 #include "sn_internal.cuh"
 #include "sweep_common.cuh"
+#include "wave.cuh"
 
 namespace sn {
 
@@ -76,14 +77,7 @@ struct KeyArgs {
     float4 *face;                // x-planes | y-planes | z-planes | inflow vectors [G][6]
     uint32_t off_y, off_z, off_in;
     float *phi_oct;              // [8][C][G][8]
-    // wavefront kernel
-    const uint32_t *all_cells;   // the hyperplane table (h->plane_cells)
-    const uint32_t *plane_off;   // [nplanes + 1] offsets into it
-    const int4 *units;           // [nunits] see sweep_ge_wave
-    uint32_t *flags;             // [nunits] done flags (zeroed before the sweep)
-    uint32_t *next;              // hand-out counter (zeroed before the sweep)
-    double *abort;               // the sweep's abort flag (an accumulator slot, zeroed)
-    int nunits;
+    WaveCtl w;                   // wavefront kernel
 };
 
 struct KeySmem {
@@ -229,17 +223,6 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
     });
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // The persistent wavefront kernel (see the file header).  units[u] = (first key of
 // the tile within its hyperplane and octant, s | o << 12 | lch << 15, first unit of
 // hyperplane s - 1 it depends on, how many).  Thread 0 fetches the next unit's index
@@ -251,45 +234,24 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(Key
     __shared__ int s_next, s_stop;
     const int t = threadIdx.x;
     for (int e = t; e < a.Do; e += kKeyBlock) sm.dsm[e] = a.dir[e];
-    if (t == 0) s_next = (int)atomicAdd(a.next, 1u);
+    if (t == 0) s_next = (int)atomicAdd(a.w.next, 1u);
     __syncthreads();
     for (;;) {
         const int u = s_next;
-        if (u >= a.nunits) break;
+        if (u >= a.w.nunits) break;
         __syncthreads();   // every thread has read s_next
-        const int4 ud = a.units[u];
-        if (t == 0) s_next = (int)atomicAdd(a.next, 1u);
+        const int4 ud = a.w.units[u];
+        if (t == 0) s_next = (int)atomicAdd(a.w.next, 1u);
         const int s = ud.y & 4095, o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
-        const uint32_t c0 = a.plane_off[s], c1 = a.plane_off[s + 1];
-        const bool ok = key_tile<REFINE>(a, sm, o, a.all_cells + c0, (int)(c1 - c0) * a.G, ud.x, lch, [&] {
-            if (t == 0) {
-                int stop = 0;
-                const long long t0 = clock64();
-                for (int v = ud.z; v < ud.z + ud.w && !stop; ++v) {
-                    while (ld_acquire_u32(a.flags + v) == 0u) {
-                        if (*reinterpret_cast<volatile double *>(a.abort) != 0.0) {
-                            stop = 1;
-                            break;
-                        }
-                        if (clock64() - t0 > (1LL << 31)) {
-                            *reinterpret_cast<volatile double *>(a.abort) = 1.0;
-                            stop = 1;
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
-                }
-                s_stop = stop;
-            }
+        const uint32_t c0 = a.w.plane_off[s], c1 = a.w.plane_off[s + 1];
+        const bool ok = key_tile<REFINE>(a, sm, o, a.w.all_cells + c0, (int)(c1 - c0) * a.G, ud.x, lch, [&] {
+            if (t == 0) s_stop = wave_wait_deps(a.w, ud.z, ud.w) ? 0 : 1;
             __syncthreads();
             return s_stop == 0;
         });
         if (!ok) break;
         __syncthreads();   // every store of this unit has been issued
-        if (t == 0) {
-            __threadfence();
-            st_release_u32(a.flags + u, 1u);
-        }
+        if (t == 0) wave_done(a.w, u);
     }
     cp_async_wait_all();
 }
@@ -341,15 +303,6 @@ static int key_chunks_log2(int64_t keys, int Do)
     while (l < 3 && (2 << l) <= Do && keys * (1 << l) < slots) ++l;
     return l;
 }
-
-// Unit tables of the wavefront kernel (built once by sn_setup).
-struct WaveTables {
-    int4 *units = nullptr;
-    uint32_t *flags = nullptr;     // [nunits] done flags, then the hand-out counter
-    uint32_t *plane_off = nullptr;
-    int nunits = 0;
-    int grid = 0;
-};
 
 void free_wave(sn_handle h)
 {
@@ -449,6 +402,21 @@ sn_status build_wave(sn_handle h)
     return SN_OK;
 }
 
+WaveCtl wave_ctl(sn_handle h)
+{
+    const WaveTables *w = static_cast<const WaveTables *>(h->wave);
+    WaveCtl c = {};
+    if (!w) return c;
+    c.all_cells = h->plane_cells;
+    c.plane_off = w->plane_off;
+    c.units = w->units;
+    c.flags = w->flags;
+    c.next = w->flags + w->nunits;
+    c.abort = h->acc + ACC_ABORT;
+    c.nunits = w->nunits;
+    return c;
+}
+
 template <bool REFINE, int LCH>
 static cudaError_t launch_keys_plane(bool pdl, const KeyArgs &a, cudaStream_t st)
 {
@@ -483,13 +451,7 @@ sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool re
     a.phi_oct = phi_oct;
     const WaveTables *w = static_cast<const WaveTables *>(h->wave);
     if (w) {
-        a.all_cells = h->plane_cells;
-        a.plane_off = w->plane_off;
-        a.units = w->units;
-        a.flags = w->flags;
-        a.next = w->flags + w->nunits;
-        a.abort = h->acc + ACC_ABORT;
-        a.nunits = w->nunits;
+        a.w = wave_ctl(h);
         SN_CK(h, cudaMemsetAsync(w->flags, 0, sizeof(uint32_t) * (size_t)(w->nunits + 1), st));
     }
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
@@ -513,6 +475,11 @@ sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool re
         SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));
         h->prof_pending = true;
     }
+    return launch_leak_keys(h, st);
+}
+
+sn_status launch_leak_keys(sn_handle h, cudaStream_t st)
+{
     const uint32_t total = (uint32_t)(h->face_x + h->face_y + h->face_z);
     const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 8);
     leak_keys_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(h->face), (uint32_t)h->face_x,

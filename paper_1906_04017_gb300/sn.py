@@ -14,8 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsn_gb300.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ENOCONV, SN_ETIMEOUT, SN_ENAN, SN_ESTATE = range(8)
-GE32R, GE32, ANN, ANN_GATED, GE64, OCTNET = 0, 1, 2, 3, 4, 5
-MODES = {"ge32r": GE32R, "ge32": GE32, "ann": ANN, "ann_gated": ANN_GATED, "ge64": GE64, "octnet": OCTNET}
+GE32R, GE32, ANN, ANN_GATED, GE64, OCTNET, ANN_FROZEN = 0, 1, 2, 3, 4, 5, 6
+MODES = {"ge32r": GE32R, "ge32": GE32, "ann": ANN, "ann_gated": ANN_GATED, "ge64": GE64, "octnet": OCTNET,
+         "ann_frozen": ANN_FROZEN}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.c_void_p
@@ -88,6 +89,7 @@ _API = [
     ("sn_surrogate_apply", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int64)]),
     ("sn_selftest_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("sn_surrogate_freeze_gate", ctypes.c_int, [ctypes.c_void_p, _fp]),
     ("sn_surrogate_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]),
     ("sn_adjoint_sweep", ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_double, ctypes.c_int32, _fp, _fp, _fp,
@@ -452,6 +454,13 @@ class Problem:
         b = ctypes.c_int64(0)
         _check(lib().sn_surrogate_stats(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
         return a.value, b.value
+
+    def surrogate_freeze_gate(self, S):
+        """Record the residual gate's decisions of one gated sweep from S [G, C, 8] for
+        later ANN_FROZEN sweeps; returns the number of rows sent to elimination."""
+        self._sync_stream()
+        _check(lib().sn_surrogate_freeze_gate(self.h, _dev(S, torch.float32, (8,))), self.h)
+        return self.surrogate_stats()[0]
 
     def selftest_wait(self, limit_cycles=100000):
         """Run the bounded-wait self-test (sn_selftest_wait); returns its status code

@@ -370,3 +370,40 @@ def test_ann_sweep_blocked_32_sampled_group(sn):
     err = np.abs(phi[2] - ref[2]).max() / np.abs(ref[2]).max()
     print("blocked_32 ANN sweep vs oracle BF16 network sweep, group 2: max-norm rel err %.3e" % err)
     assert err < 1e-4        # measured 1.7e-5 on GB300
+
+
+def test_frozen_gate_repeats_the_gated_sweep_and_converges(sn):
+    """sn_surrogate_freeze_gate records the gate's decisions of one gated sweep; a
+    frozen sweep from the same source takes the same solver in every row, so it gives
+    the gated sweep's flux bit for bit and the same number of elimination rows; the
+    frozen source iteration is a fixed linear map and converges; changing the
+    threshold drops the frozen decisions."""
+    wl = W.random_small(6, 5, 7, order=6, G=3, seed=5, psi_inc=True)
+    P = sn.Problem(wl)
+    P.surrogate_set_weights(bounded_weights(3))
+    rng = np.random.default_rng(3)
+    S = cuda(rng.uniform(0.0, 1.0, (P.G, P.ncell, 8)).astype(np.float32))
+    n = P.solves_per_sweep
+    tau, seen = None, []
+    for t in 10.0 ** np.arange(-4.0, 1.01, 0.25):
+        P.surrogate_set_gate(float(t))
+        P.sweep(S, mode=sn.ANN_GATED)
+        seen.append((float(t), P.surrogate_stats()[0] / n))
+        if 0.2 < seen[-1][1] < 0.8:
+            tau = float(t)
+            break
+    assert tau is not None, seen
+    gated = P.sweep(S, mode=sn.ANN_GATED)
+    fb_gated = P.surrogate_stats()[0]
+    fb_freeze = P.surrogate_freeze_gate(S)
+    frozen = P.sweep(S, mode=sn.ANN_FROZEN)
+    fb_frozen = P.surrogate_stats()[0]
+    assert fb_freeze == fb_gated == fb_frozen
+    assert torch.equal(frozen, gated)
+    r = P.source_iterate(tol=1e-6, max_it=500, mode=sn.ANN_FROZEN)
+    assert r["converged"]
+    P.surrogate_set_gate(tau * 2)
+    with pytest.raises(sn.SnError) as e:
+        P.sweep(S, mode=sn.ANN_FROZEN)
+    P.close()
+    assert e.value.status == sn.SN_ESTATE
