@@ -2,8 +2,9 @@
 (14); Eqs. (9), (13), (21)) against the FP64 oracle, through the C ABI.
 
 Bar: per-group max-norm relative error of the scalar flux within 1e-5 of the
-oracle for FP32 elimination with one refinement step; pointwise relative error
-within 1e-4 wherever |phi| is at least 1% of the group maximum."""
+oracle for FP32 elimination with one refinement step, and pointwise relative error
+within 1e-5 wherever |phi| is at least 1% of the group maximum (measured over all of
+blocked_64: 2.9e-7 and 1.9e-6)."""
 import numpy as np
 import pytest
 import torch
@@ -38,7 +39,7 @@ def test_sweep_matches_oracle(sn, shape, order, G):
     wl = W.random_small(*shape, order=order, G=G, seed=sum(shape), psi_inc=True)
     phi, ref, bal, tal = one_sweep(sn, wl)
     assert rel_err(phi, ref) < TOL
-    assert point_err(phi, ref) < 10 * TOL
+    assert point_err(phi, ref) < TOL
     # balance of the GPU sweep: leakage + collisions = emission + inflow
     assert abs(bal[0] + bal[1] - bal[2] - bal[3]) < 1e-5 * (bal[2] + bal[3])
     assert np.allclose(bal, tal, rtol=1e-5)
@@ -153,5 +154,5 @@ def test_blocked_64_sampled_group(sn):
     P.close()
     ref, _ = oracle.OracleProblem(wl).sweep(S.astype(np.float64), groups=(5, 6))
     assert rel_err(phi[5], ref[5]) < TOL
-    assert point_err(phi[5], ref[5]) < 10 * TOL
+    assert point_err(phi[5], ref[5]) < TOL
     assert abs(bal[0] + bal[1] - bal[2] - bal[3]) < 1e-5 * (bal[2] + bal[3])
