@@ -570,9 +570,10 @@ __device__ __forceinline__ void hidden_to_tmem(uint32_t twarp)
     tmem_wait_st();
 }
 
-// Weights to shared memory, the mbarrier, 64 TMEM columns; returns the TMEM base.
+// Weights to shared memory, nbar mbarriers (8 bytes apart from offbar), ncols TMEM
+// columns; returns the TMEM base.
 __device__ __forceinline__ uint32_t ann_setup(unsigned char *smem, const AnnArgs &a, uint32_t offw1, uint32_t offw2,
-                                              uint32_t offbar, int *misc)
+                                              uint32_t offbar, int *misc, uint32_t ncols = kTmemCols, int nbar = 1)
 {
     const uint4 *g1 = reinterpret_cast<const uint4 *>(a.w1p), *g2 = reinterpret_cast<const uint4 *>(a.w2p);
     uint4 *s1 = reinterpret_cast<uint4 *>(smem + offw1), *s2 = reinterpret_cast<uint4 *>(smem + offw2);
@@ -581,12 +582,12 @@ __device__ __forceinline__ uint32_t ann_setup(unsigned char *smem, const AnnArgs
     if (threadIdx.x == 0) {
         misc[1] = 0;   // queue count
         misc[2] = 0;   // abort flag
-        mbar_init(smem_u32(smem + offbar), 1);
+        for (int b = 0; b < nbar; ++b) mbar_init(smem_u32(smem + offbar + 8 * b), 1);
         fence_mbar_init();
     }
     __syncwarp();
     if (threadIdx.x < 32) {
-        tmem_alloc(smem_u32(misc), kTmemCols);
+        tmem_alloc(smem_u32(misc), ncols);
         tmem_relinquish();
     }
     fence_async_smem();
@@ -596,14 +597,15 @@ __device__ __forceinline__ uint32_t ann_setup(unsigned char *smem, const AnnArgs
     return *reinterpret_cast<volatile uint32_t *>(misc);
 }
 
-__device__ __forceinline__ void ann_teardown(uint32_t tbase, const AnnArgs &a, const int *misc)
+__device__ __forceinline__ void ann_teardown(uint32_t tbase, const AnnArgs &a, const int *misc,
+                                             uint32_t ncols = kTmemCols)
 {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (threadIdx.x == 0 && reinterpret_cast<const volatile int *>(misc)[2]) atomicAdd(a.counter + 1, 1ull);
     __syncwarp();
-    if (threadIdx.x < 32) tmem_dealloc(tbase, kTmemCols);
+    if (threadIdx.x < 32) tmem_dealloc(tbase, ncols);
 }
 
 // Self-test of the bounded tensor-core waits (not in the paper): the set-up of a
@@ -1199,30 +1201,39 @@ struct AnnKeyArgs {
 };
 
 // shared memory (bytes)
-constexpr uint32_t kAkW1 = 0, kAkW2 = kAkW1 + kW1Bytes, kAkX = kAkW2 + kW2Bytes;
-constexpr uint32_t kAkStage = kAkX + kXBytes;           // [2][3][128] float4 inflow stages
+constexpr uint32_t kAkW1 = 0, kAkW2 = kAkW1 + kW1Bytes, kAkX = kAkW2 + kW2Bytes;   // two X tiles
+constexpr uint32_t kAkStage = kAkX + 2 * kXBytes;       // [2][3][128] float4 inflow stages
 constexpr uint32_t kAkSrc = kAkStage + 2 * 3 * kTile * 16;   // [128][8] canonical source of each key
 constexpr uint32_t kAkKey = kAkSrc + kTile * 32;        // [128] sigma_t of each key
 constexpr uint32_t kAkOff = kAkKey + kTile * 4;         // [128] uint4 (slots of d0, d0)
 constexpr uint32_t kAkDir = kAkOff + kTile * 16;        // [64] float4 directions
 constexpr uint32_t kAkDab = kAkDir + 64 * 16;           // [64] float4 |Omega|
 constexpr uint32_t kAkQ = kAkDab + 64 * 16;             // [128] rejected rows: 12 faces, owner, d
-constexpr uint32_t kAkRes = kAkQ + kTile * 64;          // [128][8] w_d psi of the rejected rows, by owner
-constexpr uint32_t kAkRed = kAkRes + kTile * 32;        // [128][8] chunk partials of the flux
+constexpr int kAkQf = 14;                               // floats a rejected row
+// [128][8] w_d psi of a step's rejected rows, by owner; at the end of a unit the same
+// space holds the chunk partials of the flux (never both at once)
+constexpr uint32_t kAkRes = kAkQ + kTile * kAkQf * 4;
+constexpr uint32_t kAkRed = kAkRes;
 constexpr uint32_t kAkDst = kAkRed + kTile * 32;        // [128] flux-partial index of each key
 constexpr uint32_t kAkCnt = kAkDst + kTile * 4;         // [8] ints: warp counts, next unit, stop
-constexpr uint32_t kAkBar = kAkCnt + 32;                // mbarrier
-constexpr uint32_t kAkMisc = kAkBar + 8;                // tmem slot, (unused), abort
+constexpr uint32_t kAkBar = kAkCnt + 32;                // two mbarriers: layer 1, layer 2
+constexpr uint32_t kAkMisc = kAkBar + 16;               // tmem slot, (unused), abort
 constexpr uint32_t kAkSmem = kAkMisc + 16;
+constexpr uint32_t kAkTmemCols = 2 * kTmemCols;         // two steps in flight
 
+// Two direction steps are in flight per CTA: while the hidden layer and the outputs
+// of step j run, step j+1's features are in its own X tile and its first layer in its
+// own TMEM region (64 columns each), so one CTA barrier a step separates the phases:
+//   features(j+1) -> X[(j+1)&1] | wait layer 1 (j) | hidden(j) -> TMEM region j&1 |
+//   barrier | issue layer 2 (j), layer 1 (j+1) | wait layer 2 (j) | outputs(j)
 template <int MODE>
 __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_wave(AnnKeyArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     int *misc = reinterpret_cast<int *>(smem + kAkMisc);
-    const uint32_t tbase = ann_setup(smem, a.ann, kAkW1, kAkW2, kAkBar, misc);
+    const uint32_t tbase = ann_setup(smem, a.ann, kAkW1, kAkW2, kAkBar, misc, kAkTmemCols, 2);
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const uint32_t sbase = smem_u32(smem), bar = sbase + kAkBar;
+    const uint32_t sbase = smem_u32(smem), barA = sbase + kAkBar, barB = barA + 8;
     const uint32_t twarp = tbase + ((uint32_t)(t & ~31) << 16);
     float4 *sdir = reinterpret_cast<float4 *>(smem + kAkDir), *sdab = reinterpret_cast<float4 *>(smem + kAkDab);
     float *ssrc = reinterpret_cast<float *>(smem + kAkSrc), *ssig = reinterpret_cast<float *>(smem + kAkKey);
@@ -1239,7 +1250,7 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
 #pragma unroll
     for (int q = 0; q < 8; ++q) b2[q] = a.ann.b2[q];
     const float lsig_scale = 0.69314718f / kLogSigScale;   // log2 -> the sigma_t input
-    uint32_t phase = 0;
+    uint32_t phA = 0, phB = 0;
     unsigned long long nfb = 0;
     bool late = false, stop = false;
     if (t == 0) cnt[4] = (int)atomicAdd(a.w.next, 1u);
@@ -1303,77 +1314,96 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
 
         constexpr uint32_t AX = kTile * 16, SP = 3 * AX;
         const uint32_t sb = sbase + kAkStage + 16 * t;
-        auto issue = [&](uint32_t buf, uint32_t f0, uint32_t f1, uint32_t f2) {
-            const uint32_t nb = sb + buf * SP;
-            cp_async16(nb, a.face + ((bnd & 1u) ? inb + (uint32_t)(o & 1) : f0));
-            cp_async16(nb + AX, a.face + ((bnd & 2u) ? inb + 2u + (uint32_t)((o >> 1) & 1) : f1));
-            cp_async16(nb + 2 * AX, a.face + ((bnd & 4u) ? inb + 4u + (uint32_t)((o >> 2) & 1) : f2));
+        // inflow faces of step j (direction d0 + j) into stage buffer j & 1
+        auto issue = [&](int jj) {
+            const uint32_t step = (uint32_t)jj * (uint32_t)G;
+            const uint32_t nb = sb + (uint32_t)(jj & 1) * SP;
+            cp_async16(nb, a.face + ((bnd & 1u) ? inb + (uint32_t)(o & 1) : ou0 + step));
+            cp_async16(nb + AX, a.face + ((bnd & 2u) ? inb + 2u + (uint32_t)((o >> 1) & 1) : ou1 + step));
+            cp_async16(nb + 2 * AX, a.face + ((bnd & 4u) ? inb + 4u + (uint32_t)((o >> 2) & 1) : ou2 + step));
         };
-        if (act && d0 < d1) issue(0u, ou0, ou1, ou2);
-        cp_async_commit();
+        // step jj's faces from its stage into registers, its scale, and (valid rows)
+        // its X row in tile jj & 1
+        auto features = [&](int jj, float (&f)[12], float &scale) {
+            const float4 *stg = reinterpret_cast<const float4 *>(smem + kAkStage) + (jj & 1) * 3 * kTile + t;
+            const float4 fx = stg[0], fy = stg[kTile], fz = stg[2 * kTile];
+            f[0] = fx.x; f[1] = fx.y; f[2] = fx.z; f[3] = fx.w;
+            f[4] = fy.x; f[5] = fy.y; f[6] = fy.z; f[7] = fy.w;
+            f[8] = fz.x; f[9] = fz.y; f[10] = fz.z; f[11] = fz.w;
+            scale = 0.f;
+            if (!(act && d0 + jj < d1)) return;
+            scale = smax;
+#pragma unroll
+            for (int q = 0; q < 12; ++q) scale = fmaxf(scale, fabsf(f[q]));
+            const float inv = scale > kScaleFloor ? rcp_approx(scale) : 0.f;
+            const float4 ab = sdab[d0 + jj];
+            float x[kNin];
+            x[0] = 2.f * ab.x - 1.f; x[1] = 2.f * ab.y - 1.f; x[2] = 2.f * ab.z - 1.f;
+            x[3] = a.lhx; x[4] = a.lhy; x[5] = a.lhz;
+            x[6] = lsig;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) x[7 + n] = ssrc[t * 8 + n] * inv;
+#pragma unroll
+            for (int q = 0; q < 12; ++q) x[15 + q] = f[q] * inv;
+            write_x_row(smem + kAkX + (uint32_t)(jj & 1) * kXBytes, t, x);
+        };
+
         float phi[8];
 #pragma unroll
         for (int n = 0; n < 8; ++n) phi[n] = 0.f;
+        float fc[12], fn[12], sc = 0.f, scn = 0.f;
+        // prologue: step 0's faces and features, step 1's faces in flight, layer 1 (0)
+        if (act && d0 < d1) issue(0);
+        cp_async_commit();
+        if (act && d0 + 1 < d1) issue(1);
+        cp_async_commit();
+        cp_async_wait_pending<1>();
+        features(0, fc, sc);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) {
+            mma_layer1(sbase, kAkX, kAkW1, tbase, barA);
+        }
         for (int jst = 0; jst < nsteps; ++jst) {
             const int d = d0 + jst;
             const bool valid = act && d < d1;
-            const int cur = jst & 1;
-            if (valid && d + 1 < d1) issue((uint32_t)(cur ^ 1), ou0 + (uint32_t)G, ou1 + (uint32_t)G, ou2 + (uint32_t)G);
-            cp_async_commit();
-            cp_async_wait_pending<1>();
-            const float4 *stg = reinterpret_cast<const float4 *>(smem + kAkStage) + cur * 3 * kTile + t;
-            const float4 fx = stg[0], fy = stg[kTile], fz = stg[2 * kTile];
-            const float ux[4] = {fx.x, fx.y, fx.z, fx.w};
-            const float uy[4] = {fy.x, fy.y, fy.z, fy.w};
-            const float uz[4] = {fz.x, fz.y, fz.z, fz.w};
-            float sc = 0.f;
-            float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid) {
-                dd = sdir[d];
-                sc = smax;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) sc = fmaxf(sc, fmaxf(fabsf(ux[q]), fmaxf(fabsf(uy[q]), fabsf(uz[q]))));
-                const float inv = sc > kScaleFloor ? rcp_approx(sc) : 0.f;
-                const float4 ab = sdab[d];
-                float x[kNin];
-                x[0] = 2.f * ab.x - 1.f; x[1] = 2.f * ab.y - 1.f; x[2] = 2.f * ab.z - 1.f;
-                x[3] = a.lhx; x[4] = a.lhy; x[5] = a.lhz;
-                x[6] = lsig;
-#pragma unroll
-                for (int n = 0; n < 8; ++n) x[7 + n] = ssrc[t * 8 + n] * inv;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    x[15 + q] = ux[q] * inv;
-                    x[19 + q] = uy[q] * inv;
-                    x[23 + q] = uz[q] * inv;
-                }
-                write_x_row(smem + kAkX, t, x);
+            const uint32_t treg = (uint32_t)(jst & 1) * kTmemCols;   // this step's TMEM region
+            const bool more = jst + 1 < nsteps;
+            // step j+1: its faces have landed (step j+2's start copying), its features
+            if (more) {
+                if (act && d + 2 < d1) issue(jst + 2);
+                cp_async_commit();
+                cp_async_wait_pending<1>();
+                features(jst + 1, fn, scn);
             }
+            // step j: layer 1 done -> hidden layer into its region
+            if (lane == 0) late = !mbar_wait_bounded(barA, phA);
+            __syncwarp();
+            phA ^= 1u;
+            tc_fence_after();
+            hidden_to_tmem(twarp + treg);
             fence_async_smem();
             tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-            if (t == 0) mma_layer1(sbase, kAkX, kAkW1, tbase, bar);
-            if (lane == 0) late = !mbar_wait_bounded(bar, phase);
-            __syncwarp();
-            phase ^= 1u;
-            tc_fence_after();
-            hidden_to_tmem(twarp);
-            tc_fence_before();
             if (__syncthreads_or(late)) { stop = true; break; }
             tc_fence_after();
-            if (t == 0) mma_layer2(sbase, kAkW2, tbase, bar);
-            if (lane == 0) late = !mbar_wait_bounded(bar, phase);
+            if (t == 0) {
+                mma_layer2(sbase, kAkW2, tbase + treg, barB);
+                if (more) mma_layer1(sbase, kAkX + (uint32_t)((jst + 1) & 1) * kXBytes, kAkW1,
+                                     tbase + (treg ^ kTmemCols), barA);
+            }
+            if (lane == 0) late = !mbar_wait_bounded(barB, phB);
             __syncwarp();
-            phase ^= 1u;
+            phB ^= 1u;
             tc_fence_after();
             uint32_t r8[8];
-            tmem_ld8(twarp + 32, r8);
+            tmem_ld8(twarp + treg + 32, r8);
             tmem_wait_ld();
-            if (__syncthreads_or(late)) { stop = true; break; }
             float psi[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) psi[q] = sc * (__uint_as_float(r8[q]) + b2[q]);
+            const float4 dd = valid ? sdir[d] : make_float4(0.f, 0.f, 0.f, 0.f);
             bool keep = valid;
             if (MODE == ANN_GATED && valid && sc != 0.f) {
                 CanonCell<float> cc;
@@ -1381,7 +1411,7 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
 #pragma unroll
                 for (int n = 0; n < 8; ++n) cc.S[n] = ssrc[t * 8 + n];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { cc.ux[q] = ux[q]; cc.uy[q] = uy[q]; cc.uz[q] = uz[q]; }
+                for (int q = 0; q < 4; ++q) { cc.ux[q] = fc[q]; cc.uy[q] = fc[4 + q]; cc.uz[q] = fc[8 + q]; }
                 keep = gate_pass(cc, psi, a.ann.tau);
             }
             if (MODE == ANN_GATED && valid && a.record && keep) {
@@ -1412,15 +1442,15 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
                     total += cnt[w2];
                 }
                 if (rej) {
-                    float *e = sq + 16 * (base + __popc(m & ((1u << lane) - 1u)));
+                    float *e = sq + kAkQf * (base + __popc(m & ((1u << lane) - 1u)));
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) { e[q] = ux[q]; e[4 + q] = uy[q]; e[8 + q] = uz[q]; }
+                    for (int q = 0; q < 12; ++q) e[q] = fc[q];
                     e[12] = __int_as_float(t);
                     e[13] = __int_as_float(d);
                 }
                 __syncthreads();
                 if (t < total) {
-                    const float *e = sq + 16 * t;
+                    const float *e = sq + kAkQf * t;
                     const int ow = __float_as_int(e[12]), de = __float_as_int(e[13]);
                     const float4 de4 = sdir[de];
                     float Sm[8];
@@ -1451,7 +1481,11 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
             ou0 += (uint32_t)G;
             ou1 += (uint32_t)G;
             ou2 += (uint32_t)G;
+#pragma unroll
+            for (int q = 0; q < 12; ++q) fc[q] = fn[q];
+            sc = scn;
         }
+        if (!stop && __syncthreads_or(late)) stop = true;   // the last step's layer-2 wait
         if (stop) {
             if (t == 0) {
                 misc[2] = 1;   // counted as a timed-out CTA by the teardown
@@ -1485,7 +1519,7 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
     }
     cp_async_wait_all();
     if (MODE != ANN_UNGATED && t == 0 && nfb) atomicAdd(a.ann.counter, nfb);
-    ann_teardown(tbase, a.ann, misc);
+    ann_teardown(tbase, a.ann, misc, kAkTmemCols);
 }
 
 // The surrogate key sweep of every hyperplane (one persistent launch) and the
@@ -1523,11 +1557,11 @@ static sn_status launch_sweep_ann_keys(sn_handle h, const float *S, float *phi_o
                                   (int)cudaSharedmemCarveoutMaxShared));
     // CTAs an SM: the kernel's register bound (4 ungated, 3 with the elimination's
     // registers), its shared memory (plus the 1 KB the driver reserves a CTA) within
-    // 228 KB, and 64 of the SM's 512 TMEM columns each (the occupancy query does not
+    // 228 KB, and 128 of the SM's 512 TMEM columns each (the occupancy query does not
     // see the carveout set above and answers 1)
     int per_sm = mode == ANN_UNGATED ? 4 : 3;
     per_sm = std::min(per_sm, (int)((228 * 1024) / (kAkSmem + 1024)));
-    per_sm = std::max(1, std::min(per_sm, (int)(512 / kTmemCols)));
+    per_sm = std::max(1, std::min(per_sm, (int)(512 / kAkTmemCols)));
     SN_CK(h, cudaMemsetAsync(wt->flags, 0, sizeof(uint32_t) * (size_t)(wt->nunits + 1), st));
     if (record) SN_CK(h, cudaMemsetAsync(net->mask, 0, sizeof(uint32_t) * (size_t)net->mask_words, st));
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
