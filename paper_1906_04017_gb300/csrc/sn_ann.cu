@@ -1314,9 +1314,10 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
 
         constexpr uint32_t AX = kTile * 16, SP = 3 * AX;
         const uint32_t sb = sbase + kAkStage + 16 * t;
-        // inflow faces of step j (direction d0 + j) into stage buffer j & 1
-        auto issue = [&](int jj) {
-            const uint32_t step = (uint32_t)jj * (uint32_t)G;
+        // inflow faces of step jj (direction d0 + jj) into stage buffer jj & 1; the
+        // face offsets ou* point at the current step's slots, `ahead` steps before jj
+        auto issue = [&](int jj, int ahead) {
+            const uint32_t step = (uint32_t)ahead * (uint32_t)G;
             const uint32_t nb = sb + (uint32_t)(jj & 1) * SP;
             cp_async16(nb, a.face + ((bnd & 1u) ? inb + (uint32_t)(o & 1) : ou0 + step));
             cp_async16(nb + AX, a.face + ((bnd & 2u) ? inb + 2u + (uint32_t)((o >> 1) & 1) : ou1 + step));
@@ -1353,9 +1354,9 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
         for (int n = 0; n < 8; ++n) phi[n] = 0.f;
         float fc[12], fn[12], sc = 0.f, scn = 0.f;
         // prologue: step 0's faces and features, step 1's faces in flight, layer 1 (0)
-        if (act && d0 < d1) issue(0);
+        if (act && d0 < d1) issue(0, 0);
         cp_async_commit();
-        if (act && d0 + 1 < d1) issue(1);
+        if (act && d0 + 1 < d1) issue(1, 1);
         cp_async_commit();
         cp_async_wait_pending<1>();
         features(0, fc, sc);
@@ -1373,7 +1374,7 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
             const bool more = jst + 1 < nsteps;
             // step j+1: its faces have landed (step j+2's start copying), its features
             if (more) {
-                if (act && d + 2 < d1) issue(jst + 2);
+                if (act && d + 2 < d1) issue(jst + 2, 2);
                 cp_async_commit();
                 cp_async_wait_pending<1>();
                 features(jst + 1, fn, scn);
