@@ -239,7 +239,7 @@ sn_status sn_adjoint_sweep(sn_handle h, const float *phi, const float *resp, dou
         SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
         s = launch_planes_adjoint(h, pa, 0, h->nplanes, st);
         if (s != SN_OK) return s;
-        s = launch_reduce(h, buf[cur], buf[1 - cur], a->Sadj, true, st);
+        s = launch_reduce(h, buf[cur], buf[1 - cur], a->Sadj, nullptr, true, st);
         if (s != SN_OK) return s;
         SN_CK(h, cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT, cudaMemcpyDeviceToHost, st));
         SN_CK(h, cudaStreamSynchronize(st));

@@ -94,6 +94,8 @@ struct sn_handle_s {
     int64_t face_in = 0;         // 4-vector offset of the inflow vectors [G][6] after the planes
     void *phi_oct = nullptr;     // T[8][C][G][8] per-octant partial scalar flux
     void *S = nullptr;           // T[G][C][8]
+    void *S_b = nullptr;         // T[G][C][8] the next iteration's source (one flux moment)
+    int red_iso_per_sm = 0;      // resident blocks of the fused reduction on one SM
     void *phi_b = nullptr;       // T[G][C][8] iteration scratch
     double *acc = nullptr;       // device accumulators (see sn_sweep.cu)
     double *acc_host = nullptr;  // pinned mirror of acc
@@ -168,7 +170,7 @@ sn_status launch_octnet_cells(sn_handle h, const float *in27, float *psi, int64_
 // kernels launched by several translation units (element type from h->fp64)
 sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode mode, cudaStream_t st);
 sn_status reduce_configure(sn_handle h);
-sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, bool norms,
+sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, void *S_next, bool norms,
                         cudaStream_t st);
 sn_status launch_source(sn_handle h, const void *phi, void *S, cudaStream_t st);
 // anisotropic scattering (sn_aniso.cu, sn_sweep.cu)

@@ -169,7 +169,7 @@ static void release(sn_handle h)
     free_adjoint(h);
     free_wave(h);
     void *bufs[] = {h->sigt, h->sigs, h->q, h->xfer, h->psi_inc, h->dir, h->dir_abs, h->plane_cells, h->plane_pos,
-                    h->face, h->phi_oct, h->S, h->phi_b, h->acc, h->sigs_n, h->yhat, h->geom, h->vnode, h->omabs, h->geomB};
+                    h->face, h->phi_oct, h->S, h->S_b, h->phi_b, h->acc, h->sigs_n, h->yhat, h->geom, h->vnode, h->omabs, h->geomB};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->acc_host) cudaFreeHost(h->acc_host);
@@ -420,6 +420,7 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
     }
     SN_TRY(dalloc(h, &h->phi_oct, (size_t)8 * GC * 8));
     SN_TRY(dalloc(h, &h->S, GC * 8));
+    SN_TRY(dalloc(h, &h->S_b, GC * 8));
     SN_TRY(dalloc(h, &h->phi_b, GC * 8));
     SN_TRY(dalloc_bytes(h, (void **)&h->acc, sizeof(double) * ACC_COUNT));
     {

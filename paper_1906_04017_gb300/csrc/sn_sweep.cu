@@ -24,6 +24,7 @@
 // Element type T: float (GE32R / GE32) or double (GE64, FP64 handles).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "ge8.cuh"
 #include "hex.cuh"
@@ -1042,6 +1043,167 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T *__restrict__ phi_o
     }
 }
 
+// Isotropic scattering (one flux moment): the same octant sum and tallies over the
+// same cell tiles, with the per-element work vectorised (each thread takes 16 bytes
+// of one (group, cell): 4 nodes in FP32, 2 in FP64) and, with S_next, the source of
+// the next iteration built from the new flux while the tile is in shared memory:
+// S_next = (q_g + sum_g' xfer[g'][g] sigma_s,g' phi_g') / (4 pi) in the order and
+// rounding of source_kernel (Eqs. (2) and (6), P_0 term), so the fused iteration gives
+// the flux of the separate kernels bit for bit and saves one read and one write of it.
+template <typename T>
+__global__ void __launch_bounds__(256) reduce_iso_kernel(
+    const T *__restrict__ phi_oct, const T *__restrict__ phi_old, T *__restrict__ phi_new, const T *__restrict__ S,
+    T *__restrict__ S_next, const T *__restrict__ sigt, const T *__restrict__ sigs, const T *__restrict__ q,
+    const T *__restrict__ xfer, const T *__restrict__ vnode, int64_t C, int G, int TC, FastDiv divG8, double vol8,
+    double *acc, int norms)
+{
+    constexpr int V = 16 / (int)sizeof(T);   // elements a vector
+    constexpr int NV = 8 / V;                // vectors of one (group, cell)
+    using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    extern __shared__ __align__(16) unsigned char red_smem[];
+    const int G8 = G * 8, row = G8 + 8;
+    T *tile = reinterpret_cast<T *>(red_smem);   // [TC][G*8 + 8]
+    T *st_sig = tile + (size_t)TC * row;         // [TC][G] sigma_t
+    T *ss_sig = st_sig + (size_t)TC * G;         // [TC][G] sigma_s
+    T *sq = ss_sig + (size_t)TC * G;             // [TC][G] q
+    __shared__ double sh[8][6];
+    const int64_t stride_oct = C * G8;
+    const int64_t ntile = (C + TC - 1) / TC;
+    const int lane = threadIdx.x % 32;
+    const T inv4pi = (T)(1.0 / (4.0 * kPi));
+    double coll = 0, src = 0, mean = 0, cnt = 0;
+    T dmax = T(0), pmax = T(0);
+    int bad = 0;
+    for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int64_t c0 = t * TC;
+        const int nc = (int)min((int64_t)TC, C - c0);
+        const int nel = nc * G8;
+        const T *po = phi_oct + c0 * G8;
+        for (int i = threadIdx.x * V; i < nel; i += blockDim.x * V) {
+            alignas(16) T s[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) s[j] = T(0);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const Vec f = *reinterpret_cast<const Vec *>(po + (int64_t)o * stride_oct + i);
+                const T *fv = reinterpret_cast<const T *>(&f);
+#pragma unroll
+                for (int j = 0; j < V; ++j) s[j] += fv[j];
+            }
+            const int cl = (int)divG8.div((uint32_t)i);
+            *reinterpret_cast<Vec *>(tile + cl * row + (i - cl * G8)) = *reinterpret_cast<const Vec *>(s);
+        }
+        for (int e = threadIdx.x; e < nc * G; e += blockDim.x) {
+            const int g = e / nc, cl = e - g * nc;
+            const int64_t gc = (int64_t)g * C + c0 + cl;
+            st_sig[cl * G + g] = sigt[gc];
+            ss_sig[cl * G + g] = sigs[gc];
+            sq[cl * G + g] = q[gc];
+        }
+        __syncthreads();
+        T coll_t = T(0), src_t = T(0), mean_t = T(0);
+        int cnt_t = 0;
+        const int per_g = nc * NV, total = G * per_g;
+        // whole warps, so that the vectors of one (group, cell) meet in one shuffle group
+        for (int e = threadIdx.x; e - lane < total; e += blockDim.x) {
+            const bool in = e < total;
+            T a = T(0), b = T(0);
+            if (in) {
+                const int g = e / per_g, r = e - g * per_g;
+                const int cl = r / NV, v = r - cl * NV;
+                const int64_t off = ((int64_t)g * C + c0 + cl) * 8 + v * V;
+                alignas(16) T nv[V], sv[V], wv[V], ov[V];
+                *reinterpret_cast<Vec *>(nv) = *reinterpret_cast<const Vec *>(tile + cl * row + g * 8 + v * V);
+                *reinterpret_cast<Vec *>(phi_new + off) = *reinterpret_cast<const Vec *>(nv);
+                *reinterpret_cast<Vec *>(sv) = *reinterpret_cast<const Vec *>(S + off);
+                if (vnode) {
+                    *reinterpret_cast<Vec *>(wv) = *reinterpret_cast<const Vec *>(vnode + (c0 + cl) * 8 + v * V);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) wv[j] = T(1);
+                }
+                const T sg = st_sig[cl * G + g];
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    if (!isfinite(nv[j])) bad = 1;
+                    coll_t = fma(sg * nv[j], wv[j], coll_t);
+                    src_t = fma(sv[j], wv[j], src_t);
+                    a += nv[j];
+                }
+                if (norms) {
+                    *reinterpret_cast<Vec *>(ov) = *reinterpret_cast<const Vec *>(phi_old + off);
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        dmax = fmax(dmax, fabs(nv[j] - ov[j]));
+                        pmax = fmax(pmax, fabs(nv[j]));
+                        b += ov[j];
+                    }
+                }
+                if (S_next) {
+                    alignas(16) T s[V];
+                    const T qg = sq[cl * G + g];
+#pragma unroll
+                    for (int j = 0; j < V; ++j) s[j] = qg;
+                    for (int gp = 0; gp < G; ++gp) {
+                        const T x = __ldg(xfer + gp * G + g), sgs = ss_sig[cl * G + gp];
+                        alignas(16) T pv[V];
+                        *reinterpret_cast<Vec *>(pv) = *reinterpret_cast<const Vec *>(tile + cl * row + gp * 8 + v * V);
+#pragma unroll
+                        for (int j = 0; j < V; ++j) s[j] = fma(x, sgs * pv[j], s[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < V; ++j) s[j] *= inv4pi;
+                    *reinterpret_cast<Vec *>(S_next + off) = *reinterpret_cast<const Vec *>(s);
+                }
+            }
+            if (norms) {
+#pragma unroll
+                for (int m = 1; m < NV; m <<= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, m);
+                    b += __shfl_xor_sync(0xffffffffu, b, m);
+                }
+                if (in && (e % NV) == 0 && a != T(0)) {
+                    mean_t += fabs(a - b) / fabs(a);
+                    cnt_t += 1;
+                }
+            }
+        }
+        coll += (double)coll_t;
+        src += (double)src_t;
+        mean += (double)mean_t;
+        cnt += (double)cnt_t;
+        __syncthreads();
+    }
+    double v[6] = {coll * vol8, src * 4.0 * kPi * vol8, (double)dmax, (double)pmax, mean, cnt};
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const double t = __shfl_down_sync(0xffffffffu, v[m], off);
+            v[m] = (m == 2 || m == 3) ? fmax(v[m], t) : v[m] + t;
+        }
+    }
+    bad = __syncthreads_or(bad);
+    const int warp = threadIdx.x / 32;
+    if (lane == 0)
+        for (int m = 0; m < 6; ++m) sh[warp][m] = v[m];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x / 32;
+        for (int w = 1; w < nw; ++w)
+            for (int m = 0; m < 6; ++m) v[m] = (m == 2 || m == 3) ? fmax(v[m], sh[w][m]) : v[m] + sh[w][m];
+        atomicAdd(acc + ACC_COLL, v[0]);
+        atomicAdd(acc + ACC_SRC, v[1]);
+        if (norms) {
+            atomic_max_nonneg(acc + ACC_DMAX, v[2]);
+            atomic_max_nonneg(acc + ACC_PMAX, v[3]);
+            atomicAdd(acc + ACC_MEAN, v[4]);
+            atomicAdd(acc + ACC_MEANN, v[5]);
+        }
+        if (bad) acc[ACC_FLAG] = 1.0;
+    }
+}
+
 int num_sms()
 {
     static int n = 0;
@@ -1062,22 +1224,53 @@ static size_t reduce_tile(const sn_handle h, int *TC)
     return (size_t)*TC * (G8 + 8) * h->esz;
 }
 
-// Opts the reduction in to more than 48 KB of dynamic shared memory where the group
+// the fused isotropic reduction: the same tile plus sigma_t, sigma_s and q of its cells
+static size_t reduce_iso_smem(const sn_handle h, int TC)
+{
+    return (size_t)TC * (h->G * 8 + 8 + 3 * h->G) * h->esz;
+}
+
+// Opts the reductions in to more than 48 KB of dynamic shared memory where the group
 // count needs it (G*8 values of one cell, up to 1024 groups); called once by sn_setup
 // so that no attribute call falls inside a stream capture.
 sn_status reduce_configure(sn_handle h)
 {
     int TC = 0;
     const size_t smem = reduce_tile(h, &TC);
-    if (smem <= 48 * 1024) return SN_OK;
-    if (h->fp64)
-        SN_CK(h, cudaFuncSetAttribute(reduce_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else
-        SN_CK(h, cudaFuncSetAttribute(reduce_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem_iso = reduce_iso_smem(h, TC);
+    if (smem > 48 * 1024) {
+        if (h->fp64)
+            SN_CK(h, cudaFuncSetAttribute(reduce_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else
+            SN_CK(h, cudaFuncSetAttribute(reduce_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    if (h->K == 1) {
+        if (smem_iso > 48 * 1024) {
+            if (h->fp64)
+                SN_CK(h, cudaFuncSetAttribute(reduce_iso_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem_iso));
+            else
+                SN_CK(h, cudaFuncSetAttribute(reduce_iso_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem_iso));
+        }
+        // a grid of resident blocks: the kernel strides over the cell tiles
+        int per_sm = 0;
+        if (h->fp64)
+            SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_iso_kernel<double>, 256, smem_iso));
+        else
+            SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_iso_kernel<float>, 256, smem_iso));
+        h->red_iso_per_sm = per_sm > 0 ? per_sm : 1;
+    }
     return SN_OK;
 }
 
-sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, bool norms, cudaStream_t st)
+static bool aligned16(const void *p)
+{
+    return ((uintptr_t)p & 15u) == 0;
+}
+
+sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const void *S, void *S_next, bool norms,
+                        cudaStream_t st)
 {
     int TC = 0;
     const size_t smem = reduce_tile(h, &TC);
@@ -1087,6 +1280,25 @@ sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const v
     if (grid > cap) grid = cap;
     const double vol8 = h->vnode ? 1.0 : h->dx * h->dy * h->dz / 8.0;
     const FastDiv divG8((uint32_t)(h->G * h->K * 8));
+    // the vectorised kernel moves 16 bytes of a caller's buffer at a time
+    if (h->K == 1 && aligned16(phi_old) && aligned16(phi_new) && aligned16(S) && aligned16(S_next)) {
+        const size_t si = reduce_iso_smem(h, TC);
+        grid = std::min(ntile, (int64_t)num_sms() * h->red_iso_per_sm);
+        if (h->fp64)
+            reduce_iso_kernel<double><<<(unsigned)grid, 256, si, st>>>(
+                (const double *)h->phi_oct, (const double *)phi_old, (double *)phi_new, (const double *)S,
+                (double *)S_next, (const double *)h->sigt, (const double *)h->sigs, (const double *)h->q,
+                (const double *)h->xfer, (const double *)h->vnode, h->ncell, h->G, TC, divG8, vol8, h->acc,
+                norms ? 1 : 0);
+        else
+            reduce_iso_kernel<float><<<(unsigned)grid, 256, si, st>>>(
+                (const float *)h->phi_oct, (const float *)phi_old, (float *)phi_new, (const float *)S,
+                (float *)S_next, (const float *)h->sigt, (const float *)h->sigs, (const float *)h->q,
+                (const float *)h->xfer, (const float *)h->vnode, h->ncell, h->G, TC, divG8, vol8, h->acc,
+                norms ? 1 : 0);
+        SN_CK(h, cudaGetLastError());
+        return SN_OK;
+    }
     if (h->fp64)
         reduce_kernel<double><<<(unsigned)grid, 256, smem, st>>>(
             (const double *)h->phi_oct, (const double *)phi_old, (double *)phi_new, (const double *)S,
@@ -1098,7 +1310,7 @@ sn_status launch_reduce(sn_handle h, const void *phi_old, void *phi_new, const v
             (const float *)h->sigt, h->ncell, h->G * h->K, TC, divG8, vol8, h->acc, norms ? 1 : 0, h->K,
             (const float *)h->vnode);
     SN_CK(h, cudaGetLastError());
-    return SN_OK;
+    return S_next ? launch_source(h, phi_new, S_next, st) : SN_OK;
 }
 
 // ---------------------------------------------------------------------------------
@@ -1206,7 +1418,7 @@ static sn_status check_mode(sn_handle h, sn_solve_mode mode)
 
 // one sweep from S into phi (device), tallies into acc; queued on st
 static sn_status sweep_once(sn_handle h, const void *S, void *phi_out, const void *phi_old, sn_solve_mode mode,
-                            cudaStream_t st)
+                            cudaStream_t st, void *S_next = nullptr)
 {
     SN_CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * ACC_COUNT, st));
     if (mode == SN_SOLVE_ANN || mode == SN_SOLVE_ANN_GATED || mode == SN_SOLVE_ANN_FROZEN) {
@@ -1215,7 +1427,7 @@ static sn_status sweep_once(sn_handle h, const void *S, void *phi_out, const voi
     }
     sn_status s = launch_sweep(h, S, h->phi_oct, mode, st);
     if (s != SN_OK) return s;
-    return launch_reduce(h, phi_old, phi_out, S, phi_old != nullptr, st);
+    return launch_reduce(h, phi_old, phi_out, S, S_next, phi_old != nullptr, st);
 }
 
 static void take_tallies(sn_handle h)
@@ -1259,6 +1471,10 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
     if (s != SN_OK) return s;
     const cudaStream_t st = h->stream;
     void *buf[2] = {phi, h->phi_b};
+    // one flux moment: the reduction of each sweep builds the next sweep's source into
+    // the other source buffer, so only the first source is a launch of its own
+    const bool fused = h->K == 1;
+    void *Sb[2] = {h->S, fused ? h->S_b : h->S};
 
     if (use_graph) {
         Graphs &gr = h->graphs;
@@ -1273,8 +1489,9 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
                 cudaGraph_t graph;
                 cudaError_t be = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
                 if (be != cudaSuccess) { h->prof = prof; return cuda_fail(h, be, "cudaStreamBeginCapture"); }
-                sn_status cs = launch_source(h, buf[p], h->S, h->cap_stream);
-                if (cs == SN_OK) cs = sweep_once(h, h->S, buf[1 - p], buf[p], mode, h->cap_stream);
+                sn_status cs = fused ? SN_OK : launch_source(h, buf[p], h->S, h->cap_stream);
+                if (cs == SN_OK)
+                    cs = sweep_once(h, Sb[p], buf[1 - p], buf[p], mode, h->cap_stream, fused ? Sb[1 - p] : nullptr);
                 cudaError_t me = cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT,
                                                  cudaMemcpyDeviceToHost, h->cap_stream);
                 cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -1298,12 +1515,16 @@ sn_status sn_source_iterate(sn_handle h, double tol, int32_t max_it, sn_solve_mo
     int it = 0, cur = 0;
     double cmax = 0, cmean = 0;
     sn_status rc = SN_ENOCONV;
+    if (fused) {
+        s = launch_source(h, phi, Sb[0], st);
+        if (s != SN_OK) return s;
+    }
     for (it = 0; it < max_it; ++it) {
         if (use_graph) {
             SN_CK(h, cudaGraphLaunch(h->graphs.exec[cur], st));
         } else {
-            s = launch_source(h, buf[cur], h->S, st);
-            if (s == SN_OK) s = sweep_once(h, h->S, buf[1 - cur], buf[cur], mode, st);
+            s = fused ? SN_OK : launch_source(h, buf[cur], h->S, st);
+            if (s == SN_OK) s = sweep_once(h, Sb[cur], buf[1 - cur], buf[cur], mode, st, fused ? Sb[1 - cur] : nullptr);
             if (s != SN_OK) return s;
             SN_CK(h, cudaMemcpyAsync(h->acc_host, h->acc, sizeof(double) * ACC_COUNT, cudaMemcpyDeviceToHost, st));
         }

@@ -118,6 +118,35 @@ def test_source_iteration_fixed_count(sn, use_graph):
     assert abs(r["change_max"] - ref["change_max"]) < 1e-4 * ref["change_max"]
 
 
+@pytest.mark.parametrize("fp64", [False, True])
+def test_fused_source_iteration_repeats_the_separate_kernels(sn, fp64):
+    """With one flux moment the reduction of each sweep also builds the next sweep's
+    source; the iteration gives the flux of phi <- sweep(source(phi)) made of separate
+    calls bit for bit, from a captured graph or not, and through the scalar reduction
+    that a caller's buffer off the 16-byte grid takes (315 cells: 4 reduction tiles of
+    85 cells, the last one ragged)."""
+    wl = W.random_small(9, 7, 5, order=4, G=3, seed=4, psi_inc=True)
+    P = sn.Problem(wl, fp64=fp64)
+    rng = np.random.default_rng(6)
+    phi0 = torch.from_numpy(rng.uniform(0.0, 1.0, (P.G, P.ncell, 8))).to(P.dtype).cuda()
+    ref = phi0.clone()
+    for _ in range(4):
+        ref = P.sweep(P.source(ref))
+    got = []
+    for use_graph in (False, True):
+        phi = phi0.clone()
+        P.source_iterate(phi=phi, tol=0.0, max_it=4, use_graph=use_graph, allow_noconv=True)
+        got.append(phi)
+    raw = torch.zeros(phi0.numel() + 1, dtype=P.dtype, device="cuda")
+    off = raw[1:].view(phi0.shape)
+    off.copy_(phi0)
+    P.source_iterate(phi=off, tol=0.0, max_it=4, use_graph=False, allow_noconv=True)
+    P.close()
+    assert off.data_ptr() % 16 != 0
+    for phi in got + [off]:
+        assert torch.equal(phi, ref)
+
+
 def test_paper_problem_4(sn):
     """The paper's Problem 4 (thick scattering medium, psi_inc = 1 on 3 faces) on a
     10^3 mesh, LQ_4: FP32 to a 2e-6 change, FP64 oracle converged; the iteration
