@@ -36,15 +36,16 @@ UNIT = "solves/s"
 FLOPS_PER_SOLVE = 1450
 # algorithmic HBM bytes of one solve: 12 inflow + 12 outflow face floats
 BYTES_PER_SOLVE = 96
-# DRAM bytes (read + write) per solve of the key sweep (sweep_ge_keys<true, 1>) measured
-# by ncu on blocked_64 hyperplane 95 (cold cache, full-set capture of one launch); None
-# once that kernel changes
-DRAM_BYTES_PER_SOLVE_NCU = None
+# DRAM bytes (read + write) per solve of the wavefront sweep kernel (sweep_ge_wave<true>)
+# from one full-set ncu capture of a whole blocked_64 sweep (6.515 GB read + 6.301 GB
+# written over 167,772,160 solves); None once that kernel changes
+DRAM_BYTES_PER_SOLVE_NCU = 76.39
 FP32_LANES_PER_SM = 128
 N_SM = 152
-# this library's kernels in one source-iteration step: source build, the sweep kernel,
-# the boundary-leakage sum, the octant reduction
-LAUNCHES_PER_STEP = 4
+# this library's kernels in one source-iteration step: the sweep kernel, the
+# boundary-leakage sum, the octant reduction (which also builds the next source); one
+# source build before the first step of a source_iterate call
+LAUNCHES_PER_STEP = 3
 
 
 def workload_config():
@@ -255,11 +256,24 @@ def eps_p(phi, ref):
     return float(((a - b).abs() / (b.abs() + 1e-8)).mean())
 
 
-def ann_form(P, steps):
-    """The surrogate form on the same workload: train the 27-64-8 network on 2^20 random
-    one-cell problems labelled by the library's elimination, then time the gated
-    surrogate sweep at the largest gate threshold whose converged flux stays within 3%
-    (mean, Eq. (20) style) of the elimination form's converged flux."""
+def flux_errors(phi, ref):
+    """Errors of a flux against a reference [G, C, 8]: the paper's Eq. (20) (mean over
+    cells and groups of |phi - ref| / (|ref| + 1e-8) on the cell-averaged flux), the
+    mean and max nodal relative error under a floor of 1e-8 of the group maximum."""
+    a = phi.double().view(phi.shape[0], -1, 8)
+    b = ref.double().view(ref.shape[0], -1, 8)
+    am, bm = a.mean(-1), b.mean(-1)
+    gmax = b.abs().amax(dim=(1, 2), keepdim=True)
+    nod = (a - b).abs() / (b.abs() + 1e-8 * gmax)
+    return {"eq20": float(((am - bm).abs() / (bm.abs() + 1e-8)).mean()), "nodal_mean": float(nod.mean()),
+            "nodal_max": float(nod.max())}
+
+
+def train_surrogate(P, wl_harvest):
+    """The workload's surrogate: 2^20 one-cell problems of the specified distribution
+    labelled by the library's elimination, 20,000 Adam steps; then fine-tuning on 2^20
+    one-cell problems harvested from an elimination iteration of another instance of
+    the same family (wl_harvest).  Returns the training report."""
     import torch
     from paper_1906_04017_gb300 import sn, workloads
     x = torch.from_numpy(workloads.onecell_problems(1 << 20, seed=0).astype(np.float32)).cuda()
@@ -267,67 +281,94 @@ def ann_form(P, steps):
     tr, te = P.surrogate_train(x, n_test=1 << 16, steps=20000, batch=8192, lr=2e-3, seed=1)
     train_s = time.perf_counter() - t0
     del x
-    ref = P.source_iterate(tol=1e-6, max_it=500, mode=sn.GE32R, use_graph=True, allow_noconv=True)["phi"].clone()
-    stream = torch.cuda.current_stream()
-
-    S_ref = P.source(ref)
-
-    def sweep_rate(mode, reps=5):
-        """Kernel-level solves/s of one sweep from the converged source (CUDA events
-        around the hyperplane launches)."""
-        out_phi = P.flux_tensor()
-        P.sweep(S_ref, out_phi, mode=mode)
-        P.set_profiling(True)
-        P.profile(reset=True)
-        for _ in range(reps):
-            P.sweep(S_ref, out_phi, mode=mode)
-        ms, n = P.profile(reset=True)
-        P.set_profiling(False)
-        fb, _ = P.surrogate_stats() if mode in (sn.ANN, sn.ANN_GATED) else (0, 0)
-        one = eps_p(out_phi, P.sweep(S_ref, mode=sn.GE32R))
-        return P.solves_per_sweep / (ms / n / 1e3), fb / P.solves_per_sweep, one
-
-    def run(mode, tau):
-        if tau is not None:
-            P.surrogate_set_gate(tau)
-        rate, fb, one_sweep_err = sweep_rate(mode)
-        res = {"tau": tau, "sweep_solves_per_s": rate, "fallback_frac": fb, "one_sweep_eps_P_vs_ge": one_sweep_err}
-        phi = P.flux_tensor()
-        try:
-            r = P.source_iterate(phi=phi, tol=1e-5, max_it=300, mode=mode, use_graph=True, allow_noconv=True)
-            res.update({"eps_P_vs_ge": eps_p(phi, ref), "iters": r["iters"], "converged": r["converged"],
-                        "mean_nodal_rel_vs_ge":
-                            float(((phi - ref).abs() / (ref.abs() + 1e-8 * ref.abs().max())).mean())})
-        except sn.SnError as e:
-            res.update({"eps_P_vs_ge": None, "converged": False, "diverged": str(e)})
-        return res
-
-    out = {"train_mae": tr, "test_mae": te, "train_s": train_s, "train_samples": 1 << 20,
-           "train_samples_per_s": 20000 * 8192 / train_s,
-           "ge_sweep_solves_per_s": sweep_rate(sn.GE32R)[0], "random_trained_ungated": run(sn.ANN, None)}
-    # fine-tune on one-cell problems harvested from an elimination sweep of another
-    # instance of the same family (blocked opacity field with a different seed)
     t0 = time.perf_counter()
-    Q = sn.Problem(workloads.blocked(64, 10.0, 8, 8, 8, 16, seed=1))
+    Q = sn.Problem(wl_harvest)
     qphi = Q.source_iterate(tol=1e-4, max_it=200, allow_noconv=True)["phi"]
     cells = torch.cat([Q.harvest(Q.source(qphi), 1 << 19, seed=s) for s in (11, 12)])
     Q.close()
     # the harvested set is fixed by its seeds but arrives in the order the GPU threads
-    # claimed their slots; sort it so that the fine-tuning, and what follows, repeats
-    # from run to run
+    # claimed their slots; sort it so that the fine-tuning repeats from run to run
     host = cells.cpu().numpy()
     order = np.lexsort((host[:, 2], host[:, 1], host[:, 0], host[:, 23], host[:, 19], host[:, 15],
                         host[:, 6], host[:, 7]))
     cells = torch.from_numpy(np.ascontiguousarray(host[order])).cuda()
     feat, targ = sn.surrogate_prepare(cells)
     P.surrogate_fit(feat, targ, steps=20000, batch=8192, lr=5e-4)
-    out["finetune"] = {"harvested_cells": int(cells.shape[0]), "mae": P.surrogate_eval(feat, targ),
-                       "seconds": time.perf_counter() - t0,
-                       "source": "GE sweep of blocked_64 with opacity seed 1 (evaluation uses seed 0)"}
-    del cells, feat, targ
-    out["ungated"] = run(sn.ANN, None)
+    return {"train_mae": tr, "test_mae": te, "train_s": train_s, "train_samples": 1 << 20,
+            "train_samples_per_s": 20000 * 8192 / train_s, "finetune_mae": P.surrogate_eval(feat, targ),
+            "finetune_s": time.perf_counter() - t0, "finetune_cells": int(cells.shape[0])}
+
+
+def sweep_ms(P, S, mode, reps=5):
+    """Best-of-reps kernel time of one sweep from S (CUDA events around the sweep)."""
+    out = P.flux_tensor()
+    P.sweep(S, out, mode=mode)
+    P.set_profiling(True)
+    best = 1e30
+    for _ in range(reps):
+        P.profile(reset=True)
+        P.sweep(S, out, mode=mode)
+        ms, n = P.profile(reset=True)
+        best = min(best, ms / n)
+    P.set_profiling(False)
+    return best
+
+
+def frozen_iteration(P, tau, freeze_after=5, max_chunks=30):
+    """The gated surrogate iteration with the gate frozen: `freeze_after` gated sweeps
+    from a zero flux, the gate's decisions recorded from the source they reached, then
+    frozen sweeps until the Eq. (21) mean change is below 1e-4 (the paper's stop for
+    the network iteration) or 10 * max_chunks more iterations.  Returns (flux, report)."""
+    from paper_1906_04017_gb300 import sn
+    P.surrogate_set_gate(tau)
+    phi = P.flux_tensor()
+    P.source_iterate(phi=phi, tol=0.0, max_it=freeze_after, mode=sn.ANN_GATED, allow_noconv=True)
+    fb = P.surrogate_freeze_gate(P.source(phi))
+    it, r = freeze_after, None
+    for _ in range(max_chunks):
+        r = P.source_iterate(phi=phi, tol=0.0, max_it=10, mode=sn.ANN_FROZEN, use_graph=True, allow_noconv=True)
+        it += 10
+        if r["change_mean"] < 1e-4:
+            break
+    return phi, {"tau": tau, "fallback_frac": fb / P.solves_per_sweep, "iters": it,
+                 "change_mean": r["change_mean"], "change_max": r["change_max"],
+                 "stopped_on_eq21": r["change_mean"] < 1e-4}
+
+
+def ann_form(P, steps, wl, wl_harvest, taus=(0.02, 0.01, 0.007, 0.005)):
+    """The surrogate form on the measured workload: the trained network (train_surrogate)
+    as the cell solver of the same wavefront sweep, ungated and with the residual gate
+    frozen after 5 gated sweeps (frozen_iteration); sweep solves/s against the
+    elimination sweep on the same handle, and the converged flux's error against the
+    FP64 solution (an FP64 source iteration to 1e-10 started from the converged FP32
+    elimination flux).  `value` is the frozen sweep's solves/s at the largest tau whose
+    error (Eq. (20)) is at most 3%."""
+    import torch
+    from paper_1906_04017_gb300 import sn
+    out = {"network": train_surrogate(P, wl_harvest)}
+    ge = P.source_iterate(tol=1e-6, max_it=1000, mode=sn.GE32R, use_graph=True, allow_noconv=True)
+    P64 = sn.Problem(wl, fp64=True)
+    phi64 = ge["phi"].double().clone()
+    t0 = time.perf_counter()
+    r64 = P64.source_iterate(phi=phi64, tol=1e-10, max_it=2000, allow_noconv=True)
+    P64.close()
+    out["fp64_reference"] = {"iters_from_fp32": r64["iters"], "change_max": r64["change_max"],
+                             "seconds": time.perf_counter() - t0}
+    out["ge_vs_fp64"] = flux_errors(ge["phi"], phi64)
+    S = P.source(ge["phi"])
+    ge_ms = sweep_ms(P, S, sn.GE32R)
+    ann_ms = sweep_ms(P, S, sn.ANN)
+    n = P.solves_per_sweep
+    out["ge_sweep_solves_per_s"] = n / (ge_ms / 1e3)
+    out["ungated"] = {"sweep_solves_per_s": n / (ann_ms / 1e3), "speedup_vs_ge_sweep": ge_ms / ann_ms}
+    # the ungated network's source iteration (the paper's use, no gate)
+    phi = P.flux_tensor()
+    try:
+        r = P.source_iterate(phi=phi, tol=0.0, max_it=100, mode=sn.ANN, use_graph=True, allow_noconv=True)
+        out["ungated"].update({"iters": 100, "change_mean": r["change_mean"], **flux_errors(phi, phi64)})
+    except sn.SnError as e:
+        out["ungated"]["iteration"] = "diverged: %s" % e
     # tensor-core roofline of the ungated sweep: 2 (32*64 + 64*16) BF16 flops per row
-    # of the padded tile; the kernel is bound by its CUDA-core work, not the tensor pipe
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -335,17 +376,68 @@ def ann_form(P, steps):
     except OSError:
         pass
     tpeak = peaks.get("bf16_tflops", 1900.0)
-    tach = out["ungated"]["sweep_solves_per_s"] * 2 * (32 * 64 + 64 * 16) / 1e12
-    out["roofline_ungated"] = {"bound": "alu", "tensor_achieved": tach, "tensor_peak": tpeak, "unit": "TFLOP/s",
-                               "tensor_frac": tach / tpeak,
+    tach = n / (ann_ms / 1e3) * 2 * (32 * 64 + 64 * 16) / 1e12
+    out["roofline_ungated"] = {"bound": "latency", "tensor_achieved": tach, "tensor_peak": tpeak,
+                               "unit": "TFLOP/s", "tensor_frac": tach / tpeak,
                                "peak_note": "measured bf16 burst" if "bf16_tflops" in peaks else "fallback"}
-    sweep = [run(sn.ANN_GATED, t) for t in (0.1, 0.05, 0.03, 0.02, 0.01, 0.005)]
-    ok = [r for r in sweep if r.get("eps_P_vs_ge") is not None and r["eps_P_vs_ge"] <= 0.03]
-    best = max(ok, key=lambda r: r["sweep_solves_per_s"]) if ok else None
-    out.update({"gated_sweep": sweep, "value": best["sweep_solves_per_s"] if best else None,
-                "unit": UNIT, "at_tau": best["tau"] if best else None,
-                "speedup_vs_ge_sweep": (best["sweep_solves_per_s"] / out["ge_sweep_solves_per_s"]) if best else None,
-                "error_ref": "converged FP32 GE flux (itself within 1e-5 of FP64)"})
+    rows = []
+    for tau in taus:
+        try:
+            phi, rep = frozen_iteration(P, tau)
+            rep.update(flux_errors(phi, phi64))
+            fz = sweep_ms(P, P.source(phi), sn.ANN_FROZEN)
+            rep.update({"frozen_sweep_solves_per_s": n / (fz / 1e3), "speedup_vs_ge_sweep": ge_ms / fz})
+        except sn.SnError as e:
+            rep = {"tau": tau, "error": str(e)}
+        rows.append(rep)
+    ok = [r for r in rows if r.get("eq20") is not None and r["eq20"] <= 0.03]
+    best = max(ok, key=lambda r: r["tau"]) if ok else None
+    out.update({"gated_frozen": rows, "value": best["frozen_sweep_solves_per_s"] if best else None, "unit": UNIT,
+                "at_tau": best["tau"] if best else None,
+                "speedup_vs_ge_sweep": best["speedup_vs_ge_sweep"] if best else None,
+                "error_ref": "FP64 source iteration (converged to 1e-10)"})
+    return out
+
+
+def ann_large_form():
+    """The large mixed workload (spheres_96: 96^3 cells, LQ_12 = 168 directions, 16
+    groups, high-opacity spheres) in the surrogate form: the network trained as for
+    blocked_64 but fine-tuned on problems harvested from another spheres instance;
+    the graph-captured elimination iteration to 1e-6 (its time is the reference step
+    time), the ungated and frozen-gated sweeps, and the frozen iteration's error
+    against the converged FP32 elimination flux (itself within ~1e-6 of FP64 by the
+    parity measurements; an FP64 iteration of this size does not fit the bench's time)."""
+    import torch
+    from paper_1906_04017_gb300 import sn, workloads
+    wl = workloads.spheres_96()
+    P = sn.Problem(wl)
+    out = {"workload": "spheres_96: 96^3 cells, LQ_12 (168 dirs), 16 groups, 200 spheres",
+           "network": train_surrogate(P, workloads.spheres_96(seed=1))}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ge = P.source_iterate(tol=1e-6, max_it=400, use_graph=True, allow_noconv=True)
+    torch.cuda.synchronize()
+    out["ge_iteration"] = {"iters": ge["iters"], "converged": ge["converged"], "seconds": time.perf_counter() - t0}
+    S = P.source(ge["phi"])
+    n = P.solves_per_sweep
+    t_ge = sweep_ms(P, S, sn.GE32R, reps=3)
+    t_ann = sweep_ms(P, S, sn.ANN, reps=3)
+    out["ge_sweep_solves_per_s"] = n / (t_ge / 1e3)
+    out["ungated_sweep_solves_per_s"] = n / (t_ann / 1e3)
+    out["ungated_speedup_vs_ge_sweep"] = t_ge / t_ann
+    rows = []
+    for tau in (0.01, 0.005):
+        try:
+            phi, rep = frozen_iteration(P, tau, max_chunks=5)
+            rep.update(flux_errors(phi, ge["phi"]))
+            fz = sweep_ms(P, P.source(phi), sn.ANN_FROZEN, reps=3)
+            rep.update({"frozen_sweep_solves_per_s": n / (fz / 1e3), "speedup_vs_ge_sweep": t_ge / fz})
+        except sn.SnError as e:
+            rep = {"tau": tau, "error": str(e)}
+        rows.append(rep)
+    out["gated_frozen"] = rows
+    out["error_ref"] = "converged FP32 elimination flux"
+    P.close()
     return out
 
 
@@ -661,11 +753,12 @@ def run_gpu(args):
         else:
             parity = cb = res
 
-    ann = None if args.no_ann else guarded(ann_form, P, args.steps)
+    ann = None if args.no_ann else guarded(ann_form, P, args.steps, wl, workloads.blocked_64(seed=1))
     octnet = None if args.no_octnet else guarded(octnet_form, P)
 
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dist, "cuda")
     P.close()
+    ann_large = None if args.no_ann else guarded(ann_large_form)
     aniso = None if args.no_aniso else guarded(aniso_form, min(args.steps, 10), ms / args.steps)
     geom = None if args.no_geom else guarded(geom_form, min(args.steps, 10), ms / args.steps)
     if rank != 0:
@@ -694,8 +787,9 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": "sweep_ge_wave<true>", "achieved": achieved_tf,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                      "traffic": (solves * DRAM_BYTES_PER_SOLVE_NCU if DRAM_BYTES_PER_SOLVE_NCU else None),
-                     "traffic_note": "DRAM bytes of one sweep kernel launch (ncu), null until captured for this "
-                                     "kernel",
+                     "traffic_note": "DRAM bytes of one sweep kernel launch from one full-set ncu capture of "
+                                     "this kernel (76.4 B a solve, under the 96 B of the faces: a face written "
+                                     "by one hyperplane is read by the next from L2)",
                      "flops_per_solve": FLOPS_PER_SOLVE,
                      "hbm_achieved_gbs": solves * BYTES_PER_SOLVE / sweep_s / 1e9,
                      "hbm_peak_gbs": hbm_peak,
@@ -707,7 +801,7 @@ def run_gpu(args):
                 "what": "one source iteration a step through sn_source_iterate, the flux copied in from pinned "
                         "host memory and the new flux copied back every step (copies on a second stream, "
                         "overlapping the neighbouring steps)"},
-        "gpu_launches": int(args.steps * LAUNCHES_PER_STEP),
+        "gpu_launches": int(args.steps * LAUNCHES_PER_STEP + 1),
         "clocks": clk,
     }
     if ws > 1:
@@ -716,6 +810,8 @@ def run_gpu(args):
         line["parity"] = parity
     if ann is not None:
         line["ann"] = ann
+    if ann_large is not None:
+        line["ann_large"] = ann_large
     if octnet is not None:
         line["octnet"] = octnet
     if aniso is not None:
