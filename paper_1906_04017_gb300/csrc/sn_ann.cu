@@ -1260,10 +1260,11 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
         if (u >= a.w.nunits) break;
         __syncthreads();   // every thread has read the unit index
         const int4 ud = a.w.units[u];
+        const uint2 up = a.w.uplane[u];
         if (t == 0) cnt[4] = (int)atomicAdd(a.w.next, 1u);
-        const int s = ud.y & 4095, o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
-        const uint32_t c0 = a.w.plane_off[s];
-        const int nkeys = (int)(a.w.plane_off[s + 1] - c0) * G;
+        const int o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
+        const uint32_t c0 = up.x;
+        const int nkeys = (int)up.y;
         const int KB = kTile >> lch, nch = 1 << lch;
         const int chunk = t >> (31 - __clz(KB)), lk = t & (KB - 1);
         const int key = ud.x + lk;
@@ -1308,7 +1309,10 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
         ssig[t] = sig;
         soff[t] = make_uint4(ou0, ou1, ou2, (uint32_t)d0);
         sdst[t] = dst;
-        if (t == 0) cnt[5] = wave_wait_deps(a.w, ud.z, ud.w) ? 0 : 1;
+        if (t < 32) {
+            const bool fine = wave_wait_deps_warp(a.w, ud.z, ud.w);
+            if (t == 0) cnt[5] = fine ? 0 : 1;
+        }
         __syncthreads();
         if (cnt[5]) break;
 

@@ -225,32 +225,59 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
 
 // The persistent wavefront kernel (see the file header).  units[u] = (first key of
 // the tile within its hyperplane and octant, s | o << 12 | lch << 15, first unit of
-// hyperplane s - 1 it depends on, how many).  Thread 0 fetches the next unit's index
-// while the CTA works on the current one, and alone waits for the dependencies.
+// hyperplane s - 1 it depends on, how many); uplane[u] = (first cell of hyperplane s
+// in the hyperplane table, its keys).  Thread 0 takes the next unit's index when the
+// CTA starts a unit and copies its descriptor into shared memory (cp.async) once the
+// current unit's wait is over, so a unit starts without a global round trip; warp 0
+// waits for the dependencies, testing their flags together.  Two CTA barriers a unit:
+// after the wait (which also orders every read of the descriptor before thread 0
+// overwrites it) and after the unit's stores (which also publishes the next one).
 template <bool REFINE>
 __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(KeyArgs a)
 {
     __shared__ __align__(16) KeySmem sm;
-    __shared__ int s_next, s_stop;
+    __shared__ __align__(16) int4 s_ud;
+    __shared__ __align__(8) uint2 s_up;
+    __shared__ int s_u, s_stop;
     const int t = threadIdx.x;
     for (int e = t; e < a.Do; e += kKeyBlock) sm.dsm[e] = a.dir[e];
-    if (t == 0) s_next = (int)atomicAdd(a.w.next, 1u);
+    if (t == 0) {
+        const int u = (int)atomicAdd(a.w.next, 1u);
+        s_u = u;
+        if (u < a.w.nunits) {
+            s_ud = a.w.units[u];
+            s_up = a.w.uplane[u];
+        }
+    }
     __syncthreads();
     for (;;) {
-        const int u = s_next;
+        const int u = s_u;
         if (u >= a.w.nunits) break;
-        __syncthreads();   // every thread has read s_next
-        const int4 ud = a.w.units[u];
-        if (t == 0) s_next = (int)atomicAdd(a.w.next, 1u);
-        const int s = ud.y & 4095, o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
-        const uint32_t c0 = a.w.plane_off[s], c1 = a.w.plane_off[s + 1];
-        const bool ok = key_tile<REFINE>(a, sm, o, a.w.all_cells + c0, (int)(c1 - c0) * a.G, ud.x, lch, [&] {
-            if (t == 0) s_stop = wave_wait_deps(a.w, ud.z, ud.w) ? 0 : 1;
-            __syncthreads();
-            return s_stop == 0;
+        const int4 ud = s_ud;
+        const uint2 up = s_up;
+        int un = 0;
+        if (t == 0) un = (int)atomicAdd(a.w.next, 1u);
+        const int o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
+        const bool ok = key_tile<REFINE>(a, sm, o, a.w.all_cells + up.x, (int)up.y, ud.x, lch, [&] {
+            if (t < 32) {
+                const bool fine = wave_wait_deps_warp(a.w, ud.z, ud.w);
+                if (t == 0) s_stop = fine ? 0 : 1;
+            }
+            __syncthreads();   // after every thread's read of this unit's descriptor
+            const bool go = s_stop == 0;
+            if (t == 0 && go && un < a.w.nunits) {
+                cp_async16(smem_u32(&s_ud), a.w.units + un);
+                cp_async8(smem_u32(&s_up), a.w.uplane + un);
+                cp_async_commit();
+            }
+            return go;
         });
         if (!ok) break;
-        __syncthreads();   // every store of this unit has been issued
+        if (t == 0) {
+            cp_async_wait_all();   // the next unit's descriptor has landed
+            s_u = un;
+        }
+        __syncthreads();   // every store of this unit has been issued; the next unit is published
         if (t == 0) wave_done(a.w, u);
     }
     cp_async_wait_all();
@@ -309,6 +336,7 @@ void free_wave(sn_handle h)
     if (!h || !h->wave) return;
     WaveTables *w = static_cast<WaveTables *>(h->wave);
     cudaFree(w->units);
+    cudaFree(w->uplane);
     cudaFree(w->flags);
     cudaFree(w->plane_off);
     delete w;
@@ -348,6 +376,7 @@ sn_status build_wave(sn_handle h)
     }
     if (first[np] >= (1LL << 30) || np > 4095) return SN_OK;   // the per-hyperplane kernel serves it
     std::vector<int4> units((size_t)first[np]);
+    std::vector<uint2> uplane((size_t)first[np]);
     for (int s = 0; s < np; ++s) {
         const int64_t kb = kKeyBlock >> lch[s];
         const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
@@ -378,6 +407,7 @@ sn_status build_wave(sn_handle h)
                 const int64_t u = first[s] + (int64_t)o * ntile[s] + tl;
                 units[u] = make_int4((int)(tl * kb), s | (o << 12) | (lch[s] << 15),
                                      s > 0 ? (int)(first[s - 1] + (int64_t)o * ntile[s - 1] + dlo) : 0, (int)dn);
+                uplane[u] = make_uint2((uint32_t)h->plane_off[s], (uint32_t)(n * G));
             }
         }
     }
@@ -387,10 +417,14 @@ sn_status build_wave(sn_handle h)
     std::vector<uint32_t> poff(np + 1);
     for (int s = 0; s <= np; ++s) poff[s] = (uint32_t)h->plane_off[s];
     SN_CK(h, cudaMalloc(&w->units, sizeof(int4) * units.size()));
+    SN_CK(h, cudaMalloc(&w->uplane, sizeof(uint2) * uplane.size()));
     SN_CK(h, cudaMalloc(&w->flags, sizeof(uint32_t) * (units.size() + 1)));
     SN_CK(h, cudaMalloc(&w->plane_off, sizeof(uint32_t) * poff.size()));
-    h->device_bytes += (int64_t)(sizeof(int4) * units.size() + sizeof(uint32_t) * (units.size() + 1 + poff.size()));
+    h->device_bytes += (int64_t)((sizeof(int4) + sizeof(uint2)) * units.size() +
+                                 sizeof(uint32_t) * (units.size() + 1 + poff.size()));
     SN_CK(h, cudaMemcpyAsync(w->units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, h->stream));
+    SN_CK(h, cudaMemcpyAsync(w->uplane, uplane.data(), sizeof(uint2) * uplane.size(), cudaMemcpyHostToDevice,
+                             h->stream));
     SN_CK(h, cudaMemcpyAsync(w->plane_off, poff.data(), sizeof(uint32_t) * poff.size(), cudaMemcpyHostToDevice,
                              h->stream));
     int per_sm = 0;
@@ -410,6 +444,7 @@ WaveCtl wave_ctl(sn_handle h)
     c.all_cells = h->plane_cells;
     c.plane_off = w->plane_off;
     c.units = w->units;
+    c.uplane = w->uplane;
     c.flags = w->flags;
     c.next = w->flags + w->nunits;
     c.abort = h->acc + ACC_ABORT;
