@@ -1260,7 +1260,7 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
         if (u >= a.w.nunits) break;
         __syncthreads();   // every thread has read the unit index
         const int4 ud = a.w.units[u];
-        const uint2 up = a.w.uplane[u];
+        const int4 up = a.w.uplane[u];
         if (t == 0) cnt[4] = (int)atomicAdd(a.w.next, 1u);
         const int o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
         const uint32_t c0 = up.x;
@@ -1310,7 +1310,7 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
         soff[t] = make_uint4(ou0, ou1, ou2, (uint32_t)d0);
         sdst[t] = dst;
         if (t < 32) {
-            const bool fine = wave_wait_deps_warp(a.w, ud.z, ud.w);
+            const bool fine = wave_wait_deps_warp(a.w, ud.z, ud.w, up.z, up.w);
             if (t == 0) cnt[5] = fine ? 0 : 1;
         }
         __syncthreads();

@@ -136,7 +136,7 @@ struct sn_handle_s {
     void *sigs_n = nullptr;
     void *yhat = nullptr;
 
-    // unit tables of the wavefront kernel of the key sweep (sn_sweep_keys.cu)
+    // unit tables of the wavefront kernels (sn_sweep_keys.cu)
     void *wave = nullptr;
 
     // the paper's per-octant networks (sn_octnet_init / sn_octnet_set)

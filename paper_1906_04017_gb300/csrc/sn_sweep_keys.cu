@@ -223,21 +223,22 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
     });
 }
 
-// The persistent wavefront kernel (see the file header).  units[u] = (first key of
-// the tile within its hyperplane and octant, s | o << 12 | lch << 15, first unit of
-// hyperplane s - 1 it depends on, how many); uplane[u] = (first cell of hyperplane s
-// in the hyperplane table, its keys).  Thread 0 takes the next unit's index when the
-// CTA starts a unit and copies its descriptor into shared memory (cp.async) once the
-// current unit's wait is over, so a unit starts without a global round trip; warp 0
-// waits for the dependencies, testing their flags together.  Two CTA barriers a unit:
-// after the wait (which also orders every read of the descriptor before thread 0
-// overwrites it) and after the unit's stores (which also publishes the next one).
+// The persistent wavefront kernel (see the file header), one unit a CTA: units[u] =
+// (first key of the tile within its hyperplane and octant, s | o << 12 | lch << 15,
+// first unit of hyperplane s - 1 it depends on, how many) with kKeyBlock >> lch keys
+// a tile; uplane[u] = (first cell of hyperplane s in the hyperplane table, its keys,
+// the second range of units it depends on).  Thread 0 takes the next unit's index
+// when the CTA starts a unit and copies its descriptor into shared memory (cp.async)
+// once the current unit's wait is over, so a unit starts without a global round trip;
+// warp 0 waits for the dependencies, testing their flags together.  Two CTA barriers a
+// unit: after the wait (which also orders every read of the descriptor before thread
+// 0 overwrites it) and after the unit's stores (which also publishes the next one).
 template <bool REFINE>
 __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(KeyArgs a)
 {
     __shared__ __align__(16) KeySmem sm;
     __shared__ __align__(16) int4 s_ud;
-    __shared__ __align__(8) uint2 s_up;
+    __shared__ __align__(16) int4 s_up;
     __shared__ int s_u, s_stop;
     const int t = threadIdx.x;
     for (int e = t; e < a.Do; e += kKeyBlock) sm.dsm[e] = a.dir[e];
@@ -253,21 +254,22 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(Key
     for (;;) {
         const int u = s_u;
         if (u >= a.w.nunits) break;
-        const int4 ud = s_ud;
-        const uint2 up = s_up;
+        const int2 ud = make_int2(s_ud.x, s_ud.y);   // first key; s, o, lch
+        const int2 up = make_int2(s_up.x, s_up.y);   // the hyperplane's first cell, keys
         int un = 0;
         if (t == 0) un = (int)atomicAdd(a.w.next, 1u);
         const int o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
-        const bool ok = key_tile<REFINE>(a, sm, o, a.w.all_cells + up.x, (int)up.y, ud.x, lch, [&] {
+        const bool ok = key_tile<REFINE>(a, sm, o, a.w.all_cells + up.x, up.y, ud.x, lch, [&] {
             if (t < 32) {
-                const bool fine = wave_wait_deps_warp(a.w, ud.z, ud.w);
+                const int4 d1 = s_ud, d2 = s_up;   // the dependency ranges (not kept in registers)
+                const bool fine = wave_wait_deps_warp(a.w, d1.z, d1.w, d2.z, d2.w);
                 if (t == 0) s_stop = fine ? 0 : 1;
             }
             __syncthreads();   // after every thread's read of this unit's descriptor
             const bool go = s_stop == 0;
             if (t == 0 && go && un < a.w.nunits) {
                 cp_async16(smem_u32(&s_ud), a.w.units + un);
-                cp_async8(smem_u32(&s_up), a.w.uplane + un);
+                cp_async16(smem_u32(&s_up), a.w.uplane + un);
                 cp_async_commit();
             }
             return go;
@@ -331,15 +333,19 @@ static int key_chunks_log2(int64_t keys, int Do)
     return l;
 }
 
-void free_wave(sn_handle h)
+static void free_tables(WaveTables *w)
 {
-    if (!h || !h->wave) return;
-    WaveTables *w = static_cast<WaveTables *>(h->wave);
+    if (!w) return;
     cudaFree(w->units);
     cudaFree(w->uplane);
     cudaFree(w->flags);
-    cudaFree(w->plane_off);
     delete w;
+}
+
+void free_wave(sn_handle h)
+{
+    if (!h) return;
+    free_tables(static_cast<WaveTables *>(h->wave));
     h->wave = nullptr;
 }
 
@@ -347,23 +353,14 @@ void free_wave(sn_handle h)
 // consecutive keys (key = position of the cell within the hyperplane x G + g); it
 // depends on the tiles of hyperplane s - 1 of the same octant (the octants are
 // independent) that hold the upwind neighbours (i'-1,j',k'), (i',j'-1,k'),
-// (i',j',k'-1) of its cells: a contiguous range, since a hyperplane's cells are
-// listed by (k', j').
-// SN_KEY_WAVE=0 keeps the per-hyperplane launches (the form the wavefront kernel is
-// measured against)
-#ifndef SN_KEY_WAVE
-#define SN_KEY_WAVE 1
-#endif
-sn_status build_wave(sn_handle h)
+// (i',j',k'-1) of its cells.  A hyperplane's cells are listed by (k', j'), so those
+// tiles form two clusters (the neighbours in the tile's own k' rows, and those in the
+// rows k' - 1): each unit carries two ranges, split at the largest gap.
+static sn_status build_tables(sn_handle h, const std::vector<uint32_t> &cells, const std::vector<uint32_t> &pos,
+                              WaveTables **out)
 {
-    free_wave(h);
-    if (!SN_KEY_WAVE || !key_sweep_ok(h)) return SN_OK;
+    *out = nullptr;
     const int np = h->nplanes, G = h->G;
-    std::vector<uint32_t> cells(h->ncell), pos(h->ncell);
-    SN_CK(h, cudaMemcpyAsync(cells.data(), h->plane_cells, sizeof(uint32_t) * h->ncell, cudaMemcpyDeviceToHost,
-                             h->stream));
-    SN_CK(h, cudaMemcpyAsync(pos.data(), h->plane_pos, sizeof(uint32_t) * h->ncell, cudaMemcpyDeviceToHost, h->stream));
-    SN_CK(h, cudaStreamSynchronize(h->stream));
     std::vector<int> lch(np), ntile(np);
     std::vector<int64_t> first(np + 1);   // first unit of each hyperplane
     first[0] = 0;
@@ -375,17 +372,17 @@ sn_status build_wave(sn_handle h)
         first[s + 1] = first[s] + 8 * (int64_t)ntile[s];
     }
     if (first[np] >= (1LL << 30) || np > 4095) return SN_OK;   // the per-hyperplane kernel serves it
-    std::vector<int4> units((size_t)first[np]);
-    std::vector<uint2> uplane((size_t)first[np]);
+    std::vector<int4> units((size_t)first[np]), uplane((size_t)first[np]);
+    std::vector<int64_t> dep;
     for (int s = 0; s < np; ++s) {
         const int64_t kb = kKeyBlock >> lch[s];
         const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
         const int64_t kbp = s > 0 ? (kKeyBlock >> lch[s - 1]) : 1;
         for (int tl = 0; tl < ntile[s]; ++tl) {
-            int64_t dlo = 0, dn = 0;
+            int64_t lo1 = 0, n1 = 0, lo2 = 0, n2 = 0;
             if (s > 0) {
+                dep.clear();
                 const int64_t p0 = tl * kb / G, p1 = std::min<int64_t>(n - 1, (tl * kb + kb - 1) / G);
-                int64_t lo = INT64_MAX, hi = -1;
                 for (int64_t q = p0; q <= p1; ++q) {
                     const uint32_t pk = cells[h->plane_off[s] + q];
                     const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
@@ -394,45 +391,77 @@ sn_status build_wave(sn_handle h)
                         if (nb[m][0] < 0 || nb[m][1] < 0 || nb[m][2] < 0) continue;
                         const int64_t lin = nb[m][0] + (int64_t)h->nx * (nb[m][1] + (int64_t)h->ny * nb[m][2]);
                         const int64_t pp = pos[lin];
-                        lo = std::min(lo, pp);
-                        hi = std::max(hi, pp);
+                        for (int64_t d = pp * G / kbp; d <= (pp * G + G - 1) / kbp; ++d) dep.push_back(d);
                     }
                 }
-                if (hi >= 0) {
-                    dlo = lo * G / kbp;
-                    dn = (hi * G + G - 1) / kbp - dlo + 1;
+                if (!dep.empty()) {
+                    std::sort(dep.begin(), dep.end());
+                    dep.erase(std::unique(dep.begin(), dep.end()), dep.end());
+                    size_t cut = dep.size();   // start of the second cluster
+                    int64_t gap = 1;
+                    for (size_t e = 1; e < dep.size(); ++e)
+                        if (dep[e] - dep[e - 1] > gap) {
+                            gap = dep[e] - dep[e - 1];
+                            cut = e;
+                        }
+                    lo1 = dep[0];
+                    n1 = dep[cut - 1] - dep[0] + 1;
+                    if (cut < dep.size()) {
+                        lo2 = dep[cut];
+                        n2 = dep.back() - dep[cut] + 1;
+                    }
                 }
             }
             for (int o = 0; o < 8; ++o) {
                 const int64_t u = first[s] + (int64_t)o * ntile[s] + tl;
-                units[u] = make_int4((int)(tl * kb), s | (o << 12) | (lch[s] << 15),
-                                     s > 0 ? (int)(first[s - 1] + (int64_t)o * ntile[s - 1] + dlo) : 0, (int)dn);
-                uplane[u] = make_uint2((uint32_t)h->plane_off[s], (uint32_t)(n * G));
+                const int64_t base = s > 0 ? first[s - 1] + (int64_t)o * ntile[s - 1] : 0;
+                units[u] = make_int4((int)(tl * kb), s | (o << 12) | (lch[s] << 15), (int)(base + lo1), (int)n1);
+                uplane[u] = make_int4((int)h->plane_off[s], (int)(n * G), (int)(base + lo2), (int)n2);
             }
         }
     }
     WaveTables *w = new WaveTables();
-    h->wave = w;
     w->nunits = (int)first[np];
-    std::vector<uint32_t> poff(np + 1);
-    for (int s = 0; s <= np; ++s) poff[s] = (uint32_t)h->plane_off[s];
-    SN_CK(h, cudaMalloc(&w->units, sizeof(int4) * units.size()));
-    SN_CK(h, cudaMalloc(&w->uplane, sizeof(uint2) * uplane.size()));
-    SN_CK(h, cudaMalloc(&w->flags, sizeof(uint32_t) * (units.size() + 1)));
-    SN_CK(h, cudaMalloc(&w->plane_off, sizeof(uint32_t) * poff.size()));
-    h->device_bytes += (int64_t)((sizeof(int4) + sizeof(uint2)) * units.size() +
-                                 sizeof(uint32_t) * (units.size() + 1 + poff.size()));
-    SN_CK(h, cudaMemcpyAsync(w->units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, h->stream));
-    SN_CK(h, cudaMemcpyAsync(w->uplane, uplane.data(), sizeof(uint2) * uplane.size(), cudaMemcpyHostToDevice,
+    cudaError_t e = cudaMalloc(&w->units, sizeof(int4) * units.size());
+    if (e == cudaSuccess) e = cudaMalloc(&w->uplane, sizeof(int4) * uplane.size());
+    if (e == cudaSuccess) e = cudaMalloc(&w->flags, sizeof(uint32_t) * (units.size() + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->uplane, uplane.data(), sizeof(int4) * uplane.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // the host vectors go out of scope
+    if (e != cudaSuccess) {
+        free_tables(w);
+        return cuda_fail(h, e, "build_wave");
+    }
+    h->device_bytes += (int64_t)(2 * sizeof(int4) * units.size() + sizeof(uint32_t) * (units.size() + 1));
+    *out = w;
+    return SN_OK;
+}
+
+// SN_KEY_WAVE=0 keeps the per-hyperplane launches (the form the wavefront kernel is
+// measured against)
+#ifndef SN_KEY_WAVE
+#define SN_KEY_WAVE 1
+#endif
+// The unit tables of the wavefront kernels (the elimination and the surrogate sweep).
+sn_status build_wave(sn_handle h)
+{
+    free_wave(h);
+    if (!SN_KEY_WAVE || !key_sweep_ok(h)) return SN_OK;
+    std::vector<uint32_t> cells(h->ncell), pos(h->ncell);
+    SN_CK(h, cudaMemcpyAsync(cells.data(), h->plane_cells, sizeof(uint32_t) * h->ncell, cudaMemcpyDeviceToHost,
                              h->stream));
-    SN_CK(h, cudaMemcpyAsync(w->plane_off, poff.data(), sizeof(uint32_t) * poff.size(), cudaMemcpyHostToDevice,
-                             h->stream));
-    int per_sm = 0;
+    SN_CK(h, cudaMemcpyAsync(pos.data(), h->plane_pos, sizeof(uint32_t) * h->ncell, cudaMemcpyDeviceToHost, h->stream));
+    SN_CK(h, cudaStreamSynchronize(h->stream));
+    WaveTables *w = nullptr;
+    sn_status r = build_tables(h, cells, pos, &w);
+    if (r != SN_OK || !w) return r;
+    int per_sm = 0, per_sm2 = 0;
     SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_ge_wave<true>, kKeyBlock, 0));
-    int per_sm2 = 0;
     SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, sweep_ge_wave<false>, kKeyBlock, 0));
     w->grid = std::max(1, std::min(std::min(per_sm, per_sm2), SN_KEY_MINBLOCKS) * num_sms());
-    SN_CK(h, cudaStreamSynchronize(h->stream));
+    h->wave = w;
     return SN_OK;
 }
 
@@ -442,7 +471,6 @@ WaveCtl wave_ctl(sn_handle h)
     WaveCtl c = {};
     if (!w) return c;
     c.all_cells = h->plane_cells;
-    c.plane_off = w->plane_off;
     c.units = w->units;
     c.uplane = w->uplane;
     c.flags = w->flags;
