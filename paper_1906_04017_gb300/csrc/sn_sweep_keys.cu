@@ -80,8 +80,16 @@ struct KeyArgs {
     WaveCtl w;                   // wavefront kernel
 };
 
+// Inflow-face stages a thread cycles through: the faces of the next NST - 1 directions
+// are in flight while one is solved.  Three stages measured faster for the solve
+// without refinement (3.94 against 4.11 ms on blocked_64) and slower with it, whose
+// registers they push into spills (4.59 against 4.56 ms).
+template <bool REFINE>
+constexpr int key_stages() { return REFINE ? 2 : 3; }
+
+template <int NST>
 struct KeySmem {
-    float4 stage[2][3][kKeyBlock];   // per-thread inflow stages
+    float4 stage[NST][3][kKeyBlock];   // per-thread inflow stages
     float4 msrc[2][kKeyBlock];       // per-thread (Mh x Mh x Mh) S
     float4 dsm[kKeyMaxDo];           // direction table
     float red[8 * kKeyBlock];        // chunk partials of the flux (more than one chunk)
@@ -94,7 +102,8 @@ struct KeySmem {
 // must contain a CTA barrier, and returns once the upwind faces are complete (false:
 // give the tile up).  Returns false if the tile was given up.
 template <bool REFINE, typename Wait>
-__device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem &sm, int o, const uint32_t *cells, int nkeys,
+__device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<REFINE>()> &sm, int o,
+                                         const uint32_t *cells, int nkeys,
                                          int key0, int lch, Wait wait)
 {
     const int t = threadIdx.x;
@@ -156,14 +165,25 @@ __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem &sm, int o, c
             cp_async16(nb + AX, a.face + ((bnd & 2u) ? inb + 2u + (uint32_t)((o >> 1) & 1) : s1));
             cp_async16(nb + 2 * AX, a.face + ((bnd & 4u) ? inb + 4u + (uint32_t)((o >> 2) & 1) : s2));
         };
+        constexpr int kKeyStages = key_stages<REFINE>();
         issue(0u, ou0, ou1, ou2);
         cp_async_commit();
-        for (int d = d0; d < d1; ++d) {
-            const int cur = (d - d0) & 1;
-            if (d + 1 < d1) issue((uint32_t)(cur ^ 1), ou0 + (uint32_t)G, ou1 + (uint32_t)G, ou2 + (uint32_t)G);
+        if constexpr (kKeyStages == 3) {
+            if (d0 + 1 < d1) issue(1u, ou0 + (uint32_t)G, ou1 + (uint32_t)G, ou2 + (uint32_t)G);
             cp_async_commit();
-            cp_async_wait_pending<1>();   // this direction's faces have landed
+        }
+        int cur = 0;   // this direction's stage
+        for (int d = d0; d < d1; ++d) {
+            // the stage of direction d + kKeyStages - 1, which the slot offsets (advanced
+            // one direction a step) reach at + (kKeyStages - 1) G
+            const int nxt = cur == 0 ? kKeyStages - 1 : cur - 1;
+            constexpr uint32_t ahead = kKeyStages - 1;
+            if (d + (int)ahead < d1)
+                issue((uint32_t)nxt, ou0 + ahead * (uint32_t)G, ou1 + ahead * (uint32_t)G, ou2 + ahead * (uint32_t)G);
+            cp_async_commit();
+            cp_async_wait_pending<kKeyStages - 1>();   // this direction's faces have landed
             const float4 fx = sm.stage[cur][0][t], fy = sm.stage[cur][1][t], fz = sm.stage[cur][2][t];
+            cur = cur + 1 == kKeyStages ? 0 : cur + 1;
             const float4 m0 = sm.msrc[0][t], m1 = sm.msrc[1][t];
             const float4 dd = sm.dsm[d];
             const float ux[4] = {fx.x, fx.y, fx.z, fx.w};
@@ -213,7 +233,7 @@ __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem &sm, int o, c
 template <bool REFINE, int LCH>
 __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(KeyArgs a)
 {
-    __shared__ __align__(16) KeySmem sm;
+    __shared__ __align__(16) KeySmem<key_stages<REFINE>()> sm;
     griddep_launch();
     for (int e = threadIdx.x; e < a.Do; e += kKeyBlock) sm.dsm[e] = a.dir[e];
     key_tile<REFINE>(a, sm, (int)blockIdx.y, a.cells, a.nkeys, (int)blockIdx.x * (kKeyBlock >> LCH), LCH, [] {
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
 template <bool REFINE>
 __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(KeyArgs a)
 {
-    __shared__ __align__(16) KeySmem sm;
+    __shared__ __align__(16) KeySmem<key_stages<REFINE>()> sm;
     __shared__ __align__(16) int4 s_ud;
     __shared__ __align__(16) int4 s_up;
     __shared__ int s_u, s_stop;

@@ -171,6 +171,27 @@ def test_nan_is_reported(sn):
     assert e.value.status == sn.SN_ENAN
 
 
+def test_unrefined_elimination_sweep_long_keys(sn):
+    """SN_SOLVE_GE32 (FP32 elimination without the refinement step) on 16^3 cells,
+    LQ_8, 128 groups: the central hyperplanes hold more keys than the grid's threads,
+    so a key runs all 10 of its octant's directions through the three-stage face
+    prefetch of this mode.  Groups 5 and 6 against the FP64 oracle: without the
+    refinement step the FP32 elimination keeps its rounding error (about the condition
+    number times 2^-24), so the bar is 1e-4 of the group maximum, and the refined mode
+    on the same source is closer to the oracle than the unrefined one."""
+    wl = W.blocked(16, 2.5, 8, 128, 8, 4, seed=3)
+    P = sn.Problem(wl)
+    rng = np.random.default_rng(12)
+    S = rng.uniform(0.0, 1.0, (P.G, P.ncell, 8)).astype(np.float32)
+    phi = P.sweep(cuda32(S), mode=sn.GE32).cpu().numpy()
+    phir = P.sweep(cuda32(S), mode=sn.GE32R).cpu().numpy()
+    P.close()
+    ref, _ = oracle.OracleProblem(wl).sweep(S.astype(np.float64), groups=(5, 7))
+    e, er = rel_err(phi[5:7], ref[5:7]), rel_err(phir[5:7], ref[5:7])
+    print("long keys: GE32 max-norm rel err %.2e, GE32R %.2e" % (e, er))
+    assert e < 1e-4 and er < TOL and er <= e
+
+
 def test_blocked_64_sampled_group(sn):
     """The plain method at scale (64^3, LQ_8, 8 groups): one GPU sweep of every
     group from a random source, with group 5 recomputed by the oracle."""
