@@ -1218,7 +1218,8 @@ constexpr uint32_t kAkDst = kAkRed + kTile * 32;        // [128] flux-partial in
 constexpr uint32_t kAkCnt = kAkDst + kTile * 4;         // [8] ints: warp counts, next unit, stop
 constexpr uint32_t kAkBar = kAkCnt + 32;                // two mbarriers: layer 1, layer 2
 constexpr uint32_t kAkMisc = kAkBar + 16;               // tmem slot, (unused), abort
-constexpr uint32_t kAkSmem = kAkMisc + 16;
+constexpr uint32_t kAkB2 = kAkMisc + 16;                // [8] the output bias
+constexpr uint32_t kAkSmem = kAkB2 + 32;
 constexpr uint32_t kAkTmemCols = 2 * kTmemCols;         // two steps in flight
 
 // Two direction steps are in flight per CTA: while the hidden layer and the outputs
@@ -1246,9 +1247,9 @@ __global__ void __launch_bounds__(kTile, MODE == ANN_UNGATED ? 4 : 3) sweep_ann_
         sdir[e] = a.dir[e];
         sdab[e] = a.dir_abs[e];
     }
-    float b2[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) b2[q] = a.ann.b2[q];
+    // the output bias from shared memory (registers are the gated modes' limit)
+    float *b2 = reinterpret_cast<float *>(smem + kAkB2);
+    if (t < 8) b2[t] = a.ann.b2[t];
     const float lsig_scale = 0.69314718f / kLogSigScale;   // log2 -> the sigma_t input
     uint32_t phA = 0, phB = 0;
     unsigned long long nfb = 0;
@@ -1556,17 +1557,22 @@ static sn_status launch_sweep_ann_keys(sn_handle h, const float *S, float *phi_o
     void (*kern)(AnnKeyArgs) = mode == ANN_UNGATED ? sweep_ann_wave<ANN_UNGATED>
                                : mode == ANN_GATED ? sweep_ann_wave<ANN_GATED> : sweep_ann_wave<ANN_FROZEN>;
     SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAkSmem));
-    // the whole unified L1 / shared array as shared memory, so that the CTAs the
-    // registers allow also fit their 54 KB each
-    SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  (int)cudaSharedmemCarveoutMaxShared));
     // CTAs an SM: the kernel's register bound (4 ungated, 3 with the elimination's
     // registers), its shared memory (plus the 1 KB the driver reserves a CTA) within
     // 228 KB, and 128 of the SM's 512 TMEM columns each (the occupancy query does not
-    // see the carveout set above and answers 1)
+    // see the carveout set below and answers 1)
     int per_sm = mode == ANN_UNGATED ? 4 : 3;
     per_sm = std::min(per_sm, (int)((228 * 1024) / (kAkSmem + 1024)));
     per_sm = std::max(1, std::min(per_sm, (int)(512 / kAkTmemCols)));
+    // The unified L1 / shared array: the whole of it as shared memory for the ungated
+    // kernel (4 CTAs of 55 KB), and no more than its 3 CTAs take for the gated modes,
+    // whose elimination spills a few registers: their local-memory traffic then stays in
+    // L1 (with the whole array as shared memory it went to L2; the frozen sweep at half
+    // the rows to elimination took 11.1 ms that way on blocked_64, 10.6 ms this way).
+    int carve = (int)cudaSharedmemCarveoutMaxShared;
+    if (mode != ANN_UNGATED)
+        carve = std::min(100, (int)((100 * (int64_t)per_sm * (kAkSmem + 1024) + 228 * 1024 - 1) / (228 * 1024)));
+    SN_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
     SN_CK(h, cudaMemsetAsync(wt->flags, 0, sizeof(uint32_t) * (size_t)(wt->nunits + 1), st));
     if (record) SN_CK(h, cudaMemsetAsync(net->mask, 0, sizeof(uint32_t) * (size_t)net->mask_words, st));
     if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
