@@ -663,10 +663,13 @@ __global__ void __launch_bounds__(SN_GE_BLOCK, (tile_min_blocks<T, false>())) sw
     ge_tiles_body<T, REFINE, 0, false, true>(a);
 }
 
-// CTAs per SM of the general-cell sweep: at 4 (128 registers, with spills) it measured
-// as fast as at 3 (168) and faster than at 2 (254, no spills)
+// CTAs per SM of the general-cell sweep.  With the matrices staged in shared memory
+// (49 KB a CTA), 4 CTAs (128 registers) leave little of the unified array to L1 for
+// their spills (796 bytes a thread); 3 (168 registers, 268 bytes of spill) measured
+// 9% faster on deformed blocked_64 (29.6 against 32.4 ms a step), 2 (254 registers, no
+// spills) slower than either
 #ifndef SN_GEOM_MINBLOCKS
-#define SN_GEOM_MINBLOCKS 4
+#define SN_GEOM_MINBLOCKS 3
 #endif
 template <typename T, bool REFINE>
 __global__ void __launch_bounds__(SN_GE_BLOCK, (sizeof(T) == 4 ? SN_GEOM_MINBLOCKS : 1)) sweep_ge_hex(SweepArgs<T> a)
