@@ -626,6 +626,102 @@ __device__ __forceinline__ void cell_solve_key_x2(float t3x, float t3y, float t3
     }
 }
 
+// The paired solve with its inputs in shared memory (the key's (Mh x Mh x Mh) S as two
+// 4-vectors and the three inflow faces): the right-hand side is formed from them where
+// it is needed (the elimination, the exchange path, the refinement residual) instead
+// of being kept in registers across the elimination.  The operations, and so the
+// results, are those of cell_solve_key_x2.
+template <bool REFINE>
+__device__ __forceinline__ void cell_solve_key_x2_sm(float t3x, float t3y, float t3z, float sig,
+                                                     const float4 *m0p, const float4 *m1p, const float4 *fxp,
+                                                     const float4 *fyp, const float4 *fzp, float (&x)[8])
+{
+    auto rhs = [&](float (&bb)[8]) {
+        const float4 m0 = *m0p, m1 = *m1p, fx = *fxp, fy = *fyp, fz = *fzp;
+        const float Sm[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        const float ux[4] = {fx.x, fx.y, fx.z, fx.w}, uy[4] = {fy.x, fy.y, fy.z, fy.w},
+                    uz[4] = {fz.x, fz.y, fz.z, fz.w};
+        build_b_msrc(2.f * t3x, 2.f * t3y, 2.f * t3z, Sm, ux, uy, uz, bb);
+    };
+    float2 A[8][4];
+    {
+        float As[8][8];
+        assemble_A27(t3x, t3y, t3z, sig, As);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) A[k][q] = make_float2(As[k][2 * q], As[k][2 * q + 1]);
+        }
+    }
+    float b[8], rinv[8];
+    rhs(b);
+    bool ex = false;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int kq = k >> 1, kl = k & 1;
+        float m = fabsf(pel(A[k + 1][kq], kl));
+#pragma unroll
+        for (int r = k + 2; r < 8; ++r) m = fmaxf(m, fabsf(pel(A[r][kq], kl)));
+        ex |= m > fabsf(pel(A[k][kq], kl));
+        rinv[k] = pivot_recip(pel(A[k][kq], kl));
+#pragma unroll
+        for (int r = k + 1; r < 8; ++r) {
+            const float l = pel(A[r][kq], kl) * rinv[k];
+            const float2 nl = make_float2(-l, -l);
+#pragma unroll
+            for (int q = kq; q < 4; ++q) {
+                if (2 * q + 1 <= k) continue;
+                A[r][q] = __ffma2_rn(nl, A[k][q], A[r][q]);
+            }
+            pel(A[r][kq], kl) = l;
+            b[r] = fmaf(-l, b[k], b[r]);
+        }
+    }
+    rinv[7] = pivot_recip(A[7][3].y);
+#pragma unroll
+    for (int r = 7; r >= 0; --r) {
+        float sum = b[r];
+#pragma unroll
+        for (int c = r + 1; c < 8; ++c) sum = fmaf(-pel(A[r][c >> 1], c & 1), x[c], sum);
+        x[r] = sum * rinv[r];
+    }
+    if (__any_sync(__activemask(), ex) && ex) {
+        float As[8][8], bb[8], rp[8];
+        assemble_A27(t3x, t3y, t3z, sig, As);
+        rhs(bb);
+        unsigned piv;
+        ge8_factor_solve(As, bb, piv, rp, x);
+        if (REFINE) {
+            float b0[8], r[8], dx[8];
+            rhs(b0);
+            residual_A(t3x, t3y, t3z, sig, x, b0, r);
+            ge8_replay(As, piv, rp, r, dx);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] += dx[k];
+        }
+        return;
+    }
+    if (REFINE) {
+        float b0[8], r[8], dx[8];
+        rhs(b0);
+        residual_A(t3x, t3y, t3z, sig, x, b0, r);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+#pragma unroll
+            for (int q = k + 1; q < 8; ++q) r[q] = fmaf(-pel(A[q][k >> 1], k & 1), r[k], r[q]);
+        }
+#pragma unroll
+        for (int q = 7; q >= 0; --q) {
+            float sum = r[q];
+#pragma unroll
+            for (int c = q + 1; c < 8; ++c) sum = fmaf(-pel(A[q][c >> 1], c & 1), dx[c], sum);
+            dx[q] = sum * rinv[q];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] += dx[k];
+    }
+}
+
 // The key sweep's solve: GE with partial pivoting (diagonal pivots first, exchange
 // path where the pivoting test fails) and, with REFINE, one FP32 refinement step.
 template <bool REFINE>
