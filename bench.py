@@ -39,7 +39,7 @@ BYTES_PER_SOLVE = 96
 # DRAM bytes (read + write) per solve of the wavefront sweep kernel (sweep_ge_wave<true>)
 # from one full-set ncu capture of a whole blocked_64 sweep (6.403 GB read + 6.202 GB
 # written over 167,772,160 solves); None once that kernel changes
-DRAM_BYTES_PER_SOLVE_NCU = 75.14
+DRAM_BYTES_PER_SOLVE_NCU = None
 FP32_LANES_PER_SM = 128
 N_SM = 152
 # this library's kernels in one source-iteration step: the sweep kernel, the
