@@ -37,9 +37,9 @@ FLOPS_PER_SOLVE = 1450
 # algorithmic HBM bytes of one solve: 12 inflow + 12 outflow face floats
 BYTES_PER_SOLVE = 96
 # DRAM bytes (read + write) per solve of the wavefront sweep kernel (sweep_ge_wave<true>)
-# from one full-set ncu capture of a whole blocked_64 sweep (6.403 GB read + 6.202 GB
+# from one full-set ncu capture of a whole blocked_64 sweep (6.391 GB read + 6.194 GB
 # written over 167,772,160 solves); None once that kernel changes
-DRAM_BYTES_PER_SOLVE_NCU = None
+DRAM_BYTES_PER_SOLVE_NCU = 75.01
 FP32_LANES_PER_SM = 128
 N_SM = 152
 # this library's kernels in one source-iteration step: the sweep kernel, the
@@ -788,7 +788,7 @@ def run_gpu(args):
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                      "traffic": (solves * DRAM_BYTES_PER_SOLVE_NCU if DRAM_BYTES_PER_SOLVE_NCU else None),
                      "traffic_note": "DRAM bytes of one sweep kernel launch from one full-set ncu capture of "
-                                     "this kernel (75.1 B a solve, under the 96 B of the faces: a face written "
+                                     "this kernel (75.0 B a solve, under the 96 B of the faces: a face written "
                                      "by one hyperplane is read by the next from L2)",
                      "flops_per_solve": FLOPS_PER_SOLVE,
                      "hbm_achieved_gbs": solves * BYTES_PER_SOLVE / sweep_s / 1e9,
