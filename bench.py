@@ -537,7 +537,7 @@ def octnet_form(P):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm = net_rate * BYTES_PER_SOLVE / 1e9
-    out["roofline"] = {"bound": "alu", "kernel": "sweep_net_tiles<10>", "achieved": ach, "peak": peak_tf,
+    out["roofline"] = {"bound": "alu", "kernel": "sweep_net_wave", "achieved": ach, "peak": peak_tf,
                        "unit": "TFLOP/s", "frac": ach / peak_tf, "flops_per_solve": OCTNET_FLOPS_PER_SOLVE,
                        "hbm_achieved_gbs": hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm / hbm_peak,
                        "peak_note": "FP32 peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock); "

@@ -82,6 +82,60 @@ __device__ __forceinline__ void octnet_forward(const float *__restrict__ w, cons
     }
 }
 
+// The key's part of each hidden unit's input: the bias (with the cell sizes already
+// folded in), the 8 canonical sources and sigma_t.  Shared by every direction of the
+// key, so the key sweep forms it once per key (octnet_key_row adds the rest).
+__device__ __forceinline__ void octnet_key_part(const float *__restrict__ w, const float (&S)[8], float sig,
+                                                float (&ak)[kOnHid])
+{
+#pragma unroll
+    for (int k = 0; k < kOnHid; ++k) {
+        const float4 *r = reinterpret_cast<const float4 *>(w + 24 * k);
+        const float4 c3 = r[3], c4 = r[4], c5 = r[5];
+        float a = c5.w;
+        a = fmaf(c3.x, S[0], a); a = fmaf(c3.y, S[1], a); a = fmaf(c3.z, S[2], a); a = fmaf(c3.w, S[3], a);
+        a = fmaf(c4.x, S[4], a); a = fmaf(c4.y, S[5], a); a = fmaf(c4.z, S[6], a); a = fmaf(c4.w, S[7], a);
+        ak[k] = fmaf(c5.z, sig, a);
+    }
+}
+
+// One direction of a key: psi (canonical node order) from the key's part ak of the
+// hidden inputs (octnet_key_part, two 4-vectors at ak0 / ak1), the direction's |mu|
+// and |eta|, and the three inflow faces (4-vectors at fx, fy, fz); the same function
+// as octnet_forward with the sums grouped differently.
+__device__ __forceinline__ void octnet_key_row(const float *__restrict__ w, const float4 *ak0, const float4 *ak1,
+                                               const float4 *fx, const float4 *fy, const float4 *fz, float amu,
+                                               float aeta, float (&psi)[8])
+{
+    const float4 ux = *fx, uy = *fy, uz = *fz, a0 = *ak0, a1 = *ak1;
+    const float ak[kOnHid] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    float bm = fmaxf(fmaxf(fmaxf(fabsf(ux.x), fabsf(ux.y)), fmaxf(fabsf(ux.z), fabsf(ux.w))),
+                     fmaxf(fmaxf(fabsf(uy.x), fabsf(uy.y)), fmaxf(fabsf(uy.z), fabsf(uy.w))));
+    bm = fmaxf(bm, fmaxf(fmaxf(fabsf(uz.x), fabsf(uz.y)), fmaxf(fabsf(uz.z), fabsf(uz.w))));
+    const float beta = kOnBetaFrac * bm;
+    float h[kOnHid];
+#pragma unroll
+    for (int k = 0; k < kOnHid; ++k) {
+        const float4 *r = reinterpret_cast<const float4 *>(w + 24 * k);
+        const float4 c0 = r[0], c1 = r[1], c2 = r[2], c5 = r[5];
+        float a = fmaf(c5.x, amu, ak[k]);
+        a = fmaf(c5.y, aeta, a);
+        a = fmaf(c0.x, ux.x, a); a = fmaf(c0.y, ux.y, a); a = fmaf(c0.z, ux.z, a); a = fmaf(c0.w, ux.w, a);
+        a = fmaf(c1.x, uy.x, a); a = fmaf(c1.y, uy.y, a); a = fmaf(c1.z, uy.z, a); a = fmaf(c1.w, uy.w, a);
+        a = fmaf(c2.x, uz.x, a); a = fmaf(c2.y, uz.y, a); a = fmaf(c2.z, uz.z, a); a = fmaf(c2.w, uz.w, a);
+        h[k] = octnet_tanh(a);
+    }
+#pragma unroll
+    for (int t = 0; t < kOnOut; ++t) {
+        const float4 *r = reinterpret_cast<const float4 *>(w + kOnFoldW2 + 8 * t);
+        const float4 c0 = r[0], c1 = r[1];
+        float z = w[kOnFoldB2 + t];
+        z = fmaf(c0.x, h[0], z); z = fmaf(c0.y, h[1], z); z = fmaf(c0.z, h[2], z); z = fmaf(c0.w, h[3], z);
+        z = fmaf(c1.x, h[4], z); z = fmaf(c1.y, h[5], z); z = fmaf(c1.z, h[6], z); z = fmaf(c1.w, h[7], z);
+        psi[t] = z >= 0.f ? z : beta * (__expf(z) - 1.f);
+    }
+}
+
 // Two canonical one-cell problems through the same folded network (weights at w,
 // the cell-size terms already in the biases): every weight read feeds two
 // multiply-adds.  Same arithmetic, in the same order, as octnet_forward<false>.

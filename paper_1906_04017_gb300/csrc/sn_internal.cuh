@@ -184,6 +184,7 @@ bool ann_frozen(sn_handle h);
 // the key sweep (sn_sweep_keys.cu): FP32 elimination on box cells, isotropic scattering
 bool key_sweep_ok(sn_handle h);
 sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st);
+sn_status launch_sweep_net_keys(sn_handle h, const float *S, float *phi_oct, cudaStream_t st);
 sn_status build_wave(sn_handle h);
 sn_status launch_leak_keys(sn_handle h, cudaStream_t st);
 void free_wave(sn_handle h);

@@ -880,6 +880,8 @@ sn_status launch_sweep(sn_handle h, const void *S, void *phi_oct, sn_solve_mode 
                                 mode == SN_SOLVE_ANN ? 0 : (mode == SN_SOLVE_ANN_GATED ? 1 : 2), st);
     if ((mode == SN_SOLVE_GE32R || mode == SN_SOLVE_GE32) && key_sweep_ok(h))
         return launch_sweep_keys(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R, st);
+    if (mode == SN_SOLVE_OCTNET && key_sweep_ok(h) && h->wave)
+        return launch_sweep_net_keys(h, (const float *)S, (float *)phi_oct, st);
     return launch_sweep_t<float>(h, (const float *)S, (float *)phi_oct, mode == SN_SOLVE_GE32R,
                                  mode == SN_SOLVE_OCTNET, st);
 }

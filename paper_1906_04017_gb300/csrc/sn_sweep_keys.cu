@@ -49,6 +49,7 @@
 #include <vector>
 
 #include "ge8.cuh"
+#include "octnet.cuh"
 #include "sn_internal.cuh"
 #include "sweep_common.cuh"
 #include "wave.cuh"
@@ -79,14 +80,19 @@ struct KeyArgs {
     uint32_t off_y, off_z, off_in;
     float *phi_oct;              // [8][C][G][8]
     WaveCtl w;                   // wavefront kernel
+    // the paper's octant networks (network sweep): folded weights [8][288], |Omega| of
+    // the octant's directions [Do], the cell sizes
+    const float *onet;
+    const float4 *dir_abs;
+    float hx, hy, hz;
 };
 
 // Inflow-face stages a thread cycles through: the faces of the next NST - 1 directions
 // are in flight while one is solved.  Three stages measured faster for the solve
 // without refinement (3.94 against 4.11 ms on blocked_64) and slower with it, whose
 // registers they push into spills (4.59 against 4.56 ms).
-template <bool REFINE>
-constexpr int key_stages() { return REFINE ? 2 : 3; }
+template <bool REFINE, bool NET = false>
+constexpr int key_stages() { return (REFINE && !NET) ? 2 : 3; }
 
 template <int NST>
 struct KeySmem {
@@ -102,10 +108,13 @@ struct KeySmem {
 // chunks (KB = kKeyBlock >> lch keys a tile).  wait() runs after the keys' set-up,
 // must contain a CTA barrier, and returns once the upwind faces are complete (false:
 // give the tile up).  Returns false if the tile was given up.
-template <bool REFINE, typename Wait>
-__device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<REFINE>()> &sm, int o,
-                                         const uint32_t *cells, int nkeys,
-                                         int key0, int lch, Wait wait)
+// NET: the per-direction solve is the octant network of the key's octant (folded
+// weights of all 8 octants at wn, |Omega| of the directions at dab); the key's part of
+// the hidden inputs takes the place of (Mh x Mh x Mh) S in msrc.
+template <bool REFINE, bool NET, typename Wait>
+__device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<REFINE, NET>()> &sm, const float *wn,
+                                         const float4 *dab, int o, const uint32_t *cells, int nkeys, int key0,
+                                         int lch, Wait wait)
 {
     const int t = threadIdx.x;
     const int KB = kKeyBlock >> lch;
@@ -135,11 +144,18 @@ __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<RE
         const float4 s1 = __ldg(reinterpret_cast<const float4 *>(a.S) + 2 * (int64_t)gc + 1);
         float Sm[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
         mirror8(Sm, o);          // canonical node n = physical n ^ o
-        mh_axis<0>(Sm);
-        mh_axis<1>(Sm);
-        mh_axis<2>(Sm);
-        sm.msrc[0][t] = make_float4(Sm[0], Sm[1], Sm[2], Sm[3]);
-        sm.msrc[1][t] = make_float4(Sm[4], Sm[5], Sm[6], Sm[7]);
+        if constexpr (NET) {
+            float ak[kOnHid];
+            octnet_key_part(wn + kOnFold * o, Sm, sig, ak);
+            sm.msrc[0][t] = make_float4(ak[0], ak[1], ak[2], ak[3]);
+            sm.msrc[1][t] = make_float4(ak[4], ak[5], ak[6], ak[7]);
+        } else {
+            mh_axis<0>(Sm);
+            mh_axis<1>(Sm);
+            mh_axis<2>(Sm);
+            sm.msrc[0][t] = make_float4(Sm[0], Sm[1], Sm[2], Sm[3]);
+            sm.msrc[1][t] = make_float4(Sm[4], Sm[5], Sm[6], Sm[7]);
+        }
         const uint32_t DG = (uint32_t)(Do * G), first = (uint32_t)(d0 * G + g);
         ou0 = (uint32_t)(o * a.ny * a.nz + jp + a.ny * kp) * DG + first;
         ou1 = a.off_y + (uint32_t)(o * a.nx * a.nz + ip + a.nx * kp) * DG + first;
@@ -166,7 +182,7 @@ __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<RE
             cp_async16(nb + AX, a.face + ((bnd & 2u) ? inb + 2u + (uint32_t)((o >> 1) & 1) : s1));
             cp_async16(nb + 2 * AX, a.face + ((bnd & 4u) ? inb + 4u + (uint32_t)((o >> 2) & 1) : s2));
         };
-        constexpr int kKeyStages = key_stages<REFINE>();
+        constexpr int kKeyStages = key_stages<REFINE, NET>();
         issue(0u, ou0, ou1, ou2);
         cp_async_commit();
         if constexpr (kKeyStages == 3) {
@@ -189,8 +205,14 @@ __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<RE
             // before the next direction): no register copy of them, nor of b, across the
             // elimination (168 registers without spills; 4.52 against 4.59 ms a blocked_64
             // sweep with the register copies)
-            cell_solve_key_x2_sm<REFINE>(dd.x, dd.y, dd.z, sig, &sm.msrc[0][t], &sm.msrc[1][t], &sm.stage[cur][0][t],
-                                         &sm.stage[cur][1][t], &sm.stage[cur][2][t], x);
+            if constexpr (NET) {
+                const float4 ab = dab[d];
+                octnet_key_row(wn + kOnFold * o, &sm.msrc[0][t], &sm.msrc[1][t], &sm.stage[cur][0][t],
+                               &sm.stage[cur][1][t], &sm.stage[cur][2][t], ab.x, ab.y, x);
+            } else {
+                cell_solve_key_x2_sm<REFINE>(dd.x, dd.y, dd.z, sig, &sm.msrc[0][t], &sm.msrc[1][t],
+                                             &sm.stage[cur][0][t], &sm.stage[cur][1][t], &sm.stage[cur][2][t], x);
+            }
             cur = cur + 1 == kKeyStages ? 0 : cur + 1;
             // outflow faces (canonical in-face order): x-face a = 1, y-face b = 1, z-face c = 1
             a.face[ou0] = make_float4(x[1], x[3], x[5], x[7]);
@@ -236,7 +258,8 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
     __shared__ __align__(16) KeySmem<key_stages<REFINE>()> sm;
     griddep_launch();
     for (int e = threadIdx.x; e < a.Do; e += kKeyBlock) sm.dsm[e] = a.dir[e];
-    key_tile<REFINE>(a, sm, (int)blockIdx.y, a.cells, a.nkeys, (int)blockIdx.x * (kKeyBlock >> LCH), LCH, [] {
+    key_tile<REFINE, false>(a, sm, nullptr, nullptr, (int)blockIdx.y, a.cells, a.nkeys,
+                            (int)blockIdx.x * (kKeyBlock >> LCH), LCH, [] {
         __syncthreads();   // direction table, key records
         griddep_wait();    // the previous hyperplane's outflow faces are complete
         return true;
@@ -253,10 +276,10 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_keys(Key
 // warp 0 waits for the dependencies, testing their flags together.  Two CTA barriers a
 // unit: after the wait (which also orders every read of the descriptor before thread
 // 0 overwrites it) and after the unit's stores (which also publishes the next one).
-template <bool REFINE>
-__global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(KeyArgs a)
+template <bool REFINE, bool NET>
+__device__ __forceinline__ void wave_body(const KeyArgs &a, KeySmem<key_stages<REFINE, NET>()> &sm, const float *wn,
+                                          const float4 *dab)
 {
-    __shared__ __align__(16) KeySmem<key_stages<REFINE>()> sm;
     __shared__ __align__(16) int4 s_ud;
     __shared__ __align__(16) int4 s_up;
     __shared__ int s_u, s_stop;
@@ -279,7 +302,7 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(Key
         int un = 0;
         if (t == 0) un = (int)atomicAdd(a.w.next, 1u);
         const int o = (ud.y >> 12) & 7, lch = (ud.y >> 15) & 7;
-        const bool ok = key_tile<REFINE>(a, sm, o, a.w.all_cells + up.x, up.y, ud.x, lch, [&] {
+        const bool ok = key_tile<REFINE, NET>(a, sm, wn, dab, o, a.w.all_cells + up.x, up.y, ud.x, lch, [&] {
             if (t < 32) {
                 const int4 d1 = s_ud, d2 = s_up;   // the dependency ranges (not kept in registers)
                 const bool fine = wave_wait_deps_warp(a.w, d1.z, d1.w, d2.z, d2.w);
@@ -303,6 +326,42 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(Key
         if (t == 0) wave_done(a.w, u);
     }
     cp_async_wait_all();
+}
+
+template <bool REFINE>
+__global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(KeyArgs a)
+{
+    __shared__ __align__(16) KeySmem<key_stages<REFINE>()> sm;
+    wave_body<REFINE, false>(a, sm, nullptr, nullptr);
+}
+
+// The paper's octant networks (Secs. 3-4, Eqs. (15)-(18)) as the cell solver of the
+// same wavefront sweep.  The folded networks of all 8 octants (9 KB) and the
+// directions' |Omega| stay in shared memory; the mesh's uniform cell size is folded
+// into each hidden unit's bias once per CTA.  A network row is far lighter than the
+// elimination (about 300 FP32 operations), so the kernel runs more CTAs an SM: 5 (96
+// registers, 38 KB of shared memory each) measured 3.65 against 3.70 ms at 4 on
+// blocked_64.
+#ifndef SN_NETKEY_MINBLOCKS
+#define SN_NETKEY_MINBLOCKS 5
+#endif
+__global__ void __launch_bounds__(kKeyBlock, SN_NETKEY_MINBLOCKS) sweep_net_wave(KeyArgs a)
+{
+    __shared__ __align__(16) KeySmem<key_stages<false, true>()> sm;
+    __shared__ __align__(16) float wn[8 * kOnFold];
+    __shared__ __align__(16) float4 dab[kKeyMaxDo];
+    const int t = threadIdx.x;
+    for (int e = t; e < 8 * kOnFold; e += kKeyBlock) wn[e] = a.onet[e];
+    for (int e = t; e < a.Do; e += kKeyBlock) dab[e] = a.dir_abs[e];
+    __syncthreads();
+    if (t < 8 * kOnHid) {
+        float *w = wn + kOnFold * (t / kOnHid);
+        const int k = t % kOnHid;
+        w[24 * k + 23] = fmaf(w[kOnFoldH + 3 * k], a.hx,
+                              fmaf(w[kOnFoldH + 3 * k + 1], a.hy, fmaf(w[kOnFoldH + 3 * k + 2], a.hz, w[24 * k + 23])));
+    }
+    // (wave_body's first barrier orders the folded biases before their first use)
+    wave_body<false, true>(a, sm, wn, dab);
 }
 
 // Boundary leakage of a key sweep: after the last hyperplane every face slot holds
@@ -481,6 +540,9 @@ sn_status build_wave(sn_handle h)
     SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_ge_wave<true>, kKeyBlock, 0));
     SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, sweep_ge_wave<false>, kKeyBlock, 0));
     w->grid = std::max(1, std::min(std::min(per_sm, per_sm2), SN_KEY_MINBLOCKS) * num_sms());
+    int per_sm_net = 0;
+    SN_CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_net, sweep_net_wave, kKeyBlock, 0));
+    w->grid_net = std::max(1, std::min(per_sm_net, SN_NETKEY_MINBLOCKS) * num_sms());
     h->wave = w;
     return SN_OK;
 }
@@ -519,7 +581,7 @@ static cudaError_t launch_keys_lch(int lch, bool pdl, const KeyArgs &a, cudaStre
     }
 }
 
-sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st)
+static KeyArgs key_args(sn_handle h, const float *S, float *phi_oct)
 {
     KeyArgs a = {};
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.G = h->G; a.Do = h->Do; a.C = (int)h->ncell;
@@ -532,6 +594,12 @@ sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool re
     a.off_z = (uint32_t)(h->face_x + h->face_y);
     a.off_in = (uint32_t)h->face_in;
     a.phi_oct = phi_oct;
+    return a;
+}
+
+sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st)
+{
+    KeyArgs a = key_args(h, S, phi_oct);
     const WaveTables *w = static_cast<const WaveTables *>(h->wave);
     if (w) {
         a.w = wave_ctl(h);
@@ -553,6 +621,30 @@ sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool re
             SN_CK(h, refine ? launch_keys_lch<true>(lch, s > 0, a, st) : launch_keys_lch<false>(lch, s > 0, a, st));
         }
     }
+    SN_CK(h, cudaGetLastError());
+    if (h->prof) {
+        SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));
+        h->prof_pending = true;
+    }
+    return launch_leak_keys(h, st);
+}
+
+// The octant-network sweep on the wavefront schedule (box cells with unit tables).
+sn_status launch_sweep_net_keys(sn_handle h, const float *S, float *phi_oct, cudaStream_t st)
+{
+    const WaveTables *w = static_cast<const WaveTables *>(h->wave);
+    if (!w) return fail(h, SN_ESTATE, "octant-network key sweep without unit tables");
+    KeyArgs a = key_args(h, S, phi_oct);
+    a.onet = octnet_folded(h);
+    if (!a.onet) return fail(h, SN_ESTATE, "octant-network sweep without networks");
+    a.dir_abs = h->dir_abs;
+    a.hx = (float)h->dx;
+    a.hy = (float)h->dy;
+    a.hz = (float)h->dz;
+    a.w = wave_ctl(h);
+    SN_CK(h, cudaMemsetAsync(w->flags, 0, sizeof(uint32_t) * (size_t)(w->nunits + 1), st));
+    if (h->prof) SN_CK(h, cudaEventRecord(h->ev_sweep[0], st));
+    sweep_net_wave<<<w->grid_net, kKeyBlock, 0, st>>>(a);
     SN_CK(h, cudaGetLastError());
     if (h->prof) {
         SN_CK(h, cudaEventRecord(h->ev_sweep[1], st));

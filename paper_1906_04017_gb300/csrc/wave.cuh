@@ -21,6 +21,7 @@ struct WaveTables {
     uint32_t *flags = nullptr;     // [nunits] done flags, then the hand-out counter
     int nunits = 0;
     int grid = 0;                  // persistent CTAs of the elimination sweep
+    int grid_net = 0;              // persistent CTAs of the octant-network sweep
 };
 
 struct WaveCtl {
