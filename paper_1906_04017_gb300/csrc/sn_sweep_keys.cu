@@ -108,9 +108,9 @@ struct KeySmem {
 // chunks (KB = kKeyBlock >> lch keys a tile).  wait() runs after the keys' set-up,
 // must contain a CTA barrier, and returns once the upwind faces are complete (false:
 // give the tile up).  Returns false if the tile was given up.
-// NET: the per-direction solve is the octant network of the key's octant (folded
-// weights of all 8 octants at wn, |Omega| of the directions at dab); the key's part of
-// the hidden inputs takes the place of (Mh x Mh x Mh) S in msrc.
+// NET: the per-direction solve is the octant network of the key's octant (all 8
+// octants' networks at wn in the row layout of octnet.cuh, |Omega| of the directions at
+// dab); the key's part of the hidden inputs takes the place of (Mh x Mh x Mh) S in msrc.
 template <bool REFINE, bool NET, typename Wait>
 __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<REFINE, NET>()> &sm, const float *wn,
                                          const float4 *dab, int o, const uint32_t *cells, int nkeys, int key0,
@@ -146,7 +146,7 @@ __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<RE
         mirror8(Sm, o);          // canonical node n = physical n ^ o
         if constexpr (NET) {
             float ak[kOnHid];
-            octnet_key_part(wn + kOnFold * o, Sm, sig, ak);
+            octnet_key_part_rows(wn + kOnRows * o, Sm, sig, ak);
             sm.msrc[0][t] = make_float4(ak[0], ak[1], ak[2], ak[3]);
             sm.msrc[1][t] = make_float4(ak[4], ak[5], ak[6], ak[7]);
         } else {
@@ -207,8 +207,8 @@ __device__ __forceinline__ bool key_tile(const KeyArgs &a, KeySmem<key_stages<RE
             // sweep with the register copies)
             if constexpr (NET) {
                 const float4 ab = dab[d];
-                octnet_key_row(wn + kOnFold * o, &sm.msrc[0][t], &sm.msrc[1][t], &sm.stage[cur][0][t],
-                               &sm.stage[cur][1][t], &sm.stage[cur][2][t], ab.x, ab.y, x);
+                octnet_key_row_rows(wn + kOnRows * o, &sm.msrc[0][t], &sm.msrc[1][t], &sm.stage[cur][0][t],
+                                    &sm.stage[cur][1][t], &sm.stage[cur][2][t], ab.x, ab.y, x);
             } else {
                 cell_solve_key_x2_sm<REFINE>(dd.x, dd.y, dd.z, sig, &sm.msrc[0][t], &sm.msrc[1][t],
                                              &sm.stage[cur][0][t], &sm.stage[cur][1][t], &sm.stage[cur][2][t], x);
@@ -336,31 +336,26 @@ __global__ void __launch_bounds__(kKeyBlock, SN_KEY_MINBLOCKS) sweep_ge_wave(Key
 }
 
 // The paper's octant networks (Secs. 3-4, Eqs. (15)-(18)) as the cell solver of the
-// same wavefront sweep.  The folded networks of all 8 octants (9 KB) and the
-// directions' |Omega| stay in shared memory; the mesh's uniform cell size is folded
-// into each hidden unit's bias once per CTA.  A network row is far lighter than the
-// elimination (about 300 FP32 operations), so the kernel runs more CTAs an SM: 5 (96
-// registers, 38 KB of shared memory each) measured 3.65 against 3.70 ms at 4 on
-// blocked_64.
+// same wavefront sweep.  The folded networks of all 8 octants (8 KB in the row layout,
+// two hidden units or outputs a two-lane FMA) and the directions' |Omega| stay in
+// shared memory; the mesh's uniform cell size is folded into each hidden unit's bias
+// once per CTA.  A network row is far lighter than the
+// elimination (about 300 FP32 operations): 4 CTAs an SM (128 registers, 37 KB of shared
+// memory each) measured 3.61 ms a blocked_64 sweep, 5 (96 registers, with spills)
+// 3.64 ms.
 #ifndef SN_NETKEY_MINBLOCKS
-#define SN_NETKEY_MINBLOCKS 5
+#define SN_NETKEY_MINBLOCKS 4
 #endif
 __global__ void __launch_bounds__(kKeyBlock, SN_NETKEY_MINBLOCKS) sweep_net_wave(KeyArgs a)
 {
     __shared__ __align__(16) KeySmem<key_stages<false, true>()> sm;
-    __shared__ __align__(16) float wn[8 * kOnFold];
+    __shared__ __align__(16) float wn[8 * kOnRows];
     __shared__ __align__(16) float4 dab[kKeyMaxDo];
     const int t = threadIdx.x;
-    for (int e = t; e < 8 * kOnFold; e += kKeyBlock) wn[e] = a.onet[e];
+    for (int e = t; e < 8 * kOnRows; e += kKeyBlock)
+        wn[e] = octnet_row_layout(a.onet + kOnFold * (e / kOnRows), e % kOnRows, a.hx, a.hy, a.hz);
     for (int e = t; e < a.Do; e += kKeyBlock) dab[e] = a.dir_abs[e];
-    __syncthreads();
-    if (t < 8 * kOnHid) {
-        float *w = wn + kOnFold * (t / kOnHid);
-        const int k = t % kOnHid;
-        w[24 * k + 23] = fmaf(w[kOnFoldH + 3 * k], a.hx,
-                              fmaf(w[kOnFoldH + 3 * k + 1], a.hy, fmaf(w[kOnFoldH + 3 * k + 2], a.hz, w[24 * k + 23])));
-    }
-    // (wave_body's first barrier orders the folded biases before their first use)
+    // (wave_body's first barrier orders the tables before their first use)
     wave_body<false, true>(a, sm, wn, dab);
 }
 
