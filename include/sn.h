@@ -316,6 +316,32 @@ sn_status sn_surrogate_stats(sn_handle h, int64_t *fallbacks, int64_t *timeouts)
 sn_status sn_set_profiling(sn_handle h, int32_t enable);
 sn_status sn_get_profile(sn_handle h, double *sweep_ms, int64_t *sweeps, int32_t reset);
 
+/* sn_wave_plan: the work units of the wavefront sweeps (the sweep order of Sec. 2,
+ * after (14): a cell is solved after its three upwind neighbours, so the cells of
+ * hyperplane s = i'+j'+k' of the canonical octant are independent of each other).
+ * Host only, no GPU call: the records a float handle of an nx x ny x nz box mesh with
+ * G groups and Do directions per octant builds on a GPU with nsm SMs, for inspection
+ * and tests.
+ *   A key is (cell, group): its index on hyperplane s is (place of the cell on s) x G
+ *   + g, the cells of s listed by (k', j', i').  A unit is one tile of keys of one
+ *   hyperplane and one octant; units are numbered by (s, octant, tile).
+ *   units [nunits][4]: first key of the tile; s | octant << 12 | lch << 15 (the tile
+ *     holds 128 >> lch keys, and each key's directions are split in 2^lch chunks:
+ *     the fewest, at most 8 and at most Do, for which 8 x keys of s x 2^lch reaches
+ *     nsm x 3 x 128 thread slots); first unit and count of the first range of units
+ *     the tile waits for.
+ *   uplane [nunits][4]: first cell of hyperplane s in the hyperplane cell list; keys
+ *     on s (cells x G); first unit and count of the second range (count 0: none).
+ *   Both ranges lie in the units of hyperplane s - 1 of the same octant and together
+ *   hold every tile that has a key of an upwind neighbour of a cell of the tile.
+ * *nunits receives the number of units, 0 where the mesh is left to one launch per
+ * hyperplane (2^30 units or more, or more than 4095 hyperplanes).  With units and
+ * uplane both NULL the call only sizes; otherwise both must hold 4 x cap int32 and
+ * cap >= *nunits.  SN_EINVAL for sizes outside 1..1023 cells per axis, 1..1024
+ * groups, 1..64 directions per octant, nsm < 1, or too small a cap. */
+sn_status sn_wave_plan(int32_t nx, int32_t ny, int32_t nz, int32_t G, int32_t Do, int32_t nsm, int32_t *units,
+                       int32_t *uplane, int64_t cap, int64_t *nunits);
+
 /* ---------------------------------------------------------------------------
  * sn_set_scattering_order: anisotropic scattering (Sec. 2, Eqs. (3)-(8)).  The
  * differential scattering cross section is expanded in Legendre polynomials up to

@@ -186,6 +186,16 @@ bool key_sweep_ok(sn_handle h);
 sn_status launch_sweep_keys(sn_handle h, const float *S, float *phi_oct, bool refine, cudaStream_t st);
 sn_status launch_sweep_net_keys(sn_handle h, const float *S, float *phi_oct, cudaStream_t st);
 sn_status build_wave(sn_handle h);
+// Host tables of the hyperplanes i'+j'+k' = s (sn_setup.cu): off [nplanes + 1]
+// offsets, cells [C] packed i' | j' << 10 | k' << 20 listed by (k', j', i') within a
+// hyperplane, pos [C] (by linear cell index) the cell's place in its hyperplane.
+void hyperplane_tables(int nx, int ny, int nz, std::vector<int64_t> &off, std::vector<uint32_t> &cells,
+                       std::vector<uint32_t> &pos);
+// Host: the wavefront unit records of the key sweeps (sn_sweep_keys.cu) for a GPU
+// with nsm SMs; false when the mesh is left to the per-hyperplane launches.
+bool wave_plan(int nx, int ny, int G, int Do, int nsm, const std::vector<int64_t> &off,
+               const std::vector<uint32_t> &cells, const std::vector<uint32_t> &pos, std::vector<int4> &units,
+               std::vector<int4> &uplane);
 sn_status launch_leak_keys(sn_handle h, cudaStream_t st);
 void free_wave(sn_handle h);
 struct WaveCtl;

@@ -180,6 +180,33 @@ static void release(sn_handle h)
     free_octnet(h);
 }
 
+// The sweep order of Sec. 2 in the canonical octant: cell (i',j',k') is solved on
+// hyperplane s = i'+j'+k', after its three upwind neighbours on hyperplane s - 1.
+void hyperplane_tables(int nx, int ny, int nz, std::vector<int64_t> &off, std::vector<uint32_t> &cells,
+                       std::vector<uint32_t> &pos)
+{
+    const int np = nx + ny + nz - 2;
+    const int64_t C = (int64_t)nx * ny * nz;
+    off.assign(np + 1, 0);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) off[i + j + k + 1]++;
+    for (int s = 0; s < np; ++s) off[s + 1] += off[s];
+    cells.assign(C, 0u);
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                cells[fill[i + j + k]++] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
+    pos.assign(C, 0u);
+    for (int s = 0; s < np; ++s)
+        for (int64_t q = off[s]; q < off[s + 1]; ++q) {
+            const uint32_t pk = cells[q];
+            const int64_t lin = (pk & 1023) + (int64_t)nx * (((pk >> 10) & 1023) + (int64_t)ny * (pk >> 20));
+            pos[lin] = (uint32_t)(q - off[s]);
+        }
+}
+
 }  // namespace sn
 
 using namespace sn;
@@ -373,29 +400,12 @@ sn_status sn_setup(sn_handle *out, const sn_mesh *mesh, const sn_quadrature *qua
 
     // hyperplane table: cells (i',j',k') with i'+j'+k' = s, packed 10 bits per index
     {
-        std::vector<int64_t> count(h->nplanes + 1, 0);
-        for (int k = 0; k < h->nz; ++k)
-            for (int j = 0; j < h->ny; ++j)
-                for (int i = 0; i < h->nx; ++i) count[i + j + k + 1]++;
-        for (int s2 = 0; s2 < h->nplanes; ++s2) count[s2 + 1] += count[s2];
-        h->plane_off = count;
-        std::vector<uint32_t> cells(C);
-        std::vector<int64_t> fill(count.begin(), count.end() - 1);
-        for (int k = 0; k < h->nz; ++k)
-            for (int j = 0; j < h->ny; ++j)
-                for (int i = 0; i < h->nx; ++i)
-                    cells[fill[i + j + k]++] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
+        std::vector<uint32_t> cells, pos;
+        hyperplane_tables(h->nx, h->ny, h->nz, h->plane_off, cells, pos);
         SN_TRY(dalloc_bytes(h, (void **)&h->plane_cells, sizeof(uint32_t) * (size_t)C));
         cudaError_t e = cudaMemcpyAsync(h->plane_cells, cells.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice,
                                         h->stream);
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpyAsync(plane_cells)"));
-        std::vector<uint32_t> pos(C);
-        for (int s2 = 0; s2 < h->nplanes; ++s2)
-            for (int64_t q = count[s2]; q < count[s2 + 1]; ++q) {
-                const uint32_t pk = cells[q];
-                const int64_t lin = (pk & 1023) + (int64_t)h->nx * (((pk >> 10) & 1023) + (int64_t)h->ny * (pk >> 20));
-                pos[lin] = (uint32_t)(q - count[s2]);
-            }
         SN_TRY(dalloc_bytes(h, (void **)&h->plane_pos, sizeof(uint32_t) * (size_t)C));
         e = cudaMemcpyAsync(h->plane_pos, pos.data(), sizeof(uint32_t) * C, cudaMemcpyHostToDevice, h->stream);
         if (e != cudaSuccess) SN_TRY(cuda_fail(h, e, "cudaMemcpyAsync(plane_pos)"));

@@ -46,6 +46,7 @@
 // but the hand-out of units: the flux is bit-reproducible run to run.
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <vector>
 
 #include "ge8.cuh"
@@ -398,14 +399,17 @@ bool key_sweep_ok(sn_handle h)
 
 // log2 of the chunks a key's directions are split in on a hyperplane with `keys`
 // keys (all octants): the fewest that still give about one thread per resident
-// thread slot of the GPU, at most 8 chunks and no more chunks than directions.
-static int key_chunks_log2(int64_t keys, int Do)
+// thread slot of a GPU with nsm SMs, at most 8 chunks and no more chunks than
+// directions.
+static int key_chunks_log2(int64_t keys, int Do, int nsm)
 {
-    const int64_t slots = (int64_t)num_sms() * SN_KEY_MINBLOCKS * kKeyBlock;
+    const int64_t slots = (int64_t)nsm * SN_KEY_MINBLOCKS * kKeyBlock;
     int l = 0;
     while (l < 3 && (2 << l) <= Do && keys * (1 << l) < slots) ++l;
     return l;
 }
+
+static int key_chunks_log2(int64_t keys, int Do) { return key_chunks_log2(keys, Do, num_sms()); }
 
 static void free_tables(WaveTables *w)
 {
@@ -430,27 +434,30 @@ void free_wave(sn_handle h)
 // (i',j',k'-1) of its cells.  A hyperplane's cells are listed by (k', j'), so those
 // tiles form two clusters (the neighbours in the tile's own k' rows, and those in the
 // rows k' - 1): each unit carries two ranges, split at the largest gap.
-static sn_status build_tables(sn_handle h, const std::vector<uint32_t> &cells, const std::vector<uint32_t> &pos,
-                              WaveTables **out)
+bool wave_plan(int nx, int ny, int G, int Do, int nsm, const std::vector<int64_t> &off,
+               const std::vector<uint32_t> &cells, const std::vector<uint32_t> &pos, std::vector<int4> &units,
+               std::vector<int4> &uplane)
 {
-    *out = nullptr;
-    const int np = h->nplanes, G = h->G;
+    units.clear();
+    uplane.clear();
+    const int np = (int)off.size() - 1;
     std::vector<int> lch(np), ntile(np);
     std::vector<int64_t> first(np + 1);   // first unit of each hyperplane
     first[0] = 0;
     for (int s = 0; s < np; ++s) {
-        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
-        lch[s] = key_chunks_log2(8 * n * G, h->Do);
+        const int64_t n = off[s + 1] - off[s];
+        lch[s] = key_chunks_log2(8 * n * G, Do, nsm);
         const int64_t kb = kKeyBlock >> lch[s];
         ntile[s] = (int)((n * G + kb - 1) / kb);
         first[s + 1] = first[s] + 8 * (int64_t)ntile[s];
     }
-    if (first[np] >= (1LL << 30) || np > 4095) return SN_OK;   // the per-hyperplane kernel serves it
-    std::vector<int4> units((size_t)first[np]), uplane((size_t)first[np]);
+    if (first[np] >= (1LL << 30) || np > 4095) return false;   // the per-hyperplane kernel serves it
+    units.resize((size_t)first[np]);
+    uplane.resize((size_t)first[np]);
     std::vector<int64_t> dep;
     for (int s = 0; s < np; ++s) {
         const int64_t kb = kKeyBlock >> lch[s];
-        const int64_t n = h->plane_off[s + 1] - h->plane_off[s];
+        const int64_t n = off[s + 1] - off[s];
         const int64_t kbp = s > 0 ? (kKeyBlock >> lch[s - 1]) : 1;
         for (int tl = 0; tl < ntile[s]; ++tl) {
             int64_t lo1 = 0, n1 = 0, lo2 = 0, n2 = 0;
@@ -458,12 +465,12 @@ static sn_status build_tables(sn_handle h, const std::vector<uint32_t> &cells, c
                 dep.clear();
                 const int64_t p0 = tl * kb / G, p1 = std::min<int64_t>(n - 1, (tl * kb + kb - 1) / G);
                 for (int64_t q = p0; q <= p1; ++q) {
-                    const uint32_t pk = cells[h->plane_off[s] + q];
+                    const uint32_t pk = cells[off[s] + q];
                     const int ip = pk & 1023, jp = (pk >> 10) & 1023, kp = pk >> 20;
                     const int nb[3][3] = {{ip - 1, jp, kp}, {ip, jp - 1, kp}, {ip, jp, kp - 1}};
                     for (int m = 0; m < 3; ++m) {
                         if (nb[m][0] < 0 || nb[m][1] < 0 || nb[m][2] < 0) continue;
-                        const int64_t lin = nb[m][0] + (int64_t)h->nx * (nb[m][1] + (int64_t)h->ny * nb[m][2]);
+                        const int64_t lin = nb[m][0] + (int64_t)nx * (nb[m][1] + (int64_t)ny * nb[m][2]);
                         const int64_t pp = pos[lin];
                         for (int64_t d = pp * G / kbp; d <= (pp * G + G - 1) / kbp; ++d) dep.push_back(d);
                     }
@@ -490,12 +497,21 @@ static sn_status build_tables(sn_handle h, const std::vector<uint32_t> &cells, c
                 const int64_t u = first[s] + (int64_t)o * ntile[s] + tl;
                 const int64_t base = s > 0 ? first[s - 1] + (int64_t)o * ntile[s - 1] : 0;
                 units[u] = make_int4((int)(tl * kb), s | (o << 12) | (lch[s] << 15), (int)(base + lo1), (int)n1);
-                uplane[u] = make_int4((int)h->plane_off[s], (int)(n * G), (int)(base + lo2), (int)n2);
+                uplane[u] = make_int4((int)off[s], (int)(n * G), (int)(base + lo2), (int)n2);
             }
         }
     }
+    return true;
+}
+
+static sn_status build_tables(sn_handle h, const std::vector<uint32_t> &cells, const std::vector<uint32_t> &pos,
+                              WaveTables **out)
+{
+    *out = nullptr;
+    std::vector<int4> units, uplane;
+    if (!wave_plan(h->nx, h->ny, h->G, h->Do, num_sms(), h->plane_off, cells, pos, units, uplane)) return SN_OK;
     WaveTables *w = new WaveTables();
-    w->nunits = (int)first[np];
+    w->nunits = (int)units.size();
     cudaError_t e = cudaMalloc(&w->units, sizeof(int4) * units.size());
     if (e == cudaSuccess) e = cudaMalloc(&w->uplane, sizeof(int4) * uplane.size());
     if (e == cudaSuccess) e = cudaMalloc(&w->flags, sizeof(uint32_t) * (units.size() + 1));
@@ -661,3 +677,29 @@ sn_status launch_leak_keys(sn_handle h, cudaStream_t st)
 }
 
 }  // namespace sn
+
+using namespace sn;
+
+extern "C" sn_status sn_wave_plan(int32_t nx, int32_t ny, int32_t nz, int32_t G, int32_t Do, int32_t nsm,
+                                  int32_t *units, int32_t *uplane, int64_t cap, int64_t *nunits)
+{
+    if (!nunits) return fail(nullptr, SN_EINVAL, "sn_wave_plan: nunits is NULL");
+    *nunits = 0;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 1023 || ny > 1023 || nz > 1023)
+        return fail(nullptr, SN_EINVAL, "sn_wave_plan: cells per axis must be in 1..1023");
+    if (G < 1 || G > 1024) return fail(nullptr, SN_EINVAL, "sn_wave_plan: G must be in 1..1024");
+    if (Do < 1 || Do > kKeyMaxDo) return fail(nullptr, SN_EINVAL, "sn_wave_plan: Do must be in 1..64");
+    if (nsm < 1) return fail(nullptr, SN_EINVAL, "sn_wave_plan: nsm must be positive");
+    std::vector<int64_t> off;
+    std::vector<uint32_t> cells, pos;
+    hyperplane_tables(nx, ny, nz, off, cells, pos);
+    std::vector<int4> u, up;
+    if (!wave_plan(nx, ny, G, Do, nsm, off, cells, pos, u, up)) return SN_OK;
+    *nunits = (int64_t)u.size();
+    if (!units && !uplane) return SN_OK;
+    if (!units || !uplane || cap < *nunits)
+        return fail(nullptr, SN_EINVAL, "sn_wave_plan: the output arrays hold fewer than *nunits records");
+    std::memcpy(units, u.data(), sizeof(int4) * u.size());
+    std::memcpy(uplane, up.data(), sizeof(int4) * up.size());
+    return SN_OK;
+}

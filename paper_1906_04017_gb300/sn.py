@@ -74,6 +74,9 @@ _API = [
                                   ctypes.POINTER(ctypes.c_int64)]),
     ("sn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("sn_get_profile", ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("sn_wave_plan", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_int64)]),
     ("sn_surrogate_prepare", ctypes.c_int, [_fp, ctypes.c_int64, _fp, _fp, ctypes.c_void_p]),
     ("sn_surrogate_init", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("sn_surrogate_set_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
@@ -179,6 +182,20 @@ def cell_solve_batch_f64(in27, out=None):
                                        n, _stream())
     _check(st)
     return out
+
+
+def wave_plan(nx, ny, nz, G, Do, nsm):
+    """(units [n, 4], uplane [n, 4]) int32: the wavefront unit records a float handle
+    of this box mesh builds on a GPU with nsm SMs (host only; n = 0 where the mesh is
+    left to one launch per hyperplane)."""
+    n = ctypes.c_int64()
+    _check(lib().sn_wave_plan(nx, ny, nz, G, Do, nsm, None, None, 0, ctypes.byref(n)))
+    units = np.zeros((n.value, 4), dtype=np.int32)
+    uplane = np.zeros((n.value, 4), dtype=np.int32)
+    if n.value:
+        _check(lib().sn_wave_plan(nx, ny, nz, G, Do, nsm, units.ctypes.data_as(ctypes.c_void_p),
+                                  uplane.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)))
+    return units, uplane
 
 
 NPARAM = 2312
