@@ -280,6 +280,7 @@ class Problem:
         xs = XS(G, *[_dptr(a) for a in arrs])
         h = ctypes.c_void_p()
         torch.cuda.init()
+        self.device = torch.cuda.current_device()
         opts = Options(1 if fp64 else 0)
         st = lib().sn_setup(ctypes.byref(h), ctypes.byref(mesh), ctypes.byref(quad), ctypes.byref(xs),
                             ctypes.byref(opts), _stream())
@@ -304,6 +305,23 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+    def _flux(self, *ts, dtype=None, moments=True):
+        """Device pointers of tensors in the handle's flux layout: [G, ncell, 8], or
+        [G, K, ncell, 8] under anisotropic scattering where the call takes moments.
+        The kernels index G x K x ncell x 8 values, so any other shape (every
+        argument's shape is checked first), dtype or device is refused here, before
+        any library call."""
+        want = (self.G, self.ncell, 8) if (self.K == 1 or not moments) else (self.G, self.K, self.ncell, 8)
+        for t in ts:
+            if not isinstance(t, torch.Tensor) or tuple(t.shape) != want:
+                raise ValueError("bad flux shape %s, want %s" % (tuple(getattr(t, "shape", ())), want))
+        ps = []
+        for t in ts:
+            ps.append(_dev(t, self.dtype if dtype is None else dtype))
+            if t.device.index != self.device:
+                raise ValueError("tensor on %s, the problem on cuda:%d" % (t.device, self.device))
+        return ps[0] if len(ps) == 1 else ps
 
     def _sync_stream(self):
         _check(lib().sn_set_stream(self.h, _stream()), self.h)
@@ -340,25 +358,25 @@ class Problem:
 
     def sweep(self, S, phi=None, mode=None):
         """One sweep: phi[G, ncell, 8] from the isotropic nodal source S[G, ncell, 8]."""
-        self._sync_stream()
         if phi is None:
             phi = torch.empty_like(S)
+        pS, pphi = self._flux(S, phi)
+        self._sync_stream()
         mode = self.default_mode if mode is None else mode
-        _check(lib().sn_sweep(self.h, _dev(S, self.dtype, (self.ncell, 8)),
-                              _dev(phi, self.dtype, (self.ncell, 8)), int(mode)), self.h)
+        _check(lib().sn_sweep(self.h, pS, pphi, int(mode)), self.h)
         return phi
 
     def source_iterate(self, phi=None, tol=1e-6, max_it=500, mode=None, use_graph=True, allow_noconv=False):
         """Source iteration in place on phi[G, ncell, 8]; returns a dict of results."""
-        self._sync_stream()
         mode = self.default_mode if mode is None else mode
         if phi is None:
             phi = self.flux_tensor()
+        pphi = self._flux(phi)
+        self._sync_stream()
         it = ctypes.c_int32(0)
         cmax = ctypes.c_double(0)
         cmean = ctypes.c_double(0)
-        st = lib().sn_source_iterate(self.h, float(tol), int(max_it), int(mode),
-                                     _dev(phi, self.dtype, (self.ncell, 8)), ctypes.byref(it),
+        st = lib().sn_source_iterate(self.h, float(tol), int(max_it), int(mode), pphi, ctypes.byref(it),
                                      ctypes.byref(cmax), ctypes.byref(cmean), 1 if use_graph else 0)
         if not (st == SN_ENOCONV and allow_noconv):
             _check(st, self.h)
@@ -367,21 +385,24 @@ class Problem:
 
     def source(self, phi, S=None):
         """The isotropic nodal source S[G, ncell, 8] built from phi by the library."""
-        self._sync_stream()
         if S is None:
             S = torch.empty_like(phi)
-        _check(lib().sn_source(self.h, _dev(phi, self.dtype, (self.ncell, 8)), _dev(S, self.dtype, (self.ncell, 8))),
-               self.h)
+        pphi, pS = self._flux(phi, S)
+        self._sync_stream()
+        _check(lib().sn_source(self.h, pphi, pS), self.h)
         return S
 
     def harvest(self, S, cap, seed=0):
         """One elimination sweep from S that returns about `cap` of its solves as
         one-cell problems in27 [n, 27] (positive-octant frame)."""
+        if int(cap) < 0:
+            raise ValueError("cap must be non-negative")
+        pS = self._flux(S, dtype=torch.float32, moments=False)
         self._sync_stream()
         out = torch.empty((int(cap), 27), dtype=torch.float32, device=S.device)
         n = ctypes.c_int64(0)
-        _check(lib().sn_harvest(self.h, _dev(S, torch.float32, (self.ncell, 8)), _dev(out, torch.float32, (27,)),
-                                int(cap), int(seed), ctypes.byref(n)), self.h)
+        _check(lib().sn_harvest(self.h, pS, _dev(out, torch.float32, (27,)), int(cap), int(seed), ctypes.byref(n)),
+               self.h)
         return out[:n.value]
 
     def set_profiling(self, on=True):
@@ -571,6 +592,7 @@ class Problem:
         """Gradients of R = resp . phi at the converged forward flux phi (device
         [G, ncell, 8]): dict(Lam [G, ncell, 8], grad_sigt, grad_sigs, grad_q [G, ncell]
         FP64, iters)."""
+        pphi, presp = self._flux(phi, resp, dtype=torch.float32, moments=False)
         self._sync_stream()
         G, C = self.G, self.ncell
         Lam = torch.empty((G, C, 8), dtype=torch.float32, device=phi.device)
@@ -578,19 +600,19 @@ class Problem:
         gs = torch.empty_like(gt)
         gq = torch.empty_like(gt)
         it = ctypes.c_int32(0)
-        st = lib().sn_adjoint_sweep(self.h, _dev(phi, torch.float32, (C, 8)), _dev(resp, torch.float32, (C, 8)),
-                                    float(tol), int(max_it), _dev(Lam, torch.float32, (C, 8)), _dev(gt, torch.float64),
-                                    _dev(gs, torch.float64), _dev(gq, torch.float64), ctypes.byref(it))
+        st = lib().sn_adjoint_sweep(self.h, pphi, presp, float(tol), int(max_it), _dev(Lam, torch.float32, (C, 8)),
+                                    _dev(gt, torch.float64), _dev(gs, torch.float64), _dev(gq, torch.float64),
+                                    ctypes.byref(it))
         if not (st == SN_ENOCONV and allow_noconv):
             _check(st, self.h)
         return dict(Lam=Lam, grad_sigt=gt, grad_sigs=gs, grad_q=gq, iters=it.value, converged=(st == SN_OK))
 
     def response(self, phi, resp):
         """R = sum resp * phi (device [G, ncell, 8] tensors of the handle's dtype), FP64."""
+        pphi, presp = self._flux(phi, resp, moments=False)
         self._sync_stream()
         R = ctypes.c_double(0.0)
-        _check(lib().sn_response(self.h, _dev(phi, self.dtype, (self.ncell, 8)), _dev(resp, self.dtype, (self.ncell, 8)),
-                                 ctypes.byref(R)), self.h)
+        _check(lib().sn_response(self.h, pphi, presp, ctypes.byref(R)), self.h)
         return R.value
 
 

@@ -143,3 +143,50 @@ def test_noalloc_wrapper_refuses_host_tensors(monkeypatch):
     with pytest.raises(TypeError):
         sn.surrogate_grad_noalloc(torch.zeros(sn.NPARAM), torch.zeros(8, 27), torch.zeros(8, 8),
                                   torch.zeros(sn.NPARAM), torch.zeros(1, dtype=torch.float64))
+
+
+def _bare_problem(G=2, ncell=8, K=1):
+    """A Problem with sizes but no handle: enough for the argument checks, which
+    run before any stream or library call."""
+    import torch
+    from paper_1906_04017_gb300 import sn
+    P = sn.Problem.__new__(sn.Problem)
+    P.h = None
+    P.G, P.ncell, P.K = G, ncell, K
+    P.dtype, P.device, P.default_mode = torch.float32, 0, sn.GE32R
+    return P
+
+
+@pytest.mark.parametrize("call", ["sweep", "sweep_out", "source", "source_iterate", "response", "adjoint",
+                                  "harvest"])
+def test_problem_refuses_a_flux_of_the_wrong_shape(call):
+    """The kernels index G x ncell x 8 values of every flux argument: a tensor one
+    group short (or one cell short) is refused before any launch."""
+    import torch
+    P = _bare_problem()
+    good = torch.zeros((2, 8, 8))
+    for bad in (torch.zeros((1, 8, 8)), torch.zeros((2, 7, 8)), torch.zeros((16, 8))):
+        run = {"sweep": lambda: P.sweep(bad), "sweep_out": lambda: P.sweep(good, phi=bad),
+               "source": lambda: P.source(bad), "source_iterate": lambda: P.source_iterate(phi=bad),
+               "response": lambda: P.response(good, bad), "adjoint": lambda: P.adjoint(bad, good),
+               "harvest": lambda: P.harvest(bad, cap=4)}[call]
+        with pytest.raises(ValueError):
+            run()
+    # the right shape gets past the shape check and stops at the device check
+    with pytest.raises(TypeError, match="CUDA"):
+        P.sweep(good)
+
+
+def test_problem_flux_shape_follows_the_scattering_order():
+    """Under anisotropic scattering sweeps take moments [G, K, ncell, 8]; the
+    response and the adjoint stay isotropic [G, ncell, 8]."""
+    import torch
+    P = _bare_problem(K=4)
+    with pytest.raises(ValueError):
+        P.sweep(torch.zeros((2, 8, 8)))
+    with pytest.raises(TypeError, match="CUDA"):
+        P.sweep(torch.zeros((2, 4, 8, 8)))
+    with pytest.raises(ValueError):
+        P.response(torch.zeros((2, 4, 8, 8)), torch.zeros((2, 4, 8, 8)))
+    with pytest.raises(ValueError):
+        P.harvest(torch.zeros((2, 8, 8)), cap=-1)
