@@ -162,11 +162,25 @@ def _dptr(a):
     return a.ctypes.data_as(_dp)
 
 
+def _batch(in27, out):
+    """Row count n of one-cell problems in27 [n, 27] and their result out [n, 8]:
+    ValueError unless both are 2-D with those widths, the same n and one device
+    (the kernels read n x 27 and write n x 8 values)."""
+    for name, t, w in (("in27", in27, 27), ("out", out, 8)):
+        if not isinstance(t, torch.Tensor) or t.dim() != 2 or t.shape[1] != w:
+            raise ValueError("%s must be [n, %d], got %s" % (name, w, tuple(getattr(t, "shape", ()))))
+    if out.shape[0] != in27.shape[0]:
+        raise ValueError("out has %d rows, in27 %d" % (out.shape[0], in27.shape[0]))
+    if out.device != in27.device:
+        raise ValueError("in27 on %s, out on %s" % (in27.device, out.device))
+    return in27.shape[0]
+
+
 def cell_solve_batch(in27, mode=GE32R, handle=None, out=None):
     """psi[N, 8] of N one-cell problems in27[N, 27] (FP32, CUDA)."""
-    n = in27.shape[0]
     if out is None:
-        out = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+        out = torch.empty((in27.shape[0], 8), dtype=torch.float32, device=in27.device)
+    n = _batch(in27, out)
     h = handle.h if handle is not None else None
     st = lib().sn_cell_solve_batch(h, _dev(in27, torch.float32, (27,)), _dev(out, torch.float32, (8,)),
                                    n, int(mode), _stream())
@@ -175,9 +189,9 @@ def cell_solve_batch(in27, mode=GE32R, handle=None, out=None):
 
 
 def cell_solve_batch_f64(in27, out=None):
-    n = in27.shape[0]
     if out is None:
-        out = torch.empty((n, 8), dtype=torch.float64, device=in27.device)
+        out = torch.empty((in27.shape[0], 8), dtype=torch.float64, device=in27.device)
+    n = _batch(in27, out)
     st = lib().sn_cell_solve_batch_f64(_dev(in27, torch.float64, (27,)), _dev(out, torch.float64, (8,)),
                                        n, _stream())
     _check(st)
@@ -477,10 +491,10 @@ class Problem:
 
     def surrogate_apply(self, in27, gated=True, out=None):
         """psi [N, 8] from the tensor-core network; returns (psi, number of gate fallbacks)."""
-        self._sync_stream()
-        n = in27.shape[0]
         if out is None:
-            out = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+            out = torch.empty((in27.shape[0], 8), dtype=torch.float32, device=in27.device)
+        n = _batch(in27, out)
+        self._sync_stream()
         nfb = ctypes.c_int64(0)
         _check(lib().sn_surrogate_apply(self.h, _dev(in27, torch.float32, (27,)), _dev(out, torch.float32, (8,)),
                                         n, 1 if gated else 0, ctypes.byref(nfb)), self.h)
@@ -579,9 +593,9 @@ class Problem:
 
     def octnet_apply(self, in27, out=None):
         """psi [N, 8] of one-cell problems by the networks of their octants."""
-        n = in27.shape[0]
         if out is None:
-            out = torch.empty((n, 8), dtype=torch.float32, device=in27.device)
+            out = torch.empty((in27.shape[0], 8), dtype=torch.float32, device=in27.device)
+        n = _batch(in27, out)
         self._sync_stream()
         _check(lib().sn_octnet_apply(self.h, _dev(in27, torch.float32, (27,)), _dev(out, torch.float32, (8,)), n),
                self.h)

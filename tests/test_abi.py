@@ -190,3 +190,18 @@ def test_problem_flux_shape_follows_the_scattering_order():
         P.response(torch.zeros((2, 4, 8, 8)), torch.zeros((2, 4, 8, 8)))
     with pytest.raises(ValueError):
         P.harvest(torch.zeros((2, 8, 8)), cap=-1)
+
+
+@pytest.mark.parametrize("shapes", [((4, 27), (3, 8)), ((4, 27), (5, 8)), ((4, 27), (4, 7)), ((4, 26), (4, 8)),
+                                    ((108,), (4, 8)), ((4, 27), (32,))])
+def test_batch_wrappers_refuse_mismatched_rows(shapes):
+    """An out with fewer rows than in27 would be written past its end: every batch
+    entry point refuses it (and any other shape) before any library call."""
+    import torch
+    from paper_1906_04017_gb300 import sn
+    in27, out = torch.zeros(shapes[0]), torch.zeros(shapes[1])
+    P = _bare_problem()
+    for run in (lambda: sn.cell_solve_batch(in27, out=out), lambda: sn.cell_solve_batch_f64(in27, out=out),
+                lambda: P.surrogate_apply(in27, out=out), lambda: P.octnet_apply(in27, out=out)):
+        with pytest.raises(ValueError):
+            run()
