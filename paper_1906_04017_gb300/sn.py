@@ -237,6 +237,15 @@ def _rows(feat, targ):
     return int(feat.shape[0])
 
 
+def _octant_rows(feat, targ):
+    """m of octant-grouped features [8m, 27] and targets [8m, 8] (8 equal blocks of m
+    rows, octant 0 first); ValueError otherwise."""
+    n = _rows(feat, targ)
+    if n % 8:
+        raise ValueError("features and targets must hold 8 equal octant blocks, got %d rows" % n)
+    return n // 8
+
+
 def surrogate_grad_noalloc(params, feat, targ, grad, loss):
     """Loss and gradient of Eq. (19) without any device allocation by the library:
     params [2312], feat [n, 27], targ [n, 8], grad [2312] (out) FP32 and loss [1]
@@ -561,33 +570,37 @@ class Problem:
         """(loss [8], gradient [8, 288]) of Eq. (19) per octant at the current parameters."""
         g = np.zeros((8, OCTNET_NPARAM), dtype=np.float32)
         loss = np.zeros(8)
+        m = _octant_rows(feat, targ)
         self._sync_stream()
         _check(lib().sn_octnet_grad(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
-                                    feat.shape[0] // 8, _f32p(g), _dptr(loss)), self.h)
+                                    m, _f32p(g), _dptr(loss)), self.h)
         return loss, g
 
     def octnet_fit(self, feat, targ, steps, lr):
         loss = np.zeros(8)
+        m = _octant_rows(feat, targ)
         self._sync_stream()
         _check(lib().sn_octnet_fit(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
-                                   feat.shape[0] // 8, int(steps), float(lr), _dptr(loss)), self.h)
+                                   m, int(steps), float(lr), _dptr(loss)), self.h)
         return loss
 
     def octnet_eval(self, feat, targ):
         """(mean absolute error [8], mean squared error [8]) per octant."""
         mae = np.zeros(8)
         mse = np.zeros(8)
+        m = _octant_rows(feat, targ)
         self._sync_stream()
         _check(lib().sn_octnet_eval(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
-                                    feat.shape[0] // 8, _dptr(mae), _dptr(mse)), self.h)
+                                    m, _dptr(mae), _dptr(mse)), self.h)
         return mae, mse
 
     def octnet_prune(self, feat, targ, retrain_steps, lr, tol=1e-3, max_drops=272):
         """Connection dropping (Sec. 3); returns the drops kept per octant [8]."""
         d = (ctypes.c_int32 * 8)()
+        m = _octant_rows(feat, targ)
         self._sync_stream()
         _check(lib().sn_octnet_prune(self.h, _dev(feat, torch.float32, (27,)), _dev(targ, torch.float32, (8,)),
-                                     feat.shape[0] // 8, int(retrain_steps), float(lr), float(tol), int(max_drops), d),
+                                     m, int(retrain_steps), float(lr), float(tol), int(max_drops), d),
                self.h)
         return np.array(list(d))
 

@@ -205,3 +205,17 @@ def test_batch_wrappers_refuse_mismatched_rows(shapes):
                 lambda: P.surrogate_apply(in27, out=out), lambda: P.octnet_apply(in27, out=out)):
         with pytest.raises(ValueError):
             run()
+
+
+@pytest.mark.parametrize("rows", [(16, 15), (16, 17), (12, 12)])
+def test_octnet_wrappers_refuse_unequal_or_ragged_batches(rows):
+    """Features and targets of the octant networks are 8 equal blocks of m rows: a
+    target array with other rows than the features, or a row count that is not a
+    multiple of 8, is refused before any library call."""
+    import torch
+    P = _bare_problem()
+    feat, targ = torch.zeros((rows[0], 27)), torch.zeros((rows[1], 8))
+    for run in (lambda: P.octnet_grad(feat, targ), lambda: P.octnet_fit(feat, targ, 1, 1e-3),
+                lambda: P.octnet_eval(feat, targ), lambda: P.octnet_prune(feat, targ, 0, 0.0)):
+        with pytest.raises(ValueError):
+            run()
