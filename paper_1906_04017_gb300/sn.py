@@ -450,7 +450,8 @@ class Problem:
 
     def surrogate_set_weights(self, params):
         p = np.ascontiguousarray(params, dtype=np.float32)
-        assert p.size == NPARAM
+        if p.size != NPARAM:
+            raise ValueError("the surrogate has %d parameters, got %d" % (NPARAM, p.size))
         self._sync_stream()
         _check(lib().sn_surrogate_set_weights(self.h, _f32p(p)), self.h)
 

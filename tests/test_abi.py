@@ -219,3 +219,14 @@ def test_octnet_wrappers_refuse_unequal_or_ragged_batches(rows):
                 lambda: P.octnet_eval(feat, targ), lambda: P.octnet_prune(feat, targ, 0, 0.0)):
         with pytest.raises(ValueError):
             run()
+
+
+def test_weight_setters_refuse_wrong_sizes():
+    """The C setters read a fixed number of host values: a shorter array is refused."""
+    P = _bare_problem()
+    with pytest.raises(ValueError):
+        P.surrogate_set_weights(np.zeros(2311, dtype=np.float32))
+    with pytest.raises(ValueError):
+        P.octnet_set(np.zeros((8, 287), dtype=np.float32))
+    with pytest.raises(ValueError):
+        P.octnet_init(np.zeros((8, 25)), np.ones((8, 25)))
