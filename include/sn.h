@@ -153,13 +153,19 @@ sn_status sn_cell_solve_batch_f64(const double *in27, double *psi, int64_t n, vo
  * (14)) for the isotropic nodal source S (device [G][ncell][8] of the
  * handle's element type, angular
  * density, i.e. already divided by 4 pi); writes phi (device [G][ncell][8]).
- * Hyperplane-wavefront order; all octants, directions and groups of one
- * hyperplane run in one launch.  Balance tallies of this sweep are kept for
- * sn_get_balance; reading them synchronises the handle's stream before the call
- * returns.  S and phi must not overlap.  The GE modes and SN_SOLVE_ANN give the
- * same bits on every run; with SN_SOLVE_ANN_GATED the rows the gate rejects are
- * re-solved by elimination between hyperplanes and added to the flux with
- * atomics, so the last bits may differ from run to run.
+ * Hyperplane-wavefront order (a cell after its three upwind neighbours).  FP32
+ * handles with box cells and isotropic scattering run the whole sweep as one
+ * persistent launch whose work units (hyperplane, octant, tile of (cell, group)
+ * keys; sn_wave_plan) each wait only for their upwind units; other handles run one
+ * launch per hyperplane with all its octants, directions and groups.  Balance
+ * tallies of this sweep are kept for sn_get_balance; reading them synchronises the
+ * handle's stream before the call returns.  S and phi must not overlap.  The GE
+ * modes, SN_SOLVE_ANN and SN_SOLVE_OCTNET give the same bits on every run, and so
+ * do the gated modes on the persistent launch (the rows the gate rejects are solved
+ * by elimination inside their unit and added in direction order); on the
+ * per-hyperplane launches the gated modes re-solve the rejected rows between
+ * hyperplanes and add them to the flux with atomics, so the last bits may differ
+ * from run to run.
  * ------------------------------------------------------------------------- */
 sn_status sn_sweep(sn_handle h, const void *S, void *phi, sn_solve_mode mode);
 
